@@ -1,0 +1,246 @@
+"""Mixed RT0 x P0 discretisation of the reaction-diffusion SPDE (oracle).
+
+Test infrastructure (oracle): never imported by the library.
+
+Sec. 4, Eq. (SPDE): (kappa^2 - Laplace) theta = g W on the embedding box,
+homogeneous Neumann (no-flux) boundary.  Mixed weak form, Eq.
+(reac_diff_weak): find u in RT0, theta in P0 with
+    m(u, v) + b(v, theta) = 0,
+    b(u, q) - kappa^2 w(theta, q) = -g F^W(q),   u.n = 0 on the box boundary,
+with m the L2 inner product of fluxes, w that of cell values and b(u, q) =
+(div u, q).  The linear system is Eq. (linsys)/(linsys_blocks):
+    [[M, B^T], [B, -kappa^2 W]] [u; theta] = [0; -g f],  f = W^{1/2} xi.
+Eliminating u gives S theta = g f with S = kappa^2 W + B M^{-1} B^T, so
+theta ~ N(0, g^2 S^{-1} W S^{-1}) (the covariance stated after
+Eq. (linsys_blocks), with the g^2 factor written out).
+
+The normaliser g follows Sec. 4: g = (4 pi)^{d/4} kappa^nu
+sqrt(Gamma(nu + d/2) / Gamma(nu)), times sigma for marginal variance sigma^2;
+at nu = 1/2, d = 3 this is g^2 = 8 pi kappa sigma^2.
+
+Grid: n^3 cubes of edge h on [lo, lo + n h]^3.  Unknown ordering of this
+module (its own; unrelated to any device layout):
+  x-faces (i = 1..n-1, j, k)  id = (i-1) + (n-1) (j + n k)
+  y-faces (i, j = 1..n-1, k)  id = Nx + i + n ((j-1) + (n-1) k)
+  z-faces (i, j, k = 1..n-1)  id = Nx + Ny + i + n (j + n (k-1))
+  cells   (i, j, k)           id = Nu + i + n (j + n k)
+RT0 degree of freedom = the normal component u.e_axis on the face (the
+paper fixes no scaling; theta does not depend on it).  Boundary faces carry
+the essential condition u.n = 0 and are eliminated.
+"""
+import math
+
+import numpy as np
+import scipy.fft
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def g_normaliser(kappa, sigma=1.0, nu=0.5, d=3):
+    """g of Sec. 4 times sigma: sigma (4 pi)^{d/4} kappa^nu sqrt(G(nu+d/2)/G(nu))."""
+    return sigma * (4.0 * math.pi) ** (d / 4.0) * kappa ** nu * math.sqrt(
+        math.gamma(nu + d / 2.0) / math.gamma(nu))
+
+
+# --- local RT0 basis on the reference cube [0,1]^3 --------------------------
+# local faces: 0 x-left, 1 x-right, 2 y-left, 3 y-right, 4 z-left, 5 z-right;
+# each basis function is the lowest-order RT field whose normal component is
+# 1 on its face and 0 on the other five, oriented along +axis.
+def _local_basis(a, xi):
+    axis, side = divmod(a, 2)
+    v = np.zeros(xi.shape[:-1] + (3,))
+    t = xi[..., axis]
+    v[..., axis] = t if side == 1 else 1.0 - t
+    return v
+
+
+def _local_matrices():
+    """6x6 reference mass and 6 reference divergence integrals.
+
+    Mass by the tensor 2-point Gauss rule (exact for the quadratic
+    integrands); divergence by the divergence of each (linear) basis field,
+    evaluated by a centred difference, which is exact for linear fields.
+    """
+    gp = np.array([0.5 - 0.5 / math.sqrt(3.0), 0.5 + 0.5 / math.sqrt(3.0)])
+    pts = np.array([[x, y, z] for z in gp for y in gp for x in gp])
+    wts = np.full(len(pts), 1.0 / 8.0)
+    vals = [_local_basis(a, pts) for a in range(6)]
+    mass = np.array([[np.sum(wts * np.einsum("pi,pi->p", vals[a], vals[b]))
+                      for b in range(6)] for a in range(6)])
+    div = np.zeros(6)
+    eps = 0.125
+    centre = np.array([[0.5, 0.5, 0.5]])
+    for a in range(6):
+        s = 0.0
+        for ax in range(3):
+            e = np.zeros(3)
+            e[ax] = eps
+            s += (_local_basis(a, centre + e)[0, ax] - _local_basis(a, centre - e)[0, ax]) / (2 * eps)
+        div[a] = s  # constant over the cell; integral over the unit cube
+    return mass, div
+
+
+class MixedSystem:
+    """Assembled [[M, B^T], [B, -kappa^2 W]] on an n^3 grid of spacing h."""
+
+    def __init__(self, n, h=None, lo=0.0):
+        self.n = n = int(n)
+        self.h = h = (1.0 / n) if h is None else float(h)
+        self.lo = lo
+        self.Nx = self.Ny = self.Nz = (n - 1) * n * n
+        self.Nu = 3 * (n - 1) * n * n
+        self.Nt = n ** 3
+        mass_ref, div_ref = _local_matrices()
+        # physical cell: phi(x) = phi_ref((x - x0)/h), so
+        #   int phi_a.phi_b = h^3 mass_ref,  int div phi_a = h^3 (1/h) div_ref
+        mloc = h ** 3 * mass_ref
+        bloc = h ** 2 * div_ref
+        i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        i, j, k = i.ravel(), j.ravel(), k.ravel()
+        cell = i + n * (j + n * k)
+        gids = np.full((len(cell), 6), -1, dtype=np.int64)
+        for a in range(6):
+            axis, side = divmod(a, 2)
+            fi = [i.copy(), j.copy(), k.copy()]
+            fi[axis] = fi[axis] + side  # face position along axis, 0..n
+            pos = fi[axis]
+            inner = (pos >= 1) & (pos <= n - 1)
+            if axis == 0:
+                gid = (fi[0] - 1) + (n - 1) * (fi[1] + n * fi[2])
+            elif axis == 1:
+                gid = self.Nx + fi[0] + n * ((fi[1] - 1) + (n - 1) * fi[2])
+            else:
+                gid = self.Nx + self.Ny + fi[0] + n * (fi[1] + n * (fi[2] - 1))
+            gids[:, a] = np.where(inner, gid, -1)
+        rows, cols, vals = [], [], []
+        for a in range(6):
+            for b in range(6):
+                if mloc[a, b] == 0.0:
+                    continue
+                ok = (gids[:, a] >= 0) & (gids[:, b] >= 0)
+                rows.append(gids[ok, a])
+                cols.append(gids[ok, b])
+                vals.append(np.full(ok.sum(), mloc[a, b]))
+        self.M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                               shape=(self.Nu, self.Nu))
+        br, bc, bv = [], [], []
+        for a in range(6):
+            ok = gids[:, a] >= 0
+            br.append(cell[ok])
+            bc.append(gids[ok, a])
+            bv.append(np.full(ok.sum(), bloc[a]))
+        self.B = sp.csr_matrix((np.concatenate(bv), (np.concatenate(br), np.concatenate(bc))),
+                               shape=(self.Nt, self.Nu))
+        self.W = sp.identity(self.Nt, format="csr") * h ** 3
+
+    def matrix(self, kappa):
+        return sp.bmat([[self.M, self.B.T], [self.B, -kappa ** 2 * self.W]], format="csc")
+
+    def apply(self, kappa, u, theta):
+        """y = A [u; theta] with the assembled blocks."""
+        yu = self.M @ u + self.B.T @ theta
+        yt = self.B @ u - kappa ** 2 * (self.W @ theta)
+        return yu, yt
+
+    def rhs(self, kappa, sigma, xi):
+        """F = [0; -g f], f = W^{1/2} xi (Sec. 4.2)."""
+        f = np.sqrt(self.W.diagonal()) * xi
+        return np.concatenate([np.zeros(self.Nu), -g_normaliser(kappa, sigma) * f])
+
+    def solve_sparse(self, kappa, sigma, xi):
+        """Sparse direct (SuperLU) solve of the full saddle-point system."""
+        lu = spla.splu(self.matrix(kappa))
+        sol = lu.solve(self.rhs(kappa, sigma, xi))
+        return sol[:self.Nu], sol[self.Nu:]
+
+    def solve_dense(self, kappa, sigma, xi):
+        sol = np.linalg.solve(self.matrix(kappa).toarray(), self.rhs(kappa, sigma, xi))
+        return sol[:self.Nu], sol[self.Nu:]
+
+
+# --- closed form on the uniform box --------------------------------------
+# Per axis the divergence maps DST-I face modes to DCT-II cell modes with
+# factor 2 h^2 sin(pi k / 2n), and the 1-D RT0 mass matrix (tridiagonal
+# h^3 (1/6, 2/3, 1/6)) is diagonal on DST-I modes with eigenvalue
+# h^3 (2 + cos(pi k / n)) / 3.  Hence S = kappa^2 W + B M^{-1} B^T is
+# diagonalised by the orthonormal 3-D DCT-II with eigenvalues
+#   Lambda(k) = kappa^2 h^3 + h sum_d 12 sin^2(pi k_d / 2n) / (2 + cos(pi k_d / n)).
+def schur_eigenvalues(n, h, kappa):
+    k = np.arange(n)
+    lam1 = 12.0 * np.sin(np.pi * k / (2 * n)) ** 2 / (2.0 + np.cos(np.pi * k / n))
+    return kappa ** 2 * h ** 3 + h * (lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :])
+
+
+def solve_dct(n, kappa, sigma, xi, h=None):
+    """theta = g S^{-1} W^{1/2} xi by the DCT-II diagonalisation.
+
+    xi is a flat array of n^3 cell values (x fastest) or [S, n^3].
+    """
+    h = (1.0 / n) if h is None else h
+    lam = schur_eigenvalues(n, h, kappa)
+    xi = np.asarray(xi, dtype=np.float64)
+    batch = xi.reshape(-1, n, n, n)  # [S, z, y, x]
+    f = h ** 1.5 * batch
+    th = scipy.fft.idctn(scipy.fft.dctn(f, type=2, norm="ortho", axes=(1, 2, 3)) / lam,
+                         type=2, norm="ortho", axes=(1, 2, 3))
+    return (g_normaliser(kappa, sigma) * th).reshape(xi.shape)
+
+
+def _dct_matrix(n):
+    k = np.arange(n)[:, None]
+    i = np.arange(n)[None, :]
+    c = np.sqrt(2.0 / n) * np.cos(np.pi * k * (2 * i + 1) / (2 * n))
+    c[0] /= np.sqrt(2.0)
+    return c
+
+
+def variance_exact(n, kappa, sigma, h=None):
+    """Exact discrete variance of every cell: diag(g^2 S^{-1} W S^{-1}).
+
+    Returned as an [z, y, x] array.
+    """
+    h = (1.0 / n) if h is None else h
+    lam = schur_eigenvalues(n, h, kappa)
+    c2 = _dct_matrix(n) ** 2  # [k, i]
+    a = 1.0 / lam ** 2
+    # contract each frequency axis with C^2: var[z,y,x] = sum_k prod C^2 a
+    v = np.einsum("abc,ax->xbc", a, c2)
+    v = np.einsum("xbc,by->xyc", v, c2)
+    v = np.einsum("xyc,cz->xyz", v, c2)
+    return g_normaliser(kappa, sigma) ** 2 * h ** 3 * v
+
+
+def covariance_column(n, kappa, sigma, cell, h=None):
+    """Column g^2 h^3 C^T Lambda^{-2} C e_cell of the exact covariance, flat."""
+    h = (1.0 / n) if h is None else h
+    lam = schur_eigenvalues(n, h, kappa)
+    e = np.zeros(n ** 3)
+    e[cell] = 1.0
+    e = e.reshape(n, n, n)
+    col = scipy.fft.idctn(scipy.fft.dctn(e, type=2, norm="ortho") / lam ** 2, type=2, norm="ortho")
+    return g_normaliser(kappa, sigma) ** 2 * h ** 3 * col.ravel()
+
+
+def neumann_image_variance(x, kappa, sigma, box=1.0, nimg=3):
+    """Continuum variance sigma^2 sum_images exp(-kappa |x - x_img|) in a box.
+
+    Neumann reflection at every face of [0, box]^3; the Green's function of
+    (kappa^2 - Laplace) is exp(-kappa r) / (4 pi r), whose self-convolution
+    normalised by g gives the exponential covariance (Sec. 4, nu = 1/2).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    tot = 0.0
+    rng = range(-nimg, nimg + 1)
+    for a in rng:
+        for b in rng:
+            for c in rng:
+                img = []
+                for d, m in zip(range(3), (a, b, c)):
+                    # image of coordinate x_d under m reflections
+                    if m % 2 == 0:
+                        img.append(x[d] + m * box)
+                    else:
+                        img.append(-x[d] + (m + 1) * box)
+                r = math.dist(x, img)
+                tot += math.exp(-kappa * r)
+    return sigma ** 2 * tot

@@ -1,0 +1,8 @@
+"""Seeded synthetic inputs shared by the oracle tests and the CUDA path.
+
+This package holds no arithmetic of the sampling method itself: it only
+generates target tet meshes and request streams from seeds.  The random
+numbers it draws (vertex jitter, request parameters) come from NumPy's PCG64,
+not from the Philox generator the method uses for white noise.
+"""
+from .mesh import kuhn_mesh, box_mesh, lprism_mesh, MeshSpec  # noqa: F401

@@ -1,0 +1,119 @@
+"""Pins of the oracle's intersection volumes, G and the projection (Sec. 5)."""
+import numpy as np
+import pytest
+
+from oracle import clip, project
+from synth import box_mesh
+
+CORNER = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+
+
+def test_tet_inside_box_is_whole_tet():
+    p = 0.1 + 0.2 * CORNER
+    assert clip.tet_box_volume(p, [0, 0, 0], [1, 1, 1]) == pytest.approx(0.2 ** 3 / 6, rel=1e-13)
+
+
+def test_disjoint_and_touching_are_zero():
+    p = 2.0 + CORNER
+    assert clip.tet_box_volume(p, [0, 0, 0], [1, 1, 1]) == 0.0
+    # shares only the face x = 1 with the box
+    q = CORNER + np.array([1.0, 0.0, 0.0])
+    assert clip.tet_box_volume(q, [0, 0, 0], [1, 1, 1]) == pytest.approx(0.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("a", [0.25, 0.5, 0.8])
+def test_corner_tet_cut_by_plane(a):
+    # corner simplex {x,y,z >= 0, x+y+z <= 1} cut at x = a: the part x >= a is a
+    # scaled simplex of volume (1-a)^3/6
+    keep = clip.tet_box_volume(CORNER, [-1, -1, -1], [a, 2, 2])
+    assert keep == pytest.approx(1 / 6 - (1 - a) ** 3 / 6, rel=1e-12)
+
+
+def test_corner_tet_in_small_cube():
+    # cube [0,a]^3 with a <= 1/3 lies inside the simplex
+    assert clip.tet_box_volume(CORNER, [0, 0, 0], [0.3, 0.3, 0.3]) == pytest.approx(0.027, rel=1e-12)
+    # cube [0,1/2]^3: the cube minus the corner region x+y+z > 1 (volume (1/2)^3/6)
+    assert clip.tet_box_volume(CORNER, [0, 0, 0], [0.5, 0.5, 0.5]) == pytest.approx(
+        0.125 - 0.125 / 6, rel=1e-12)
+
+
+def test_kuhn_split_of_aligned_cube():
+    # an unjittered mesh whose cubes are the grid cells: G = |tau| delta
+    xyz, tets = box_mesh((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 4, jitter=0.0)
+    rows = clip.coupling_rows(xyz, tets, 4)
+    for t, row in rows.items():
+        vol = clip.tet_volume(xyz[tets[t]])
+        big = {c: v for c, v in row.items() if v > 1e-14}
+        assert len(big) == 1
+        cube = t // 6
+        assert list(big) == [cube]
+        assert big[cube] == pytest.approx(vol, rel=1e-12)
+        assert vol == pytest.approx((1 / 4) ** 3 / 6, rel=1e-12)
+
+
+def test_row_and_column_sums_of_jittered_box():
+    """Rows sum to |tau| and columns to |c cap D| (D tiled exactly)."""
+    lo, hi, n = 0.15, 0.85, 8
+    xyz, tets = box_mesh((lo,) * 3, (hi,) * 3, 5)
+    rows = clip.coupling_rows(xyz, tets, n)
+    col = np.zeros(n ** 3)
+    for t, row in rows.items():
+        vol = clip.tet_volume(xyz[tets[t]])
+        assert sum(row.values()) == pytest.approx(vol, rel=1e-12)
+        for c, v in row.items():
+            col[c] += v
+    h = 1.0 / n
+    e = np.arange(n) * h
+    ov = np.clip(np.minimum(e + h, hi) - np.maximum(e, lo), 0.0, None)
+    expect = (ov[None, None, :] * ov[None, :, None] * ov[:, None, None]).ravel()
+    assert np.allclose(col, expect, rtol=1e-11, atol=1e-15)
+
+
+def test_translation_by_one_cell_shifts_columns():
+    xyz, tets = box_mesh((0.15,) * 3, (0.55,) * 3, 3)
+    n = 8
+    a = clip.coupling_rows(xyz, tets, n)
+    b = clip.coupling_rows(xyz + np.array([1.0 / n, 0, 0]), tets, n)
+    for t in a:
+        shifted = {c + 1: v for c, v in a[t].items()}
+        assert set(shifted) == set(b[t])
+        for c in shifted:
+            assert b[t][c] == pytest.approx(shifted[c], rel=1e-11, abs=1e-16)
+
+
+def test_monte_carlo_point_sampling():
+    rng = np.random.default_rng(3)
+    xyz, tets = box_mesh((0.15,) * 3, (0.85,) * 3, 4)
+    n = 6
+    h = 1.0 / n
+    for t in rng.choice(len(tets), 5, replace=False):
+        p = xyz[tets[t]]
+        row = clip.coupling_rows(xyz, tets, n, rows=[t])[t]
+        m = 200000
+        lam = rng.dirichlet(np.ones(4), size=m)  # uniform in the tet
+        x = lam @ p
+        cells = np.floor(x / h).astype(int)
+        flat = cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2])
+        vol = clip.tet_volume(p)
+        freq = np.bincount(flat, minlength=n ** 3) / m
+        for c in set(row) | set(np.nonzero(freq)[0]):
+            f = row.get(c, 0.0) / vol
+            assert abs(freq[c] - f) < 5 * np.sqrt(f * (1 - f) / m) + 2e-5
+
+
+def test_projection_preserves_constants_and_integrals():
+    xyz, tets = box_mesh((0.15,) * 3, (0.85,) * 3, 4)
+    n = 8
+    rows = clip.coupling_rows(xyz, tets, n)
+    ones = project.project_rows(xyz, tets, rows, np.ones(n ** 3))
+    assert max(abs(v - 1.0) for v in ones.values()) < 1e-12
+    rng = np.random.default_rng(0)
+    th = rng.standard_normal(n ** 3)
+    vals = project.project_rows(xyz, tets, rows, th)
+    lhs = sum(clip.tet_volume(xyz[tets[t]]) * vals[t] for t in vals)
+    col = np.zeros(n ** 3)
+    for row in rows.values():
+        for c, v in row.items():
+            col[c] += v
+    assert lhs == pytest.approx(col @ th, rel=1e-12)
+    assert project.lognormal(np.array([0.0, 1.0]))[1] == pytest.approx(np.e)
