@@ -1,0 +1,219 @@
+/*
+ * spde.h -- C ABI of the GB300 SPDE sampler (sm_103a).
+ *
+ * The sampler draws Gaussian random fields with Matern covariance
+ * (nu = 1/2 in 3-D, i.e. exponential covariance sigma^2 exp(-kappa r)) by
+ * solving the reaction-diffusion SPDE (kappa^2 - Laplace) theta = g W
+ * (Sec. 4, Eq. SPDE) in mixed RT0 x P0 form (Eq. reac_diff_weak, Eq. linsys)
+ * on a uniform hex grid of an embedding box, then L2-projects each sample
+ * onto a non-matching tet mesh (Sec. 5.1, Eq. proj_op) and applies the
+ * lognormal map exp (workflow figure of Sec. 6).
+ *
+ * Conventions shared by every entry point
+ *   - All functions return an spde_status; no C++ exception crosses the ABI.
+ *     On failure spde_last_error() returns a message for the calling thread.
+ *   - "device" pointers are CUDA global-memory pointers on the context's
+ *     device; "host" pointers are ordinary CPU memory.  The caller keeps
+ *     ownership of every buffer it passes.  Memory the library allocates
+ *     itself (grids, coupling matrices, solver workspace) is owned by the
+ *     context and released by spde_destroy().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Kernels are enqueued on it; functions that must inspect
+ *     convergence synchronise it before returning (stated per function).
+ *   - A context serialises calls on itself with an internal mutex.
+ *
+ * Discrete system (scaled form).  Grid: n^3 cubes of edge h.  The mixed
+ * unknowns of one sample are stored as four contiguous n^3 arrays
+ * [ux | uy | uz | theta], each indexed c = i + n (j + n k) (x fastest).
+ * ux[c] is the normal flux through the +x face of cell c (the face between
+ * cells i and i+1); the entry with i = n-1 lies on the box wall and is held
+ * at 0 (essential condition u.n = 0, Sec. 4.2); likewise uy (j = n-1) and
+ * uz (k = n-1).  With D = diag(h^{-3/2} on fluxes, h^{-1/2} on cells) the
+ * library solves the symmetrically scaled system  (D A D) (D^{-1} U) = D F,
+ * where A = [[M, B^T], [B, -kappa^2 W]] (Eq. linsys_blocks):
+ *     y_u   = T u + D1^T theta,   T = tridiag(1/6, 2/3, 1/6) along each
+ *             flux line, (D1^T theta)_f = theta_left - theta_right,
+ *     y_th  = D1 u - (kappa h)^2 theta,  (D1 u)_c = sum_axes (u_+ - u_-).
+ * Physical cell values are theta = h^{-1/2} (scaled theta).
+ */
+#ifndef SPDE_H
+#define SPDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPDE_OK = 0,
+    SPDE_EINVAL = 1,   /* invalid argument (sizes, NaN/inf, bad level, ...) */
+    SPDE_ENOMEM = 2,   /* device allocation failed or footprint over budget */
+    SPDE_EMESH = 3,    /* mesh rejected (inverted/degenerate tet, tet outside the box,
+                          coupling row sum != tet volume); spde_last_error names the tet */
+    SPDE_ENOCONV = 4,  /* iteration cap reached before the tolerance; outputs hold
+                          the last iterate, spde_get_stats gives the residual */
+    SPDE_ETIMEOUT = 5, /* reserved for bounded waits (no kernel of this library waits
+                          on another CTA, so no current entry point returns it) */
+    SPDE_ECUDA = 6,    /* a CUDA runtime call failed */
+    SPDE_EBUSY = 7     /* request queue full */
+} spde_status;
+
+/* precision of the field solve */
+enum {
+    SPDE_PREC_MIXED = 0, /* FP32 MINRES + V-cycle inside FP64 iterative refinement, batched */
+    SPDE_PREC_FP64 = 1   /* plain path: FP64 MINRES + FP64 V-cycle, one sample at a time */
+};
+
+/* output kinds of spde_sample / spde_project (or-ed with SPDE_OUT_F64) */
+enum {
+    SPDE_OUT_LOGNORMAL = 0,     /* exp(theta_h) on the tets, [nsamples][ntets] */
+    SPDE_OUT_GAUSSIAN = 1,      /* theta_h = W_h^{-1} G theta on the tets, [nsamples][ntets] */
+    SPDE_OUT_GRID_GAUSSIAN = 2, /* theta on the embedding grid (physical), [nsamples][n^3] */
+    SPDE_OUT_F64 = 16           /* element type double instead of float */
+};
+
+typedef struct {
+    int precision;      /* SPDE_PREC_MIXED (default) or SPDE_PREC_FP64 */
+    double tol;         /* stop when ||F - A x||_2 / ||F||_2 <= tol (scaled system, FP64); 1e-10 */
+    double inner_tol;   /* FP32 inner MINRES: stop when its preconditioned residual
+                           estimate drops by this factor; 1e-5 */
+    int max_outer;      /* refinement steps (mixed path); 8 */
+    int max_iter;       /* MINRES iterations per solve; 400 */
+    double omega;       /* damped-Jacobi weight of the V-cycle smoother; 0.8 */
+    double schur_c;     /* weight c of the 7-point Schur approximation kappa^2 h^2 I + c L; 1.0 */
+    double flux_diag;   /* flux-block preconditioner, a multiple of the identity; 1.5 = diag(T)^{-1} */
+    int check_every;    /* MINRES iterations between host convergence checks; 8 */
+    int device;         /* CUDA device ordinal; 0 */
+    int use_graphs;     /* capture the batched MINRES iteration in CUDA graphs; 1 */
+} spde_opts;
+
+typedef struct {
+    int outer_iters;        /* refinement steps of the last solve */
+    int inner_iters;        /* MINRES iterations summed over refinement steps (max over samples) */
+    double max_rel_residual;/* max over samples of the final ||F - A x|| / ||F|| (FP64) */
+    double setup_ms;        /* last spde_mesh_attach: clipping + CSR build on the device */
+    int64_t nnz;            /* nonzeros of the last attached coupling matrix */
+} spde_stats;
+
+typedef struct spde_ctx spde_ctx;
+
+/* Fill *opts with the defaults listed above. */
+spde_status spde_opts_init(spde_opts* opts);
+
+/* Create a context on opts->device (opts may be NULL for defaults).
+ * *ctx receives the handle; release it with spde_destroy. */
+spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts);
+
+/* Define embedding grid `level` (0 <= level < 16): n^3 cubic cells on the
+ * box [lo, hi] (Sec. 4.1, domain embedding; Sec. 6.1, nested grids).
+ * n must be a power of two, 2 <= n <= 1024, and hi - lo equal on all three
+ * axes (cubic cells).  Replaces an existing level of the same index. */
+spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]);
+
+/* Attach the target tet mesh of `level` and build its L2-projection operator
+ * on the device (Sec. 5.1-5.2): G[tau][c] = |tau cap c| by exact FP64
+ * clipping, Pi = W_h^{-1} G stored as CSR (rows = tets).
+ *   xyz  host, [nverts][3] double vertex coordinates
+ *   tets host, [ntets][4] int32 vertex ids (either orientation; fixed on copy)
+ * Both arrays are copied; the caller keeps them.  Every tet must lie inside
+ * the box and have volume > 1e-9 h^3; every coupling row must sum to the
+ * tet volume within 1e-10 relative -- else SPDE_EMESH naming the first bad
+ * tet.  Synchronises the default stream of the context. */
+spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const double* xyz,
+                             int64_t ntets, const int32_t* tets);
+
+/* Draw `nsamples` fields on `level` (Fig. workflow of Sec. 6; Sec. 4.2 noise,
+ * Eq. linsys solve, Eq. proj_op projection, exp).  Sample i uses the Philox
+ * sample index first_sample + i under key `seed`, so results depend only on
+ * (seed, sample index, level grid, mesh, kappa, sigma).
+ *   kappa > 0, sigma > 0 finite; nu is fixed at 1/2.
+ *   out   device (or host) buffer of the layout `out_kind` states; host
+ *         memory is detected and filled through an internal device buffer.
+ * The call returns after the results are complete (it synchronises
+ * `stream`).  SPDE_ENOCONV: tolerance not reached, `out` holds the last
+ * iterate. */
+spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma,
+                        uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream);
+
+/* Bytes of device memory spde_sample(level, nsamples) needs beyond what the
+ * level already holds (workspace of the selected precision path). */
+spde_status spde_query_footprint(spde_ctx* ctx, int level, int nsamples, int64_t* bytes);
+
+/* Statistics of the last solve / mesh attach on this context. */
+spde_status spde_get_stats(spde_ctx* ctx, spde_stats* stats);
+
+/* Size of the coupling matrix of `level`. */
+spde_status spde_mesh_info(spde_ctx* ctx, int level, int64_t* ntets, int64_t* nnz);
+
+/* Copy the coupling matrix G of `level` to host arrays (CSR, rows = tets):
+ * row_ptr [ntets+1], col [nnz] (cell index), gval [nnz] (|tau cap c|, FP64),
+ * vol [ntets] (|tau|).  Any pointer may be NULL to skip it. */
+spde_status spde_mesh_copy_csr(spde_ctx* ctx, int level, int64_t* row_ptr, int32_t* col,
+                               double* gval, double* vol);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* spde_last_error(void);
+
+/* Free every device and host resource of the context. */
+spde_status spde_destroy(spde_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Step-level entry points: one step of the path each, on device buffers,
+ * so every step can be checked on its own.  `opts` may be NULL.
+ * ------------------------------------------------------------------- */
+
+/* White noise (Sec. 4.2: f = W^{1/2} xi, xi ~ N(0, I)).  Writes
+ * out[s][c] = scale * xi_c of sample first_sample + s, s < nsamples,
+ * c < ncells (device, double, contiguous [nsamples][ncells]).
+ * xi from Philox4x32-10: key = (seed mod 2^32, seed >> 32), counter =
+ * (p, 0, sample mod 2^32, sample >> 32) for the cell pair (2p, 2p+1);
+ * 53-bit uniforms u1 = ((w0:w1 >> 11) + 1) 2^-53, u2 = (w2:w3 >> 11) 2^-53;
+ * Box-Muller xi_2p = r cos(2 pi u2), xi_2p+1 = r sin(2 pi u2),
+ * r = sqrt(-2 ln u1). */
+spde_status spde_noise(int64_t ncells, int nsamples, uint64_t seed, uint64_t first_sample,
+                       double scale, double* out, void* stream);
+
+/* Raw Philox4x32-10 words of the noise stream: out[p][0..3] (device, uint32)
+ * for counters (p, 0, sample mod 2^32, sample >> 32), p < npairs, key as
+ * spde_noise.  The integer stage of spde_noise, exposed for checking. */
+spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uint32_t* out, void* stream);
+
+/* y = (D A D) x, the scaled mixed operator (Eq. linsys_blocks) on an n^3 grid
+ * of spacing h, for nsamples stacked vectors of 4 n^3 entries (layout above).
+ * prec SPDE_PREC_FP64: x, y are double; SPDE_PREC_MIXED: float.
+ * Wall entries of y are written as 0. */
+spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x,
+                       void* y, void* stream);
+
+/* z = P^{-1} r for the block-diagonal MINRES preconditioner: flux block
+ * opts->flux_diag * I, field block one symmetric V-cycle (damped Jacobi,
+ * cell-centred linear prolongation, R = P^T, coarse operators
+ * 2^l ((kappa h)^2 4^l I + c L_l), exact one-cell solve).  Layout and prec
+ * as spde_apply.  Uses library-allocated scratch (allocated on first use per
+ * (n, nsamples, prec), kept until process exit). */
+spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec,
+                         const spde_opts* opts, const void* r, void* z, void* stream);
+
+/* Solve the scaled system (D A D) X = [0; rhs] for nsamples right-hand sides
+ * with the context's precision path (opts given at spde_grid_create).
+ *   rhs  device double [nsamples][n^3] (cell block of the scaled RHS)
+ *   x    device double [nsamples][4 n^3] solution (scaled unknowns)
+ * Synchronises `stream`; SPDE_ENOCONV as spde_sample. */
+spde_status spde_solve(spde_ctx* ctx, int level, int nsamples, double kappa, const double* rhs,
+                       double* x, void* stream);
+
+/* Project grid fields onto the tets of `level` (Eq. proj_op) and apply the
+ * output map of out_kind (SPDE_OUT_LOGNORMAL or SPDE_OUT_GAUSSIAN, with
+ * optional SPDE_OUT_F64).
+ *   theta device double [nsamples][n^3] physical cell values
+ *   out   device [nsamples][ntets] */
+spde_status spde_project(spde_ctx* ctx, int level, int nsamples, const double* theta, int out_kind,
+                         void* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPDE_H */

@@ -1,0 +1,115 @@
+// Internal host-side declarations: kernel launchers and solver structures.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace spde {
+
+constexpr int kReduceBlock = 256;
+constexpr int kMaxPartials = 4096;   // per column, per partial-sum array
+
+// Per-column MINRES state (Paige-Saunders recurrences), kept in FP64.
+struct MinresCol {
+    double beta, oldb, alpha, dbar, epsln, oldeps, phibar, cs, sn, gamma, delta, phi, beta1;
+    double tol;      // stop when phibar <= tol * beta1
+    int active;      // column still iterating
+    int upd;         // this iteration produced an update (consumed by the w/x kernel)
+    int iters;
+    int pad;
+};
+
+// Multigrid plan of one grid size for a batch of S columns.
+struct MGPlan {
+    int n = 0;          // fine cells per axis (power of two)
+    int nlev = 0;       // levels 0..nlev-1, n_l = n >> l, n_{nlev-1} = 1
+    int lc = 0;         // first level handled by the one-CTA coarse kernel (n_lc <= 16)
+    double kh2 = 0.0;   // (kappa h)^2 on level 0
+    double c = 1.0;     // Schur weight
+    double omega = 0.8; // Jacobi weight
+    // scratch (element type of the plan) for levels 1..lc: rhs b_l and result e_l,
+    // each [S][n_l^3]
+    void* b[16] = {};
+    void* e[16] = {};
+};
+
+// ---- noise.cu
+cudaError_t launch_noise(int64_t ncells, int S, uint64_t seed, uint64_t first, double scale,
+                         double* out, int64_t col_stride, cudaStream_t st);
+
+cudaError_t launch_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uint32_t* out, cudaStream_t st);
+
+// ---- stencil.cu (element type T = float or double)
+template <typename T>
+cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_t st);
+// r = [0; F] - A x (FP64), written to r32 (float, may be null) and r64 (double, may be
+// null); partial sums of r.r per column into part [S][nblk]; returns nblk
+int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x,
+                      float* r32, double* r64, double* part, const int* active, cudaStream_t st);
+// x += d (double += float) on active columns
+cudaError_t launch_add_correction(int64_t nelem, int S, double* x, const float* d, const int* active,
+                                  cudaStream_t st);
+// partial sums of a.a over columns of a strided array; returns nblk
+int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* part, cudaStream_t st);
+// out[s] = sum_b part[s][b] (fixed order)
+cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cudaStream_t st);
+
+// ---- krylov.cu
+template <typename T>
+int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_,
+                    cudaStream_t st);
+template <typename T>
+int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, T* ynext, double fd, double* partB,
+                    MinresCol* st_, cudaStream_t st);
+template <typename T>
+int launch_precond_u(int64_t N4, int n3, int S, const T* r, T* y, double fd, double* part,
+                     const MinresCol* st_, cudaStream_t st);
+cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cudaStream_t st);
+cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC,
+                          MinresCol* st_, int* nactive, cudaStream_t st);
+cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC,
+                               double tol, MinresCol* st_, int* nactive, cudaStream_t st);
+template <typename T>
+cudaError_t launch_minres_D(int64_t N4, int S, const T* ycur, T* w1, const T* w2, T* x,
+                            const MinresCol* st_, cudaStream_t st);
+template <typename T>
+cudaError_t launch_add_correction_st(int64_t N4, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st);
+cudaError_t launch_set_active(int S, const int* mask, MinresCol* st_, cudaStream_t st);
+// column activity flags used by the V-cycle and elementwise kernels
+cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStream_t st);
+
+// ---- mg.cu
+template <typename T>
+int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride,
+                  double* dot_part, const int* active, int act_stride, cudaStream_t st);
+template <typename T>
+size_t mg_scratch_elems(int n, int S);
+void mg_plan_init(MGPlan& plan, int n, double kh2, double c, double omega);
+template <typename T>
+void mg_plan_bind(MGPlan& plan, int S, T* scratch);
+
+// ---- clip.cu
+struct ClipResult {
+    int64_t nnz;
+    int bad_tet;      // first offending tet or -1
+    int bad_kind;     // 0 none, 1 degenerate, 2 outside box, 3 row sum mismatch
+};
+// Build CSR (row_ptr, col, G, Pi) for a mesh already on the device.  Allocates the CSR
+// arrays with cudaMalloc (ownership passes to the caller).  Synchronises st.
+cudaError_t build_coupling(int n, double h, const double lo[3], int64_t nverts, const double* d_xyz,
+                           int64_t ntets, const int32_t* d_tets, double* d_vol, int64_t** d_rowptr,
+                           int32_t** d_col, double** d_g, float** d_pi, ClipResult* res,
+                           cudaStream_t st);
+
+// ---- project.cu
+// theta^T[c][s] = float(scale * x[s][x_off + c]) for s < S (x column stride x_stride)
+cudaError_t launch_transpose_theta(int64_t ncell, int S, const double* x, int64_t x_stride, double scale,
+                                   float* thetaT, cudaStream_t st);
+// out[s][t] = map(sum_j pi[j] thetaT[col[j]][s]); kind 0 exp, 1 identity; f64 output if out64
+cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const int32_t* col,
+                           const float* pi, const float* thetaT, int kind, int out64, void* out,
+                           cudaStream_t st);
+// grid output: out[s][c] = scale * x[s][x_off + c]
+cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_stride, double scale,
+                            int out64, void* out, cudaStream_t st);
+
+}  // namespace spde

@@ -1,0 +1,325 @@
+// K4: batched preconditioned MINRES (Paige-Saunders recurrences) for the
+// symmetric indefinite mixed system, one column per sample.
+//
+// Vectors are [S][4 n^3]; per-column scalars live in MinresCol (FP64).  The
+// dot products are reduced deterministically: per-block partial sums in a
+// fixed-shape tree, then one fixed-order pass per column, so a column's
+// result does not depend on which other columns share the batch.
+//
+// One iteration (v = y / beta):
+//   A: z = A v - (beta / oldb) r1, alpha = v.z            (stencil, fused)
+//   B: r2' = z - (alpha / beta) r2, y' = P^{-1} r2'        (flux block here,
+//      field block by the V-cycle), beta'^2 = r2'.y'
+//   Givens rotation, residual estimate phibar, retirement
+//   D: w' = (v - oldeps w1 - delta w2) / gamma, x += phi w'
+#include "device.cuh"
+#include "internal.h"
+
+namespace spde {
+
+static inline int elem_blocks(int64_t nelem) {
+    int64_t b = (nelem + 1023) / 1024;
+    if (b > 2048) b = 2048;
+    return (int)(b < 1 ? 1 : b);
+}
+static inline int cell_blocks(int64_t n3) {
+    int64_t b = (n3 + 255) / 256;
+    if (b > 2048) b = 2048;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_minres_A(int n, T kh2, const T* __restrict__ y, T* __restrict__ r1,
+                                                  double* __restrict__ partA, const MinresCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    const MinresCol& cs = st[s];
+    if (!cs.active) return;
+    const T ib = (T)(1.0 / cs.beta);
+    const T coef = (T)(cs.oldb > 0.0 ? cs.beta / cs.oldb : 0.0);
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t off = (int64_t)s * 4 * n3;
+    const T* ys = y + off;
+    T* rs = r1 + off;
+    T acc = T(0);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((int64_t)n * n));
+        const Cell4<T> a = apply_cell<T, T>(ys, n3, n, i, j, k, c, kh2);
+        // r1 holds no data before the second iteration (coef == 0): do not read it
+        const bool use_r1 = coef != T(0);
+        const T z0 = a.ux * ib - (use_r1 ? coef * rs[c] : T(0));
+        const T z1 = a.uy * ib - (use_r1 ? coef * rs[n3 + c] : T(0));
+        const T z2 = a.uz * ib - (use_r1 ? coef * rs[2 * n3 + c] : T(0));
+        const T z3 = a.th * ib - (use_r1 ? coef * rs[3 * n3 + c] : T(0));
+        acc += (ys[c] * z0 + ys[n3 + c] * z1 + ys[2 * n3 + c] * z2 + ys[3 * n3 + c] * z3) * ib;
+        rs[c] = z0;
+        rs[n3 + c] = z1;
+        rs[2 * n3 + c] = z2;
+        rs[3 * n3 + c] = z3;
+    }
+    const double t = block_sum<256>((double)acc, red);
+    if (threadIdx.x == 0) partA[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+}
+
+template <typename T>
+int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, cudaStream_t st) {
+    const int64_t n3 = (int64_t)n * n * n;
+    const int nb = cell_blocks(n3);
+    dim3 grid(nb, S);
+    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, r1, partA, st_);
+    return nb;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_minres_B(int64_t N4, int64_t n3u, T* __restrict__ r1, const T* __restrict__ r2,
+                                                  T* __restrict__ ynext, T fd, double* __restrict__ partB,
+                                                  const MinresCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    const MinresCol& cs = st[s];
+    if (!cs.active) return;
+    const T f = (T)(cs.alpha / cs.beta);
+    const int64_t off = (int64_t)s * N4;
+    T acc = T(0);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x) {
+        const T z = r1[off + e] - f * r2[off + e];
+        r1[off + e] = z;
+        if (e < n3u) {
+            const T yv = fd * z;
+            ynext[off + e] = yv;
+            acc += z * yv;
+        }
+    }
+    const double t = block_sum<256>((double)acc, red);
+    if (threadIdx.x == 0) partB[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+}
+
+template <typename T>
+int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, T* ynext, double fd, double* partB,
+                    MinresCol* st_, cudaStream_t st) {
+    const int nb = elem_blocks(N4);
+    dim3 grid(nb, S);
+    k_minres_B<T><<<grid, 256, 0, st>>>(N4, 3 * (int64_t)n3, r1, r2, ynext, (T)fd, partB, st_);
+    return nb;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_precond_u(int64_t N4, int64_t n3u, const T* __restrict__ r, T* __restrict__ y,
+                                                   T fd, double* __restrict__ part, const MinresCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    if (st && !st[s].active) return;
+    const int64_t off = (int64_t)s * N4;
+    T acc = T(0);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3u; e += (int64_t)gridDim.x * blockDim.x) {
+        const T z = r[off + e];
+        const T yv = fd * z;
+        y[off + e] = yv;
+        acc += z * yv;
+    }
+    const double t = block_sum<256>((double)acc, red);
+    if (part && threadIdx.x == 0) part[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+}
+
+template <typename T>
+int launch_precond_u(int64_t N4, int n3, int S, const T* r, T* y, double fd, double* part, const MinresCol* st_,
+                     cudaStream_t st) {
+    const int nb = elem_blocks(3 * (int64_t)n3);
+    dim3 grid(nb, S);
+    k_precond_u<T><<<grid, 256, 0, st>>>(N4, 3 * (int64_t)n3, r, y, (T)fd, part, st_);
+    return nb;
+}
+
+__device__ __forceinline__ double col_sum(const double* part, int s, int nb, double* red) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(int64_t)s * kMaxPartials + b];
+    return block_sum<256>(acc, red);
+}
+
+__global__ void __launch_bounds__(256) k_alpha(const double* __restrict__ partA, int nA, MinresCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    if (!st[s].active) return;
+    const double a = col_sum(partA, s, nA, red);
+    if (threadIdx.x == 0) st[s].alpha = a;
+}
+
+cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cudaStream_t st) {
+    k_alpha<<<S, 256, 0, st>>>(partA, nA, st_);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB, int nB, const double* __restrict__ partC,
+                                                int nC, MinresCol* __restrict__ st, int* __restrict__ nactive) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    MinresCol& c = st[s];
+    if (!c.active) {
+        if (threadIdx.x == 0) c.upd = 0;
+        return;
+    }
+    const double b2 = col_sum(partB, s, nB, red);
+    const double b3 = col_sum(partC, s, nC, red);
+    if (threadIdx.x != 0) return;
+    const double beta2 = b2 + b3;
+    const double beta = sqrt(fmax(beta2, 0.0));
+    c.oldb = c.beta;
+    c.beta = beta;
+    c.oldeps = c.epsln;
+    const double delta = c.cs * c.dbar + c.sn * c.alpha;
+    const double gbar = c.sn * c.dbar - c.cs * c.alpha;
+    c.epsln = c.sn * beta;
+    c.dbar = -c.cs * beta;
+    double gamma = sqrt(gbar * gbar + beta2);
+    gamma = fmax(gamma, 1e-300);
+    c.cs = gbar / gamma;
+    c.sn = beta / gamma;
+    c.phi = c.cs * c.phibar;
+    c.phibar = c.sn * c.phibar;
+    c.delta = delta;
+    c.gamma = gamma;
+    c.upd = 1;
+    c.iters += 1;
+    const bool done = !(beta2 > 0.0) || !isfinite(beta) || c.phibar <= c.tol * c.beta1;
+    if (done) c.active = 0;
+    else if (nactive) atomicAdd(nactive, 1);
+}
+
+cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC, MinresCol* st_,
+                          int* nactive, cudaStream_t st) {
+    k_givens<<<S, 256, 0, st>>>(partB, nB, partC, nC, st_, nactive);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_minres_init(const double* __restrict__ partB, int nB,
+                                                     const double* __restrict__ partC, int nC, double tol,
+                                                     MinresCol* __restrict__ st, int* __restrict__ nactive) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    MinresCol& c = st[s];
+    if (!c.active) {
+        if (threadIdx.x == 0) c.upd = 0;
+        return;
+    }
+    const double b2 = col_sum(partB, s, nB, red);
+    const double b3 = col_sum(partC, s, nC, red);
+    if (threadIdx.x != 0) return;
+    const double beta2 = b2 + b3;
+    const double beta1 = sqrt(fmax(beta2, 0.0));
+    c.beta = beta1;
+    c.oldb = 0.0;
+    c.alpha = 0.0;
+    c.dbar = 0.0;
+    c.epsln = 0.0;
+    c.oldeps = 0.0;
+    c.phibar = beta1;
+    c.cs = -1.0;
+    c.sn = 0.0;
+    c.gamma = 0.0;
+    c.delta = 0.0;
+    c.phi = 0.0;
+    c.beta1 = beta1;
+    c.tol = tol;
+    c.upd = 0;
+    c.iters = 0;
+    c.active = (beta2 > 0.0 && isfinite(beta1)) ? 1 : 0;
+    if (c.active && nactive) atomicAdd(nactive, 1);
+}
+
+cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC, double tol,
+                               MinresCol* st_, int* nactive, cudaStream_t st) {
+    k_minres_init<<<S, 256, 0, st>>>(partB, nB, partC, nC, tol, st_, nactive);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_minres_D(int64_t N4, const T* __restrict__ ycur, T* __restrict__ w1,
+                                                  const T* __restrict__ w2, T* __restrict__ x,
+                                                  const MinresCol* __restrict__ st) {
+    const int s = blockIdx.y;
+    const MinresCol& c = st[s];
+    if (!c.upd) return;
+    const T iv = (T)(1.0 / c.oldb);
+    const T oe = (T)c.oldeps, de = (T)c.delta, ig = (T)(1.0 / c.gamma), ph = (T)c.phi;
+    const int64_t off = (int64_t)s * N4;
+    // iteration 1: w1 = w2 = 0 and x = 0; iteration 2: w1 = 0 (buffers hold no data yet)
+    const int it = c.iters;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x) {
+        T wn = ycur[off + e] * iv;
+        if (it >= 2) wn -= de * w2[off + e];
+        if (it >= 3) wn -= oe * w1[off + e];
+        wn *= ig;
+        w1[off + e] = wn;
+        x[off + e] = (it >= 2 ? x[off + e] : T(0)) + ph * wn;
+    }
+}
+
+template <typename T>
+cudaError_t launch_minres_D(int64_t N4, int S, const T* ycur, T* w1, const T* w2, T* x, const MinresCol* st_,
+                            cudaStream_t st) {
+    dim3 grid(elem_blocks(N4), S);
+    k_minres_D<T><<<grid, 256, 0, st>>>(N4, ycur, w1, w2, x, st_);
+    return cudaGetLastError();
+}
+
+__global__ void k_active_flags(int S, const MinresCol* __restrict__ st, int* __restrict__ flags) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) flags[s] = st[s].active;
+}
+
+cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStream_t st) {
+    k_active_flags<<<(S + 127) / 128, 128, 0, st>>>(S, st_, flags);
+    return cudaGetLastError();
+}
+
+#define SPDE_KRYLOV_INST(T)                                                                                        \
+    template int launch_minres_A<T>(int, double, int, const T*, T*, double*, MinresCol*, cudaStream_t);           \
+    template int launch_minres_B<T>(int64_t, int, int, T*, const T*, T*, double, double*, MinresCol*,             \
+                                    cudaStream_t);                                                                 \
+    template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \
+                                     cudaStream_t);                                                                \
+    template cudaError_t launch_minres_D<T>(int64_t, int, const T*, T*, const T*, T*, const MinresCol*,          \
+                                            cudaStream_t);
+SPDE_KRYLOV_INST(float)
+SPDE_KRYLOV_INST(double)
+
+}  // namespace spde
+
+namespace spde {
+
+// x64 += d for columns whose inner solve ran at least one iteration
+template <typename T>
+__global__ void __launch_bounds__(256) k_add_correction_st(int64_t N4, double* __restrict__ x, const T* __restrict__ d,
+                                                           const MinresCol* __restrict__ st) {
+    const int s = blockIdx.y;
+    if (st[s].iters == 0) return;
+    const int64_t off = (int64_t)s * N4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x)
+        x[off + e] += (double)d[off + e];
+}
+
+template <typename T>
+cudaError_t launch_add_correction_st(int64_t N4, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st) {
+    dim3 grid(elem_blocks(N4), S);
+    k_add_correction_st<T><<<grid, 256, 0, st>>>(N4, x, d, st_);
+    return cudaGetLastError();
+}
+template cudaError_t launch_add_correction_st<float>(int64_t, int, double*, const float*, const MinresCol*, cudaStream_t);
+template cudaError_t launch_add_correction_st<double>(int64_t, int, double*, const double*, const MinresCol*,
+                                                      cudaStream_t);
+
+// st[s].active = mask[s] (1 when mask is null); iteration counters cleared
+__global__ void k_set_active(int S, const int* __restrict__ mask, MinresCol* __restrict__ st) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    st[s].active = mask ? mask[s] : 1;
+    st[s].iters = 0;
+    st[s].upd = 0;
+}
+
+cudaError_t launch_set_active(int S, const int* mask, MinresCol* st_, cudaStream_t st) {
+    k_set_active<<<(S + 127) / 128, 128, 0, st>>>(S, mask, st_);
+    return cudaGetLastError();
+}
+
+}  // namespace spde

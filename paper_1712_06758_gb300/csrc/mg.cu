@@ -1,0 +1,516 @@
+// K3: field block of the MINRES preconditioner -- one symmetric geometric
+// multigrid V-cycle for the cell-centred 7-point Schur approximation
+//     A_0 = (kappa h)^2 I + c L          (L: Neumann graph Laplacian)
+// on the nested embedding grids of Sec. 6.1.
+//
+// Level l has n_l = n >> l cells per axis and operator
+//     A_l = 2^l ((kappa h)^2 4^l I + c L_l),   D_l = diag(A_l),
+// transfers P = tensor product of the 1-D cell-centred linear prolongation
+//     fine 2I <- 3/4 e_I + 1/4 e_{I-1},  fine 2I+1 <- 3/4 e_I + 1/4 e_{I+1}
+// (indices clamped at the walls: reflection for the no-flux boundary) and
+// R = P^T.  Each level: x = omega D^{-1} b (one Jacobi sweep from zero),
+// coarse correction with r = b - A x, then one more Jacobi sweep; the
+// one-cell level is solved exactly.  Same sweep before and after makes the
+// operator symmetric; with 0 < omega < 1 it is positive definite, as MINRES
+// needs.
+//
+// Kernels: levels with n_l >= 32 use shared-memory tiles (a down sweep that
+// smooths, forms the residual and restricts in one pass; an up sweep that
+// prolongs, corrects and post-smooths in one pass).  All levels with
+// n_l <= 16 run inside one CTA per sample in shared memory.
+#include "device.cuh"
+#include "internal.h"
+
+namespace spde {
+
+// tile of the fine level handled by one CTA in the down/up sweeps
+constexpr int TFX = 32, TFY = 8, TFZ = 8;
+constexpr int TCX = TFX / 2, TCY = TFY / 2, TCZ = TFZ / 2;
+constexpr int kTileThreads = 256;
+constexpr int kCoarseThreads = 512;
+constexpr int kMaxTilesPerCol = 2048;
+
+template <typename T>
+struct LevelCoef {
+    T s;         // 2^l
+    T a;         // (kappa h)^2 4^l
+    T c;         // Schur weight
+    T omega;
+    T invD[7];   // 1 / (s (a + c k)) for k neighbours
+};
+
+template <typename T>
+static LevelCoef<T> level_coef(const MGPlan& p, int l) {
+    LevelCoef<T> q;
+    const double s = (double)(1 << l);
+    const double a = p.kh2 * (double)(1ll << (2 * l));
+    q.s = (T)s;
+    q.a = (T)a;
+    q.c = (T)p.c;
+    q.omega = (T)p.omega;
+    for (int k = 0; k <= 6; ++k) q.invD[k] = (T)(1.0 / (s * (a + p.c * k)));
+    return q;
+}
+
+__device__ __forceinline__ float restrict_w(int a, int I, int nc) {
+    switch (a) {
+        case 0: return I > 0 ? 0.25f : 0.0f;
+        case 1: return I == 0 ? 1.0f : 0.75f;
+        case 2: return I == nc - 1 ? 1.0f : 0.75f;
+        default: return I < nc - 1 ? 0.25f : 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Down sweep at level l: b (fine, n_f^3) -> bc = R (b - A omega D^{-1} b)
+// Shared memory: b and x0 = omega D^{-1} b on the tile + halo 2 (zero outside
+// the box, so the Neumann Laplacian is k x0(f) - sum of the six neighbours),
+// the residual on the tile + halo 1.
+// ---------------------------------------------------------------------------
+constexpr int DBX = TFX + 4, DBY = TFY + 4, DBZ = TFZ + 4;
+constexpr int DRX = TFX + 2, DRY = TFY + 2, DRZ = TFZ + 2;
+constexpr int kDownSmem = 2 * DBX * DBY * DBZ + DRX * DRY * DRZ;
+constexpr int UXX = TFX + 2, UXY = TFY + 2, UXZ = TFZ + 2;
+constexpr int UCX = TCX + 2, UCY = TCY + 2, UCZ = TCZ + 2;
+constexpr int kUpSmem = 2 * UXX * UXY * UXZ + UCX * UCY * UCZ;
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q, const T* __restrict__ b,
+                                                          int64_t b_stride, T* __restrict__ bc, int64_t bc_stride,
+                                                          const int* __restrict__ active, int act_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sb = reinterpret_cast<T*>(smem_raw);
+    T* sx = sb + DBX * DBY * DBZ;
+    T* sr = sx + DBX * DBY * DBZ;
+    const int col = blockIdx.y;
+    if (active && !active[(int64_t)col * act_stride]) return;
+    const int nc = nf >> 1;
+    const int ntx = nc / TCX, nty = nc / TCY, ntz = nc / TCZ;
+    const int ntiles = ntx * nty * ntz;
+    const T* bs = b + (int64_t)col * b_stride;
+    T* bcs = bc + (int64_t)col * bc_stride;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+        const int cx0 = tx * TCX, cy0 = ty * TCY, cz0 = tz * TCZ;
+        const int fx0 = 2 * cx0, fy0 = 2 * cy0, fz0 = 2 * cz0;
+        for (int t = threadIdx.x; t < DBX * DBY * DBZ; t += blockDim.x) {
+            const int lx = t % DBX, ly = (t / DBX) % DBY, lz = t / (DBX * DBY);
+            const int gx = fx0 - 2 + lx, gy = fy0 - 2 + ly, gz = fz0 - 2 + lz;
+            T v = T(0), xv = T(0);
+            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf) {
+                v = bs[gx + (int64_t)nf * (gy + (int64_t)nf * gz)];
+                xv = q.omega * v * q.invD[nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf)];
+            }
+            sb[t] = v;
+            sx[t] = xv;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < DRX * DRY * DRZ; t += blockDim.x) {
+            const int lx = t % DRX, ly = (t / DRX) % DRY, lz = t / (DRX * DRY);
+            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly, gz = fz0 - 1 + lz;
+            T r = T(0);
+            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf) {
+                const int bi = (lx + 1) + DBX * ((ly + 1) + DBY * (lz + 1));
+                const int k0 = nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf);
+                const T x0 = sx[bi];
+                const T nbs = (sx[bi - 1] + sx[bi + 1]) + (sx[bi - DBX] + sx[bi + DBX]) +
+                              (sx[bi - DBX * DBY] + sx[bi + DBX * DBY]);
+                r = sb[bi] - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs));
+            }
+            sr[t] = r;
+        }
+        __syncthreads();
+        {
+            const int t = threadIdx.x;
+            const int li = t % TCX, lj = (t / TCX) % TCY, lk = t / (TCX * TCY);
+            const int I = cx0 + li, J = cy0 + lj, K = cz0 + lk;
+            T acc = T(0);
+#pragma unroll
+            for (int c3 = 0; c3 < 4; ++c3) {
+                const T wz = (T)restrict_w(c3, K, nc);
+#pragma unroll
+                for (int b3 = 0; b3 < 4; ++b3) {
+                    const T wy = (T)restrict_w(b3, J, nc) * wz;
+#pragma unroll
+                    for (int a3 = 0; a3 < 4; ++a3) {
+                        const T w = (T)restrict_w(a3, I, nc) * wy;
+                        acc += w * sr[(2 * li + a3) + DRX * ((2 * lj + b3) + DRY * (2 * lk + c3))];
+                    }
+                }
+            }
+            bcs[I + (int64_t)nc * (J + (int64_t)nc * K)] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x)
+// optional partial sums of b.y (the MINRES beta^2 contribution)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, const T* __restrict__ b,
+                                                        int64_t b_stride, const T* __restrict__ ec,
+                                                        int64_t ec_stride, T* __restrict__ y, int64_t y_stride,
+                                                        double* __restrict__ dot_part,
+                                                        const int* __restrict__ active, int act_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kTileThreads / 32];
+    T* sb = reinterpret_cast<T*>(smem_raw);
+    T* sx = sb + UXX * UXY * UXZ;
+    T* sc = sx + UXX * UXY * UXZ;
+    const int col = blockIdx.y;
+    if (active && !active[(int64_t)col * act_stride]) return;
+    const int nc = nf >> 1;
+    const int ntx = nf / TFX, nty = nf / TFY, ntz = nf / TFZ;
+    const int ntiles = ntx * nty * ntz;
+    const T* bs = b + (int64_t)col * b_stride;
+    const T* es = ec + (int64_t)col * ec_stride;
+    T* ys = y + (int64_t)col * y_stride;
+    double dacc = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+        const int fx0 = tx * TFX, fy0 = ty * TFY, fz0 = tz * TFZ;
+        const int cx0 = fx0 / 2, cy0 = fy0 / 2, cz0 = fz0 / 2;
+        for (int t = threadIdx.x; t < UCX * UCY * UCZ; t += blockDim.x) {
+            const int lx = t % UCX, ly = (t / UCX) % UCY, lz = t / (UCX * UCY);
+            const int gx = min(max(cx0 - 1 + lx, 0), nc - 1);
+            const int gy = min(max(cy0 - 1 + ly, 0), nc - 1);
+            const int gz = min(max(cz0 - 1 + lz, 0), nc - 1);
+            sc[t] = es[gx + (int64_t)nc * (gy + (int64_t)nc * gz)];
+        }
+        for (int t = threadIdx.x; t < UXX * UXY * UXZ; t += blockDim.x) {
+            const int lx = t % UXX, ly = (t / UXX) % UXY, lz = t / (UXX * UXY);
+            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly, gz = fz0 - 1 + lz;
+            T v = T(0);
+            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf)
+                v = bs[gx + (int64_t)nf * (gy + (int64_t)nf * gz)];
+            sb[t] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < UXX * UXY * UXZ; t += blockDim.x) {
+            const int lx = t % UXX, ly = (t / UXX) % UXY, lz = t / (UXX * UXY);
+            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly, gz = fz0 - 1 + lz;
+            T v = T(0);
+            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf) {
+                const int k0 = nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf);
+                // prolongation: 3/4 from the parent, 1/4 from the parent's neighbour toward f
+                const int Ix = gx >> 1, Iy = gy >> 1, Iz = gz >> 1;
+                const int Ox = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1);
+                const int Oy = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1);
+                const int Oz = min(max((gz & 1) ? Iz + 1 : Iz - 1, 0), nc - 1);
+                const int px[2] = {Ix - (cx0 - 1), Ox - (cx0 - 1)};
+                const int py[2] = {Iy - (cy0 - 1), Oy - (cy0 - 1)};
+                const int pz[2] = {Iz - (cz0 - 1), Oz - (cz0 - 1)};
+                const T w[2] = {T(0.75), T(0.25)};
+                T pe = T(0);
+#pragma unroll
+                for (int c3 = 0; c3 < 2; ++c3)
+#pragma unroll
+                    for (int b3 = 0; b3 < 2; ++b3)
+#pragma unroll
+                        for (int a3 = 0; a3 < 2; ++a3)
+                            pe += w[a3] * w[b3] * w[c3] * sc[px[a3] + UCX * (py[b3] + UCY * pz[c3])];
+                v = q.omega * sb[t] * q.invD[k0] + pe;
+            }
+            sx[t] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < TFX * TFY * TFZ; t += blockDim.x) {
+            const int ox = t % TFX, oy = (t / TFX) % TFY, oz = t / (TFX * TFY);
+            const int gx = fx0 + ox, gy = fy0 + oy, gz = fz0 + oz;
+            const int xi = (ox + 1) + UXX * ((oy + 1) + UXY * (oz + 1));
+            const T x0 = sx[xi];
+            const T nbs = (sx[xi - 1] + sx[xi + 1]) + (sx[xi - UXX] + sx[xi + UXX]) +
+                          (sx[xi - UXX * UXY] + sx[xi + UXX * UXY]);
+            const int k0 = nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf);
+            const T bv = sb[xi];
+            const T yv = x0 + q.omega * q.invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
+            ys[gx + (int64_t)nf * (gy + (int64_t)nf * gz)] = yv;
+            dacc += (double)(bv * yv);
+        }
+        __syncthreads();
+    }
+    if (dot_part) {
+        const double tsum = block_sum<kTileThreads>(dacc, red);
+        if (threadIdx.x == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// All levels n_l <= 16 in one CTA per sample (shared memory).
+// ---------------------------------------------------------------------------
+struct CoarseDesc {
+    int lc;        // first (absolute) level handled here
+    int nlev;      // total number of levels (n_{nlev-1} = 1)
+    int n0;        // n_lc
+    double kh2, c, omega;
+};
+
+template <typename T>
+__device__ __forceinline__ T cz_invD(const CoarseDesc& d, int l, int k) {
+    const T s = (T)(1 << l);
+    const T a = (T)(d.kh2 * (double)(1ll << (2 * l)));
+    return T(1) / (s * (a + (T)d.c * (T)k));
+}
+
+template <typename T>
+__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, int n, int i, int j, int k) {
+    const int f = i + n * (j + n * k);
+    const T x0 = x[f];
+    T lap = T(0);
+    if (i > 0) lap += x0 - x[f - 1];
+    if (i < n - 1) lap += x0 - x[f + 1];
+    if (j > 0) lap += x0 - x[f - n];
+    if (j < n - 1) lap += x0 - x[f + n];
+    if (k > 0) lap += x0 - x[f - n * n];
+    if (k < n - 1) lap += x0 - x[f + n * n];
+    const T s = (T)(1 << l);
+    const T a = (T)(d.kh2 * (double)(1ll << (2 * l)));
+    return s * (a * x0 + (T)d.c * lap);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, const T* __restrict__ bin, int64_t b_stride,
+                                                              T* __restrict__ eout, int64_t e_stride,
+                                                              double* __restrict__ dot_part,
+                                                              const int* __restrict__ active, int act_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kCoarseThreads / 32];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int col = blockIdx.x;
+    if (active && !active[(int64_t)col * act_stride]) return;
+    // layout: b_l and x_l for l = lc .. nlev-1, then a temp of n0^3
+    int offb[16], offx[16], nn[16];
+    int o = 0;
+    for (int l = d.lc; l < d.nlev; ++l) {
+        const int n = d.n0 >> (l - d.lc);
+        nn[l] = n;
+        offb[l] = o;
+        o += n * n * n;
+        offx[l] = o;
+        o += n * n * n;
+    }
+    T* tmp = sm + o;
+    const T* bs = bin + (int64_t)col * b_stride;
+    T* es = eout + (int64_t)col * e_stride;
+    {
+        const int n = d.n0, n3 = n * n * n;
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) sm[offb[d.lc] + f] = bs[f];
+    }
+    __syncthreads();
+    const T om = (T)d.omega;
+    // down
+    for (int l = d.lc; l < d.nlev - 1; ++l) {
+        const int n = nn[l], n3 = n * n * n, nc = n >> 1;
+        T* b = sm + offb[l];
+        T* x = sm + offx[l];
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) {
+            const int i = f % n, j = (f / n) % n, k = f / (n * n);
+            x[f] = om * b[f] * cz_invD<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n));
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) {
+            const int i = f % n, j = (f / n) % n, k = f / (n * n);
+            tmp[f] = b[f] - cz_Ax<T>(d, l, x, n, i, j, k);
+        }
+        __syncthreads();
+        T* bc = sm + offb[l + 1];
+        for (int C = threadIdx.x; C < nc * nc * nc; C += blockDim.x) {
+            const int I = C % nc, J = (C / nc) % nc, K = C / (nc * nc);
+            T acc = T(0);
+            for (int c3 = 0; c3 < 4; ++c3) {
+                const int fk = 2 * K - 1 + c3;
+                const T wz = (T)restrict_w(c3, K, nc);
+                if (wz == T(0)) continue;
+                for (int b3 = 0; b3 < 4; ++b3) {
+                    const int fj = 2 * J - 1 + b3;
+                    const T wy = (T)restrict_w(b3, J, nc) * wz;
+                    if (wy == T(0)) continue;
+                    for (int a3 = 0; a3 < 4; ++a3) {
+                        const int fi = 2 * I - 1 + a3;
+                        const T w = (T)restrict_w(a3, I, nc) * wy;
+                        if (w == T(0)) continue;
+                        acc += w * tmp[fi + n * (fj + n * fk)];
+                    }
+                }
+            }
+            bc[C] = acc;
+        }
+        __syncthreads();
+    }
+    // bottom: one cell, exact
+    {
+        const int l = d.nlev - 1;
+        if (threadIdx.x == 0) sm[offx[l]] = sm[offb[l]] * cz_invD<T>(d, l, 0);
+        __syncthreads();
+    }
+    // up
+    for (int l = d.nlev - 2; l >= d.lc; --l) {
+        const int n = nn[l], n3 = n * n * n, nc = n >> 1;
+        const T* b = sm + offb[l];
+        T* x = sm + offx[l];
+        const T* e = sm + offx[l + 1];
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) {
+            const int i = f % n, j = (f / n) % n, k = f / (n * n);
+            const int Ix = i >> 1, Iy = j >> 1, Iz = k >> 1;
+            const int Ox = min(max((i & 1) ? Ix + 1 : Ix - 1, 0), nc - 1);
+            const int Oy = min(max((j & 1) ? Iy + 1 : Iy - 1, 0), nc - 1);
+            const int Oz = min(max((k & 1) ? Iz + 1 : Iz - 1, 0), nc - 1);
+            const int px[2] = {Ix, Ox}, py[2] = {Iy, Oy}, pz[2] = {Iz, Oz};
+            const T w[2] = {T(0.75), T(0.25)};
+            T pe = T(0);
+            for (int c3 = 0; c3 < 2; ++c3)
+                for (int b3 = 0; b3 < 2; ++b3)
+                    for (int a3 = 0; a3 < 2; ++a3) pe += w[a3] * w[b3] * w[c3] * e[px[a3] + nc * (py[b3] + nc * pz[c3])];
+            tmp[f] = x[f] + pe;
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) {
+            const int i = f % n, j = (f / n) % n, k = f / (n * n);
+            const T iD = cz_invD<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n));
+            x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, n, i, j, k));
+        }
+        __syncthreads();
+    }
+    // write out (and b.e partial when this is the whole V-cycle)
+    double dacc = 0.0;
+    {
+        const int n = d.n0, n3 = n * n * n;
+        const T* x = sm + offx[d.lc];
+        const T* b = sm + offb[d.lc];
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) {
+            es[f] = x[f];
+            dacc += (double)(b[f] * x[f]);
+        }
+    }
+    if (dot_part) {
+        const double tsum = block_sum<kCoarseThreads>(dacc, red);
+        if (threadIdx.x == 0) dot_part[(int64_t)col * kMaxPartials] = tsum;
+    }
+}
+
+static int coarse_smem_elems(int n0, int lc, int nlev) {
+    int o = 0;
+    for (int l = lc; l < nlev; ++l) {
+        const int n = n0 >> (l - lc);
+        o += 2 * n * n * n;
+    }
+    return o + n0 * n0 * n0;
+}
+
+void mg_plan_init(MGPlan& plan, int n, double kh2, double c, double omega) {
+    plan.n = n;
+    plan.kh2 = kh2;
+    plan.c = c;
+    plan.omega = omega;
+    int nlev = 1;
+    while ((n >> (nlev - 1)) > 1) ++nlev;
+    plan.nlev = nlev;
+    int lc = 0;
+    while ((n >> lc) > 16) ++lc;
+    plan.lc = lc;
+}
+
+template <typename T>
+size_t mg_scratch_elems(int n, int S) {
+    MGPlan p;
+    mg_plan_init(p, n, 0.0, 1.0, 0.8);
+    size_t tot = 0;
+    for (int l = 1; l <= p.lc; ++l) {
+        const size_t nl = (size_t)(n >> l);
+        tot += 2 * nl * nl * nl;
+    }
+    return tot * (size_t)S;
+}
+
+template <typename T>
+void mg_plan_bind(MGPlan& plan, int S, T* scratch) {
+    size_t o = 0;
+    for (int l = 1; l <= plan.lc; ++l) {
+        const size_t nl = (size_t)(plan.n >> l);
+        plan.b[l] = scratch + o;
+        o += nl * nl * nl * (size_t)S;
+        plan.e[l] = scratch + o;
+        o += nl * nl * nl * (size_t)S;
+    }
+}
+
+template <typename T>
+static cudaError_t mg_attrs() {
+    static bool done = false;  // set once per instantiation and process
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mg_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kDownSmem * (int)sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmem * (int)sizeof(T));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <typename T>
+int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride, double* dot_part,
+                  const int* active, int act_stride, cudaStream_t st) {
+    if (mg_attrs<T>() != cudaSuccess) return -1;
+    const int n = plan.n;
+    CoarseDesc d;
+    d.lc = plan.lc;
+    d.nlev = plan.nlev;
+    d.n0 = n >> plan.lc;
+    d.kh2 = plan.kh2;
+    d.c = plan.c;
+    d.omega = plan.omega;
+    const size_t csm = (size_t)coarse_smem_elems(d.n0, d.lc, d.nlev) * sizeof(T);
+    if (plan.lc == 0) {
+        k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, b, b_stride, y, y_stride, dot_part, active, act_stride);
+        return 1;
+    }
+    // down sweeps
+    const T* in = b;
+    int64_t in_stride = b_stride;
+    for (int l = 0; l < plan.lc; ++l) {
+        const int nf = n >> l, nc = nf >> 1;
+        const int ntiles = (nc / TCX) * (nc / TCY) * (nc / TCZ);
+        dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
+        T* out = static_cast<T*>(plan.b[l + 1]);
+        k_mg_down<T><<<grid, kTileThreads, kDownSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
+                                                    (int64_t)nc * nc * nc, active, act_stride);
+        in = out;
+        in_stride = (int64_t)nc * nc * nc;
+    }
+    {
+        const int64_t s3 = (int64_t)d.n0 * d.n0 * d.n0;
+        k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, static_cast<const T*>(plan.b[plan.lc]), s3,
+                                                       static_cast<T*>(plan.e[plan.lc]), s3, nullptr, active,
+                                                       act_stride);
+    }
+    int nblk0 = 1;
+    for (int l = plan.lc - 1; l >= 0; --l) {
+        const int nf = n >> l, nc = nf >> 1;
+        const int ntiles = (nf / TFX) * (nf / TFY) * (nf / TFZ);
+        const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
+        dim3 grid(nb, S);
+        const T* bl = (l == 0) ? b : static_cast<const T*>(plan.b[l]);
+        const int64_t bls = (l == 0) ? b_stride : (int64_t)nf * nf * nf;
+        T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
+        const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
+        k_mg_up<T><<<grid, kTileThreads, kUpSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
+                                                  static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
+                                                  yls, (l == 0) ? dot_part : nullptr, active, act_stride);
+        if (l == 0) nblk0 = nb;
+    }
+    return nblk0;
+}
+
+#define SPDE_MG_INST(T)                                                                                            \
+    template int launch_vcycle<T>(const MGPlan&, int, const T*, int64_t, T*, int64_t, double*, const int*, int,   \
+                                  cudaStream_t);                                                                   \
+    template size_t mg_scratch_elems<T>(int, int);                                                                 \
+    template void mg_plan_bind<T>(MGPlan&, int, T*);
+SPDE_MG_INST(float)
+SPDE_MG_INST(double)
+
+}  // namespace spde

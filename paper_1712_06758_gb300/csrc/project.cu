@@ -1,0 +1,132 @@
+// K7: L2 projection onto the tet mesh fused with the output map (Eq.
+// proj_op: theta_h = W_h^{-1} G theta_bar = Pi theta_bar; lognormal
+// k = exp(theta_h) after the projection, workflow figure of Sec. 6).
+//
+// Pi is CSR with rows = tets.  The grid fields of a batch are first
+// transposed to thetaT[cell][sample] (FP32) so one CSR entry feeds all
+// samples from one contiguous row; a warp computes one tet for 32 samples
+// and a shared-memory tile turns the result into coalesced rows of
+// out[sample][tet].
+#include "device.cuh"
+#include "internal.h"
+
+namespace spde {
+
+__global__ void k_transpose_theta(int64_t ncell, int S, const double* __restrict__ x, int64_t x_stride, double scale,
+                                  float* __restrict__ thetaT) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int s0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int s = s0 + r;
+        const int64_t c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (s < S && c < ncell) ? (float)(scale * x[(int64_t)s * x_stride + c]) : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t c = c0 + r;
+        const int s = s0 + threadIdx.x;
+        if (c < ncell && s < S) thetaT[c * S + s] = tile[threadIdx.x][r];
+    }
+}
+
+cudaError_t launch_transpose_theta(int64_t ncell, int S, const double* x, int64_t x_stride, double scale,
+                                   float* thetaT, cudaStream_t st) {
+    dim3 grid((unsigned)((ncell + 31) / 32), (unsigned)((S + 31) / 32));
+    k_transpose_theta<<<grid, dim3(32, 8), 0, st>>>(ncell, S, x, x_stride, scale, thetaT);
+    return cudaGetLastError();
+}
+
+template <typename O>
+__device__ __forceinline__ O out_map(float acc, int kind) {
+    if (sizeof(O) == 8) return (O)(kind == 0 ? exp((double)acc) : (double)acc);
+    return (O)(kind == 0 ? expf(acc) : acc);
+}
+
+// warp per tet, lanes over 32 samples; block = 8 warps x 4 tets = 32 tets
+template <typename O>
+__global__ void __launch_bounds__(256) k_project_warp(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col, const float* __restrict__ pi,
+                                                      const float* __restrict__ thetaT, int kind, O* __restrict__ out) {
+    __shared__ float tile[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    for (int s0 = 0; s0 < S; s0 += 32) {
+        const int s = s0 + lane;
+        for (int rr = 0; rr < 4; ++rr) {
+            const int r = warp * 4 + rr;
+            const int64_t t = t0 + r;
+            float acc = 0.0f;
+            if (t < ntets) {
+                const int64_t a = rowptr[t], b = rowptr[t + 1];
+                for (int64_t j = a; j < b; ++j) {
+                    const float w = pi[j];
+                    const int64_t c = col[j];
+                    if (s < S) acc = fmaf(w, thetaT[c * S + s], acc);
+                }
+            }
+            tile[r][lane] = acc;
+        }
+        __syncthreads();
+        // write rows out[s][t0 .. t0+31]
+        for (int q = warp; q < 32; q += 8) {
+            const int ss = s0 + q;
+            const int64_t t = t0 + lane;
+            if (ss < S && t < ntets) out[(int64_t)ss * ntets + t] = out_map<O>(tile[lane][q], kind);
+        }
+        __syncthreads();
+    }
+}
+
+// thread per tet, loop over the few samples
+template <typename O>
+__global__ void __launch_bounds__(256) k_project_thread(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col, const float* __restrict__ pi,
+                                                        const float* __restrict__ thetaT, int kind, O* __restrict__ out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntets) return;
+    const int64_t a = rowptr[t], b = rowptr[t + 1];
+    for (int s = 0; s < S; ++s) {
+        float acc = 0.0f;
+        for (int64_t j = a; j < b; ++j) acc = fmaf(pi[j], thetaT[(int64_t)col[j] * S + s], acc);
+        out[(int64_t)s * ntets + t] = out_map<O>(acc, kind);
+    }
+}
+
+cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const int32_t* col, const float* pi,
+                           const float* thetaT, int kind, int out64, void* out, cudaStream_t st) {
+    if (S >= 8) {
+        const unsigned nb = (unsigned)((ntets + 31) / 32);
+        if (out64)
+            k_project_warp<double><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
+        else
+            k_project_warp<float><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+    } else {
+        const unsigned nb = (unsigned)((ntets + 255) / 256);
+        if (out64)
+            k_project_thread<double><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
+        else
+            k_project_thread<float><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+    }
+    return cudaGetLastError();
+}
+
+template <typename O>
+__global__ void k_grid_out(int64_t ncell, const double* __restrict__ x, int64_t x_stride, double scale,
+                           O* __restrict__ out) {
+    const int s = blockIdx.y;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
+        out[(int64_t)s * ncell + c] = (O)(scale * x[(int64_t)s * x_stride + c]);
+}
+
+cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_stride, double scale, int out64,
+                            void* out, cudaStream_t st) {
+    int64_t b = (ncell + 255) / 256;
+    if (b > 4096) b = 4096;
+    dim3 grid((unsigned)b, S);
+    if (out64) k_grid_out<double><<<grid, 256, 0, st>>>(ncell, x, x_stride, scale, (double*)out);
+    else k_grid_out<float><<<grid, 256, 0, st>>>(ncell, x, x_stride, scale, (float*)out);
+    return cudaGetLastError();
+}
+
+}  // namespace spde

@@ -1,0 +1,799 @@
+// C ABI of the sampler: contexts, embedding grids, meshes and the sampling
+// driver (noise -> FP64 iterative refinement around batched MINRES ->
+// projection + exp).  Every numerical step runs in this library's kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/spde.h"
+#include "internal.h"
+
+using namespace spde;
+
+namespace {
+
+thread_local std::string g_err;
+
+spde_status fail(spde_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+spde_status fail(spde_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(x)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (x);                                                                         \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? SPDE_ENOMEM : SPDE_ECUDA, "%s: %s (%s:%d)", \
+                        #x, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+    } while (0)
+
+#define STATUS_TRY(x)                       \
+    do {                                    \
+        spde_status s_ = (x);               \
+        if (s_ != SPDE_OK) return s_;       \
+    } while (0)
+
+// g of Sec. 4 for nu = 1/2, d = 3, times sigma:
+// (4 pi)^{3/4} kappa^{1/2} sqrt(Gamma(2) / Gamma(1/2)) sigma = sqrt(8 pi kappa) sigma
+double g_half(double kappa, double sigma) { return sigma * std::sqrt(8.0 * M_PI * kappa); }
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+template <typename T>
+spde_status dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return SPDE_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(SPDE_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    return SPDE_OK;
+}
+
+template <typename T>
+void dev_free(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Solver workspace for S columns of one grid size and inner precision.
+struct Workspace {
+    int n = 0, S = 0, inner64 = -1;
+    double* x64 = nullptr;   // [S][4n^3] refinement iterate (scaled unknowns)
+    double* F = nullptr;     // [S][n^3] cell block of the scaled RHS
+    void* vec[7] = {};       // inner vectors: d, wA, wB, r1, r2, yA, yB
+    void* mg = nullptr;      // V-cycle scratch
+    double* partA = nullptr; // partial sums [S][kMaxPartials]
+    double* partB = nullptr;
+    double* partC = nullptr;
+    double* partR = nullptr;
+    double* colv = nullptr;  // [2S] per-column reductions
+    MinresCol* st = nullptr;
+    int* nact = nullptr;
+    int* h_nact = nullptr;   // pinned
+    double* h_col = nullptr; // pinned [2S]
+    MinresCol* h_st = nullptr;
+    float* thetaT = nullptr; // [n^3][S]
+
+    void release() {
+        dev_free(x64);
+        dev_free(F);
+        for (auto& v : vec) {
+            if (v) cudaFree(v);
+            v = nullptr;
+        }
+        if (mg) cudaFree(mg);
+        mg = nullptr;
+        dev_free(partA);
+        dev_free(partB);
+        dev_free(partC);
+        dev_free(partR);
+        dev_free(colv);
+        dev_free(st);
+        dev_free(nact);
+        dev_free(thetaT);
+        if (h_nact) cudaFreeHost(h_nact);
+        if (h_col) cudaFreeHost(h_col);
+        if (h_st) cudaFreeHost(h_st);
+        h_nact = nullptr;
+        h_col = nullptr;
+        h_st = nullptr;
+        n = S = 0;
+        inner64 = -1;
+    }
+};
+
+int64_t workspace_bytes(int n, int S, bool inner64) {
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const int64_t w = inner64 ? 8 : 4;
+    int64_t b = (int64_t)S * (8 * N4 + 8 * n3 + 7 * w * N4 + 4 * n3);
+    b += (int64_t)(inner64 ? mg_scratch_elems<double>(n, S) * 8 : mg_scratch_elems<float>(n, S) * 4);
+    b += 4LL * S * kMaxPartials * 8 + 2LL * S * 8 + (int64_t)S * sizeof(MinresCol);
+    return b;
+}
+
+struct Mesh {
+    int64_t nverts = 0, ntets = 0, nnz = 0;
+    double* xyz = nullptr;
+    int32_t* tets = nullptr;
+    double* vol = nullptr;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* g = nullptr;
+    float* pi = nullptr;
+    void release() {
+        dev_free(xyz);
+        dev_free(tets);
+        dev_free(vol);
+        dev_free(rowptr);
+        dev_free(col);
+        dev_free(g);
+        dev_free(pi);
+        nverts = ntets = nnz = 0;
+    }
+};
+
+struct Level {
+    bool defined = false;
+    int n = 0;
+    double h = 0.0;
+    double lo[3] = {0, 0, 0};
+    Mesh mesh;
+    Workspace ws;
+};
+
+}  // namespace
+
+struct spde_ctx {
+    spde_opts opts;
+    std::mutex mu;
+    Level lev[16];
+    spde_stats stats;
+    void* out_tmp = nullptr;
+    size_t out_tmp_bytes = 0;
+};
+
+namespace {
+
+spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
+    if (ws.n == n && ws.S >= S && ws.inner64 == (int)inner64) return SPDE_OK;
+    ws.release();
+    const size_t n3 = (size_t)n * n * n, N4 = 4 * n3;
+    const size_t w = inner64 ? 8 : 4;
+    STATUS_TRY(dev_alloc(&ws.x64, (size_t)S * N4));
+    STATUS_TRY(dev_alloc(&ws.F, (size_t)S * n3));
+    for (auto& v : ws.vec) {
+        cudaError_t e = cudaMalloc(&v, (size_t)S * N4 * w);
+        if (e != cudaSuccess) {
+            v = nullptr;
+            cudaGetLastError();
+            ws.release();
+            return fail(SPDE_ENOMEM, "workspace allocation failed (%d columns of %d^3)", S, n);
+        }
+    }
+    const size_t mgb = inner64 ? mg_scratch_elems<double>(n, S) * 8 : mg_scratch_elems<float>(n, S) * 4;
+    if (mgb) {
+        cudaError_t e = cudaMalloc(&ws.mg, mgb);
+        if (e != cudaSuccess) {
+            ws.mg = nullptr;
+            cudaGetLastError();
+            ws.release();
+            return fail(SPDE_ENOMEM, "multigrid scratch allocation failed");
+        }
+    }
+    STATUS_TRY(dev_alloc(&ws.partA, (size_t)S * kMaxPartials));
+    STATUS_TRY(dev_alloc(&ws.partB, (size_t)S * kMaxPartials));
+    STATUS_TRY(dev_alloc(&ws.partC, (size_t)S * kMaxPartials));
+    STATUS_TRY(dev_alloc(&ws.partR, (size_t)S * kMaxPartials));
+    STATUS_TRY(dev_alloc(&ws.colv, (size_t)2 * S));
+    STATUS_TRY(dev_alloc(&ws.st, (size_t)S));
+    STATUS_TRY(dev_alloc(&ws.nact, 1));
+    STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
+    if (cudaMallocHost(&ws.h_nact, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ws.h_col, 2 * S * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&ws.h_st, S * sizeof(MinresCol)) != cudaSuccess) {
+        cudaGetLastError();
+        ws.release();
+        return fail(SPDE_ENOMEM, "pinned host allocation failed");
+    }
+    ws.n = n;
+    ws.S = S;
+    ws.inner64 = inner64 ? 1 : 0;
+    return SPDE_OK;
+}
+
+// Batched MINRES on the scaled mixed system for the columns flagged in
+// st[].active; right-hand sides in r2 (inner type T), solution in d.
+template <typename T>
+spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws, double inner_tol,
+                         int* iters_out, cudaStream_t st) {
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    T* d = static_cast<T*>(ws.vec[0]);
+    T* w1 = static_cast<T*>(ws.vec[1]);
+    T* w2 = static_cast<T*>(ws.vec[2]);
+    T* r1 = static_cast<T*>(ws.vec[3]);
+    T* r2 = static_cast<T*>(ws.vec[4]);
+    T* ycur = static_cast<T*>(ws.vec[5]);
+    T* ynext = static_cast<T*>(ws.vec[6]);
+    MGPlan plan;
+    mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
+    mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
+    const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
+    const int* act = &ws.st[0].active;
+    // y = P^{-1} r2, beta1
+    const int nB0 = launch_precond_u<T>(N4, (int)n3, S, r2, ycur, o.flux_diag, ws.partB, ws.st, st);
+    const int nC0 = launch_vcycle<T>(plan, S, r2 + 3 * n3, N4, ycur + 3 * n3, N4, ws.partC, act, act_stride, st);
+    if (nC0 < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
+    CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+    CUDA_TRY(launch_minres_init(S, ws.partB, nB0, ws.partC, nC0, inner_tol, ws.st, ws.nact, st));
+    CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    int it = 0;
+    int nactive = *ws.h_nact;
+    while (nactive > 0 && it < o.max_iter) {
+        const int chunk = std::min(o.check_every, o.max_iter - it);
+        CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+        for (int q = 0; q < chunk; ++q) {
+            const int nA = launch_minres_A<T>(n, kh2, S, ycur, r1, ws.partA, ws.st, st);
+            CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, st));
+            const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, ynext, o.flux_diag, ws.partB, ws.st, st);
+            const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
+            if (q == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, (q == chunk - 1) ? ws.nact : nullptr, st));
+            CUDA_TRY(launch_minres_D<T>(N4, S, ycur, w1, w2, d, ws.st, st));
+            std::swap(r1, r2);
+            std::swap(ycur, ynext);
+            std::swap(w1, w2);
+        }
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        it += chunk;
+        nactive = *ws.h_nact;
+    }
+    *iters_out = it;
+    return SPDE_OK;
+}
+
+// Solve (D A D) x = [0; F] for S columns: FP64 iterative refinement around an
+// inner MINRES of element type T.  F, x64 in ws; returns the max relative
+// residual in *maxrel.
+template <typename T>
+spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws, double* maxrel, int* outer_out,
+                         int* inner_out, cudaStream_t st) {
+    const spde_opts& o = ctx->opts;
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    // ||F||^2 per column
+    int nb = launch_sumsq(n3, S, ws.F, n3, ws.partR, st);
+    CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv + S, st));
+    CUDA_TRY(cudaMemsetAsync(ws.x64, 0, (size_t)S * N4 * sizeof(double), st));
+    std::vector<int> mask(S, 1);
+    int* d_mask = reinterpret_cast<int*>(ws.colv);  // reuse first S doubles' storage after use
+    int outer = 0, inner_total = 0;
+    double worst = 0.0;
+    T* r2 = static_cast<T*>(ws.vec[4]);
+    for (;;) {
+        // r = [0; F] - A x (FP64) -> r2 (inner type); ||r||^2
+        float* r32 = std::is_same<T, float>::value ? reinterpret_cast<float*>(r2) : nullptr;
+        double* r64 = std::is_same<T, double>::value ? reinterpret_cast<double*>(r2) : nullptr;
+        nb = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, st));
+        CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        int nact = 0;
+        worst = 0.0;
+        for (int s = 0; s < S; ++s) {
+            const double fn = ws.h_col[S + s];
+            const double rel = fn > 0.0 ? std::sqrt(ws.h_col[s] / fn) : 0.0;
+            worst = std::max(worst, rel);
+            mask[s] = (rel > o.tol) ? 1 : 0;
+            nact += mask[s];
+        }
+        if (nact == 0 || outer >= o.max_outer) break;
+        CUDA_TRY(cudaMemcpyAsync(d_mask, mask.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(launch_set_active(S, d_mask, ws.st, st));
+        // the inner solve only needs to reduce this step's residual by inner_tol (FP32) or
+        // to reach the overall tolerance (FP64 inner)
+        double itol = o.inner_tol;
+        if (std::is_same<T, double>::value) itol = std::max(0.1 * o.tol / std::max(worst, 1e-300), 1e-15);
+        int its = 0;
+        STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st));
+        inner_total += its;
+        CUDA_TRY(launch_add_correction_st<T>(N4, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.st, st));
+        ++outer;
+    }
+    *maxrel = worst;
+    *outer_out = outer;
+    *inner_out = inner_total;
+    if (worst > o.tol) return fail(SPDE_ENOCONV, "refinement stopped at relative residual %.3e > tol %.3e", worst, o.tol);
+    return SPDE_OK;
+}
+
+spde_status check_level(spde_ctx* ctx, int level) {
+    if (!ctx) return fail(SPDE_EINVAL, "null context");
+    if (level < 0 || level >= 16 || !ctx->lev[level].defined) return fail(SPDE_EINVAL, "level %d is not defined", level);
+    return SPDE_OK;
+}
+
+spde_status check_params(double kappa, double sigma) {
+    if (!(kappa > 0.0) || !std::isfinite(kappa)) return fail(SPDE_EINVAL, "kappa must be finite and > 0");
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(SPDE_EINVAL, "sigma must be finite and > 0");
+    return SPDE_OK;
+}
+
+// columns per batch that fit in free memory (mixed path)
+int batch_capacity(int n, int S, bool inner64) {
+    size_t freeb = 0, totb = 0;
+    if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
+        cudaGetLastError();
+        return S;
+    }
+    int cap = S;
+    while (cap > 1 && workspace_bytes(n, cap, inner64) > (int64_t)(0.85 * (double)freeb)) cap = (cap + 1) / 2;
+    return cap;
+}
+
+// Draw `S` samples starting at `first` into ws.x64 (scaled solution).
+spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double sigma, uint64_t seed, uint64_t first,
+                          cudaStream_t st) {
+    const int n = L.n;
+    const int64_t n3 = (int64_t)n * n * n;
+    const double kh2 = (kappa * L.h) * (kappa * L.h);
+    // scaled RHS cell block: h^{-1/2} (-g h^{3/2} xi) = -g h xi
+    CUDA_TRY(launch_noise(n3, S, seed, first, -g_half(kappa, sigma) * L.h, L.ws.F, n3, st));
+    double rel = 0.0;
+    int outer = 0, inner = 0;
+    spde_status s;
+    if (L.ws.inner64 == 1) s = refine_solve<double>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st);
+    else s = refine_solve<float>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st);
+    ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
+    ctx->stats.inner_iters = std::max(ctx->stats.inner_iters, inner);
+    ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
+    return s;
+}
+
+spde_status write_output(Level& L, int S, int out_kind, void* out_dev, cudaStream_t st) {
+    const int n = L.n;
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const int kind = out_kind & 15;
+    const int out64 = (out_kind & SPDE_OUT_F64) ? 1 : 0;
+    const double unscale = 1.0 / std::sqrt(L.h);  // theta = h^{-1/2} scaled theta
+    if (kind == SPDE_OUT_GRID_GAUSSIAN) {
+        CUDA_TRY(launch_grid_out(n3, S, L.ws.x64 + 3 * n3, N4, unscale, out64, out_dev, st));
+        return SPDE_OK;
+    }
+    if (!L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to this level");
+    CUDA_TRY(launch_transpose_theta(n3, S, L.ws.x64 + 3 * n3, N4, unscale, L.ws.thetaT, st));
+    CUDA_TRY(launch_project(L.mesh.ntets, S, L.mesh.rowptr, L.mesh.col, L.mesh.pi, L.ws.thetaT,
+                            kind == SPDE_OUT_LOGNORMAL ? 0 : 1, out64, out_dev, st));
+    return SPDE_OK;
+}
+
+size_t out_elem_count(const Level& L, int S, int out_kind) {
+    const int kind = out_kind & 15;
+    const size_t per = kind == SPDE_OUT_GRID_GAUSSIAN ? (size_t)L.n * L.n * L.n : (size_t)L.mesh.ntets;
+    return per * (size_t)S;
+}
+
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+spde_status spde_opts_init(spde_opts* o) {
+    if (!o) return fail(SPDE_EINVAL, "null opts");
+    o->precision = SPDE_PREC_MIXED;
+    o->tol = 1e-10;
+    o->inner_tol = 1e-5;
+    o->max_outer = 8;
+    o->max_iter = 400;
+    o->omega = 0.8;
+    o->schur_c = 1.0;
+    o->flux_diag = 1.5;
+    o->check_every = 8;
+    o->device = 0;
+    o->use_graphs = 1;
+    return SPDE_OK;
+}
+
+spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
+    if (!ctx) return fail(SPDE_EINVAL, "null ctx pointer");
+    *ctx = nullptr;
+    spde_opts o;
+    spde_opts_init(&o);
+    if (opts) o = *opts;
+    if (o.precision != SPDE_PREC_MIXED && o.precision != SPDE_PREC_FP64) return fail(SPDE_EINVAL, "bad precision");
+    if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.max_outer < 1 || o.max_iter < 1 || o.check_every < 1)
+        return fail(SPDE_EINVAL, "bad tolerance or iteration limits");
+    if (!(o.omega > 0.0 && o.omega < 1.0)) return fail(SPDE_EINVAL, "omega must lie in (0, 1)");
+    if (!(o.schur_c > 0.0) || !(o.flux_diag > 0.0)) return fail(SPDE_EINVAL, "preconditioner weights must be > 0");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (o.device < 0 || o.device >= ndev) return fail(SPDE_EINVAL, "device %d not present", o.device);
+    CUDA_TRY(cudaSetDevice(o.device));
+    spde_ctx* c = new spde_ctx();
+    c->opts = o;
+    std::memset(&c->stats, 0, sizeof c->stats);
+    *ctx = c;
+    return SPDE_OK;
+}
+
+spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]) {
+    if (!ctx || !lo || !hi) return fail(SPDE_EINVAL, "null argument");
+    if (level < 0 || level >= 16) return fail(SPDE_EINVAL, "level must lie in [0, 16)");
+    if (!is_pow2(n) || n < 2 || n > 1024) return fail(SPDE_EINVAL, "n must be a power of two in [2, 1024]");
+    const double ext = hi[0] - lo[0];
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a]))
+            return fail(SPDE_EINVAL, "box must have hi > lo on every axis");
+        if (std::fabs((hi[a] - lo[a]) - ext) > 1e-12 * ext) return fail(SPDE_EINVAL, "cells must be cubes");
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& L = ctx->lev[level];
+    L.mesh.release();
+    L.ws.release();
+    L.defined = true;
+    L.n = n;
+    L.h = ext / n;
+    for (int a = 0; a < 3; ++a) L.lo[a] = lo[a];
+    return SPDE_OK;
+}
+
+spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const double* xyz, int64_t ntets,
+                             const int32_t* tets) {
+    STATUS_TRY(check_level(ctx, level));
+    if (nverts < 4 || ntets < 1 || !xyz || !tets) return fail(SPDE_EINVAL, "empty mesh");
+    if (ntets > (int64_t)1 << 31) return fail(SPDE_EINVAL, "too many tets");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& L = ctx->lev[level];
+    L.mesh.release();
+    Mesh& m = L.mesh;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    STATUS_TRY(dev_alloc(&m.xyz, (size_t)nverts * 3));
+    STATUS_TRY(dev_alloc(&m.tets, (size_t)ntets * 4));
+    STATUS_TRY(dev_alloc(&m.vol, (size_t)ntets));
+    CUDA_TRY(cudaMemcpy(m.xyz, xyz, (size_t)nverts * 3 * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m.tets, tets, (size_t)ntets * 4 * sizeof(int32_t), cudaMemcpyHostToDevice));
+    ClipResult res;
+    CUDA_TRY(cudaEventRecord(e0, st));
+    cudaError_t e = build_coupling(L.n, L.h, L.lo, nverts, m.xyz, ntets, m.tets, m.vol, &m.rowptr, &m.col, &m.g,
+                                   &m.pi, &res, st);
+    CUDA_TRY(cudaEventRecord(e1, st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        m.release();
+        return fail(e == cudaErrorMemoryAllocation ? SPDE_ENOMEM : SPDE_ECUDA, "coupling build failed: %s",
+                    cudaGetErrorString(e));
+    }
+    if (res.bad_tet >= 0) {
+        static const char* why[4] = {"", "degenerate or invalid tet", "tet outside the embedding box",
+                                     "coupling row does not sum to the tet volume"};
+        const int t = res.bad_tet, k = res.bad_kind;
+        m.release();
+        return fail(SPDE_EMESH, "mesh rejected: tet %d: %s", t, why[k & 3]);
+    }
+    m.nverts = nverts;
+    m.ntets = ntets;
+    m.nnz = res.nnz;
+    ctx->stats.setup_ms = ms;
+    ctx->stats.nnz = res.nnz;
+    return SPDE_OK;
+}
+
+spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, uint64_t seed,
+                        uint64_t first_sample, int out_kind, void* out, void* stream) {
+    STATUS_TRY(check_level(ctx, level));
+    STATUS_TRY(check_params(kappa, sigma));
+    if (nsamples < 0) return fail(SPDE_EINVAL, "nsamples < 0");
+    const int kind = out_kind & 15;
+    if (kind > SPDE_OUT_GRID_GAUSSIAN || (out_kind & ~(15 | SPDE_OUT_F64))) return fail(SPDE_EINVAL, "bad out_kind");
+    if (nsamples == 0) return SPDE_OK;
+    if (!out) return fail(SPDE_EINVAL, "null output");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& L = ctx->lev[level];
+    if (kind != SPDE_OUT_GRID_GAUSSIAN && !L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
+    const size_t esz = (out_kind & SPDE_OUT_F64) ? 8 : 4;
+    const bool host_out = is_host_pointer(out);
+    ctx->stats.outer_iters = 0;
+    ctx->stats.inner_iters = 0;
+    ctx->stats.max_rel_residual = 0.0;
+    // plain path: one sample per solve; mixed path: batches that fit in memory
+    int cap = 1;
+    if (!plain) {
+        if (L.ws.n == L.n && L.ws.S >= nsamples && L.ws.inner64 == 0) cap = nsamples;
+        else {
+            L.ws.release();
+            cap = batch_capacity(L.n, nsamples, false);
+        }
+    }
+    spde_status worst = SPDE_OK;
+    for (int s0 = 0; s0 < nsamples; s0 += cap) {
+        const int S = std::min(cap, nsamples - s0);
+        STATUS_TRY(ensure_workspace(L.ws, L.n, plain ? 1 : std::min(cap, nsamples), plain));
+        spde_status s = solve_samples(ctx, L, S, kappa, sigma, seed, first_sample + (uint64_t)s0, st);
+        if (s != SPDE_OK && s != SPDE_ENOCONV) return s;
+        if (s == SPDE_ENOCONV) worst = s;
+        const size_t per = out_elem_count(L, 1, out_kind);
+        void* dst = static_cast<char*>(out) + (size_t)s0 * per * esz;
+        if (host_out) {
+            const size_t need = (size_t)S * per * esz;
+            if (ctx->out_tmp_bytes < need) {
+                if (ctx->out_tmp) cudaFree(ctx->out_tmp);
+                ctx->out_tmp = nullptr;
+                ctx->out_tmp_bytes = 0;
+                CUDA_TRY(cudaMalloc(&ctx->out_tmp, need));
+                ctx->out_tmp_bytes = need;
+            }
+            STATUS_TRY(write_output(L, S, out_kind, ctx->out_tmp, st));
+            CUDA_TRY(cudaMemcpyAsync(dst, ctx->out_tmp, need, cudaMemcpyDeviceToHost, st));
+        } else {
+            STATUS_TRY(write_output(L, S, out_kind, dst, st));
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (worst != SPDE_OK)
+        return fail(worst, "tolerance not reached: relative residual %.3e", ctx->stats.max_rel_residual);
+    return SPDE_OK;
+}
+
+spde_status spde_query_footprint(spde_ctx* ctx, int level, int nsamples, int64_t* bytes) {
+    STATUS_TRY(check_level(ctx, level));
+    if (!bytes || nsamples < 0) return fail(SPDE_EINVAL, "bad argument");
+    const Level& L = ctx->lev[level];
+    const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
+    *bytes = workspace_bytes(L.n, plain ? 1 : nsamples, plain);
+    return SPDE_OK;
+}
+
+spde_status spde_get_stats(spde_ctx* ctx, spde_stats* stats) {
+    if (!ctx || !stats) return fail(SPDE_EINVAL, "null argument");
+    *stats = ctx->stats;
+    return SPDE_OK;
+}
+
+spde_status spde_mesh_info(spde_ctx* ctx, int level, int64_t* ntets, int64_t* nnz) {
+    STATUS_TRY(check_level(ctx, level));
+    const Mesh& m = ctx->lev[level].mesh;
+    if (ntets) *ntets = m.ntets;
+    if (nnz) *nnz = m.nnz;
+    return SPDE_OK;
+}
+
+spde_status spde_mesh_copy_csr(spde_ctx* ctx, int level, int64_t* row_ptr, int32_t* col, double* gval, double* vol) {
+    STATUS_TRY(check_level(ctx, level));
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    const Mesh& m = ctx->lev[level].mesh;
+    if (!m.rowptr) return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
+    if (row_ptr) CUDA_TRY(cudaMemcpy(row_ptr, m.rowptr, (m.ntets + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (col) CUDA_TRY(cudaMemcpy(col, m.col, m.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (gval) CUDA_TRY(cudaMemcpy(gval, m.g, m.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    if (vol) CUDA_TRY(cudaMemcpy(vol, m.vol, m.ntets * sizeof(double), cudaMemcpyDeviceToHost));
+    return SPDE_OK;
+}
+
+const char* spde_last_error(void) { return g_err.c_str(); }
+
+spde_status spde_destroy(spde_ctx* ctx) {
+    if (!ctx) return SPDE_OK;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        cudaSetDevice(ctx->opts.device);
+        for (auto& L : ctx->lev) {
+            L.mesh.release();
+            L.ws.release();
+        }
+        if (ctx->out_tmp) cudaFree(ctx->out_tmp);
+    }
+    delete ctx;
+    return SPDE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// step-level entry points
+// ---------------------------------------------------------------------------
+spde_status spde_noise(int64_t ncells, int nsamples, uint64_t seed, uint64_t first_sample, double scale, double* out,
+                       void* stream) {
+    if (ncells < 0 || nsamples < 0) return fail(SPDE_EINVAL, "negative size");
+    if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
+    if (ncells == 0 || nsamples == 0) return SPDE_OK;
+    if (!out) return fail(SPDE_EINVAL, "null output");
+    CUDA_TRY(launch_noise(ncells, nsamples, seed, first_sample, scale, out, ncells, static_cast<cudaStream_t>(stream)));
+    return SPDE_OK;
+}
+
+spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uint32_t* out, void* stream) {
+    if (npairs < 0) return fail(SPDE_EINVAL, "negative size");
+    if (npairs == 0) return SPDE_OK;
+    if (!out) return fail(SPDE_EINVAL, "null output");
+    CUDA_TRY(launch_noise_words(npairs, seed, sample, out, static_cast<cudaStream_t>(stream)));
+    return SPDE_OK;
+}
+
+spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x, void* y, void* stream) {
+    if (n < 2 || nsamples < 0 || !(h > 0.0) || !std::isfinite(kappa) || kappa < 0.0)
+        return fail(SPDE_EINVAL, "bad size or parameters");
+    if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
+    if (nsamples == 0) return SPDE_OK;
+    if (!x || !y) return fail(SPDE_EINVAL, "null buffer");
+    const double kh2 = (kappa * h) * (kappa * h);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec == SPDE_PREC_FP64)
+        CUDA_TRY(launch_apply<double>(n, kh2, nsamples, static_cast<const double*>(x), static_cast<double*>(y), st));
+    else if (prec == SPDE_PREC_MIXED)
+        CUDA_TRY(launch_apply<float>(n, kh2, nsamples, static_cast<const float*>(x), static_cast<float*>(y), st));
+    else
+        return fail(SPDE_EINVAL, "bad precision");
+    return SPDE_OK;
+}
+
+namespace {
+struct PrecondScratch {
+    int n = 0, S = 0, prec = -1;
+    void* mg = nullptr;
+    double* part = nullptr;
+};
+std::mutex g_pc_mu;
+PrecondScratch g_pc;
+}  // namespace
+
+spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, const spde_opts* opts, const void* r,
+                         void* z, void* stream) {
+    if (!is_pow2(n) || n < 2 || n > 1024 || nsamples < 0 || !(h > 0.0) || !(kappa > 0.0) || !std::isfinite(kappa))
+        return fail(SPDE_EINVAL, "bad size or parameters");
+    if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
+    if (prec != SPDE_PREC_FP64 && prec != SPDE_PREC_MIXED) return fail(SPDE_EINVAL, "bad precision");
+    if (nsamples == 0) return SPDE_OK;
+    if (!r || !z) return fail(SPDE_EINVAL, "null buffer");
+    spde_opts o;
+    spde_opts_init(&o);
+    if (opts) o = *opts;
+    std::lock_guard<std::mutex> g(g_pc_mu);
+    if (g_pc.n != n || g_pc.S < nsamples || g_pc.prec != prec) {
+        if (g_pc.mg) cudaFree(g_pc.mg);
+        dev_free(g_pc.part);
+        g_pc = PrecondScratch();
+        const size_t b = prec == SPDE_PREC_FP64 ? mg_scratch_elems<double>(n, nsamples) * 8
+                                                 : mg_scratch_elems<float>(n, nsamples) * 4;
+        if (b) CUDA_TRY(cudaMalloc(&g_pc.mg, b));
+        STATUS_TRY(dev_alloc(&g_pc.part, (size_t)nsamples * kMaxPartials));
+        g_pc.n = n;
+        g_pc.S = nsamples;
+        g_pc.prec = prec;
+    }
+    const double kh2 = (kappa * h) * (kappa * h);
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MGPlan plan;
+    mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
+    if (prec == SPDE_PREC_FP64) {
+        mg_plan_bind<double>(plan, nsamples, static_cast<double*>(g_pc.mg));
+        const double* rr = static_cast<const double*>(r);
+        double* zz = static_cast<double*>(z);
+        launch_precond_u<double>(N4, (int)n3, nsamples, rr, zz, o.flux_diag, nullptr, nullptr, st);
+        if (launch_vcycle<double>(plan, nsamples, rr + 3 * n3, N4, zz + 3 * n3, N4, nullptr, nullptr, 0, st) < 0)
+            return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
+    } else {
+        mg_plan_bind<float>(plan, nsamples, static_cast<float*>(g_pc.mg));
+        const float* rr = static_cast<const float*>(r);
+        float* zz = static_cast<float*>(z);
+        launch_precond_u<float>(N4, (int)n3, nsamples, rr, zz, o.flux_diag, nullptr, nullptr, st);
+        if (launch_vcycle<float>(plan, nsamples, rr + 3 * n3, N4, zz + 3 * n3, N4, nullptr, nullptr, 0, st) < 0)
+            return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
+    }
+    CUDA_TRY(cudaGetLastError());
+    return SPDE_OK;
+}
+
+spde_status spde_solve(spde_ctx* ctx, int level, int nsamples, double kappa, const double* rhs, double* x,
+                       void* stream) {
+    STATUS_TRY(check_level(ctx, level));
+    STATUS_TRY(check_params(kappa, 1.0));
+    if (nsamples < 0) return fail(SPDE_EINVAL, "nsamples < 0");
+    if (nsamples == 0) return SPDE_OK;
+    if (!rhs || !x) return fail(SPDE_EINVAL, "null buffer");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& L = ctx->lev[level];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
+    const int n = L.n;
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const double kh2 = (kappa * L.h) * (kappa * L.h);
+    int cap = 1;
+    if (!plain) {
+        if (L.ws.n == n && L.ws.S >= nsamples && L.ws.inner64 == 0) cap = nsamples;
+        else {
+            L.ws.release();
+            cap = batch_capacity(n, nsamples, false);
+        }
+    }
+    ctx->stats.outer_iters = 0;
+    ctx->stats.inner_iters = 0;
+    ctx->stats.max_rel_residual = 0.0;
+    spde_status worst = SPDE_OK;
+    for (int s0 = 0; s0 < nsamples; s0 += cap) {
+        const int S = std::min(cap, nsamples - s0);
+        STATUS_TRY(ensure_workspace(L.ws, n, plain ? 1 : std::min(cap, nsamples), plain));
+        CUDA_TRY(cudaMemcpyAsync(L.ws.F, rhs + (size_t)s0 * n3, (size_t)S * n3 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+        double rel = 0.0;
+        int outer = 0, inner = 0;
+        spde_status s = plain ? refine_solve<double>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st)
+                              : refine_solve<float>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st);
+        if (s != SPDE_OK && s != SPDE_ENOCONV) return s;
+        if (s == SPDE_ENOCONV) worst = s;
+        ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
+        ctx->stats.inner_iters = std::max(ctx->stats.inner_iters, inner);
+        ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
+        CUDA_TRY(cudaMemcpyAsync(x + (size_t)s0 * N4, L.ws.x64, (size_t)S * N4 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (worst != SPDE_OK) return fail(worst, "tolerance not reached: %.3e", ctx->stats.max_rel_residual);
+    return SPDE_OK;
+}
+
+spde_status spde_project(spde_ctx* ctx, int level, int nsamples, const double* theta, int out_kind, void* out,
+                         void* stream) {
+    STATUS_TRY(check_level(ctx, level));
+    const int kind = out_kind & 15;
+    if (kind > SPDE_OUT_GAUSSIAN || (out_kind & ~(15 | SPDE_OUT_F64))) return fail(SPDE_EINVAL, "bad out_kind");
+    if (nsamples < 0) return fail(SPDE_EINVAL, "nsamples < 0");
+    if (nsamples == 0) return SPDE_OK;
+    if (!theta || !out) return fail(SPDE_EINVAL, "null buffer");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& L = ctx->lev[level];
+    if (!L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    float* tT = nullptr;
+    STATUS_TRY(dev_alloc(&tT, (size_t)nsamples * n3));
+    cudaError_t e = launch_transpose_theta(n3, nsamples, theta, n3, 1.0, tT, st);
+    if (e == cudaSuccess)
+        e = launch_project(L.mesh.ntets, nsamples, L.mesh.rowptr, L.mesh.col, L.mesh.pi, tT,
+                           kind == SPDE_OUT_LOGNORMAL ? 0 : 1, (out_kind & SPDE_OUT_F64) ? 1 : 0, out, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tT);
+    CUDA_TRY(e);
+    return SPDE_OK;
+}
+
+}  // extern "C"
