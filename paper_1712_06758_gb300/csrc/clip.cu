@@ -345,6 +345,7 @@ static cudaError_t exclusive_scan(int64_t n, const int64_t* in, int64_t* out, in
         cudaError_t e_ = (x);                    \
         if (e_ != cudaSuccess) {                 \
             err = e_;                            \
+            cudaGetLastError();                  \
             goto done;                           \
         }                                        \
     } while (0)
@@ -393,7 +394,7 @@ cudaError_t build_coupling(int n, double h, const double lo[3], int64_t nverts, 
     CK(exclusive_scan(ntets, cand, cand_off, tmp, &ncand, st));
     CK(cudaMalloc(&cvol, (ncand + 1) * sizeof(double)));
     CK(cudaMalloc(&ccell, (ncand + 1) * sizeof(int32_t)));
-    k_tet_clip<<<tb, 128, 0, st>>>(g, d_xyz, ntets, tets, range, cand_off, cand, cvol, ccell, nz);
+    k_tet_clip<<<(unsigned)((ntets + 127) / 128), 128, 0, st>>>(g, d_xyz, ntets, tets, range, cand_off, cand, cvol, ccell, nz);
     CK(cudaGetLastError());
     CK(cudaMalloc(&rowptr, (ntets + 1) * sizeof(int64_t)));
     CK(exclusive_scan(ntets, nz, rowptr, tmp, &nnz, st));

@@ -34,9 +34,11 @@ spde_status fail(spde_status s, const char* fmt, ...) {
 #define CUDA_TRY(x)                                                                                   \
     do {                                                                                              \
         cudaError_t e_ = (x);                                                                         \
-        if (e_ != cudaSuccess)                                                                        \
+        if (e_ != cudaSuccess) {                                                                      \
+            cudaGetLastError(); /* clear a non-sticky error so later calls do not report it */        \
             return fail(e_ == cudaErrorMemoryAllocation ? SPDE_ENOMEM : SPDE_ECUDA, "%s: %s (%s:%d)", \
                         #x, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+        }                                                                                             \
     } while (0)
 
 #define STATUS_TRY(x)                       \

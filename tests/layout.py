@@ -64,3 +64,8 @@ def wall_mask(n):
     m[n3:2 * n3] = (jj == n - 1).ravel()
     m[2 * n3:3 * n3] = (kk == n - 1).ravel()
     return m
+
+
+def oracle_eq_to_lib(yu, yt, n, h):
+    """Equation-space oracle vector (e.g. A x) -> scaled library layout (D y)."""
+    return oracle_to_lib(yu * h ** -3.0, yt * h ** -1.0, n, h)
