@@ -1,0 +1,374 @@
+"""Benchmark of the SPDE sampler on one node (one process per GPU).
+
+Workload (the 128^3 headline case): embedding grid 128^3 on [0,1]^3,
+kappa = 20, sigma = 1, nu = 1/2; target mesh = jittered 6-tet split of
+96^3 cubes on the L-prism [0.05,0.95]^3 minus {x > 0.5, y > 0.5}
+(3,981,312 tets); 64 samples per step, FP32 MINRES + V-cycle inside FP64
+refinement to a relative FP64 residual of 1e-10; lognormal output
+exp(theta_h) on the tets.  A step draws a fresh batch (its own Philox sample
+indices), so every step solves new systems.  The per-step working set
+(~21 GB of solver state) is far larger than L2, so no flush is needed.
+
+Metric: samples/s of the batched mixed-precision path (whole job over all
+ranks), with per-step (64-sample batch) latency p50/p99, next to the plain
+FP64 GPU path measured on the same workload and the relative L2 difference
+of their fields.  Ranks shard the samples (weak scaling, no collective on
+the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "spde_sampler_128cube_lprism96", "grid_n": 128, "kappa": 20.0, "sigma": 1.0, "nu": 0.5,
+            "mesh": "L-prism 96^3 cubes x 6 tets, jitter +-h/4 (seed 1)", "ntets": 3981312, "batch": 64,
+            "tol": 1e-10, "seed": 1, "output": "lognormal f32 on tets",
+            "l2_note": "inputs larger than L2 (solver state ~21 GB per step)"}
+METRIC = "samples/s & p50/p99 latency at 1e-6 rel L2 vs plain FP64 GPU path, 128³ grid"
+
+
+# ---------------------------------------------------------------- host logic
+def first_sample(step, rank, world, batch):
+    """Philox sample index of the first sample of (step, rank): disjoint batches."""
+    return (step * world + rank) * batch
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_max(value, world):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch per column from a committed ncu summary, if the
+    kernel source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if sha != rec["source_sha256"]:
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+class OracleCost:
+    """Time the FP64 oracle as it stands on a bounded sample of one step.
+
+    Set-up (once): the L-prism mesh and the oracle's clipping of
+    `ntet_sample` evenly spaced tets.  Per sample: Philox noise + exact DCT
+    solve on the full 128^3 grid, then projection + exp on those tets,
+    scaled to all tets.  The clipping is reported as set-up, like the GPU's.
+    """
+
+    def __init__(self, ntet_sample=2000):
+        import numpy as np
+        from oracle import clip
+        from synth import lprism_mesh
+        self.n = WORKLOAD["grid_n"]
+        self.xyz, self.tets = lprism_mesh(96)
+        idx = np.linspace(0, len(self.tets) - 1, ntet_sample).astype(np.int64)
+        t0 = time.perf_counter()
+        self.rows = clip.coupling_rows(self.xyz, self.tets, self.n, rows=idx)
+        self.t_clip = time.perf_counter() - t0
+        self.scale = len(self.tets) / float(ntet_sample)
+        self.ntet_sample = ntet_sample
+
+    def sample(self, sample_index):
+        from oracle import mixed, philox, project
+        t0 = time.perf_counter()
+        xi = philox.normals(self.n ** 3, WORKLOAD["seed"], sample_index)
+        th = mixed.solve_dct(self.n, WORKLOAD["kappa"], WORKLOAD["sigma"], xi)
+        t_solve = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        vals = project.project_rows(self.xyz, self.tets, self.rows, th)
+        _ = {t: project.lognormal(v) for t, v in vals.items()}
+        t_proj = time.perf_counter() - t0
+        per_sample = t_solve + t_proj * self.scale
+        desc = ("1 sample per step: Philox noise + DCT solve on the full 128^3 grid (%.2f s); projection+exp on "
+                "%d of %d tets (%.3f s) scaled x%.0f; Pi set-up excluded (oracle clipping of those tets took "
+                "%.1f s, x%.0f = %.0f s)" % (t_solve, self.ntet_sample, len(self.tets), t_proj, self.scale,
+                                             self.t_clip, self.scale, self.t_clip * self.scale))
+        return per_sample, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    oc = OracleCost(500)
+    for i in range(args.warmup):
+        oc.sample(1000 + i)
+    costs = []
+    desc = ""
+    for i in range(args.steps):
+        c, desc = oc.sample(i)
+        costs.append(c)
+    value = 1.0 / statistics.mean(costs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(costs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1712_06758_gb300 as pkg
+    from synth import lprism_mesh
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    W = dict(WORKLOAD)
+    if args.batch:
+        W["batch"] = args.batch
+        W["workload"] += "_batch%d" % args.batch
+    S, n = W["batch"], W["grid_n"]
+    xyz, tets = lprism_mesh(96)
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local)
+    smp.add_level(0, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    smp.attach_mesh(0, xyz, tets)
+    setup = smp.stats()
+    ntets = smp.ntets(0)
+    out = torch.empty((S, ntets), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i, dst):
+        pkg.spde_sample(smp.ctx, 0, S, W["kappa"], W["sigma"], W["seed"], first_sample(i, rank, world, S),
+                        pkg.SPDE_OUT_LOGNORMAL, dst, stream)
+
+    for i in range(args.warmup):
+        step(1000 + i, out)
+    iters = smp.stats()
+    clocks = ClockSampler(local)
+    pkg.spde_profile_enable(smp.ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(i, out)
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    prof = pkg.spde_profile(smp.ctx)
+    pkg.spde_profile_enable(smp.ctx, False)
+    elapsed_ms = reduce_max(t_start.elapsed_time(t_end), world)
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    value = world * args.steps * S / (elapsed_ms / 1000.0)
+
+    # dominant kernel, live roofline
+    peak, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda p: p["ms"])
+    achieved = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9 if dom["ms"] > 0 else 0.0
+    per_launch_bytes = dom["bytes"] / max(dom["launches"], 1)
+    tr = kernel_traffic(dom["name"])
+    traffic = None
+    if tr:
+        traffic = tr["dram_bytes_per_launch_per_column"] * per_launch_bytes / tr["algorithmic_bytes_per_launch_per_column"]
+    roofline = {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": traffic, "avg_launch_us": 1000.0 * dom["ms"] / max(dom["launches"], 1),
+                "algorithmic_bytes_per_launch": per_launch_bytes, "share_of_step": dom["ms"] / elapsed_ms}
+    kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                           "GBps": round(p["bytes"] / p["ms"] / 1e6, 1) if p["ms"] > 0 else None}
+               for p in prof if p["launches"]}
+    gpu_launches = int(sum(p["launches"] for p in prof))
+
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+                              "config": W, "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
+                              "note": "reduced run (no plain path, e2e or CPU baseline)"}), flush=True)
+        smp.close()
+        return
+    # e2e: same call with a pinned host output (device->host copy inside)
+    host = torch.empty((S, ntets), dtype=torch.float32, pin_memory=True)
+    host_np = host.numpy()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        pkg.spde_sample(smp.ctx, 0, S, W["kappa"], W["sigma"], W["seed"], first_sample(args.steps + i, rank, world, S),
+                        pkg.SPDE_OUT_LOGNORMAL, host_np, stream)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e = {"value": world * args.steps * S / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": int(S * ntets * 4)}
+
+    line = None
+    if rank == 0:
+        # plain FP64 path on the same workload (first samples of step 0), and the field difference
+        nplain = args.plain_samples
+        ref_out = torch.empty((S, ntets), dtype=torch.float32, device="cuda")
+        step(0, ref_out)
+        plain = pkg.Sampler(pkg.SPDE_PREC_FP64, tol=W["tol"], device=local)
+        plain.add_level(0, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+        plain.attach_mesh(0, xyz, tets)
+        pout = torch.empty((nplain, ntets), dtype=torch.float32, device="cuda")
+        plain.sample(0, 1, W["kappa"], W["sigma"], W["seed"], 0, pkg.SPDE_OUT_LOGNORMAL, pout[:1])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        plain.sample(0, nplain, W["kappa"], W["sigma"], W["seed"], first_sample(0, rank, world, S),
+                     pkg.SPDE_OUT_LOGNORMAL, pout, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_rate = nplain / (a.elapsed_time(b) / 1000.0)
+        pst = plain.stats()
+        d = (ref_out[:nplain].double() - pout.double()).norm(dim=1) / pout.double().norm(dim=1)
+        plain.close()
+        # the oracle on the host cores, bounded sample
+        oc = OracleCost(2000)
+        cost, desc = oc.sample(0)
+        line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": dict(W, parallelism="samples sharded over %d rank(s)" % world),
+                "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                               "per": "one %d-sample batch call" % S},
+                "plain_fp64": {"value": plain_rate, "unit": "samples/s", "samples": nplain,
+                               "ratio": value / world / plain_rate, "inner_iters": pst["inner_iters"],
+                               "max_rel_l2_vs_mixed": float(d.max())},
+                "solver": {"outer_iters": iters["outer_iters"], "inner_iters": iters["inner_iters"],
+                           "max_rel_residual": iters["max_rel_residual"]},
+                "setup": {"clip_ms": setup["setup_ms"], "nnz": setup["nnz"]},
+                "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches, "e2e": e2e,
+                "clocks": clk,
+                "cpu_baseline": {"value": 1.0 / cost, "unit": "samples/s", "cores": os.cpu_count() or 1,
+                                 "kind": "oracle", "sample": desc}}
+        print(json.dumps(line), flush=True)
+    smp.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plain-samples", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=0, help="override the 64-sample batch (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="headline loop only (profiling runs)")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,24 @@ spde_status spde_mesh_info(spde_ctx* ctx, int level, int64_t* ntets, int64_t* nn
 spde_status spde_mesh_copy_csr(spde_ctx* ctx, int level, int64_t* row_ptr, int32_t* col,
                                double* gval, double* vol);
 
+/* Per-kernel timing of this context (CUDA events recorded around every
+ * launch on the launching stream; the device time between them is that
+ * launch's duration).  enable != 0 clears the counters and starts
+ * recording, 0 stops.  Recording adds two event records per launch and no
+ * synchronisation. */
+spde_status spde_profile_enable(spde_ctx* ctx, int enable);
+
+/* Counters of kernel class k (0 <= k < 15, in launch order of the path:
+ * noise, sumsq, residual64, minres_A, alpha, minres_B, mg_down, mg_coarse,
+ * mg_up, givens, minres_D, add_correction, transpose_theta, project_exp, other
+ * (reductions, column flags, MINRES start)):
+ * *name its name, *launches its launches, *ms their summed device time,
+ * *bytes their summed algorithmic bytes (each launch's inputs read once and
+ * outputs written once, for the columns active when it was enqueued).
+ * Any output pointer may be NULL. */
+spde_status spde_profile_read(spde_ctx* ctx, int k, const char** name, int64_t* launches, double* ms,
+                              double* bytes);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* spde_last_error(void);
 

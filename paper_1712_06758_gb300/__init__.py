@@ -57,6 +57,9 @@ _SIGS = {
     "spde_destroy": [_P],
     "spde_noise": [ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, _P, _P],
     "spde_noise_words": [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, _P, _P],
+    "spde_profile_enable": [_P, ctypes.c_int],
+    "spde_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "spde_apply": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "spde_precond": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                      ctypes.POINTER(spde_opts), _P, _P, _P],
@@ -173,6 +176,25 @@ def spde_mesh_copy_csr(ctx, level):
     vol = np.zeros(nt, dtype=np.float64)
     _check(lib().spde_mesh_copy_csr(ctx, level, _ptr(rowptr), _ptr(col), _ptr(g), _ptr(vol)))
     return rowptr, col[:nz], g[:nz], vol
+
+
+def spde_profile_enable(ctx, enable=True):
+    _check(lib().spde_profile_enable(ctx, 1 if enable else 0))
+
+
+PROF_CLASSES = 15
+
+
+def spde_profile_read(ctx, k):
+    name = ctypes.c_char_p()
+    nl, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().spde_profile_read(ctx, k, ctypes.byref(name), ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(by)))
+    return {"name": name.value.decode(), "launches": nl.value, "ms": ms.value, "bytes": by.value}
+
+
+def spde_profile(ctx):
+    """All kernel classes' counters as a list of dicts."""
+    return [spde_profile_read(ctx, k) for k in range(PROF_CLASSES)]
 
 
 def spde_last_error():

@@ -26,6 +26,7 @@ struct MGPlan {
     double kh2 = 0.0;   // (kappa h)^2 on level 0
     double c = 1.0;     // Schur weight
     double omega = 0.8; // Jacobi weight
+    double prof_cols = 0.0; // columns assumed active, for the profiler's byte counts (0: all)
     // scratch (element type of the plan) for levels 1..lc: rhs b_l and result e_l,
     // each [S][n_l^3]
     void* b[16] = {};
@@ -108,6 +109,8 @@ cudaError_t launch_transpose_theta(int64_t ncell, int S, const double* x, int64_
 cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const int32_t* col,
                            const float* pi, const float* thetaT, int kind, int out64, void* out,
                            cudaStream_t st);
+// number of distinct column indices of a CSR matrix (cells touched by the projection)
+cudaError_t count_used_columns(int64_t nnz, const int32_t* col, int64_t ncell, int64_t* used, cudaStream_t st);
 // grid output: out[s][c] = scale * x[s][x_off + c]
 cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_stride, double scale,
                             int out64, void* out, cudaStream_t st);

@@ -20,6 +20,7 @@
 // n_l <= 16 run inside one CTA per sample in shared memory.
 #include "device.cuh"
 #include "internal.h"
+#include "prof.h"
 
 namespace spde {
 
@@ -454,6 +455,7 @@ static cudaError_t mg_attrs() {
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride, double* dot_part,
                   const int* active, int act_stride, cudaStream_t st) {
+    const double prof_cols = plan.prof_cols > 0 ? plan.prof_cols : (double)S;
     if (mg_attrs<T>() != cudaSuccess) return -1;
     const int n = plan.n;
     CoarseDesc d;
@@ -464,8 +466,12 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     d.c = plan.c;
     d.omega = plan.omega;
     const size_t csm = (size_t)coarse_smem_elems(d.n0, d.lc, d.nlev) * sizeof(T);
+    const double w = (double)sizeof(T);
+    const double n0c = (double)d.n0 * d.n0 * d.n0;
     if (plan.lc == 0) {
+        prof_begin(PK_MG_COARSE, st);
         k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, b, b_stride, y, y_stride, dot_part, active, act_stride);
+        prof_end(st, prof_cols * 2.0 * n0c * w);
         return 1;
     }
     // down sweeps
@@ -476,16 +482,20 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const int ntiles = (nc / TCX) * (nc / TCY) * (nc / TCZ);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
+        prof_begin(PK_MG_DOWN, st);
         k_mg_down<T><<<grid, kTileThreads, kDownSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
                                                     (int64_t)nc * nc * nc, active, act_stride);
+        prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
         in = out;
         in_stride = (int64_t)nc * nc * nc;
     }
     {
         const int64_t s3 = (int64_t)d.n0 * d.n0 * d.n0;
+        prof_begin(PK_MG_COARSE, st);
         k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, static_cast<const T*>(plan.b[plan.lc]), s3,
                                                        static_cast<T*>(plan.e[plan.lc]), s3, nullptr, active,
                                                        act_stride);
+        prof_end(st, prof_cols * 2.0 * n0c * w);
     }
     int nblk0 = 1;
     for (int l = plan.lc - 1; l >= 0; --l) {
@@ -497,9 +507,11 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const int64_t bls = (l == 0) ? b_stride : (int64_t)nf * nf * nf;
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
         const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
+        prof_begin(PK_MG_UP, st);
         k_mg_up<T><<<grid, kTileThreads, kUpSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
                                                   static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
                                                   yls, (l == 0) ? dot_part : nullptr, active, act_stride);
+        prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);
         if (l == 0) nblk0 = nb;
     }
     return nblk0;

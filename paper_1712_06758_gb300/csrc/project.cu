@@ -129,4 +129,38 @@ cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_str
     return cudaGetLastError();
 }
 
+__global__ void k_mark_cols(int64_t nnz, const int32_t* __restrict__ col, unsigned char* __restrict__ flag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x)
+        flag[col[j]] = 1;
+}
+
+__global__ void k_count_flags(int64_t n, const unsigned char* __restrict__ flag, unsigned long long* __restrict__ cnt) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += flag[i];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+cudaError_t count_used_columns(int64_t nnz, const int32_t* col, int64_t ncell, int64_t* used, cudaStream_t st) {
+    unsigned char* flag = nullptr;
+    unsigned long long* cnt = nullptr;
+    unsigned long long h = 0;
+    cudaError_t e = cudaMalloc(&flag, (size_t)ncell);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, (size_t)ncell, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && nnz > 0) {
+        k_mark_cols<<<1024, 256, 0, st>>>(nnz, col, flag);
+        k_count_flags<<<1024, 256, 0, st>>>(ncell, flag, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(flag);
+    cudaFree(cnt);
+    *used = (int64_t)h;
+    return e;
+}
+
 }  // namespace spde

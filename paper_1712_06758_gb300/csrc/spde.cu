@@ -13,8 +13,16 @@
 
 #include "../../include/spde.h"
 #include "internal.h"
+#include "prof.h"
 
 using namespace spde;
+
+namespace spde {
+thread_local Profiler* t_prof = nullptr;
+const char* const kProfNames[PK_NCLASS] = {"noise",   "sumsq",  "residual64", "minres_A",  "alpha",
+                                           "minres_B", "mg_down", "mg_coarse",  "mg_up",     "givens",
+                                           "minres_D", "add_correction", "transpose_theta", "project_exp", "other"};
+}  // namespace spde
 
 namespace {
 
@@ -129,7 +137,7 @@ int64_t workspace_bytes(int n, int S, bool inner64) {
 }
 
 struct Mesh {
-    int64_t nverts = 0, ntets = 0, nnz = 0;
+    int64_t nverts = 0, ntets = 0, nnz = 0, ncols_used = 0;
     double* xyz = nullptr;
     int32_t* tets = nullptr;
     double* vol = nullptr;
@@ -162,6 +170,7 @@ struct Level {
 
 struct spde_ctx {
     spde_opts opts;
+    Profiler prof;
     std::mutex mu;
     Level lev[16];
     spde_stats stats;
@@ -236,27 +245,47 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
     const int* act = &ws.st[0].active;
+    const double w = (double)sizeof(T);
+    const double n3d = (double)n3;
     // y = P^{-1} r2, beta1
+    plan.prof_cols = (double)S;
+    prof_begin(PK_OTHER, st);
     const int nB0 = launch_precond_u<T>(N4, (int)n3, S, r2, ycur, o.flux_diag, ws.partB, ws.st, st);
+    prof_end(st, (double)S * 6.0 * n3d * w);
     const int nC0 = launch_vcycle<T>(plan, S, r2 + 3 * n3, N4, ycur + 3 * n3, N4, ws.partC, act, act_stride, st);
     if (nC0 < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
     CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+    prof_begin(PK_OTHER, st);
     CUDA_TRY(launch_minres_init(S, ws.partB, nB0, ws.partC, nC0, inner_tol, ws.st, ws.nact, st));
+    prof_end(st, (double)S * (nB0 + nC0) * 8.0);
     CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     int it = 0;
     int nactive = *ws.h_nact;
     while (nactive > 0 && it < o.max_iter) {
         const int chunk = std::min(o.check_every, o.max_iter - it);
-        CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+        // bytes are counted for the columns active at the start of the chunk
+        const double cols = (double)nactive;
+        plan.prof_cols = cols;
         for (int q = 0; q < chunk; ++q) {
+            const int itn = it + q + 1;  // 1-based iteration of the columns that started together
+            prof_begin(PK_MINRES_A, st);
             const int nA = launch_minres_A<T>(n, kh2, S, ycur, r1, ws.partA, ws.st, st);
+            prof_end(st, cols * (itn >= 2 ? 12.0 : 8.0) * n3d * w);
+            prof_begin(PK_ALPHA, st);
             CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, st));
+            prof_end(st, cols * nA * 8.0);
+            prof_begin(PK_MINRES_B, st);
             const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, ynext, o.flux_diag, ws.partB, ws.st, st);
+            prof_end(st, cols * 15.0 * n3d * w);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
             if (q == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+            prof_begin(PK_GIVENS, st);
             CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, (q == chunk - 1) ? ws.nact : nullptr, st));
+            prof_end(st, cols * (nB + nC) * 8.0);
+            prof_begin(PK_MINRES_D, st);
             CUDA_TRY(launch_minres_D<T>(N4, S, ycur, w1, w2, d, ws.st, st));
+            prof_end(st, cols * (itn >= 3 ? 24.0 : (itn == 2 ? 20.0 : 12.0)) * n3d * w);
             std::swap(r1, r2);
             std::swap(ycur, ynext);
             std::swap(w1, w2);
@@ -264,6 +293,7 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        if (t_prof) t_prof->flush();
         it += chunk;
         nactive = *ws.h_nact;
     }
@@ -280,8 +310,12 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
     const spde_opts& o = ctx->opts;
     const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
     // ||F||^2 per column
+    prof_begin(PK_SUMSQ, st);
     int nb = launch_sumsq(n3, S, ws.F, n3, ws.partR, st);
+    prof_end(st, (double)S * 8.0 * (double)n3);
+    prof_begin(PK_OTHER, st);
     CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv + S, st));
+    prof_end(st, (double)S * nb * 8.0);
     CUDA_TRY(cudaMemsetAsync(ws.x64, 0, (size_t)S * N4 * sizeof(double), st));
     std::vector<int> mask(S, 1);
     int* d_mask = reinterpret_cast<int*>(ws.colv);  // reuse first S doubles' storage after use
@@ -292,9 +326,13 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         // r = [0; F] - A x (FP64) -> r2 (inner type); ||r||^2
         float* r32 = std::is_same<T, float>::value ? reinterpret_cast<float*>(r2) : nullptr;
         double* r64 = std::is_same<T, double>::value ? reinterpret_cast<double*>(r2) : nullptr;
+        prof_begin(PK_RESIDUAL, st);
         nb = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st);
+        prof_end(st, (double)S * (40.0 + 4.0 * sizeof(T)) * (double)n3);
         CUDA_TRY(cudaGetLastError());
+        prof_begin(PK_OTHER, st);
         CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, st));
+        prof_end(st, (double)S * nb * 8.0);
         CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         int nact = 0;
@@ -308,7 +346,9 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         }
         if (nact == 0 || outer >= o.max_outer) break;
         CUDA_TRY(cudaMemcpyAsync(d_mask, mask.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+        prof_begin(PK_OTHER, st);
         CUDA_TRY(launch_set_active(S, d_mask, ws.st, st));
+        prof_end(st, (double)S * 4.0);
         // the inner solve only needs to reduce this step's residual by inner_tol (FP32) or
         // to reach the overall tolerance (FP64 inner)
         double itol = o.inner_tol;
@@ -316,7 +356,9 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         int its = 0;
         STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st));
         inner_total += its;
+        prof_begin(PK_ADD_CORR, st);
         CUDA_TRY(launch_add_correction_st<T>(N4, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.st, st));
+        prof_end(st, (double)nact * (64.0 + 4.0 * sizeof(T)) * (double)n3);
         ++outer;
     }
     *maxrel = worst;
@@ -357,7 +399,9 @@ spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double s
     const int64_t n3 = (int64_t)n * n * n;
     const double kh2 = (kappa * L.h) * (kappa * L.h);
     // scaled RHS cell block: h^{-1/2} (-g h^{3/2} xi) = -g h xi
+    prof_begin(PK_NOISE, st);
     CUDA_TRY(launch_noise(n3, S, seed, first, -g_half(kappa, sigma) * L.h, L.ws.F, n3, st));
+    prof_end(st, (double)S * 8.0 * (double)n3);
     double rel = 0.0;
     int outer = 0, inner = 0;
     spde_status s;
@@ -380,9 +424,15 @@ spde_status write_output(Level& L, int S, int out_kind, void* out_dev, cudaStrea
         return SPDE_OK;
     }
     if (!L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to this level");
+    prof_begin(PK_TRANSPOSE, st);
     CUDA_TRY(launch_transpose_theta(n3, S, L.ws.x64 + 3 * n3, N4, unscale, L.ws.thetaT, st));
+    prof_end(st, (double)S * 12.0 * (double)n3);
+    prof_begin(PK_PROJECT, st);
     CUDA_TRY(launch_project(L.mesh.ntets, S, L.mesh.rowptr, L.mesh.col, L.mesh.pi, L.ws.thetaT,
                             kind == SPDE_OUT_LOGNORMAL ? 0 : 1, out64, out_dev, st));
+    // CSR once, the covered cells' rows of thetaT once, the output once
+    prof_end(st, 8.0 * (double)(L.mesh.ntets + 1) + 8.0 * (double)L.mesh.nnz +
+                     4.0 * (double)S * (double)L.mesh.ncols_used + (out64 ? 8.0 : 4.0) * (double)S * L.mesh.ntets);
     return SPDE_OK;
 }
 
@@ -391,6 +441,12 @@ size_t out_elem_count(const Level& L, int S, int out_kind) {
     const size_t per = kind == SPDE_OUT_GRID_GAUSSIAN ? (size_t)L.n * L.n * L.n : (size_t)L.mesh.ntets;
     return per * (size_t)S;
 }
+
+// makes the context's profiler visible to the launch wrappers for one call
+struct ProfScope {
+    explicit ProfScope(Profiler& p) { t_prof = &p; }
+    ~ProfScope() { t_prof = nullptr; }
+};
 
 bool is_host_pointer(const void* p) {
     cudaPointerAttributes a;
@@ -510,6 +566,11 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
     m.nverts = nverts;
     m.ntets = ntets;
     m.nnz = res.nnz;
+    {
+        int64_t used = 0;
+        CUDA_TRY(count_used_columns(res.nnz, m.col, (int64_t)L.n * L.n * L.n, &used, st));
+        m.ncols_used = used;
+    }
     ctx->stats.setup_ms = ms;
     ctx->stats.nnz = res.nnz;
     return SPDE_OK;
@@ -526,6 +587,7 @@ spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, do
     if (!out) return fail(SPDE_EINVAL, "null output");
     std::lock_guard<std::mutex> g(ctx->mu);
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    ProfScope ps(ctx->prof);
     Level& L = ctx->lev[level];
     if (kind != SPDE_OUT_GRID_GAUSSIAN && !L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -569,6 +631,7 @@ spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, do
         }
     }
     CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->prof.flush();
     if (worst != SPDE_OK)
         return fail(worst, "tolerance not reached: relative residual %.3e", ctx->stats.max_rel_residual);
     return SPDE_OK;
@@ -607,6 +670,26 @@ spde_status spde_mesh_copy_csr(spde_ctx* ctx, int level, int64_t* row_ptr, int32
     if (col) CUDA_TRY(cudaMemcpy(col, m.col, m.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (gval) CUDA_TRY(cudaMemcpy(gval, m.g, m.nnz * sizeof(double), cudaMemcpyDeviceToHost));
     if (vol) CUDA_TRY(cudaMemcpy(vol, m.vol, m.ntets * sizeof(double), cudaMemcpyDeviceToHost));
+    return SPDE_OK;
+}
+
+spde_status spde_profile_enable(spde_ctx* ctx, int enable) {
+    if (!ctx) return fail(SPDE_EINVAL, "null context");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return SPDE_OK;
+}
+
+spde_status spde_profile_read(spde_ctx* ctx, int k, const char** name, int64_t* launches, double* ms, double* bytes) {
+    if (!ctx) return fail(SPDE_EINVAL, "null context");
+    if (k < 0 || k >= PK_NCLASS) return fail(SPDE_EINVAL, "kernel class out of range");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->prof.flush();
+    if (name) *name = kProfNames[k];
+    if (launches) *launches = ctx->prof.launches[k];
+    if (ms) *ms = ctx->prof.ms[k];
+    if (bytes) *bytes = ctx->prof.bytes[k];
     return SPDE_OK;
 }
 

@@ -1,0 +1,55 @@
+"""Host logic of bench.py: sample sharding and the max-over-ranks reduction."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def test_first_sample_partition_is_disjoint():
+    seen = set()
+    for step in range(5):
+        for rank in range(4):
+            f = bench.first_sample(step, rank, 4, 64)
+            block = set(range(f, f + 64))
+            assert not (block & seen)
+            seen |= block
+    assert seen == set(range(5 * 4 * 64))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, _ = bench.dist_env()
+    bench.barrier(w)
+    m = bench.reduce_max(10.0 * (r + 1), w)
+    q.put((r, m, bench.first_sample(3, r, w, 64)))
+    dist.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    assert [m for _, m, _ in res] == [20.0, 20.0]
+    assert [f for _, _, f in res] == [3 * 2 * 64, (3 * 2 + 1) * 64]
