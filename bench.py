@@ -38,6 +38,14 @@ METRIC = "samples/s & p50/p99 latency at 1e-6 rel L2 vs plain FP64 GPU path, 128
 
 
 # ---------------------------------------------------------------- host logic
+_T0 = time.time()
+
+
+def log(msg):
+    sys.stderr.write("[bench %7.1fs] %s\n" % (time.time() - _T0, msg))
+    sys.stderr.flush()
+
+
 def first_sample(step, rank, world, batch):
     """Philox sample index of the first sample of (step, rank): disjoint batches."""
     return (step * world + rank) * batch
@@ -228,7 +236,9 @@ def run_ours(args):
         W["batch"] = args.batch
         W["workload"] += "_batch%d" % args.batch
     S, n = W["batch"], W["grid_n"]
+    log("mesh")
     xyz, tets = lprism_mesh(96)
+    log("attach")
     smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local)
     smp.add_level(0, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
     smp.attach_mesh(0, xyz, tets)
@@ -241,14 +251,17 @@ def run_ours(args):
         pkg.spde_sample(smp.ctx, 0, S, W["kappa"], W["sigma"], W["seed"], first_sample(i, rank, world, S),
                         pkg.SPDE_OUT_LOGNORMAL, dst, stream)
 
+    log("warmup")
     for i in range(args.warmup):
         step(1000 + i, out)
+        log("warmup step %d: %s" % (i, smp.stats()))
     iters = smp.stats()
     clocks = ClockSampler(local)
     pkg.spde_profile_enable(smp.ctx, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
+    log("timed region")
     barrier(world)
     torch.cuda.synchronize()
     t_start.record(stream)
@@ -259,6 +272,7 @@ def run_ours(args):
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(world)
+    log("timed region done")
     clk = clocks.stop()
     prof = pkg.spde_profile(smp.ctx)
     pkg.spde_profile_enable(smp.ctx, False)
@@ -293,6 +307,7 @@ def run_ours(args):
         smp.close()
         return
     # e2e: same call with a pinned host output (device->host copy inside)
+    log("e2e")
     host = torch.empty((S, ntets), dtype=torch.float32, pin_memory=True)
     host_np = host.numpy()
     barrier(world)
@@ -309,6 +324,7 @@ def run_ours(args):
     line = None
     if rank == 0:
         # plain FP64 path on the same workload (first samples of step 0), and the field difference
+        log("plain path")
         nplain = args.plain_samples
         ref_out = torch.empty((S, ntets), dtype=torch.float32, device="cuda")
         step(0, ref_out)
@@ -329,7 +345,8 @@ def run_ours(args):
         d = (ref_out[:nplain].double() - pout.double()).norm(dim=1) / pout.double().norm(dim=1)
         plain.close()
         # the oracle on the host cores, bounded sample
-        oc = OracleCost(2000)
+        log("cpu baseline")
+        oc = OracleCost(1000)
         cost, desc = oc.sample(0)
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -355,6 +372,8 @@ def run_ours(args):
 
 
 def main(argv=None):
+    import faulthandler
+    faulthandler.dump_traceback_later(120, repeat=True, file=sys.stderr)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -40,6 +40,20 @@ def _barycentric(p, x):
     return np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1)
 
 
+def _merge_coincident(pts, tol=1e-14):
+    """Keep one point of every group of (numerically) coincident points.
+
+    The candidate list repeats vertices that several facet triples define
+    (a tet vertex on a box face is also an edge/plane meet).  The polytope's
+    vertex set does not change, but Qhull can stall on exact duplicates.
+    """
+    keep = []
+    for x in pts:
+        if not any(np.max(np.abs(x - y)) <= tol for y in keep):
+            keep.append(x)
+    return np.array(keep)
+
+
 def tet_box_volume(p, lo, hi, eps=1e-12):
     """Exact volume of tet p [4,3] intersected with the box [lo, hi]."""
     lo = np.asarray(lo, dtype=np.float64)
@@ -89,9 +103,9 @@ def tet_box_volume(p, lo, hi, eps=1e-12):
                     if blo[ax] - eps <= x[ax] <= bhi[ax] + eps:
                         if np.all(_barycentric(q, x[None, :])[0] >= -eps):
                             pts.append(x)
+    pts = _merge_coincident(np.array(pts))
     if len(pts) < 4:
         return 0.0
-    pts = np.array(pts)
     try:
         vol = ConvexHull(pts).volume
     except QhullError:

@@ -117,3 +117,23 @@ def test_projection_preserves_constants_and_integrals():
             col[c] += v
     assert lhs == pytest.approx(col @ th, rel=1e-12)
     assert project.lognormal(np.array([0.0, 1.0]))[1] == pytest.approx(np.e)
+
+
+def test_coincident_candidate_points():
+    """Tet with a face on a box plane and an edge on another: the candidate
+    vertex list holds exact duplicates (once a Qhull stall).  Checked against
+    point sampling."""
+    p = np.array([[0.11682211, 0.81982355, 0.9401086],
+                  [0.115625, 0.81875, 0.95],
+                  [0.125, 0.828125, 0.95],
+                  [0.115625, 0.828125, 0.95]])
+    h = 1.0 / 128
+    lo = h * np.array([14, 105, 121])
+    v = clip.tet_box_volume(p, lo, lo + h)
+    rng = np.random.default_rng(5)
+    lam = rng.dirichlet(np.ones(4), size=400000)
+    x = lam @ p
+    inside = np.all((x >= lo) & (x <= lo + h), axis=1).mean()
+    f = v / clip.tet_volume(p)
+    assert abs(inside - f) < 5 * np.sqrt(f * (1 - f) / len(x)) + 1e-4
+    assert 0.0 < f < 1.0
