@@ -108,7 +108,7 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts);
 
 /* Define embedding grid `level` (0 <= level < 16): n^3 cubic cells on the
  * box [lo, hi] (Sec. 4.1, domain embedding; Sec. 6.1, nested grids).
- * n must be a power of two, 2 <= n <= 1024, and hi - lo equal on all three
+ * n must be a power of two, 4 <= n <= 1024, and hi - lo equal on all three
  * axes (cubic cells).  Replaces an existing level of the same index. */
 spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]);
 
@@ -160,10 +160,10 @@ spde_status spde_mesh_copy_csr(spde_ctx* ctx, int level, int64_t* row_ptr, int32
  * synchronisation. */
 spde_status spde_profile_enable(spde_ctx* ctx, int enable);
 
-/* Counters of kernel class k (0 <= k < 15, in launch order of the path:
+/* Counters of kernel class k (0 <= k < 16, in launch order of the path:
  * noise, sumsq, residual64, minres_A, alpha, minres_B, mg_down, mg_coarse,
- * mg_up, givens, minres_D, add_correction, transpose_theta, project_exp, other
- * (reductions, column flags, MINRES start)):
+ * mg_up, givens, minres_D, add_correction, transpose_theta, project_exp,
+ * flux_from_theta, other (reductions, column flags, MINRES start)):
  * *name its name, *launches its launches, *ms their summed device time,
  * *bytes their summed algorithmic bytes (each launch's inputs read once and
  * outputs written once, for the columns active when it was enqueued).
@@ -200,7 +200,8 @@ spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uin
 
 /* y = (D A D) x, the scaled mixed operator (Eq. linsys_blocks) on an n^3 grid
  * of spacing h, for nsamples stacked vectors of 4 n^3 entries (layout above).
- * prec SPDE_PREC_FP64: x, y are double; SPDE_PREC_MIXED: float.
+ * prec SPDE_PREC_FP64: x, y are double; SPDE_PREC_MIXED: float.  n is a
+ * power of two in [4, 1024]; x and y are 16-byte aligned.
  * Wall entries of y are written as 0. */
 spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x,
                        void* y, void* stream);

@@ -182,7 +182,7 @@ def spde_profile_enable(ctx, enable=True):
     _check(lib().spde_profile_enable(ctx, 1 if enable else 0))
 
 
-PROF_CLASSES = 15
+PROF_CLASSES = 16
 
 
 def spde_profile_read(ctx, k):

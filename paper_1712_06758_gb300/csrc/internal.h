@@ -49,6 +49,12 @@ int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_strid
 // x += d (double += float) on active columns
 cudaError_t launch_add_correction(int64_t nelem, int S, double* x, const float* d, const int* active,
                                   cudaStream_t st);
+// u = -T^{-1} D1^T theta into the flux blocks of x ([S][4 n^3], FP64), line by line;
+// tri: Thomas factors (2n - 2 doubles, see k_flux_lines)
+cudaError_t launch_flux_from_theta(int n, int S, double* x, int64_t col_stride, const double* tri, cudaStream_t st);
+// x cell block += d ([S][n^3]) for columns whose inner solve ran
+template <typename T>
+cudaError_t launch_add_theta(int64_t n3, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st);
 // partial sums of a.a over columns of a strided array; returns nblk
 int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* part, cudaStream_t st);
 // out[s] = sum_b part[s][b] (fixed order)
@@ -69,8 +75,9 @@ cudaError_t launch_givens(int S, const double* partB, int nB, const double* part
                           MinresCol* st_, int* nactive, cudaStream_t st);
 cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC,
                                double tol, MinresCol* st_, int* nactive, cudaStream_t st);
+// cell-block update: w1, w2, x are [S][n^3]; ycur is [S][4 n^3]
 template <typename T>
-cudaError_t launch_minres_D(int64_t N4, int S, const T* ycur, T* w1, const T* w2, T* x,
+cudaError_t launch_minres_D(int64_t n3, int S, const T* ycur, T* w1, const T* w2, T* x,
                             const MinresCol* st_, cudaStream_t st);
 template <typename T>
 cudaError_t launch_add_correction_st(int64_t N4, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st);

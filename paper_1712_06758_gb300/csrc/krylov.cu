@@ -37,25 +37,41 @@ __global__ void __launch_bounds__(256) k_minres_A(int n, T kh2, const T* __restr
     if (!cs.active) return;
     const T ib = (T)(1.0 / cs.beta);
     const T coef = (T)(cs.oldb > 0.0 ? cs.beta / cs.oldb : 0.0);
-    const int64_t n3 = (int64_t)n * n * n;
+    // r1 holds no data before the second iteration (coef == 0): do not read it
+    const bool use_r1 = coef != T(0);
+    const int logn = ilog2(n);
+    const int n3 = 1 << (3 * logn);
+    const int nq = n3 >> 2;
     const int64_t off = (int64_t)s * 4 * n3;
     const T* ys = y + off;
     T* rs = r1 + off;
     T acc = T(0);
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((int64_t)n * n));
-        const Cell4<T> a = apply_cell<T, T>(ys, n3, n, i, j, k, c, kh2);
-        // r1 holds no data before the second iteration (coef == 0): do not read it
-        const bool use_r1 = coef != T(0);
-        const T z0 = a.ux * ib - (use_r1 ? coef * rs[c] : T(0));
-        const T z1 = a.uy * ib - (use_r1 ? coef * rs[n3 + c] : T(0));
-        const T z2 = a.uz * ib - (use_r1 ? coef * rs[2 * n3 + c] : T(0));
-        const T z3 = a.th * ib - (use_r1 ? coef * rs[3 * n3 + c] : T(0));
-        acc += (ys[c] * z0 + ys[n3 + c] * z1 + ys[2 * n3 + c] * z2 + ys[3 * n3 + c] * z3) * ib;
-        rs[c] = z0;
-        rs[n3 + c] = z1;
-        rs[2 * n3 + c] = z2;
-        rs[3 * n3 + c] = z3;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const QuadPos p = quad_pos(q, logn);
+        T yu[4], yv[4], yw[4], yt[4];
+        apply_quad<T, T>(ys, n, logn, p, kh2, yu, yv, yw, yt);
+        const V4<T> v0 = ld4(ys + p.c), v1 = ld4(ys + n3 + p.c), v2 = ld4(ys + 2 * n3 + p.c), v3 = ld4(ys + 3 * n3 + p.c);
+        V4<T> z0, z1, z2, z3;
+        if (use_r1) {
+            z0 = ld4(rs + p.c);
+            z1 = ld4(rs + n3 + p.c);
+            z2 = ld4(rs + 2 * n3 + p.c);
+            z3 = ld4(rs + 3 * n3 + p.c);
+        } else {
+            z0 = z1 = z2 = z3 = zero4<T>();
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            z0.v[e] = yu[e] * ib - coef * z0.v[e];
+            z1.v[e] = yv[e] * ib - coef * z1.v[e];
+            z2.v[e] = yw[e] * ib - coef * z2.v[e];
+            z3.v[e] = yt[e] * ib - coef * z3.v[e];
+            acc += (v0.v[e] * z0.v[e] + v1.v[e] * z1.v[e] + v2.v[e] * z2.v[e] + v3.v[e] * z3.v[e]) * ib;
+        }
+        st4(rs + p.c, z0);
+        st4(rs + n3 + p.c, z1);
+        st4(rs + 2 * n3 + p.c, z2);
+        st4(rs + 3 * n3 + p.c, z3);
     }
     const double t = block_sum<256>((double)acc, red);
     if (threadIdx.x == 0) partA[(int64_t)s * kMaxPartials + blockIdx.x] = t;
@@ -64,7 +80,7 @@ __global__ void __launch_bounds__(256) k_minres_A(int n, T kh2, const T* __restr
 template <typename T>
 int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, cudaStream_t st) {
     const int64_t n3 = (int64_t)n * n * n;
-    const int nb = cell_blocks(n3);
+    const int nb = cell_blocks(n3 / 4);
     dim3 grid(nb, S);
     k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, r1, partA, st_);
     return nb;
@@ -232,8 +248,10 @@ cudaError_t launch_minres_init(int S, const double* partB, int nB, const double*
     return cudaGetLastError();
 }
 
+// Update of the solution recurrences on the cell block only: the caller keeps
+// w1, w2, x as [S][n^3]; v = y / oldb is read from the cell block of y.
 template <typename T>
-__global__ void __launch_bounds__(256) k_minres_D(int64_t N4, const T* __restrict__ ycur, T* __restrict__ w1,
+__global__ void __launch_bounds__(256) k_minres_D(int64_t n3, const T* __restrict__ ycur, T* __restrict__ w1,
                                                   const T* __restrict__ w2, T* __restrict__ x,
                                                   const MinresCol* __restrict__ st) {
     const int s = blockIdx.y;
@@ -241,24 +259,33 @@ __global__ void __launch_bounds__(256) k_minres_D(int64_t N4, const T* __restric
     if (!c.upd) return;
     const T iv = (T)(1.0 / c.oldb);
     const T oe = (T)c.oldeps, de = (T)c.delta, ig = (T)(1.0 / c.gamma), ph = (T)c.phi;
-    const int64_t off = (int64_t)s * N4;
+    const T* ys = ycur + (int64_t)s * 4 * n3 + 3 * n3;
+    const int64_t off = (int64_t)s * n3;
     // iteration 1: w1 = w2 = 0 and x = 0; iteration 2: w1 = 0 (buffers hold no data yet)
     const int it = c.iters;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x) {
-        T wn = ycur[off + e] * iv;
-        if (it >= 2) wn -= de * w2[off + e];
-        if (it >= 3) wn -= oe * w1[off + e];
-        wn *= ig;
-        w1[off + e] = wn;
-        x[off + e] = (it >= 2 ? x[off + e] : T(0)) + ph * wn;
+    const int64_t nq = n3 >> 2;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 4 * q;
+        const V4<T> yv = ld4(ys + e);
+        const V4<T> w2v = (it >= 2) ? ld4(w2 + off + e) : zero4<T>();
+        const V4<T> w1v = (it >= 3) ? ld4(w1 + off + e) : zero4<T>();
+        const V4<T> xv = (it >= 2) ? ld4(x + off + e) : zero4<T>();
+        V4<T> wn, xn;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wn.v[k] = (yv.v[k] * iv - oe * w1v.v[k] - de * w2v.v[k]) * ig;
+            xn.v[k] = xv.v[k] + ph * wn.v[k];
+        }
+        st4(w1 + off + e, wn);
+        st4(x + off + e, xn);
     }
 }
 
 template <typename T>
-cudaError_t launch_minres_D(int64_t N4, int S, const T* ycur, T* w1, const T* w2, T* x, const MinresCol* st_,
+cudaError_t launch_minres_D(int64_t n3, int S, const T* ycur, T* w1, const T* w2, T* x, const MinresCol* st_,
                             cudaStream_t st) {
-    dim3 grid(elem_blocks(N4), S);
-    k_minres_D<T><<<grid, 256, 0, st>>>(N4, ycur, w1, w2, x, st_);
+    dim3 grid(elem_blocks(n3), S);
+    k_minres_D<T><<<grid, 256, 0, st>>>(n3, ycur, w1, w2, x, st_);
     return cudaGetLastError();
 }
 

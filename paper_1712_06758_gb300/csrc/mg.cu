@@ -38,6 +38,7 @@ struct LevelCoef {
     T c;         // Schur weight
     T omega;
     T invD[7];   // 1 / (s (a + c k)) for k neighbours
+    T D[7];      // s (a + c k)
 };
 
 template <typename T>
@@ -49,7 +50,10 @@ static LevelCoef<T> level_coef(const MGPlan& p, int l) {
     q.a = (T)a;
     q.c = (T)p.c;
     q.omega = (T)p.omega;
-    for (int k = 0; k <= 6; ++k) q.invD[k] = (T)(1.0 / (s * (a + p.c * k)));
+    for (int k = 0; k <= 6; ++k) {
+        q.invD[k] = (T)(1.0 / (s * (a + p.c * k)));
+        q.D[k] = (T)(s * (a + p.c * k));
+    }
     return q;
 }
 
@@ -63,81 +67,122 @@ __device__ __forceinline__ float restrict_w(int a, int I, int nc) {
 }
 
 // ---------------------------------------------------------------------------
-// Down sweep at level l: b (fine, n_f^3) -> bc = R (b - A omega D^{-1} b)
-// Shared memory: b and x0 = omega D^{-1} b on the tile + halo 2 (zero outside
-// the box, so the Neumann Laplacian is k x0(f) - sum of the six neighbours),
-// the residual on the tile + halo 1.
+// Down sweep at level l: b (fine, n_f^3) -> bc = R (b - A omega D^{-1} b).
+// With x0 = omega D^{-1} b the residual is
+//     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g),
+// so one shared array of x0 on the tile + halo 2 (zero outside the box,
+// which makes the sum run over existing neighbours only) gives r on the
+// tile + halo 1, from which the 4^3-point restriction gathers.
+// Thread block (32, 8): x along threadIdx.x, y along threadIdx.y, loops in z.
 // ---------------------------------------------------------------------------
 constexpr int DBX = TFX + 4, DBY = TFY + 4, DBZ = TFZ + 4;
 constexpr int DRX = TFX + 2, DRY = TFY + 2, DRZ = TFZ + 2;
-constexpr int kDownSmem = 2 * DBX * DBY * DBZ + DRX * DRY * DRZ;
+constexpr int kDownSmem = DBX * DBY * DBZ + DRX * DRY * DRZ;
 constexpr int UXX = TFX + 2, UXY = TFY + 2, UXZ = TFZ + 2;
 constexpr int UCX = TCX + 2, UCY = TCY + 2, UCZ = TCZ + 2;
 constexpr int kUpSmem = 2 * UXX * UXY * UXZ + UCX * UCY * UCZ;
+
+__device__ __forceinline__ bool in_box(int x, int y, int z, int n) {
+    return (unsigned)x < (unsigned)n && (unsigned)y < (unsigned)n && (unsigned)z < (unsigned)n;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_coef(const LevelCoef<T>& q, T* s_invD, T* s_D) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (tid < 7) {
+        s_invD[tid] = q.invD[tid];
+        s_D[tid] = q.D[tid];
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q, const T* __restrict__ b,
                                                           int64_t b_stride, T* __restrict__ bc, int64_t bc_stride,
                                                           const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sb = reinterpret_cast<T*>(smem_raw);
-    T* sx = sb + DBX * DBY * DBZ;
+    __shared__ T s_invD[8], s_D[8];
+    T* sx = reinterpret_cast<T*>(smem_raw);
     T* sr = sx + DBX * DBY * DBZ;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
+    load_coef(q, s_invD, s_D);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
     const int nc = nf >> 1;
     const int ntx = nc / TCX, nty = nc / TCY, ntz = nc / TCZ;
     const int ntiles = ntx * nty * ntz;
+    const int64_t plane = (int64_t)nf * nf;
     const T* bs = b + (int64_t)col * b_stride;
     T* bcs = bc + (int64_t)col * bc_stride;
+    const T rc = (T(1) / q.omega - T(1));
+    const T sc = q.s * q.c;
+    const T om = q.omega;
+    __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-        const int cx0 = tx * TCX, cy0 = ty * TCY, cz0 = tz * TCZ;
+        const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
+        const int cx0 = tX * TCX, cy0 = tY * TCY, cz0 = tZ * TCZ;
         const int fx0 = 2 * cx0, fy0 = 2 * cy0, fz0 = 2 * cz0;
-        for (int t = threadIdx.x; t < DBX * DBY * DBZ; t += blockDim.x) {
-            const int lx = t % DBX, ly = (t / DBX) % DBY, lz = t / (DBX * DBY);
-            const int gx = fx0 - 2 + lx, gy = fy0 - 2 + ly, gz = fz0 - 2 + lz;
-            T v = T(0), xv = T(0);
-            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf) {
-                v = bs[gx + (int64_t)nf * (gy + (int64_t)nf * gz)];
-                xv = q.omega * v * q.invD[nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf)];
+        // x0 = omega D^{-1} b on tile + halo 2; each thread owns (x, y) columns
+        for (int cidx = tid; cidx < DBX * DBY; cidx += kTileThreads) {
+            const int lx = cidx % DBX, ly = cidx / DBX;
+            const int gx = fx0 - 2 + lx, gy = fy0 - 2 + ly;
+            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
+            const int kxy = inxy ? nb_count1(gx, nf) + nb_count1(gy, nf) : 0;
+            const T* src = bs + (gx + (int64_t)nf * gy) + plane * (fz0 - 2);
+            T v[DBZ];
+#pragma unroll
+            for (int lz = 0; lz < DBZ; ++lz) {
+                const int gz = fz0 - 2 + lz;
+                v[lz] = (inxy && (unsigned)gz < (unsigned)nf) ? src[plane * lz] : T(0);
             }
-            sb[t] = v;
-            sx[t] = xv;
+#pragma unroll
+            for (int lz = 0; lz < DBZ; ++lz) {
+                const int gz = fz0 - 2 + lz;
+                const int kz = ((unsigned)gz < (unsigned)nf) ? nb_count1(gz, nf) : 0;
+                sx[lx + DBX * (ly + DBY * lz)] = om * v[lz] * s_invD[kxy + kz];
+            }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < DRX * DRY * DRZ; t += blockDim.x) {
-            const int lx = t % DRX, ly = (t / DRX) % DRY, lz = t / (DRX * DRY);
-            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly, gz = fz0 - 1 + lz;
-            T r = T(0);
-            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf) {
-                const int bi = (lx + 1) + DBX * ((ly + 1) + DBY * (lz + 1));
-                const int k0 = nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf);
-                const T x0 = sx[bi];
-                const T nbs = (sx[bi - 1] + sx[bi + 1]) + (sx[bi - DBX] + sx[bi + DBX]) +
-                              (sx[bi - DBX * DBY] + sx[bi + DBX * DBY]);
-                r = sb[bi] - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs));
+        // residual on tile + halo 1
+        for (int cidx = tid; cidx < DRX * DRY; cidx += kTileThreads) {
+            const int lx = cidx % DRX, ly = cidx / DRX;
+            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
+            const int kxy = inxy ? nb_count1(gx, nf) + nb_count1(gy, nf) : 0;
+#pragma unroll
+            for (int lz = 0; lz < DRZ; ++lz) {
+                const int gz = fz0 - 1 + lz;
+                T r = T(0);
+                if (inxy && (unsigned)gz < (unsigned)nf) {
+                    const int bi = (lx + 1) + DBX * ((ly + 1) + DBY * (lz + 1));
+                    const T nbs = (sx[bi - 1] + sx[bi + 1]) + (sx[bi - DBX] + sx[bi + DBX]) +
+                                  (sx[bi - DBX * DBY] + sx[bi + DBX * DBY]);
+                    r = rc * s_D[kxy + nb_count1(gz, nf)] * sx[bi] + sc * nbs;
+                }
+                sr[lx + DRX * (ly + DRY * lz)] = r;
             }
-            sr[t] = r;
         }
         __syncthreads();
         {
-            const int t = threadIdx.x;
-            const int li = t % TCX, lj = (t / TCX) % TCY, lk = t / (TCX * TCY);
+            const int li = tid & (TCX - 1), lj = (tid / TCX) & (TCY - 1), lk = tid / (TCX * TCY);
             const int I = cx0 + li, J = cy0 + lj, K = cz0 + lk;
+            T wx[4], wy[4], wz[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                wx[a] = (T)restrict_w(a, I, nc);
+                wy[a] = (T)restrict_w(a, J, nc);
+                wz[a] = (T)restrict_w(a, K, nc);
+            }
             T acc = T(0);
 #pragma unroll
             for (int c3 = 0; c3 < 4; ++c3) {
-                const T wz = (T)restrict_w(c3, K, nc);
+                T accy = T(0);
 #pragma unroll
                 for (int b3 = 0; b3 < 4; ++b3) {
-                    const T wy = (T)restrict_w(b3, J, nc) * wz;
-#pragma unroll
-                    for (int a3 = 0; a3 < 4; ++a3) {
-                        const T w = (T)restrict_w(a3, I, nc) * wy;
-                        acc += w * sr[(2 * li + a3) + DRX * ((2 * lj + b3) + DRY * (2 * lk + c3))];
-                    }
+                    const T* row = sr + (2 * li) + DRX * ((2 * lj + b3) + DRY * (2 * lk + c3));
+                    const T accx = wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3];
+                    accy += wy[b3] * accx;
                 }
+                acc += wz[c3] * accy;
             }
             bcs[I + (int64_t)nc * (J + (int64_t)nc * K)] = acc;
         }
@@ -147,7 +192,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q
 
 // ---------------------------------------------------------------------------
 // Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x)
-// optional partial sums of b.y (the MINRES beta^2 contribution)
+// optional partial sums of b.y (the MINRES beta^2 contribution).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, const T* __restrict__ b,
@@ -157,84 +202,110 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, 
                                                         const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
+    __shared__ T s_invD[8], s_D[8];
     T* sb = reinterpret_cast<T*>(smem_raw);
     T* sx = sb + UXX * UXY * UXZ;
     T* sc = sx + UXX * UXY * UXZ;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
+    load_coef(q, s_invD, s_D);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + 32 * ty;
     const int nc = nf >> 1;
     const int ntx = nf / TFX, nty = nf / TFY, ntz = nf / TFZ;
     const int ntiles = ntx * nty * ntz;
+    const int64_t plane = (int64_t)nf * nf, cplane = (int64_t)nc * nc;
     const T* bs = b + (int64_t)col * b_stride;
     const T* es = ec + (int64_t)col * ec_stride;
     T* ys = y + (int64_t)col * y_stride;
+    const T om = q.omega;
     double dacc = 0.0;
+    __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-        const int fx0 = tx * TFX, fy0 = ty * TFY, fz0 = tz * TFZ;
+        const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
+        const int fx0 = tX * TFX, fy0 = tY * TFY, fz0 = tZ * TFZ;
         const int cx0 = fx0 / 2, cy0 = fy0 / 2, cz0 = fz0 / 2;
-        for (int t = threadIdx.x; t < UCX * UCY * UCZ; t += blockDim.x) {
-            const int lx = t % UCX, ly = (t / UCX) % UCY, lz = t / (UCX * UCY);
-            const int gx = min(max(cx0 - 1 + lx, 0), nc - 1);
-            const int gy = min(max(cy0 - 1 + ly, 0), nc - 1);
-            const int gz = min(max(cz0 - 1 + lz, 0), nc - 1);
-            sc[t] = es[gx + (int64_t)nc * (gy + (int64_t)nc * gz)];
+        // coarse correction on the coarse tile + halo 1 (indices clamped: wall reflection)
+        if (tid < UCX * UCY) {
+            const int lx = tid % UCX, ly = tid / UCX;
+            const int gx = min(max(cx0 - 1 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
+            const T* src = es + gx + (int64_t)nc * gy;
+            T v[UCZ];
+#pragma unroll
+            for (int lz = 0; lz < UCZ; ++lz) v[lz] = src[cplane * min(max(cz0 - 1 + lz, 0), nc - 1)];
+#pragma unroll
+            for (int lz = 0; lz < UCZ; ++lz) sc[lx + UCX * (ly + UCY * lz)] = v[lz];
         }
-        for (int t = threadIdx.x; t < UXX * UXY * UXZ; t += blockDim.x) {
-            const int lx = t % UXX, ly = (t / UXX) % UXY, lz = t / (UXX * UXY);
-            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly, gz = fz0 - 1 + lz;
-            T v = T(0);
-            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf)
-                v = bs[gx + (int64_t)nf * (gy + (int64_t)nf * gz)];
-            sb[t] = v;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < UXX * UXY * UXZ; t += blockDim.x) {
-            const int lx = t % UXX, ly = (t / UXX) % UXY, lz = t / (UXX * UXY);
-            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly, gz = fz0 - 1 + lz;
-            T v = T(0);
-            if (gx >= 0 && gx < nf && gy >= 0 && gy < nf && gz >= 0 && gz < nf) {
-                const int k0 = nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf);
-                // prolongation: 3/4 from the parent, 1/4 from the parent's neighbour toward f
-                const int Ix = gx >> 1, Iy = gy >> 1, Iz = gz >> 1;
-                const int Ox = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1);
-                const int Oy = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1);
-                const int Oz = min(max((gz & 1) ? Iz + 1 : Iz - 1, 0), nc - 1);
-                const int px[2] = {Ix - (cx0 - 1), Ox - (cx0 - 1)};
-                const int py[2] = {Iy - (cy0 - 1), Oy - (cy0 - 1)};
-                const int pz[2] = {Iz - (cz0 - 1), Oz - (cz0 - 1)};
-                const T w[2] = {T(0.75), T(0.25)};
-                T pe = T(0);
+        // b on the tile + halo 1
+        for (int cidx = tid; cidx < UXX * UXY; cidx += kTileThreads) {
+            const int lx = cidx % UXX, ly = cidx / UXX;
+            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
+            const T* src = bs + (gx + (int64_t)nf * gy) + plane * (fz0 - 1);
+            T v[UXZ];
 #pragma unroll
-                for (int c3 = 0; c3 < 2; ++c3)
-#pragma unroll
-                    for (int b3 = 0; b3 < 2; ++b3)
-#pragma unroll
-                        for (int a3 = 0; a3 < 2; ++a3)
-                            pe += w[a3] * w[b3] * w[c3] * sc[px[a3] + UCX * (py[b3] + UCY * pz[c3])];
-                v = q.omega * sb[t] * q.invD[k0] + pe;
+            for (int lz = 0; lz < UXZ; ++lz) {
+                const int gz = fz0 - 1 + lz;
+                v[lz] = (inxy && (unsigned)gz < (unsigned)nf) ? src[plane * lz] : T(0);
             }
-            sx[t] = v;
+#pragma unroll
+            for (int lz = 0; lz < UXZ; ++lz) sb[lx + UXX * (ly + UXY * lz)] = v[lz];
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < TFX * TFY * TFZ; t += blockDim.x) {
-            const int ox = t % TFX, oy = (t / TFX) % TFY, oz = t / (TFX * TFY);
-            const int gx = fx0 + ox, gy = fy0 + oy, gz = fz0 + oz;
-            const int xi = (ox + 1) + UXX * ((oy + 1) + UXY * (oz + 1));
-            const T x0 = sx[xi];
-            const T nbs = (sx[xi - 1] + sx[xi + 1]) + (sx[xi - UXX] + sx[xi + UXX]) +
-                          (sx[xi - UXX * UXY] + sx[xi + UXX * UXY]);
-            const int k0 = nb_count1(gx, nf) + nb_count1(gy, nf) + nb_count1(gz, nf);
-            const T bv = sb[xi];
-            const T yv = x0 + q.omega * q.invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
-            ys[gx + (int64_t)nf * (gy + (int64_t)nf * gz)] = yv;
-            dacc += (double)(bv * yv);
+        // x = omega D^{-1} b + P ec on the tile + halo 1 (zero outside the box)
+        const T w0 = T(0.75), w1 = T(0.25);
+        for (int cidx = tid; cidx < UXX * UXY; cidx += kTileThreads) {
+            const int lx = cidx % UXX, ly = cidx / UXX;
+            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
+            const int kxy = inxy ? nb_count1(gx, nf) + nb_count1(gy, nf) : 0;
+            const int Ix = gx >> 1, Iy = gy >> 1;
+            const int px0 = Ix - (cx0 - 1), px1 = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1) - (cx0 - 1);
+            const int py0 = Iy - (cy0 - 1), py1 = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1) - (cy0 - 1);
+#pragma unroll
+            for (int lz = 0; lz < UXZ; ++lz) {
+                const int gz = fz0 - 1 + lz;
+                const int xi = lx + UXX * (ly + UXY * lz);
+                T v = T(0);
+                if (inxy && (unsigned)gz < (unsigned)nf) {
+                    const int Iz = gz >> 1;
+                    const int pz0 = Iz - (cz0 - 1), pz1 = min(max((gz & 1) ? Iz + 1 : Iz - 1, 0), nc - 1) - (cz0 - 1);
+                    const T* r00 = sc + UCX * (py0 + UCY * pz0);
+                    const T* r10 = sc + UCX * (py1 + UCY * pz0);
+                    const T* r01 = sc + UCX * (py0 + UCY * pz1);
+                    const T* r11 = sc + UCX * (py1 + UCY * pz1);
+                    const T a00 = w0 * r00[px0] + w1 * r00[px1], a10 = w0 * r10[px0] + w1 * r10[px1];
+                    const T a01 = w0 * r01[px0] + w1 * r01[px1], a11 = w0 * r11[px0] + w1 * r11[px1];
+                    const T pe = w0 * (w0 * a00 + w1 * a10) + w1 * (w0 * a01 + w1 * a11);
+                    v = om * sb[xi] * s_invD[kxy + nb_count1(gz, nf)] + pe;
+                }
+                sx[xi] = v;
+            }
+        }
+        __syncthreads();
+        {
+            const int gx = fx0 + tx, gy = fy0 + ty;
+            const int kxy = nb_count1(gx, nf) + nb_count1(gy, nf);
+            T* dst = ys + gx + (int64_t)nf * gy + plane * fz0;
+#pragma unroll
+            for (int oz = 0; oz < TFZ; ++oz) {
+                const int gz = fz0 + oz;
+                const int xi = (tx + 1) + UXX * ((ty + 1) + UXY * (oz + 1));
+                const T x0 = sx[xi];
+                const T nbs = (sx[xi - 1] + sx[xi + 1]) + (sx[xi - UXX] + sx[xi + UXX]) +
+                              (sx[xi - UXX * UXY] + sx[xi + UXX * UXY]);
+                const int k0 = kxy + nb_count1(gz, nf);
+                const T bv = sb[xi];
+                const T yv = x0 + om * s_invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
+                dst[plane * oz] = yv;
+                dacc += (double)(bv * yv);
+            }
         }
         __syncthreads();
     }
     if (dot_part) {
         const double tsum = block_sum<kTileThreads>(dacc, red);
-        if (threadIdx.x == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
+        if (tid == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
     }
 }
 
@@ -483,7 +554,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
         prof_begin(PK_MG_DOWN, st);
-        k_mg_down<T><<<grid, kTileThreads, kDownSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
+        k_mg_down<T><<<grid, dim3(32, 8), kDownSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
                                                     (int64_t)nc * nc * nc, active, act_stride);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
         in = out;
@@ -508,7 +579,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
         const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
         prof_begin(PK_MG_UP, st);
-        k_mg_up<T><<<grid, kTileThreads, kUpSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
+        k_mg_up<T><<<grid, dim3(32, 8), kUpSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
                                                   static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
                                                   yls, (l == 0) ? dot_part : nullptr, active, act_stride);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);

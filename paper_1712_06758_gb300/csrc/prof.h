@@ -24,6 +24,7 @@ enum ProfClass {
     PK_ADD_CORR,
     PK_TRANSPOSE,
     PK_PROJECT,
+    PK_FLUX,
     PK_OTHER,  // small bookkeeping launches (reductions, flags, init)
     PK_NCLASS
 };

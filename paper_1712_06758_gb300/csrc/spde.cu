@@ -21,7 +21,7 @@ namespace spde {
 thread_local Profiler* t_prof = nullptr;
 const char* const kProfNames[PK_NCLASS] = {"noise",   "sumsq",  "residual64", "minres_A",  "alpha",
                                            "minres_B", "mg_down", "mg_coarse",  "mg_up",     "givens",
-                                           "minres_D", "add_correction", "transpose_theta", "project_exp", "other"};
+                                           "minres_D", "add_correction", "transpose_theta", "project_exp", "flux_from_theta", "other"};
 }  // namespace spde
 
 namespace {
@@ -85,7 +85,8 @@ struct Workspace {
     int n = 0, S = 0, inner64 = -1;
     double* x64 = nullptr;   // [S][4n^3] refinement iterate (scaled unknowns)
     double* F = nullptr;     // [S][n^3] cell block of the scaled RHS
-    void* vec[7] = {};       // inner vectors: d, wA, wB, r1, r2, yA, yB
+    void* vec[7] = {};       // inner vectors: d, wA, wB ([S][n^3], cell block only), r1, r2, yA, yB
+    double* tri = nullptr;   // Thomas factors of the flux mass matrix T (2n - 2)
     void* mg = nullptr;      // V-cycle scratch
     double* partA = nullptr; // partial sums [S][kMaxPartials]
     double* partB = nullptr;
@@ -116,6 +117,7 @@ struct Workspace {
         dev_free(st);
         dev_free(nact);
         dev_free(thetaT);
+        dev_free(tri);
         if (h_nact) cudaFreeHost(h_nact);
         if (h_col) cudaFreeHost(h_col);
         if (h_st) cudaFreeHost(h_st);
@@ -130,7 +132,7 @@ struct Workspace {
 int64_t workspace_bytes(int n, int S, bool inner64) {
     const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
     const int64_t w = inner64 ? 8 : 4;
-    int64_t b = (int64_t)S * (8 * N4 + 8 * n3 + 7 * w * N4 + 4 * n3);
+    int64_t b = (int64_t)S * (8 * N4 + 8 * n3 + 4 * w * N4 + 3 * w * n3 + 4 * n3);
     b += (int64_t)(inner64 ? mg_scratch_elems<double>(n, S) * 8 : mg_scratch_elems<float>(n, S) * 4);
     b += 4LL * S * kMaxPartials * 8 + 2LL * S * 8 + (int64_t)S * sizeof(MinresCol);
     return b;
@@ -187,8 +189,9 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
     const size_t w = inner64 ? 8 : 4;
     STATUS_TRY(dev_alloc(&ws.x64, (size_t)S * N4));
     STATUS_TRY(dev_alloc(&ws.F, (size_t)S * n3));
-    for (auto& v : ws.vec) {
-        cudaError_t e = cudaMalloc(&v, (size_t)S * N4 * w);
+    for (int iv = 0; iv < 7; ++iv) {
+        void*& v = ws.vec[iv];
+        cudaError_t e = cudaMalloc(&v, (size_t)S * (iv < 3 ? n3 : N4) * w);
         if (e != cudaSuccess) {
             v = nullptr;
             cudaGetLastError();
@@ -214,6 +217,23 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
     STATUS_TRY(dev_alloc(&ws.st, (size_t)S));
     STATUS_TRY(dev_alloc(&ws.nact, 1));
     STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
+    {
+        // Thomas factors of tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of a line
+        std::vector<double> tri(2 * (size_t)n - 2);
+        double cprev = 0.0;
+        for (int f = 0; f < n - 1; ++f) {
+            const double piv = 2.0 / 3.0 - (f ? cprev / 6.0 : 0.0);
+            tri[f] = (1.0 / 6.0) / piv;
+            tri[(n - 1) + f] = 1.0 / piv;
+            cprev = tri[f];
+        }
+        STATUS_TRY(dev_alloc(&ws.tri, tri.size()));
+        if (cudaMemcpy(ws.tri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            ws.release();
+            return fail(SPDE_ECUDA, "upload of line-solve factors failed");
+        }
+    }
     if (cudaMallocHost(&ws.h_nact, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ws.h_col, 2 * S * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&ws.h_st, S * sizeof(MinresCol)) != cudaSuccess) {
@@ -284,8 +304,8 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, (q == chunk - 1) ? ws.nact : nullptr, st));
             prof_end(st, cols * (nB + nC) * 8.0);
             prof_begin(PK_MINRES_D, st);
-            CUDA_TRY(launch_minres_D<T>(N4, S, ycur, w1, w2, d, ws.st, st));
-            prof_end(st, cols * (itn >= 3 ? 24.0 : (itn == 2 ? 20.0 : 12.0)) * n3d * w);
+            CUDA_TRY(launch_minres_D<T>(n3, S, ycur, w1, w2, d, ws.st, st));
+            prof_end(st, cols * (itn >= 3 ? 6.0 : (itn == 2 ? 5.0 : 3.0)) * n3d * w);
             std::swap(r1, r2);
             std::swap(ycur, ynext);
             std::swap(w1, w2);
@@ -326,6 +346,12 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         // r = [0; F] - A x (FP64) -> r2 (inner type); ||r||^2
         float* r32 = std::is_same<T, float>::value ? reinterpret_cast<float*>(r2) : nullptr;
         double* r64 = std::is_same<T, double>::value ? reinterpret_cast<double*>(r2) : nullptr;
+        if (outer > 0) {
+            // flux rows exact for the current cell field: u = -T^{-1} D1^T theta
+            prof_begin(PK_FLUX, st);
+            CUDA_TRY(launch_flux_from_theta(n, S, ws.x64, N4, ws.tri, st));
+            prof_end(st, (double)S * 96.0 * (double)n3);
+        }
         prof_begin(PK_RESIDUAL, st);
         nb = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st);
         prof_end(st, (double)S * (40.0 + 4.0 * sizeof(T)) * (double)n3);
@@ -357,8 +383,8 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st));
         inner_total += its;
         prof_begin(PK_ADD_CORR, st);
-        CUDA_TRY(launch_add_correction_st<T>(N4, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.st, st));
-        prof_end(st, (double)nact * (64.0 + 4.0 * sizeof(T)) * (double)n3);
+        CUDA_TRY(launch_add_theta<T>(n3, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.st, st));
+        prof_end(st, (double)nact * (16.0 + sizeof(T)) * (double)n3);
         ++outer;
     }
     *maxrel = worst;
@@ -503,7 +529,7 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
 spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]) {
     if (!ctx || !lo || !hi) return fail(SPDE_EINVAL, "null argument");
     if (level < 0 || level >= 16) return fail(SPDE_EINVAL, "level must lie in [0, 16)");
-    if (!is_pow2(n) || n < 2 || n > 1024) return fail(SPDE_EINVAL, "n must be a power of two in [2, 1024]");
+    if (!is_pow2(n) || n < 4 || n > 1024) return fail(SPDE_EINVAL, "n must be a power of two in [4, 1024]");
     const double ext = hi[0] - lo[0];
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a]))
@@ -732,7 +758,7 @@ spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uin
 }
 
 spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x, void* y, void* stream) {
-    if (n < 2 || nsamples < 0 || !(h > 0.0) || !std::isfinite(kappa) || kappa < 0.0)
+    if (!is_pow2(n) || n < 4 || n > 1024 || nsamples < 0 || !(h > 0.0) || !std::isfinite(kappa) || kappa < 0.0)
         return fail(SPDE_EINVAL, "bad size or parameters");
     if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
     if (nsamples == 0) return SPDE_OK;
@@ -760,7 +786,7 @@ PrecondScratch g_pc;
 
 spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, const spde_opts* opts, const void* r,
                          void* z, void* stream) {
-    if (!is_pow2(n) || n < 2 || n > 1024 || nsamples < 0 || !(h > 0.0) || !(kappa > 0.0) || !std::isfinite(kappa))
+    if (!is_pow2(n) || n < 4 || n > 1024 || nsamples < 0 || !(h > 0.0) || !(kappa > 0.0) || !std::isfinite(kappa))
         return fail(SPDE_EINVAL, "bad size or parameters");
     if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
     if (prec != SPDE_PREC_FP64 && prec != SPDE_PREC_MIXED) return fail(SPDE_EINVAL, "bad precision");

@@ -20,24 +20,26 @@ static inline int stencil_blocks(int64_t n3) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply(int n, T kh2, const T* __restrict__ x, T* __restrict__ y) {
-    const int64_t n3 = (int64_t)n * n * n;
+    const int logn = ilog2(n);
+    const int n3 = 1 << (3 * logn);
     const int64_t off = (int64_t)blockIdx.y * 4 * n3;
     const T* xs = x + off;
     T* ys = y + off;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((int64_t)n * n));
-        const Cell4<T> r = apply_cell<T, T>(xs, n3, n, i, j, k, c, kh2);
-        ys[c] = r.ux;
-        ys[n3 + c] = r.uy;
-        ys[2 * n3 + c] = r.uz;
-        ys[3 * n3 + c] = r.th;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (n3 >> 2); q += gridDim.x * blockDim.x) {
+        const QuadPos p = quad_pos(q, logn);
+        V4<T> a, b, c, d;
+        apply_quad<T, T>(xs, n, logn, p, kh2, a.v, b.v, c.v, d.v);
+        st4(ys + p.c, a);
+        st4(ys + n3 + p.c, b);
+        st4(ys + 2 * n3 + p.c, c);
+        st4(ys + 3 * n3 + p.c, d);
     }
 }
 
 template <typename T>
 cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_t st) {
     const int64_t n3 = (int64_t)n * n * n;
-    dim3 grid(stencil_blocks(n3), S);
+    dim3 grid(stencil_blocks(n3 / 4), S);
     k_apply<T><<<grid, 256, 0, st>>>(n, (T)kh2, x, y);
     return cudaGetLastError();
 }
@@ -52,29 +54,46 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
     __shared__ double red[8];
     const int s = blockIdx.y;
     if (active && !active[s]) return;
-    const int64_t n3 = (int64_t)n * n * n;
+    const int logn = ilog2(n);
+    const int n3 = 1 << (3 * logn);
     const int64_t off = (int64_t)s * 4 * n3;
     const double* xs = x + off;
     const double* Fs = F + (int64_t)s * F_stride;
     double acc = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n3; c += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % n), j = (int)((c / n) % n), k = (int)(c / ((int64_t)n * n));
-        const Cell4<double> a = apply_cell<double, double>(xs, n3, n, i, j, k, c, kh2);
-        const double ru = -a.ux, rv = -a.uy, rw = -a.uz, rt = Fs[c] - a.th;
-        acc += ru * ru + rv * rv + rw * rw + rt * rt;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (n3 >> 2); q += gridDim.x * blockDim.x) {
+        const QuadPos p = quad_pos(q, logn);
+        V4<double> a, b, c, d;
+        apply_quad<double, double>(xs, n, logn, p, kh2, a.v, b.v, c.v, d.v);
+        const V4<double> f = ld4(Fs + p.c);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            a.v[e] = -a.v[e];
+            b.v[e] = -b.v[e];
+            c.v[e] = -c.v[e];
+            d.v[e] = f.v[e] - d.v[e];
+            acc += a.v[e] * a.v[e] + b.v[e] * b.v[e] + c.v[e] * c.v[e] + d.v[e] * d.v[e];
+        }
         if (r32) {
             float* o = r32 + off;
-            o[c] = (float)ru;
-            o[n3 + c] = (float)rv;
-            o[2 * n3 + c] = (float)rw;
-            o[3 * n3 + c] = (float)rt;
+            V4<float> fa, fb, fc, fd;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                fa.v[e] = (float)a.v[e];
+                fb.v[e] = (float)b.v[e];
+                fc.v[e] = (float)c.v[e];
+                fd.v[e] = (float)d.v[e];
+            }
+            st4(o + p.c, fa);
+            st4(o + n3 + p.c, fb);
+            st4(o + 2 * n3 + p.c, fc);
+            st4(o + 3 * n3 + p.c, fd);
         }
         if (r64) {
             double* o = r64 + off;
-            o[c] = ru;
-            o[n3 + c] = rv;
-            o[2 * n3 + c] = rw;
-            o[3 * n3 + c] = rt;
+            st4(o + p.c, a);
+            st4(o + n3 + p.c, b);
+            st4(o + 2 * n3 + p.c, c);
+            st4(o + 3 * n3 + p.c, d);
         }
     }
     const double t = block_sum<256>(acc, red);
@@ -84,7 +103,7 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
 int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x, float* r32,
                       double* r64, double* part, const int* active, cudaStream_t st) {
     const int64_t n3 = (int64_t)n * n * n;
-    const int nb = stencil_blocks(n3);
+    const int nb = stencil_blocks(n3 / 4);
     dim3 grid(nb, S);
     k_residual64<<<grid, 256, 0, st>>>(n, kh2, F, F_stride, x, r32, r64, part, active);
     return nb;
@@ -142,5 +161,89 @@ cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cuda
     k_reduce<<<S, 256, 0, st>>>(part, nblk, out);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Exact flux of a cell field: u = -T^{-1} D1^T theta, i.e. the first block row
+// of the scaled system (T u + D1^T theta = 0) solved line by line.  T is
+// tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of every line; the wall
+// face (index n-1 in the line) stays 0.  Thomas elimination with the
+// line-independent factors tri[0..n-2] = c'_f (super-diagonal after
+// elimination) and tri[n-1 .. 2n-3] = 1 / pivot_f, computed on the host.
+// One thread per line; consecutive threads take neighbouring lines.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_flux_lines(int n, int logn, int axis, const double* __restrict__ x,
+                                                    double* __restrict__ xu, int64_t col_stride,
+                                                    const double* __restrict__ tri) {
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= (1 << (2 * logn))) return;
+    const int64_t off = (int64_t)blockIdx.y * col_stride;
+    const int n3 = 1 << (3 * logn);
+    const double* th = x + off + 3 * (int64_t)n3;
+    double* u = xu + off + (int64_t)axis * n3;
+    int base, stride;
+    if (axis == 0) {  // lines along x, indexed by (j, k)
+        base = L << logn;
+        stride = 1;
+    } else if (axis == 1) {  // along y, indexed by (i, k)
+        base = (L & (n - 1)) + ((L >> logn) << (2 * logn));
+        stride = n;
+    } else {  // along z, indexed by (i, j)
+        base = L;
+        stride = n << logn;
+    }
+    const double* cp = tri;
+    const double* inv = tri + (n - 1);
+    const double a = 1.0 / 6.0;
+    // forward elimination of T u = -(theta_f - theta_{f+1}) = theta_{f+1} - theta_f
+    double prev = 0.0, tcur = th[base];
+    for (int f = 0; f < n - 1; ++f) {
+        const double tnext = th[base + (f + 1) * stride];
+        const double dp = ((tnext - tcur) - a * prev) * inv[f];
+        u[base + f * stride] = dp;
+        prev = dp;
+        tcur = tnext;
+    }
+    u[base + (n - 1) * stride] = 0.0;
+    // back substitution
+    double xn = prev;
+    for (int f = n - 3; f >= 0; --f) {
+        const double xf = u[base + f * stride] - cp[f] * xn;
+        u[base + f * stride] = xf;
+        xn = xf;
+    }
+}
+
+cudaError_t launch_flux_from_theta(int n, int S, double* x, int64_t col_stride, const double* tri, cudaStream_t st) {
+    const int logn = 31 - __builtin_clz(n);
+    const int lines = n * n;
+    dim3 grid((lines + 255) / 256, S);
+    for (int axis = 0; axis < 3; ++axis) {
+        k_flux_lines<<<grid, 256, 0, st>>>(n, logn, axis, x, x, col_stride, tri);
+    }
+    return cudaGetLastError();
+}
+
+// x_theta += d (d holds only the cell block, n^3 per column)
+template <typename T>
+__global__ void __launch_bounds__(256) k_add_theta(int64_t n3, double* __restrict__ x, const T* __restrict__ d,
+                                                   const MinresCol* __restrict__ st) {
+    const int s = blockIdx.y;
+    if (st[s].iters == 0) return;
+    double* xs = x + (int64_t)s * 4 * n3 + 3 * n3;
+    const T* ds = d + (int64_t)s * n3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
+        xs[e] += (double)ds[e];
+}
+
+template <typename T>
+cudaError_t launch_add_theta(int64_t n3, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st) {
+    int64_t b = (n3 + 1023) / 1024;
+    if (b > 2048) b = 2048;
+    dim3 grid((unsigned)(b < 1 ? 1 : b), S);
+    k_add_theta<T><<<grid, 256, 0, st>>>(n3, x, d, st_);
+    return cudaGetLastError();
+}
+template cudaError_t launch_add_theta<float>(int64_t, int, double*, const float*, const MinresCol*, cudaStream_t);
+template cudaError_t launch_add_theta<double>(int64_t, int, double*, const double*, const MinresCol*, cudaStream_t);
 
 }  // namespace spde

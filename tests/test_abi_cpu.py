@@ -44,6 +44,7 @@ def test_opts_defaults_and_argument_errors(built):
     lib = pkg.lib()
     assert lib.spde_noise(-1, 1, 1, 0, 1.0, None, None) == pkg.SPDE_EINVAL
     assert lib.spde_apply(1, 0.1, 1.0, 1, 0, None, None, None) == pkg.SPDE_EINVAL
+    assert lib.spde_apply(2, 0.1, 1.0, 1, 0, None, None, None) == pkg.SPDE_EINVAL
     assert lib.spde_precond(12, 0.1, 1.0, 1, 0, None, None, None, None) == pkg.SPDE_EINVAL
     assert lib.spde_sample(None, 0, 1, 1.0, 1.0, 1, 0, 0, None, None) == pkg.SPDE_EINVAL
     assert "context" in pkg.spde_last_error()
