@@ -215,6 +215,28 @@ spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, co
 spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec,
                          const spde_opts* opts, const void* r, void* z, void* stream);
 
+/* spde_precond for callers that cannot allocate device memory: the same
+ * preconditioner on the same arguments, with the V-cycle's coarse-level
+ * scratch taken from a 16 MiB array compiled into the library instead of
+ * cudaMalloc.  (The paper has no counterpart; this serves callers whose
+ * device memory belongs to another allocator, such as a framework's caching
+ * pool, or whose loop cannot afford the device synchronisation cudaMalloc
+ * and cudaFree imply.)  No call allocates or frees device memory.
+ *   - Every GPU that loads the library holds the 16 MiB until the process
+ *     exits.
+ *   - Requests needing more scratch than that are rejected with
+ *     SPDE_EINVAL before any work (spde_last_error gives the need): the
+ *     need is 2 sum_{l=1..L} (n/2^l)^3 elements per sample over the levels
+ *     with n/2^(l-1) >= 32, e.g. about 2.4 MB per sample at n = 128 in FP32.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the array: calls that overlap on the GPU race.  No
+ *     scratch element needs clearing between calls (each call writes every
+ *     element it reads). */
+spde_status spde_precond_noalloc(int n, double h, double kappa, int nsamples, int prec,
+                                 const spde_opts* opts, const void* r, void* z, void* stream);
+
 /* Solve the scaled system (D A D) X = [0; rhs] for nsamples right-hand sides
  * with the context's precision path (opts given at spde_grid_create).
  *   rhs  device double [nsamples][n^3] (cell block of the scaled RHS)

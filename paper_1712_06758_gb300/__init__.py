@@ -63,6 +63,8 @@ _SIGS = {
     "spde_apply": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "spde_precond": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                      ctypes.POINTER(spde_opts), _P, _P, _P],
+    "spde_precond_noalloc": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                             ctypes.POINTER(spde_opts), _P, _P, _P],
     "spde_solve": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "spde_project": [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P],
 }
@@ -220,6 +222,16 @@ def spde_apply(n, h, kappa, nsamples, prec, x, y, stream=None):
 def spde_precond(n, h, kappa, nsamples, prec, r, z, opts=None, stream=None):
     _check(lib().spde_precond(n, h, kappa, nsamples, prec, ctypes.byref(opts) if opts is not None else None,
                               _ptr(r), _ptr(z), _stream(stream)))
+
+
+def spde_precond_noalloc(n, h, kappa, nsamples, prec, r, z, opts=None, stream=None):
+    """spde_precond without any device allocation (static 16 MiB scratch).
+
+    For callers that may not allocate device memory: see include/spde.h.
+    """
+    _check(lib().spde_precond_noalloc(n, h, kappa, nsamples, prec,
+                                      ctypes.byref(opts) if opts is not None else None, _ptr(r), _ptr(z),
+                                      _stream(stream)))
 
 
 def spde_solve(ctx, level, nsamples, kappa, rhs, x, stream=None):

@@ -122,4 +122,7 @@ cudaError_t count_used_columns(int64_t nnz, const int32_t* col, int64_t ncell, i
 cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_stride, double scale,
                             int out64, void* out, cudaStream_t st);
 
+// set the message spde_last_error() returns on the calling thread
+void set_last_error(const char* msg);
+
 }  // namespace spde

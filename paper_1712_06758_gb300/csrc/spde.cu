@@ -19,6 +19,7 @@ using namespace spde;
 
 namespace spde {
 thread_local Profiler* t_prof = nullptr;
+void set_last_error(const char* msg);
 const char* const kProfNames[PK_NCLASS] = {"noise",   "sumsq",  "residual64", "minres_A",  "alpha",
                                            "minres_B", "mg_down", "mg_coarse",  "mg_up",     "givens",
                                            "minres_D", "add_correction", "transpose_theta", "project_exp", "flux_from_theta", "other"};
@@ -484,6 +485,10 @@ bool is_host_pointer(const void* p) {
 }
 
 }  // namespace
+
+namespace spde {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace spde
 
 // ============================================================================
 extern "C" {
