@@ -21,9 +21,12 @@ module states that V-cycle operator as the library defines it:
   the one-cell level is solved exactly.
 The resulting operator is symmetric positive definite for 0 < omega < 1.
 
-Parity unpinned against the paper (the paper uses BoomerAMG on a
-hybridised system; this V-cycle is this sampler's design), pinned instead
-against a dense matrix construction and its algebraic properties.
+The paper prints no value for this operator (it uses BoomerAMG on a
+hybridised system; this V-cycle is the sampler's own design), so it is
+pinned against an independent dense statement (Kronecker products of the
+1-D transfers, explicit matrices) and against its algebraic properties:
+symmetry, positive definiteness, convergence, exactness of the one-cell
+level, reproduction of linear functions by the prolongation.
 """
 import numpy as np
 
