@@ -75,12 +75,6 @@ __device__ __forceinline__ float restrict_w(int a, int I, int nc) {
 // tile + halo 1, from which the 4^3-point restriction gathers.
 // Thread block (32, 8): x along threadIdx.x, y along threadIdx.y, loops in z.
 // ---------------------------------------------------------------------------
-constexpr int DBX = TFX + 4, DBY = TFY + 4, DBZ = TFZ + 4;
-constexpr int DRX = TFX + 2, DRY = TFY + 2, DRZ = TFZ + 2;
-constexpr int kDownSmem = DBX * DBY * DBZ + DRX * DRY * DRZ;
-constexpr int UXX = TFX + 2, UXY = TFY + 2, UXZ = TFZ + 2;
-constexpr int UCX = TCX + 2, UCY = TCY + 2, UCZ = TCZ + 2;
-constexpr int kUpSmem = 2 * UXX * UXY * UXZ + UCX * UCY * UCZ;
 
 __device__ __forceinline__ bool in_box(int x, int y, int z, int n) {
     return (unsigned)x < (unsigned)n && (unsigned)y < (unsigned)n && (unsigned)z < (unsigned)n;
@@ -95,20 +89,70 @@ __device__ __forceinline__ void load_coef(const LevelCoef<T>& q, T* s_invD, T* s
     }
 }
 
+// Streaming sweeps: a CTA owns a fine (x, y) tile of SX x SY cells and marches
+// along z through SZ fine planes, keeping a few planes in shared-memory rings.
+// Fine planes are fetched as 16-byte vectors starting 4 cells left of the tile
+// (tiles and grids are multiples of 32, so a vector lies wholly inside or
+// wholly outside the box), one plane ahead into registers, so the loads of
+// plane f+2 are in flight while plane f is computed.
+constexpr int SX = 32, SY = 16, SZ = 32;
+constexpr int PW = SX + 8;               // plane row width in shared memory (x from fx0 - 4)
+constexpr int XH = SY + 4;               // x0 rows, halo 2 (down sweep)
+constexpr int RW = SX + 2, RH = SY + 2;  // residual plane, halo 1
+constexpr int BH = SY + 2;               // b / x rows, halo 1 (up sweep)
+constexpr int CW = SX / 2 + 2, CH = SY / 2 + 2;  // coarse plane with halo 1 (up sweep)
+constexpr int kDownSSmem = 3 * PW * XH + 4 * RW * RH;
+constexpr int kUpSSmem = 3 * PW * BH + 3 * PW * BH + 3 * CW * CH;
+constexpr int kQ = PW / 4;               // float4 per plane row
+
+__device__ __forceinline__ int ring3(int f) { return (f + 3) % 3; }  // f >= -3
+__device__ __forceinline__ int ring4(int f) { return (f + 4) & 3; }  // f >= -4
+
+template <typename T>
+struct PlaneRegs {
+    V4<T> v[2];
+};
+
+// fetch rows y0 .. y0+rows-1 of plane f (x from x0, PW wide) as vectors; zero outside the box
+template <typename T>
+__device__ __forceinline__ void fetch_plane(PlaneRegs<T>& r, const T* bs, int nf, int64_t plane, int f, int x0,
+                                            int y0, int rows, int tid) {
+    const bool zin = (unsigned)f < (unsigned)nf;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int idx = tid + u * kTileThreads;
+        r.v[u] = zero4<T>();
+        if (idx < kQ * rows && zin) {
+            const int ly = idx / kQ, q4 = idx - ly * kQ;
+            const int gx = x0 + 4 * q4, gy = y0 + ly;
+            if ((unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf)
+                r.v[u] = ld4(bs + gx + (int64_t)nf * gy + plane * f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Down sweep at level l: bc = R (b - A omega D^{-1} b).  With x0 = omega D^{-1} b
+//     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g)
+// (x0 = 0 outside the box, so the sum runs over existing neighbours).
+// Per fine plane: store the x0 plane f+1, fetch plane f+2, form r on plane
+// f, and after every second plane restrict one coarse plane from the four r
+// planes 2Z-1 .. 2Z+2.
+// ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q, const T* __restrict__ b,
                                                           int64_t b_stride, T* __restrict__ bc, int64_t bc_stride,
                                                           const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T s_invD[8], s_D[8];
-    T* sx = reinterpret_cast<T*>(smem_raw);
-    T* sr = sx + DBX * DBY * DBZ;
+    T* X = reinterpret_cast<T*>(smem_raw);  // 3 x0 planes, PW x XH
+    T* R = X + 3 * PW * XH;                  // 4 residual planes, RW x RH
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
     load_coef(q, s_invD, s_D);
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const int nc = nf >> 1;
-    const int ntx = nc / TCX, nty = nc / TCY, ntz = nc / TCZ;
+    const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
     const int ntiles = ntx * nty * ntz;
     const int64_t plane = (int64_t)nf * nf;
     const T* bs = b + (int64_t)col * b_stride;
@@ -119,80 +163,94 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
-        const int cx0 = tX * TCX, cy0 = tY * TCY, cz0 = tZ * TCZ;
-        const int fx0 = 2 * cx0, fy0 = 2 * cy0, fz0 = 2 * cz0;
-        // x0 = omega D^{-1} b on tile + halo 2; each thread owns (x, y) columns
-        for (int cidx = tid; cidx < DBX * DBY; cidx += kTileThreads) {
-            const int lx = cidx % DBX, ly = cidx / DBX;
-            const int gx = fx0 - 2 + lx, gy = fy0 - 2 + ly;
-            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
-            const int kxy = inxy ? nb_count1(gx, nf) + nb_count1(gy, nf) : 0;
-            const T* src = bs + (gx + (int64_t)nf * gy) + plane * (fz0 - 2);
-            T v[DBZ];
+        const int fx0 = tX * SX, fy0 = tY * SY, fz0 = tZ * SZ;
+        const int cx0 = fx0 >> 1, cy0 = fy0 >> 1;
+        // x0 = omega D^{-1} b into ring slot of plane f
+        auto commit = [&](const PlaneRegs<T>& r, int f) {
+            T* dst = X + ring3(f) * (PW * XH);
+            const bool zin = (unsigned)f < (unsigned)nf;
+            const int kz = zin ? nb_count1(f, nf) : 0;
 #pragma unroll
-            for (int lz = 0; lz < DBZ; ++lz) {
-                const int gz = fz0 - 2 + lz;
-                v[lz] = (inxy && (unsigned)gz < (unsigned)nf) ? src[plane * lz] : T(0);
-            }
+            for (int u = 0; u < 2; ++u) {
+                const int idx = tid + u * kTileThreads;
+                if (idx < kQ * XH) {
+                    const int ly = idx / kQ, q4 = idx - ly * kQ;
+                    const int gy = fy0 - 2 + ly;
+                    const int ky = ((unsigned)gy < (unsigned)nf) ? nb_count1(gy, nf) : 0;
 #pragma unroll
-            for (int lz = 0; lz < DBZ; ++lz) {
-                const int gz = fz0 - 2 + lz;
-                const int kz = ((unsigned)gz < (unsigned)nf) ? nb_count1(gz, nf) : 0;
-                sx[lx + DBX * (ly + DBY * lz)] = om * v[lz] * s_invD[kxy + kz];
-            }
-        }
-        __syncthreads();
-        // residual on tile + halo 1
-        for (int cidx = tid; cidx < DRX * DRY; cidx += kTileThreads) {
-            const int lx = cidx % DRX, ly = cidx / DRX;
-            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
-            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
-            const int kxy = inxy ? nb_count1(gx, nf) + nb_count1(gy, nf) : 0;
-#pragma unroll
-            for (int lz = 0; lz < DRZ; ++lz) {
-                const int gz = fz0 - 1 + lz;
-                T r = T(0);
-                if (inxy && (unsigned)gz < (unsigned)nf) {
-                    const int bi = (lx + 1) + DBX * ((ly + 1) + DBY * (lz + 1));
-                    const T nbs = (sx[bi - 1] + sx[bi + 1]) + (sx[bi - DBX] + sx[bi + DBX]) +
-                                  (sx[bi - DBX * DBY] + sx[bi + DBX * DBY]);
-                    r = rc * s_D[kxy + nb_count1(gz, nf)] * sx[bi] + sc * nbs;
+                    for (int e = 0; e < 4; ++e) {
+                        const int gx = fx0 - 4 + 4 * q4 + e;
+                        const int kx = ((unsigned)gx < (unsigned)nf) ? nb_count1(gx, nf) : 0;
+                        dst[4 * q4 + e + PW * ly] = om * r.v[u].v[e] * s_invD[kx + ky + kz];
+                    }
                 }
-                sr[lx + DRX * (ly + DRY * lz)] = r;
             }
-        }
-        __syncthreads();
-        {
-            const int li = tid & (TCX - 1), lj = (tid / TCX) & (TCY - 1), lk = tid / (TCX * TCY);
-            const int I = cx0 + li, J = cy0 + lj, K = cz0 + lk;
-            T wx[4], wy[4], wz[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                wx[a] = (T)restrict_w(a, I, nc);
-                wy[a] = (T)restrict_w(a, J, nc);
-                wz[a] = (T)restrict_w(a, K, nc);
-            }
-            T acc = T(0);
-#pragma unroll
-            for (int c3 = 0; c3 < 4; ++c3) {
-                T accy = T(0);
-#pragma unroll
-                for (int b3 = 0; b3 < 4; ++b3) {
-                    const T* row = sr + (2 * li) + DRX * ((2 * lj + b3) + DRY * (2 * lk + c3));
-                    const T accx = wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3];
-                    accy += wy[b3] * accx;
+        };
+        PlaneRegs<T> pr;
+        fetch_plane(pr, bs, nf, plane, fz0 - 2, fx0 - 4, fy0 - 2, XH, tid);
+        commit(pr, fz0 - 2);
+        fetch_plane(pr, bs, nf, plane, fz0 - 1, fx0 - 4, fy0 - 2, XH, tid);
+        commit(pr, fz0 - 1);
+        fetch_plane(pr, bs, nf, plane, fz0, fx0 - 4, fy0 - 2, XH, tid);
+        for (int f = fz0 - 1; f <= fz0 + SZ; ++f) {
+            commit(pr, f + 1);
+            if (f + 2 <= fz0 + SZ + 1) fetch_plane(pr, bs, nf, plane, f + 2, fx0 - 4, fy0 - 2, XH, tid);
+            __syncthreads();
+            {
+                const T* Xm = X + ring3(f - 1) * (PW * XH);
+                const T* Xc = X + ring3(f) * (PW * XH);
+                const T* Xp = X + ring3(f + 1) * (PW * XH);
+                T* Rd = R + ring4(f) * (RW * RH);
+                const bool zin = (unsigned)f < (unsigned)nf;
+                const int kz = zin ? nb_count1(f, nf) : 0;
+                for (int idx = tid; idx < RW * RH; idx += kTileThreads) {
+                    const int ly = idx / RW, lx = idx - ly * RW;
+                    const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+                    T r = T(0);
+                    if (zin && (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf) {
+                        const int xi = (lx + 3) + PW * (ly + 1);
+                        const T nbs = (Xc[xi - 1] + Xc[xi + 1]) + (Xc[xi - PW] + Xc[xi + PW]) + (Xm[xi] + Xp[xi]);
+                        r = rc * s_D[nb_count1(gx, nf) + nb_count1(gy, nf) + kz] * Xc[xi] + sc * nbs;
+                    }
+                    Rd[idx] = r;
                 }
-                acc += wz[c3] * accy;
             }
-            bcs[I + (int64_t)nc * (J + (int64_t)nc * K)] = acc;
+            __syncthreads();
+            if (f >= fz0 + 2 && ((f - fz0) & 1) == 0 && tid < (SX / 2) * (SY / 2)) {
+                const int Z = (f - 2) >> 1;
+                const int li = tid & (SX / 2 - 1), lj = tid / (SX / 2);
+                const int I = cx0 + li, J = cy0 + lj;
+                T wx[4], wy[4], wz[4];
+#pragma unroll
+                for (int a3 = 0; a3 < 4; ++a3) {
+                    wx[a3] = (T)restrict_w(a3, I, nc);
+                    wy[a3] = (T)restrict_w(a3, J, nc);
+                    wz[a3] = (T)restrict_w(a3, Z, nc);
+                }
+                T acc = T(0);
+#pragma unroll
+                for (int c3 = 0; c3 < 4; ++c3) {
+                    const T* Rp = R + ring4(2 * Z - 1 + c3) * (RW * RH);
+                    T accy = T(0);
+#pragma unroll
+                    for (int b3 = 0; b3 < 4; ++b3) {
+                        const T* row = Rp + 2 * li + RW * (2 * lj + b3);
+                        accy += wy[b3] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3]);
+                    }
+                    acc += wz[c3] * accy;
+                }
+                bcs[I + (int64_t)nc * (J + (int64_t)nc * Z)] = acc;
+            }
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x)
-// optional partial sums of b.y (the MINRES beta^2 contribution).
+// Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x),
+// optional partial sums of b.y (the MINRES beta^2 contribution).  Per fine
+// plane g: store b(g) and (for even g) coarse plane g/2 + 1, fetch the next
+// ones, form x(g) on the tile + halo 1, then y(g - 1) from x planes g-2 .. g.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, const T* __restrict__ b,
@@ -203,102 +261,122 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
     __shared__ T s_invD[8], s_D[8];
-    T* sb = reinterpret_cast<T*>(smem_raw);
-    T* sx = sb + UXX * UXY * UXZ;
-    T* sc = sx + UXX * UXY * UXZ;
+    T* B = reinterpret_cast<T*>(smem_raw);  // 3 b planes, PW x BH
+    T* Xr = B + 3 * PW * BH;                 // 3 x planes, PW x BH
+    T* C = Xr + 3 * PW * BH;                 // 3 coarse planes, CW x CH
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
     load_coef(q, s_invD, s_D);
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = tx + 32 * ty;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
     const int nc = nf >> 1;
-    const int ntx = nf / TFX, nty = nf / TFY, ntz = nf / TFZ;
+    const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
     const int ntiles = ntx * nty * ntz;
     const int64_t plane = (int64_t)nf * nf, cplane = (int64_t)nc * nc;
     const T* bs = b + (int64_t)col * b_stride;
     const T* es = ec + (int64_t)col * ec_stride;
     T* ys = y + (int64_t)col * y_stride;
     const T om = q.omega;
+    const T w0 = T(0.75), w1 = T(0.25);
     double dacc = 0.0;
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
-        const int fx0 = tX * TFX, fy0 = tY * TFY, fz0 = tZ * TFZ;
-        const int cx0 = fx0 / 2, cy0 = fy0 / 2, cz0 = fz0 / 2;
-        // coarse correction on the coarse tile + halo 1 (indices clamped: wall reflection)
-        if (tid < UCX * UCY) {
-            const int lx = tid % UCX, ly = tid / UCX;
-            const int gx = min(max(cx0 - 1 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
-            const T* src = es + gx + (int64_t)nc * gy;
-            T v[UCZ];
-#pragma unroll
-            for (int lz = 0; lz < UCZ; ++lz) v[lz] = src[cplane * min(max(cz0 - 1 + lz, 0), nc - 1)];
-#pragma unroll
-            for (int lz = 0; lz < UCZ; ++lz) sc[lx + UCX * (ly + UCY * lz)] = v[lz];
-        }
-        // b on the tile + halo 1
-        for (int cidx = tid; cidx < UXX * UXY; cidx += kTileThreads) {
-            const int lx = cidx % UXX, ly = cidx / UXX;
-            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
-            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
-            const T* src = bs + (gx + (int64_t)nf * gy) + plane * (fz0 - 1);
-            T v[UXZ];
-#pragma unroll
-            for (int lz = 0; lz < UXZ; ++lz) {
-                const int gz = fz0 - 1 + lz;
-                v[lz] = (inxy && (unsigned)gz < (unsigned)nf) ? src[plane * lz] : T(0);
+        const int fx0 = tX * SX, fy0 = tY * SY, fz0 = tZ * SZ;
+        const int cx0 = fx0 >> 1, cy0 = fy0 >> 1;
+        // coarse plane Z (clamped indices: wall reflection), one value per thread
+        auto fetch_c = [&](int Z) -> T {
+            T v = T(0);
+            if (tid < CW * CH) {
+                const int ly = tid / CW, lx = tid - ly * CW;
+                const int gx = min(max(cx0 - 1 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
+                v = es[gx + (int64_t)nc * gy + cplane * min(max(Z, 0), nc - 1)];
             }
+            return v;
+        };
+        auto commit_c = [&](T v, int Z) {
+            if (tid < CW * CH) C[ring3(Z) * (CW * CH) + tid] = v;
+        };
+        auto commit_b = [&](const PlaneRegs<T>& r, int g) {
+            T* dst = B + ring3(g) * (PW * BH);
 #pragma unroll
-            for (int lz = 0; lz < UXZ; ++lz) sb[lx + UXX * (ly + UXY * lz)] = v[lz];
-        }
-        __syncthreads();
-        // x = omega D^{-1} b + P ec on the tile + halo 1 (zero outside the box)
-        const T w0 = T(0.75), w1 = T(0.25);
-        for (int cidx = tid; cidx < UXX * UXY; cidx += kTileThreads) {
-            const int lx = cidx % UXX, ly = cidx / UXX;
-            const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
-            const bool inxy = (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf;
-            const int kxy = inxy ? nb_count1(gx, nf) + nb_count1(gy, nf) : 0;
-            const int Ix = gx >> 1, Iy = gy >> 1;
-            const int px0 = Ix - (cx0 - 1), px1 = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1) - (cx0 - 1);
-            const int py0 = Iy - (cy0 - 1), py1 = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1) - (cy0 - 1);
-#pragma unroll
-            for (int lz = 0; lz < UXZ; ++lz) {
-                const int gz = fz0 - 1 + lz;
-                const int xi = lx + UXX * (ly + UXY * lz);
+            for (int u = 0; u < 2; ++u) {
+                const int idx = tid + u * kTileThreads;
+                if (idx < kQ * BH) st4(dst + 4 * idx, r.v[u]);
+            }
+        };
+        auto make_x = [&](int g) {
+            const T* Bg = B + ring3(g) * (PW * BH);
+            T* Xg = Xr + ring3(g) * (PW * BH);
+            const bool zin = (unsigned)g < (unsigned)nf;
+            const int Iz = g >> 1;
+            const T* Cz0 = C + ring3(Iz) * (CW * CH);
+            const T* Cz1 = C + ring3((g & 1) ? Iz + 1 : Iz - 1) * (CW * CH);
+            const int kz = zin ? nb_count1(g, nf) : 0;
+            for (int idx = tid; idx < RW * BH; idx += kTileThreads) {
+                const int ly = idx / RW, lx = idx - ly * RW;
+                const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+                const int xi = (lx + 3) + PW * ly;
                 T v = T(0);
-                if (inxy && (unsigned)gz < (unsigned)nf) {
-                    const int Iz = gz >> 1;
-                    const int pz0 = Iz - (cz0 - 1), pz1 = min(max((gz & 1) ? Iz + 1 : Iz - 1, 0), nc - 1) - (cz0 - 1);
-                    const T* r00 = sc + UCX * (py0 + UCY * pz0);
-                    const T* r10 = sc + UCX * (py1 + UCY * pz0);
-                    const T* r01 = sc + UCX * (py0 + UCY * pz1);
-                    const T* r11 = sc + UCX * (py1 + UCY * pz1);
-                    const T a00 = w0 * r00[px0] + w1 * r00[px1], a10 = w0 * r10[px0] + w1 * r10[px1];
-                    const T a01 = w0 * r01[px0] + w1 * r01[px1], a11 = w0 * r11[px0] + w1 * r11[px1];
+                if (zin && (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf) {
+                    const int Ix = gx >> 1, Iy = gy >> 1;
+                    const int px0 = Ix - (cx0 - 1);
+                    const int px1 = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1) - (cx0 - 1);
+                    const int py0 = Iy - (cy0 - 1);
+                    const int py1 = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1) - (cy0 - 1);
+                    const T a00 = w0 * Cz0[px0 + CW * py0] + w1 * Cz0[px1 + CW * py0];
+                    const T a10 = w0 * Cz0[px0 + CW * py1] + w1 * Cz0[px1 + CW * py1];
+                    const T a01 = w0 * Cz1[px0 + CW * py0] + w1 * Cz1[px1 + CW * py0];
+                    const T a11 = w0 * Cz1[px0 + CW * py1] + w1 * Cz1[px1 + CW * py1];
                     const T pe = w0 * (w0 * a00 + w1 * a10) + w1 * (w0 * a01 + w1 * a11);
-                    v = om * sb[xi] * s_invD[kxy + nb_count1(gz, nf)] + pe;
+                    v = om * Bg[xi] * s_invD[nb_count1(gx, nf) + nb_count1(gy, nf) + kz] + pe;
                 }
-                sx[xi] = v;
+                Xg[xi] = v;
             }
-        }
+        };
+        const int cz0 = fz0 >> 1;
+        PlaneRegs<T> pb;
+        commit_c(fetch_c(cz0 - 1), cz0 - 1);
+        commit_c(fetch_c(cz0), cz0);
+        fetch_plane(pb, bs, nf, plane, fz0 - 1, fx0 - 4, fy0 - 1, BH, tid);
+        commit_b(pb, fz0 - 1);
         __syncthreads();
-        {
-            const int gx = fx0 + tx, gy = fy0 + ty;
-            const int kxy = nb_count1(gx, nf) + nb_count1(gy, nf);
-            T* dst = ys + gx + (int64_t)nf * gy + plane * fz0;
+        make_x(fz0 - 1);
+        fetch_plane(pb, bs, nf, plane, fz0, fx0 - 4, fy0 - 1, BH, tid);
+        T pc = fetch_c(cz0 + 1);
+        for (int g = fz0; g <= fz0 + SZ; ++g) {
+            if ((g & 1) == 0) commit_c(pc, (g >> 1) + 1);
+            commit_b(pb, g);
+            if (g + 1 <= fz0 + SZ) {
+                fetch_plane(pb, bs, nf, plane, g + 1, fx0 - 4, fy0 - 1, BH, tid);
+                if (((g + 1) & 1) == 0) pc = fetch_c(((g + 1) >> 1) + 1);
+            }
+            __syncthreads();
+            make_x(g);
+            __syncthreads();
+            const int f = g - 1;  // output plane
+            if (f >= fz0 && tid < SX * SY / 4) {
+                const T* Xm = Xr + ring3(f - 1) * (PW * BH);
+                const T* Xc = Xr + ring3(f) * (PW * BH);
+                const T* Xp = Xr + ring3(f + 1) * (PW * BH);
+                const T* Bc = B + ring3(f) * (PW * BH);
+                const int kz = nb_count1(f, nf);
+                const int oy = tid / (SX / 4), ox0 = 4 * (tid - oy * (SX / 4));
+                const int gy = fy0 + oy;
+                const int ky = nb_count1(gy, nf);
+                V4<T> out;
 #pragma unroll
-            for (int oz = 0; oz < TFZ; ++oz) {
-                const int gz = fz0 + oz;
-                const int xi = (tx + 1) + UXX * ((ty + 1) + UXY * (oz + 1));
-                const T x0 = sx[xi];
-                const T nbs = (sx[xi - 1] + sx[xi + 1]) + (sx[xi - UXX] + sx[xi + UXX]) +
-                              (sx[xi - UXX * UXY] + sx[xi + UXX * UXY]);
-                const int k0 = kxy + nb_count1(gz, nf);
-                const T bv = sb[xi];
-                const T yv = x0 + om * s_invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
-                dst[plane * oz] = yv;
-                dacc += (double)(bv * yv);
+                for (int e = 0; e < 4; ++e) {
+                    const int gx = fx0 + ox0 + e;
+                    const int xi = (ox0 + e + 4) + PW * (oy + 1);
+                    const T x0 = Xc[xi];
+                    const T nbs = (Xc[xi - 1] + Xc[xi + 1]) + (Xc[xi - PW] + Xc[xi + PW]) + (Xm[xi] + Xp[xi]);
+                    const int k0 = nb_count1(gx, nf) + ky + kz;
+                    const T bv = Bc[xi];
+                    const T yv = x0 + om * s_invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
+                    out.v[e] = yv;
+                    dacc += (double)(bv * yv);
+                }
+                st4(ys + (fx0 + ox0) + (int64_t)nf * gy + plane * f, out);
             }
         }
         __syncthreads();
@@ -516,9 +594,10 @@ static cudaError_t mg_attrs() {
                                          coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kDownSmem * (int)sizeof(T));
+                                 kDownSSmem * (int)sizeof(T));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmem * (int)sizeof(T));
+        e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kUpSSmem * (int)sizeof(T));
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -550,11 +629,11 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     int64_t in_stride = b_stride;
     for (int l = 0; l < plan.lc; ++l) {
         const int nf = n >> l, nc = nf >> 1;
-        const int ntiles = (nc / TCX) * (nc / TCY) * (nc / TCZ);
+        const int ntiles = (nf / SX) * (nf / SY) * (nf / SZ);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
         prof_begin(PK_MG_DOWN, st);
-        k_mg_down<T><<<grid, dim3(32, 8), kDownSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
+        k_mg_down<T><<<grid, dim3(32, 8), kDownSSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
                                                     (int64_t)nc * nc * nc, active, act_stride);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
         in = out;
@@ -571,7 +650,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     int nblk0 = 1;
     for (int l = plan.lc - 1; l >= 0; --l) {
         const int nf = n >> l, nc = nf >> 1;
-        const int ntiles = (nf / TFX) * (nf / TFY) * (nf / TFZ);
+        const int ntiles = (nf / SX) * (nf / SY) * (nf / SZ);
         const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
         dim3 grid(nb, S);
         const T* bl = (l == 0) ? b : static_cast<const T*>(plan.b[l]);
@@ -579,7 +658,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
         const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
         prof_begin(PK_MG_UP, st);
-        k_mg_up<T><<<grid, dim3(32, 8), kUpSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
+        k_mg_up<T><<<grid, dim3(32, 8), kUpSSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
                                                   static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
                                                   yls, (l == 0) ? dot_part : nullptr, active, act_stride);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);
