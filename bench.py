@@ -134,7 +134,7 @@ def measured_peaks():
 
 def kernel_traffic(name):
     """DRAM bytes per launch per column from a committed ncu summary, if the
-    kernel source is unchanged since the capture (else None)."""
+    kernel's sources are unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -143,12 +143,11 @@ def kernel_traffic(name):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, rec["source"])
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        blob = b"".join(open(os.path.join(ROOT, s), "rb").read() for s in rec["sources"])
     except OSError:
         return None
-    if sha != rec["source_sha256"]:
+    if hashlib.sha256(blob).hexdigest() != rec["sources_sha256"]:
         return None
     return rec
 
