@@ -12,10 +12,12 @@ constexpr int kMaxPartials = 4096;   // per column, per partial-sum array
 struct MinresCol {
     double beta, oldb, alpha, dbar, epsln, oldeps, phibar, cs, sn, gamma, delta, phi, beta1;
     double tol;      // stop when phibar <= tol * beta1
+    // coefficients of the pending w/x update (saved by the Givens step)
+    double d_oldb, d_oldeps, d_delta, d_gamma, d_phi;
     int active;      // column still iterating
-    int upd;         // this iteration produced an update (consumed by the w/x kernel)
+    int upd;         // a w/x update is pending (consumed by the next fused pass or the final D)
     int iters;
-    int pad;
+    int d_iter;      // iteration number of the pending update
 };
 
 // Multigrid plan of one grid size for a batch of S columns.
@@ -61,9 +63,10 @@ int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* 
 cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cudaStream_t st);
 
 // ---- krylov.cu
+// A(k+1) fused with the pending D(k) when yprev != null (see krylov.cu)
 template <typename T>
-int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_,
-                    cudaStream_t st);
+int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, const T* yprev,
+                    T* w1, const T* w2, T* xd, cudaStream_t st);
 template <typename T>
 int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, T* ynext, double fd, double* partB,
                     MinresCol* st_, cudaStream_t st);

@@ -28,17 +28,24 @@ static inline int cell_blocks(int64_t n3) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// A(k+1) fused with D(k): both become ready after the Givens step of
+// iteration k and touch disjoint arrays, so one pass streams both.
+//   A part (column active):   z = A y / beta - (beta / oldb) r1 -> r1, alpha partial
+//   D part (column upd set):  w' = (yprev_cell / oldb_D - oldeps w1 - delta w2) / gamma,
+//                             x += phi w'   (cell block, [S][n^3] arrays)
+// The D coefficients were saved by the Givens step in MinresCol (d_* fields)
+// because beta / oldb have already advanced for the A part.
 template <typename T>
-__global__ void __launch_bounds__(256) k_minres_A(int n, T kh2, const T* __restrict__ y, T* __restrict__ r1,
-                                                  double* __restrict__ partA, const MinresCol* __restrict__ st) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n, T kh2, const T* __restrict__ y, T* __restrict__ r1,
+                                                     double* __restrict__ partA, const MinresCol* __restrict__ st,
+                                                     const T* __restrict__ yprev, T* __restrict__ w1,
+                                                     const T* __restrict__ w2, T* __restrict__ xd) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     const MinresCol& cs = st[s];
-    if (!cs.active) return;
-    const T ib = (T)(1.0 / cs.beta);
-    const T coef = (T)(cs.oldb > 0.0 ? cs.beta / cs.oldb : 0.0);
-    // r1 holds no data before the second iteration (coef == 0): do not read it
-    const bool use_r1 = coef != T(0);
+    const bool doA = cs.active != 0;
+    const bool doD = yprev != nullptr && cs.upd != 0;
+    if (!doA && !doD) return;
     const int logn = ilog2(n);
     const int n3 = 1 << (3 * logn);
     const int nq = n3 >> 2;
@@ -46,43 +53,75 @@ __global__ void __launch_bounds__(256) k_minres_A(int n, T kh2, const T* __restr
     const T* ys = y + off;
     T* rs = r1 + off;
     T acc = T(0);
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-        const QuadPos p = quad_pos(q, logn);
-        T yu[4], yv[4], yw[4], yt[4];
-        apply_quad<T, T>(ys, n, logn, p, kh2, yu, yv, yw, yt);
-        const V4<T> v0 = ld4(ys + p.c), v1 = ld4(ys + n3 + p.c), v2 = ld4(ys + 2 * n3 + p.c), v3 = ld4(ys + 3 * n3 + p.c);
-        V4<T> z0, z1, z2, z3;
-        if (use_r1) {
-            z0 = ld4(rs + p.c);
-            z1 = ld4(rs + n3 + p.c);
-            z2 = ld4(rs + 2 * n3 + p.c);
-            z3 = ld4(rs + 3 * n3 + p.c);
-        } else {
-            z0 = z1 = z2 = z3 = zero4<T>();
-        }
+    if (doA) {
+        const T ib = (T)(1.0 / cs.beta);
+        const T coef = (T)(cs.oldb > 0.0 ? cs.beta / cs.oldb : 0.0);
+        // r1 holds no data before the second iteration (coef == 0): do not read it
+        const bool use_r1 = coef != T(0);
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+            const QuadPos p = quad_pos(q, logn);
+            T yu[4], yv[4], yw[4], yt[4];
+            apply_quad<T, T>(ys, n, logn, p, kh2, yu, yv, yw, yt);
+            const V4<T> v0 = ld4(ys + p.c), v1 = ld4(ys + n3 + p.c), v2 = ld4(ys + 2 * n3 + p.c),
+                        v3 = ld4(ys + 3 * n3 + p.c);
+            V4<T> z0, z1, z2, z3;
+            if (use_r1) {
+                z0 = ld4(rs + p.c);
+                z1 = ld4(rs + n3 + p.c);
+                z2 = ld4(rs + 2 * n3 + p.c);
+                z3 = ld4(rs + 3 * n3 + p.c);
+            } else {
+                z0 = z1 = z2 = z3 = zero4<T>();
+            }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            z0.v[e] = yu[e] * ib - coef * z0.v[e];
-            z1.v[e] = yv[e] * ib - coef * z1.v[e];
-            z2.v[e] = yw[e] * ib - coef * z2.v[e];
-            z3.v[e] = yt[e] * ib - coef * z3.v[e];
-            acc += (v0.v[e] * z0.v[e] + v1.v[e] * z1.v[e] + v2.v[e] * z2.v[e] + v3.v[e] * z3.v[e]) * ib;
+            for (int e = 0; e < 4; ++e) {
+                z0.v[e] = yu[e] * ib - coef * z0.v[e];
+                z1.v[e] = yv[e] * ib - coef * z1.v[e];
+                z2.v[e] = yw[e] * ib - coef * z2.v[e];
+                z3.v[e] = yt[e] * ib - coef * z3.v[e];
+                acc += (v0.v[e] * z0.v[e] + v1.v[e] * z1.v[e] + v2.v[e] * z2.v[e] + v3.v[e] * z3.v[e]) * ib;
+            }
+            st4(rs + p.c, z0);
+            st4(rs + n3 + p.c, z1);
+            st4(rs + 2 * n3 + p.c, z2);
+            st4(rs + 3 * n3 + p.c, z3);
         }
-        st4(rs + p.c, z0);
-        st4(rs + n3 + p.c, z1);
-        st4(rs + 2 * n3 + p.c, z2);
-        st4(rs + 3 * n3 + p.c, z3);
     }
-    const double t = block_sum<256>((double)acc, red);
-    if (threadIdx.x == 0) partA[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+    if (doD) {
+        const T iv = (T)(1.0 / cs.d_oldb);
+        const T oe = (T)cs.d_oldeps, de = (T)cs.d_delta, ig = (T)(1.0 / cs.d_gamma), ph = (T)cs.d_phi;
+        const int it = cs.d_iter;
+        const T* yc = yprev + off + 3 * (int64_t)n3;
+        const int64_t o3 = (int64_t)s * n3;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+            const int64_t e0 = 4 * (int64_t)q;
+            const V4<T> yv = ld4(yc + e0);
+            const V4<T> w2v = (it >= 2) ? ld4(w2 + o3 + e0) : zero4<T>();
+            const V4<T> w1v = (it >= 3) ? ld4(w1 + o3 + e0) : zero4<T>();
+            const V4<T> xv = (it >= 2) ? ld4(xd + o3 + e0) : zero4<T>();
+            V4<T> wn, xn;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                wn.v[k] = (yv.v[k] * iv - oe * w1v.v[k] - de * w2v.v[k]) * ig;
+                xn.v[k] = xv.v[k] + ph * wn.v[k];
+            }
+            st4(w1 + o3 + e0, wn);
+            st4(xd + o3 + e0, xn);
+        }
+    }
+    if (doA) {
+        const double t = block_sum<256>((double)acc, red);
+        if (threadIdx.x == 0) partA[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+    }
 }
 
 template <typename T>
-int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, cudaStream_t st) {
+int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, const T* yprev,
+                    T* w1, const T* w2, T* xd, cudaStream_t st) {
     const int64_t n3 = (int64_t)n * n * n;
     const int nb = cell_blocks(n3 / 4);
     dim3 grid(nb, S);
-    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, r1, partA, st_);
+    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, r1, partA, st_, yprev, w1, w2, xd);
     return nb;
 }
 
@@ -196,6 +235,13 @@ __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB
     c.gamma = gamma;
     c.upd = 1;
     c.iters += 1;
+    // coefficients of this iteration's w/x update, applied by the next fused pass
+    c.d_oldb = c.oldb;
+    c.d_oldeps = c.oldeps;
+    c.d_delta = delta;
+    c.d_gamma = gamma;
+    c.d_phi = c.phi;
+    c.d_iter = c.iters;
     const bool done = !(beta2 > 0.0) || !isfinite(beta) || c.phibar <= c.tol * c.beta1;
     if (done) c.active = 0;
     else if (nactive) atomicAdd(nactive, 1);
@@ -257,12 +303,12 @@ __global__ void __launch_bounds__(256) k_minres_D(int64_t n3, const T* __restric
     const int s = blockIdx.y;
     const MinresCol& c = st[s];
     if (!c.upd) return;
-    const T iv = (T)(1.0 / c.oldb);
-    const T oe = (T)c.oldeps, de = (T)c.delta, ig = (T)(1.0 / c.gamma), ph = (T)c.phi;
+    const T iv = (T)(1.0 / c.d_oldb);
+    const T oe = (T)c.d_oldeps, de = (T)c.d_delta, ig = (T)(1.0 / c.d_gamma), ph = (T)c.d_phi;
     const T* ys = ycur + (int64_t)s * 4 * n3 + 3 * n3;
     const int64_t off = (int64_t)s * n3;
     // iteration 1: w1 = w2 = 0 and x = 0; iteration 2: w1 = 0 (buffers hold no data yet)
-    const int it = c.iters;
+    const int it = c.d_iter;
     const int64_t nq = n3 >> 2;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = 4 * q;
@@ -300,7 +346,8 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 }
 
 #define SPDE_KRYLOV_INST(T)                                                                                        \
-    template int launch_minres_A<T>(int, double, int, const T*, T*, double*, MinresCol*, cudaStream_t);           \
+    template int launch_minres_A<T>(int, double, int, const T*, T*, double*, MinresCol*, const T*, T*, const T*, \
+                                    T*, cudaStream_t);                                                             \
     template int launch_minres_B<T>(int64_t, int, int, T*, const T*, T*, double, double*, MinresCol*,             \
                                     cudaStream_t);                                                                 \
     template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \

@@ -24,9 +24,6 @@
 
 namespace spde {
 
-// tile of the fine level handled by one CTA in the down/up sweeps
-constexpr int TFX = 32, TFY = 8, TFZ = 8;
-constexpr int TCX = TFX / 2, TCY = TFY / 2, TCZ = TFZ / 2;
 constexpr int kTileThreads = 256;
 constexpr int kCoarseThreads = 512;
 constexpr int kMaxTilesPerCol = 2048;
@@ -95,13 +92,12 @@ __device__ __forceinline__ void load_coef(const LevelCoef<T>& q, T* s_invD, T* s
 // (tiles and grids are multiples of 32, so a vector lies wholly inside or
 // wholly outside the box), one plane ahead into registers, so the loads of
 // plane f+2 are in flight while plane f is computed.
-constexpr int SX = 32, SY = 16, SZ = 32;
+constexpr int SX = 32, SY = 16;  // the z extent per CTA (8, 16 or 32 planes) is chosen per launch
 constexpr int PW = SX + 8;               // plane row width in shared memory (x from fx0 - 4)
 constexpr int XH = SY + 4;               // x0 rows, halo 2 (down sweep)
 constexpr int RW = SX + 2, RH = SY + 2;  // residual plane, halo 1
 constexpr int BH = SY + 2;               // b / x rows, halo 1 (up sweep)
 constexpr int CW = SX / 2 + 2, CH = SY / 2 + 2;  // coarse plane with halo 1 (up sweep)
-constexpr int kDownSSmem = 3 * PW * XH + 4 * RW * RH;
 constexpr int kUpSSmem = 3 * PW * BH + 3 * PW * BH + 3 * CW * CH;
 constexpr int kQ = PW / 4;               // float4 per plane row
 
@@ -135,18 +131,25 @@ __device__ __forceinline__ void fetch_plane(PlaneRegs<T>& r, const T* bs, int nf
 // Down sweep at level l: bc = R (b - A omega D^{-1} b).  With x0 = omega D^{-1} b
 //     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g)
 // (x0 = 0 outside the box, so the sum runs over existing neighbours).
-// Per fine plane: store the x0 plane f+1, fetch plane f+2, form r on plane
-// f, and after every second plane restrict one coarse plane from the four r
-// planes 2Z-1 .. 2Z+2.
+// Per fine plane f: store the x0 plane f+1, fetch plane f+2, form r on plane
+// f and restrict it in x and y at once (Rxy, 16 x 8 values); every second
+// plane one coarse plane is the 4-tap z combination of four Rxy planes.
+// Each thread's plane positions (offsets, neighbour counts, box tests) are
+// fixed for a tile and computed once before the z-march.
 // ---------------------------------------------------------------------------
+constexpr int kRS = (RW * RH + kTileThreads - 1) / kTileThreads;  // r positions per thread (3)
+constexpr int RXY = (SX / 2) * (SY / 2);                            // restricted plane (128)
+constexpr int kDownS2Smem = 3 * PW * XH + RW * RH + 4 * RXY;
+
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q, const T* __restrict__ b,
-                                                          int64_t b_stride, T* __restrict__ bc, int64_t bc_stride,
-                                                          const int* __restrict__ active, int act_stride) {
+__global__ void __launch_bounds__(kTileThreads, 4) k_mg_down(int nf, int SZ, LevelCoef<T> q, const T* __restrict__ b,
+                                                             int64_t b_stride, T* __restrict__ bc, int64_t bc_stride,
+                                                             const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T s_invD[8], s_D[8];
-    T* X = reinterpret_cast<T*>(smem_raw);  // 3 x0 planes, PW x XH
-    T* R = X + 3 * PW * XH;                  // 4 residual planes, RW x RH
+    T* const Xbase = reinterpret_cast<T*>(smem_raw);  // 3 x0 planes, PW x XH
+    T* const Rp = Xbase + 3 * PW * XH;                 // residual plane, RW x RH
+    T* const Rxy = Rp + RW * RH;                       // 4 x-y restricted planes
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
     load_coef(q, s_invD, s_D);
@@ -165,82 +168,110 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
         const int fx0 = tX * SX, fy0 = tY * SY, fz0 = tZ * SZ;
         const int cx0 = fx0 >> 1, cy0 = fy0 >> 1;
-        // x0 = omega D^{-1} b into ring slot of plane f
-        auto commit = [&](const PlaneRegs<T>& r, int f) {
-            T* dst = X + ring3(f) * (PW * XH);
-            const bool zin = (unsigned)f < (unsigned)nf;
-            const int kz = zin ? nb_count1(f, nf) : 0;
+        // --- per-tile slot data
+        // commit: one 4-wide row segment per thread (tid < kQ * XH)
+        int c_off = -1, c_k[4] = {0, 0, 0, 0};
+        if (tid < kQ * XH) {
+            const int ly = tid / kQ, q4 = tid - ly * kQ;
+            const int gy = fy0 - 2 + ly;
+            const int ky = ((unsigned)gy < (unsigned)nf) ? nb_count1(gy, nf) : 0;
+            c_off = 4 * q4 + PW * ly;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int idx = tid + u * kTileThreads;
-                if (idx < kQ * XH) {
-                    const int ly = idx / kQ, q4 = idx - ly * kQ;
-                    const int gy = fy0 - 2 + ly;
-                    const int ky = ((unsigned)gy < (unsigned)nf) ? nb_count1(gy, nf) : 0;
+            for (int e = 0; e < 4; ++e) {
+                const int gx = fx0 - 4 + 4 * q4 + e;
+                c_k[e] = ky + (((unsigned)gx < (unsigned)nf) ? nb_count1(gx, nf) : 0);
+            }
+        }
+        // residual positions: X offset and kx + ky, or -1 when outside the box in x/y
+        int r_xi[kRS], r_k[kRS];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int gx = fx0 - 4 + 4 * q4 + e;
-                        const int kx = ((unsigned)gx < (unsigned)nf) ? nb_count1(gx, nf) : 0;
-                        dst[4 * q4 + e + PW * ly] = om * r.v[u].v[e] * s_invD[kx + ky + kz];
-                    }
-                }
+        for (int u = 0; u < kRS; ++u) {
+            const int idx = tid + u * kTileThreads;
+            r_xi[u] = 0;
+            r_k[u] = -2;  // -2: no position; -1: outside the box
+            if (idx < RW * RH) {
+                const int ly = idx / RW, lx = idx - ly * RW;
+                const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+                r_xi[u] = (lx + 3) + PW * (ly + 1);
+                r_k[u] = ((unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf)
+                             ? nb_count1(gx, nf) + nb_count1(gy, nf)
+                             : -1;
+            }
+        }
+        // x-y restriction of one coarse (I, J) per thread (tid < RXY)
+        T wx[4], wy[4];
+        int rb = 0;
+        {
+            const int li = tid & (SX / 2 - 1), lj = (tid / (SX / 2)) & (SY / 2 - 1);
+            const int I = cx0 + li, J = cy0 + lj;
+#pragma unroll
+            for (int a3 = 0; a3 < 4; ++a3) {
+                wx[a3] = (T)restrict_w(a3, I, nc);
+                wy[a3] = (T)restrict_w(a3, J, nc);
+            }
+            rb = 2 * li + RW * (2 * lj);
+        }
+        T* Xm = Xbase;
+        T* Xc = Xbase + PW * XH;
+        T* Xp = Xbase + 2 * PW * XH;
+        auto commit = [&](const PlaneRegs<T>& r, T* dst, int f) {
+            const int kz = ((unsigned)f < (unsigned)nf) ? nb_count1(f, nf) : 0;
+            if (c_off >= 0) {
+                V4<T> v;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v.v[e] = om * r.v[0].v[e] * s_invD[c_k[e] + kz];
+                st4(dst + c_off, v);
             }
         };
         PlaneRegs<T> pr;
         fetch_plane(pr, bs, nf, plane, fz0 - 2, fx0 - 4, fy0 - 2, XH, tid);
-        commit(pr, fz0 - 2);
+        commit(pr, Xm, fz0 - 2);
         fetch_plane(pr, bs, nf, plane, fz0 - 1, fx0 - 4, fy0 - 2, XH, tid);
-        commit(pr, fz0 - 1);
+        commit(pr, Xc, fz0 - 1);
         fetch_plane(pr, bs, nf, plane, fz0, fx0 - 4, fy0 - 2, XH, tid);
         for (int f = fz0 - 1; f <= fz0 + SZ; ++f) {
-            commit(pr, f + 1);
+            commit(pr, Xp, f + 1);
             if (f + 2 <= fz0 + SZ + 1) fetch_plane(pr, bs, nf, plane, f + 2, fx0 - 4, fy0 - 2, XH, tid);
             __syncthreads();
             {
-                const T* Xm = X + ring3(f - 1) * (PW * XH);
-                const T* Xc = X + ring3(f) * (PW * XH);
-                const T* Xp = X + ring3(f + 1) * (PW * XH);
-                T* Rd = R + ring4(f) * (RW * RH);
                 const bool zin = (unsigned)f < (unsigned)nf;
                 const int kz = zin ? nb_count1(f, nf) : 0;
-                for (int idx = tid; idx < RW * RH; idx += kTileThreads) {
-                    const int ly = idx / RW, lx = idx - ly * RW;
-                    const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
+#pragma unroll
+                for (int u = 0; u < kRS; ++u) {
+                    if (r_k[u] == -2) continue;
                     T r = T(0);
-                    if (zin && (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf) {
-                        const int xi = (lx + 3) + PW * (ly + 1);
+                    if (zin && r_k[u] >= 0) {
+                        const int xi = r_xi[u];
                         const T nbs = (Xc[xi - 1] + Xc[xi + 1]) + (Xc[xi - PW] + Xc[xi + PW]) + (Xm[xi] + Xp[xi]);
-                        r = rc * s_D[nb_count1(gx, nf) + nb_count1(gy, nf) + kz] * Xc[xi] + sc * nbs;
+                        r = rc * s_D[r_k[u] + kz] * Xc[xi] + sc * nbs;
                     }
-                    Rd[idx] = r;
+                    Rp[tid + u * kTileThreads] = r;
                 }
             }
             __syncthreads();
-            if (f >= fz0 + 2 && ((f - fz0) & 1) == 0 && tid < (SX / 2) * (SY / 2)) {
-                const int Z = (f - 2) >> 1;
-                const int li = tid & (SX / 2 - 1), lj = tid / (SX / 2);
-                const int I = cx0 + li, J = cy0 + lj;
-                T wx[4], wy[4], wz[4];
-#pragma unroll
-                for (int a3 = 0; a3 < 4; ++a3) {
-                    wx[a3] = (T)restrict_w(a3, I, nc);
-                    wy[a3] = (T)restrict_w(a3, J, nc);
-                    wz[a3] = (T)restrict_w(a3, Z, nc);
-                }
+            if (tid < RXY) {
                 T acc = T(0);
 #pragma unroll
-                for (int c3 = 0; c3 < 4; ++c3) {
-                    const T* Rp = R + ring4(2 * Z - 1 + c3) * (RW * RH);
-                    T accy = T(0);
-#pragma unroll
-                    for (int b3 = 0; b3 < 4; ++b3) {
-                        const T* row = Rp + 2 * li + RW * (2 * lj + b3);
-                        accy += wy[b3] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3]);
-                    }
-                    acc += wz[c3] * accy;
+                for (int b3 = 0; b3 < 4; ++b3) {
+                    const T* row = Rp + rb + RW * b3;
+                    acc += wy[b3] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3]);
                 }
-                bcs[I + (int64_t)nc * (J + (int64_t)nc * Z)] = acc;
+                Rxy[ring4(f) * RXY + tid] = acc;
+                if (f >= fz0 + 2 && ((f - fz0) & 1) == 0) {
+                    // coarse plane Z = f/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = f-3 .. f
+                    const int Z = (f - 2) >> 1;
+                    T z = T(0);
+#pragma unroll
+                    for (int c3 = 0; c3 < 4; ++c3)
+                        z += (T)restrict_w(c3, Z, nc) * ((c3 == 3) ? acc : Rxy[ring4(f - 3 + c3) * RXY + tid]);
+                    const int li = tid & (SX / 2 - 1), lj = tid / (SX / 2);
+                    bcs[(cx0 + li) + (int64_t)nc * ((cy0 + lj) + (int64_t)nc * Z)] = z;
+                }
             }
+            T* t = Xm;
+            Xm = Xc;
+            Xc = Xp;
+            Xp = t;
         }
         __syncthreads();
     }
@@ -251,19 +282,23 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_down(int nf, LevelCoef<T> q
 // optional partial sums of b.y (the MINRES beta^2 contribution).  Per fine
 // plane g: store b(g) and (for even g) coarse plane g/2 + 1, fetch the next
 // ones, form x(g) on the tile + halo 1, then y(g - 1) from x planes g-2 .. g.
+// Per-thread positions, neighbour counts and prolongation offsets are fixed
+// for a tile and computed once before the z-march.
 // ---------------------------------------------------------------------------
+constexpr int kXS = (RW * BH + kTileThreads - 1) / kTileThreads;  // x positions per thread (3)
+
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, const T* __restrict__ b,
-                                                        int64_t b_stride, const T* __restrict__ ec,
-                                                        int64_t ec_stride, T* __restrict__ y, int64_t y_stride,
-                                                        double* __restrict__ dot_part,
-                                                        const int* __restrict__ active, int act_stride) {
+__global__ void __launch_bounds__(kTileThreads, 3) k_mg_up(int nf, int SZ, LevelCoef<T> q, const T* __restrict__ b,
+                                                           int64_t b_stride, const T* __restrict__ ec,
+                                                           int64_t ec_stride, T* __restrict__ y, int64_t y_stride,
+                                                           double* __restrict__ dot_part,
+                                                           const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
     __shared__ T s_invD[8], s_D[8];
-    T* B = reinterpret_cast<T*>(smem_raw);  // 3 b planes, PW x BH
-    T* Xr = B + 3 * PW * BH;                 // 3 x planes, PW x BH
-    T* C = Xr + 3 * PW * BH;                 // 3 coarse planes, CW x CH
+    T* const Bbase = reinterpret_cast<T*>(smem_raw);  // 3 b planes, PW x BH
+    T* const Xbase = Bbase + 3 * PW * BH;              // 3 x planes, PW x BH
+    T* const Cbase = Xbase + 3 * PW * BH;              // 3 coarse planes, CW x CH
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
     load_coef(q, s_invD, s_D);
@@ -277,112 +312,152 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up(int nf, LevelCoef<T> q, 
     T* ys = y + (int64_t)col * y_stride;
     const T om = q.omega;
     const T w0 = T(0.75), w1 = T(0.25);
-    double dacc = 0.0;
+    T dacc = T(0);  // per-thread partial of b.y in the element type; FP64 across threads
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
         const int fx0 = tX * SX, fy0 = tY * SY, fz0 = tZ * SZ;
         const int cx0 = fx0 >> 1, cy0 = fy0 >> 1;
-        // coarse plane Z (clamped indices: wall reflection), one value per thread
-        auto fetch_c = [&](int Z) -> T {
-            T v = T(0);
-            if (tid < CW * CH) {
-                const int ly = tid / CW, lx = tid - ly * CW;
-                const int gx = min(max(cx0 - 1 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
-                v = es[gx + (int64_t)nc * gy + cplane * min(max(Z, 0), nc - 1)];
-            }
-            return v;
-        };
-        auto commit_c = [&](T v, int Z) {
-            if (tid < CW * CH) C[ring3(Z) * (CW * CH) + tid] = v;
-        };
-        auto commit_b = [&](const PlaneRegs<T>& r, int g) {
-            T* dst = B + ring3(g) * (PW * BH);
+        const int cz0 = fz0 >> 1;
+        // --- per-tile slot data
+        int c_src = -1;  // coarse plane element of this thread (clamped x, y), or -1
+        if (tid < CW * CH) {
+            const int ly = tid / CW, lx = tid - ly * CW;
+            const int gx = min(max(cx0 - 1 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
+            c_src = gx + nc * gy;
+        }
+        int x_xi[kXS], x_k[kXS], x_c00[kXS], x_c10[kXS], x_c01[kXS], x_c11[kXS];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int idx = tid + u * kTileThreads;
-                if (idx < kQ * BH) st4(dst + 4 * idx, r.v[u]);
-            }
-        };
-        auto make_x = [&](int g) {
-            const T* Bg = B + ring3(g) * (PW * BH);
-            T* Xg = Xr + ring3(g) * (PW * BH);
-            const bool zin = (unsigned)g < (unsigned)nf;
-            const int Iz = g >> 1;
-            const T* Cz0 = C + ring3(Iz) * (CW * CH);
-            const T* Cz1 = C + ring3((g & 1) ? Iz + 1 : Iz - 1) * (CW * CH);
-            const int kz = zin ? nb_count1(g, nf) : 0;
-            for (int idx = tid; idx < RW * BH; idx += kTileThreads) {
+        for (int u = 0; u < kXS; ++u) {
+            const int idx = tid + u * kTileThreads;
+            x_xi[u] = 0;
+            x_k[u] = -2;
+            x_c00[u] = x_c10[u] = x_c01[u] = x_c11[u] = 0;
+            if (idx < RW * BH) {
                 const int ly = idx / RW, lx = idx - ly * RW;
                 const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
-                const int xi = (lx + 3) + PW * ly;
-                T v = T(0);
-                if (zin && (unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf) {
+                x_xi[u] = (lx + 3) + PW * ly;
+                if ((unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf) {
+                    x_k[u] = nb_count1(gx, nf) + nb_count1(gy, nf);
                     const int Ix = gx >> 1, Iy = gy >> 1;
                     const int px0 = Ix - (cx0 - 1);
                     const int px1 = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1) - (cx0 - 1);
                     const int py0 = Iy - (cy0 - 1);
                     const int py1 = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1) - (cy0 - 1);
-                    const T a00 = w0 * Cz0[px0 + CW * py0] + w1 * Cz0[px1 + CW * py0];
-                    const T a10 = w0 * Cz0[px0 + CW * py1] + w1 * Cz0[px1 + CW * py1];
-                    const T a01 = w0 * Cz1[px0 + CW * py0] + w1 * Cz1[px1 + CW * py0];
-                    const T a11 = w0 * Cz1[px0 + CW * py1] + w1 * Cz1[px1 + CW * py1];
-                    const T pe = w0 * (w0 * a00 + w1 * a10) + w1 * (w0 * a01 + w1 * a11);
-                    v = om * Bg[xi] * s_invD[nb_count1(gx, nf) + nb_count1(gy, nf) + kz] + pe;
+                    x_c00[u] = px0 + CW * py0;
+                    x_c10[u] = px1 + CW * py0;
+                    x_c01[u] = px0 + CW * py1;
+                    x_c11[u] = px1 + CW * py1;
+                } else {
+                    x_k[u] = -1;
                 }
-                Xg[xi] = v;
+            }
+        }
+        // output: 4 consecutive cells per thread (tid < SX * SY / 4)
+        const int oy = tid / (SX / 4), ox0 = 4 * (tid - oy * (SX / 4));
+        const bool has_out = tid < SX * SY / 4;
+        const int o_xi = (ox0 + 4) + PW * (oy + 1);
+        int o_k[4];
+        {
+            const int ky = has_out ? nb_count1(fy0 + oy, nf) : 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) o_k[e] = ky + (has_out ? nb_count1(fx0 + ox0 + e, nf) : 0);
+        }
+        T* Bm = Bbase;  // b planes g-2, g-1, g (rotating)
+        T* Bc = Bbase + PW * BH;
+        T* Bp = Bbase + 2 * PW * BH;
+        T* Xm = Xbase;  // x planes g-2, g-1, g (rotating)
+        T* Xc = Xbase + PW * BH;
+        T* Xp = Xbase + 2 * PW * BH;
+        T* Cm = Cbase;  // coarse planes Z-1, Z, Z+1 with Z = g >> 1 (rotating at even g)
+        T* Cc = Cbase + CW * CH;
+        T* Cp = Cbase + 2 * CW * CH;
+        auto fetch_c = [&](int Z) -> T {
+            return (c_src >= 0) ? es[c_src + cplane * min(max(Z, 0), nc - 1)] : T(0);
+        };
+        auto commit_b = [&](const PlaneRegs<T>& r, T* dst) {
+            if (tid < kQ * BH) st4(dst + 4 * tid, r.v[0]);
+        };
+        auto make_x = [&](int g, const T* Bg, T* Xg, const T* C0, const T* C1) {
+            const bool zin = (unsigned)g < (unsigned)nf;
+            const int kz = zin ? nb_count1(g, nf) : 0;
+#pragma unroll
+            for (int u = 0; u < kXS; ++u) {
+                if (x_k[u] == -2) continue;
+                T v = T(0);
+                if (zin && x_k[u] >= 0) {
+                    const T a00 = w0 * C0[x_c00[u]] + w1 * C0[x_c10[u]];
+                    const T a10 = w0 * C0[x_c01[u]] + w1 * C0[x_c11[u]];
+                    const T a01 = w0 * C1[x_c00[u]] + w1 * C1[x_c10[u]];
+                    const T a11 = w0 * C1[x_c01[u]] + w1 * C1[x_c11[u]];
+                    const T pe = w0 * (w0 * a00 + w1 * a10) + w1 * (w0 * a01 + w1 * a11);
+                    v = om * Bg[x_xi[u]] * s_invD[x_k[u] + kz] + pe;
+                }
+                Xg[x_xi[u]] = v;
             }
         };
-        const int cz0 = fz0 >> 1;
         PlaneRegs<T> pb;
-        commit_c(fetch_c(cz0 - 1), cz0 - 1);
-        commit_c(fetch_c(cz0), cz0);
+        // prologue: coarse planes cz0-1 (Cc role for g = fz0-1 -> Iz = cz0-1) and cz0
+        if (c_src >= 0) {
+            Cc[tid] = fetch_c(cz0 - 1);
+            Cp[tid] = fetch_c(cz0);
+        }
         fetch_plane(pb, bs, nf, plane, fz0 - 1, fx0 - 4, fy0 - 1, BH, tid);
-        commit_b(pb, fz0 - 1);
+        commit_b(pb, Bp);
         __syncthreads();
-        make_x(fz0 - 1);
+        make_x(fz0 - 1, Bp, Xp, Cc, Cp);  // odd g: planes Iz and Iz + 1
         fetch_plane(pb, bs, nf, plane, fz0, fx0 - 4, fy0 - 1, BH, tid);
         T pc = fetch_c(cz0 + 1);
         for (int g = fz0; g <= fz0 + SZ; ++g) {
-            if ((g & 1) == 0) commit_c(pc, (g >> 1) + 1);
-            commit_b(pb, g);
+            // rotate roles: plane g goes to the freed slot
+            {
+                T* t = Bm;
+                Bm = Bc;
+                Bc = Bp;
+                Bp = t;
+                t = Xm;
+                Xm = Xc;
+                Xc = Xp;
+                Xp = t;
+            }
+            if ((g & 1) == 0) {  // Z = g/2: coarse roles become (Z-1, Z, Z+1)
+                T* t = Cm;
+                Cm = Cc;
+                Cc = Cp;
+                Cp = t;
+                if (c_src >= 0) Cp[tid] = pc;
+            }
+            commit_b(pb, Bp);
             if (g + 1 <= fz0 + SZ) {
                 fetch_plane(pb, bs, nf, plane, g + 1, fx0 - 4, fy0 - 1, BH, tid);
                 if (((g + 1) & 1) == 0) pc = fetch_c(((g + 1) >> 1) + 1);
             }
             __syncthreads();
-            make_x(g);
+            if ((g & 1) == 0) make_x(g, Bp, Xp, Cc, Cm);  // even g: planes Iz and Iz - 1
+            else make_x(g, Bp, Xp, Cc, Cp);               // odd g: planes Iz and Iz + 1
             __syncthreads();
-            const int f = g - 1;  // output plane
-            if (f >= fz0 && tid < SX * SY / 4) {
-                const T* Xm = Xr + ring3(f - 1) * (PW * BH);
-                const T* Xc = Xr + ring3(f) * (PW * BH);
-                const T* Xp = Xr + ring3(f + 1) * (PW * BH);
-                const T* Bc = B + ring3(f) * (PW * BH);
+            const int f = g - 1;  // output plane: x planes f-1, f, f+1 = Xm, Xc, Xp; b(f) = Bc
+            if (f >= fz0 && has_out) {
                 const int kz = nb_count1(f, nf);
-                const int oy = tid / (SX / 4), ox0 = 4 * (tid - oy * (SX / 4));
-                const int gy = fy0 + oy;
-                const int ky = nb_count1(gy, nf);
                 V4<T> out;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int gx = fx0 + ox0 + e;
-                    const int xi = (ox0 + e + 4) + PW * (oy + 1);
+                    const int xi = o_xi + e;
                     const T x0 = Xc[xi];
                     const T nbs = (Xc[xi - 1] + Xc[xi + 1]) + (Xc[xi - PW] + Xc[xi + PW]) + (Xm[xi] + Xp[xi]);
-                    const int k0 = nb_count1(gx, nf) + ky + kz;
+                    const int k0 = o_k[e] + kz;
                     const T bv = Bc[xi];
                     const T yv = x0 + om * s_invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
                     out.v[e] = yv;
-                    dacc += (double)(bv * yv);
+                    dacc += bv * yv;
                 }
-                st4(ys + (fx0 + ox0) + (int64_t)nf * gy + plane * f, out);
+                st4(ys + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f, out);
             }
         }
         __syncthreads();
     }
     if (dot_part) {
-        const double tsum = block_sum<kTileThreads>(dacc, red);
+        const double tsum = block_sum<kTileThreads>((double)dacc, red);
         if (tid == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
     }
 }
@@ -586,6 +661,15 @@ void mg_plan_bind(MGPlan& plan, int S, T* scratch) {
     }
 }
 
+// z planes per CTA for the level sweeps: the longest march (fewest halo planes)
+// that still gives at least four CTAs per SM of a 152-SM GPU
+static int pick_sz(int nf, int S) {
+    const int base = (nf / SX) * (nf / SY);
+    for (int sz = 32; sz > 8; sz >>= 1)
+        if (nf % sz == 0 && (int64_t)base * (nf / sz) * S >= 4 * 152) return sz;
+    return 8;
+}
+
 template <typename T>
 static cudaError_t mg_attrs() {
     static bool done = false;  // set once per instantiation and process
@@ -594,7 +678,7 @@ static cudaError_t mg_attrs() {
                                          coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kDownSSmem * (int)sizeof(T));
+                                 kDownS2Smem * (int)sizeof(T));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kUpSSmem * (int)sizeof(T));
@@ -629,11 +713,12 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     int64_t in_stride = b_stride;
     for (int l = 0; l < plan.lc; ++l) {
         const int nf = n >> l, nc = nf >> 1;
-        const int ntiles = (nf / SX) * (nf / SY) * (nf / SZ);
+        const int sz = pick_sz(nf, S);
+        const int ntiles = (nf / SX) * (nf / SY) * (nf / sz);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
         prof_begin(PK_MG_DOWN, st);
-        k_mg_down<T><<<grid, dim3(32, 8), kDownSSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), in, in_stride, out,
+        k_mg_down<T><<<grid, dim3(32, 8), kDownS2Smem * sizeof(T), st>>>(nf, sz, level_coef<T>(plan, l), in, in_stride, out,
                                                     (int64_t)nc * nc * nc, active, act_stride);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
         in = out;
@@ -650,7 +735,8 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     int nblk0 = 1;
     for (int l = plan.lc - 1; l >= 0; --l) {
         const int nf = n >> l, nc = nf >> 1;
-        const int ntiles = (nf / SX) * (nf / SY) * (nf / SZ);
+        const int sz = pick_sz(nf, S);
+        const int ntiles = (nf / SX) * (nf / SY) * (nf / sz);
         const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
         dim3 grid(nb, S);
         const T* bl = (l == 0) ? b : static_cast<const T*>(plan.b[l]);
@@ -658,7 +744,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
         const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
         prof_begin(PK_MG_UP, st);
-        k_mg_up<T><<<grid, dim3(32, 8), kUpSSmem * sizeof(T), st>>>(nf, level_coef<T>(plan, l), bl, bls,
+        k_mg_up<T><<<grid, dim3(32, 8), kUpSSmem * sizeof(T), st>>>(nf, sz, level_coef<T>(plan, l), bl, bls,
                                                   static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
                                                   yls, (l == 0) ? dot_part : nullptr, active, act_stride);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);

@@ -283,6 +283,10 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     CUDA_TRY(cudaStreamSynchronize(st));
     int it = 0;
     int nactive = *ws.h_nact;
+    bool pending = false;  // a w/x update of the last iteration waits for the next pass
+    int last_itn = 0;
+    double last_cols = (double)S;
+    T* yprev = nullptr;
     while (nactive > 0 && it < o.max_iter) {
         const int chunk = std::min(o.check_every, o.max_iter - it);
         // bytes are counted for the columns active at the start of the chunk
@@ -290,9 +294,13 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
         plan.prof_cols = cols;
         for (int q = 0; q < chunk; ++q) {
             const int itn = it + q + 1;  // 1-based iteration of the columns that started together
+            // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
-            const int nA = launch_minres_A<T>(n, kh2, S, ycur, r1, ws.partA, ws.st, st);
-            prof_end(st, cols * (itn >= 2 ? 12.0 : 8.0) * n3d * w);
+            const int nA = launch_minres_A<T>(n, kh2, S, ycur, r1, ws.partA, ws.st, pending ? yprev : nullptr, w1,
+                                              w2, d, st);
+            prof_end(st, cols * (itn >= 2 ? 12.0 : 8.0) * n3d * w +
+                             (pending ? cols * (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0));
+            if (pending) std::swap(w1, w2);
             prof_begin(PK_ALPHA, st);
             CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, st));
             prof_end(st, cols * nA * 8.0);
@@ -304,12 +312,12 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             prof_begin(PK_GIVENS, st);
             CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, (q == chunk - 1) ? ws.nact : nullptr, st));
             prof_end(st, cols * (nB + nC) * 8.0);
-            prof_begin(PK_MINRES_D, st);
-            CUDA_TRY(launch_minres_D<T>(n3, S, ycur, w1, w2, d, ws.st, st));
-            prof_end(st, cols * (itn >= 3 ? 6.0 : (itn == 2 ? 5.0 : 3.0)) * n3d * w);
+            pending = true;
+            last_itn = itn;
+            last_cols = cols;
+            yprev = ycur;
             std::swap(r1, r2);
             std::swap(ycur, ynext);
-            std::swap(w1, w2);
         }
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -317,6 +325,12 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
         if (t_prof) t_prof->flush();
         it += chunk;
         nactive = *ws.h_nact;
+    }
+    if (pending) {
+        prof_begin(PK_MINRES_D, st);
+        CUDA_TRY(launch_minres_D<T>(n3, S, yprev, w1, w2, d, ws.st, st));
+        prof_end(st, last_cols * (last_itn >= 3 ? 6.0 : (last_itn == 2 ? 5.0 : 3.0)) * n3d * w);
+        std::swap(w1, w2);
     }
     *iters_out = it;
     return SPDE_OK;
