@@ -57,7 +57,8 @@ typedef enum {
     SPDE_ETIMEOUT = 5, /* reserved for bounded waits (no kernel of this library waits
                           on another CTA, so no current entry point returns it) */
     SPDE_ECUDA = 6,    /* a CUDA runtime call failed */
-    SPDE_EBUSY = 7     /* request queue full */
+    SPDE_EBUSY = 7,    /* request table full, or grids / meshes changed while requests are in flight */
+    SPDE_ECANCELED = 8 /* (spde_poll result) the request was cancelled */
 } spde_status;
 
 /* precision of the field solve */
@@ -87,6 +88,8 @@ typedef struct {
     int check_every;    /* MINRES iterations between host convergence checks; 8 */
     int device;         /* CUDA device ordinal; 0 */
     int use_graphs;     /* capture the batched MINRES iteration in CUDA graphs; 1 */
+    int64_t serve_budget_bytes; /* device memory the serving lanes may hold; 120 GiB */
+    int serve_max_batch;        /* columns per serving lane; 64 */
 } spde_opts;
 
 typedef struct {
@@ -136,6 +139,35 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
  * iterate. */
 spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma,
                         uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream);
+
+/* ---- serving (continuous batching) ---------------------------------------
+ * Requests for samples from several levels, kappas and sigmas are served
+ * concurrently.  Samples of one (level, kappa) run as columns of one batch
+ * ("lane": its own stream, host thread and workspace); a lane works in
+ * refinement steps and, at every step boundary, retires converged columns
+ * into their requests' outputs and admits queued samples into the freed
+ * columns.  Lanes are created on demand within opts.serve_budget_bytes and
+ * released after 200 ms idle.  Every sample follows exactly the arithmetic of
+ * spde_sample, so its result is the same alone or in any mix.
+ *
+ * Submit one request (non-blocking).  Arguments as spde_sample; `out` must
+ * be device memory and stay valid until the request is done; the context's
+ * precision must be SPDE_PREC_MIXED.  *request receives its id.  While any
+ * request is in flight, spde_level_add / spde_mesh_attach return SPDE_EBUSY. */
+spde_status spde_submit(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, uint64_t seed,
+                        uint64_t first_sample, int out_kind, void* out, int64_t* request);
+
+/* Poll a request: *done = 1 once all its samples are written (then *result
+ * holds its status -- SPDE_OK, SPDE_ENOCONV, SPDE_ECANCELED or a failure --
+ * and the request is forgotten), else 0.  *latency_ms: submit-to-completion
+ * time once done, else the time waited so far.  latency_ms and result may be
+ * NULL.  Unknown ids give SPDE_EINVAL. */
+spde_status spde_poll(spde_ctx* ctx, int64_t request, int* done, double* latency_ms, int* result);
+
+/* Cancel a request: samples not yet started are dropped, running ones are
+ * discarded at the next step boundary; spde_poll then reports SPDE_ECANCELED.
+ * The output buffer may hold partial results. */
+spde_status spde_cancel(spde_ctx* ctx, int64_t request);
 
 /* Bytes of device memory spde_sample(level, nsamples) needs beyond what the
  * level already holds (workspace of the selected precision path). */

@@ -16,17 +16,19 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspde.so")
 
-SPDE_OK, SPDE_EINVAL, SPDE_ENOMEM, SPDE_EMESH, SPDE_ENOCONV, SPDE_ETIMEOUT, SPDE_ECUDA, SPDE_EBUSY = range(8)
+SPDE_OK, SPDE_EINVAL, SPDE_ENOMEM, SPDE_EMESH, SPDE_ENOCONV, SPDE_ETIMEOUT, SPDE_ECUDA, SPDE_EBUSY, SPDE_ECANCELED = range(9)
 SPDE_PREC_MIXED, SPDE_PREC_FP64 = 0, 1
 SPDE_OUT_LOGNORMAL, SPDE_OUT_GAUSSIAN, SPDE_OUT_GRID_GAUSSIAN, SPDE_OUT_F64 = 0, 1, 2, 16
-STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EMESH", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "EBUSY"}
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EMESH", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "EBUSY",
+                8: "ECANCELED"}
 
 
 class spde_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("max_iter", ctypes.c_int), ("omega", ctypes.c_double),
                 ("schur_c", ctypes.c_double), ("flux_diag", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("device", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("device", ctypes.c_int), ("use_graphs", ctypes.c_int), ("serve_budget_bytes", ctypes.c_int64),
+                ("serve_max_batch", ctypes.c_int)]
 
 
 class spde_stats(ctypes.Structure):
@@ -50,6 +52,11 @@ _SIGS = {
     "spde_mesh_attach": [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int64, _P],
     "spde_sample": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                     ctypes.c_uint64, ctypes.c_int, _P, _P],
+    "spde_submit": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                    ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)],
+    "spde_poll": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_int)],
+    "spde_cancel": [_P, ctypes.c_int64],
     "spde_query_footprint": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "spde_get_stats": [_P, ctypes.POINTER(spde_stats)],
     "spde_mesh_info": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
@@ -150,6 +157,24 @@ def spde_mesh_attach(ctx, level, xyz, tets):
 def spde_sample(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out, stream=None):
     _check(lib().spde_sample(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, _ptr(out),
                              _stream(stream)))
+
+
+def spde_submit(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out):
+    rid = ctypes.c_int64()
+    _check(lib().spde_submit(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, _ptr(out),
+                             ctypes.byref(rid)))
+    return rid.value
+
+
+def spde_poll(ctx, request):
+    """(done, latency_ms, status) of a request; a done request is forgotten."""
+    done, lat, res = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().spde_poll(ctx, request, ctypes.byref(done), ctypes.byref(lat), ctypes.byref(res)))
+    return bool(done.value), lat.value, res.value
+
+
+def spde_cancel(ctx, request):
+    _check(lib().spde_cancel(ctx, request))
 
 
 def spde_query_footprint(ctx, level, nsamples):

@@ -41,6 +41,9 @@ cudaError_t launch_noise(int64_t ncells, int S, uint64_t seed, uint64_t first, d
 
 cudaError_t launch_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uint32_t* out, cudaStream_t st);
 
+cudaError_t launch_noise_cols(int64_t ncells, int S, const uint64_t* seed, const uint64_t* sample, const double* scale,
+                              const int* mask, double* out, int64_t col_stride, cudaStream_t st);
+
 // ---- stencil.cu (element type T = float or double)
 template <typename T>
 cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_t st);
@@ -119,6 +122,10 @@ cudaError_t launch_transpose_theta(int64_t ncell, int S, const double* x, int64_
 cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const int32_t* col,
                            const float* pi, const float* thetaT, int kind, int out64, void* out,
                            cudaStream_t st);
+cudaError_t launch_transpose_cols(int64_t ncell, int R, const int* cols, const double* x, int64_t x_stride,
+                                  double scale, float* thetaT, cudaStream_t st);
+cudaError_t launch_project_ptrs(int64_t ntets, int R, const int64_t* rowptr, const int32_t* col, const float* pi,
+                                const float* thetaT, int kind, int out64, void* const* outs, cudaStream_t st);
 // number of distinct column indices of a CSR matrix (cells touched by the projection)
 cudaError_t count_used_columns(int64_t nnz, const int32_t* col, int64_t ncell, int64_t* used, cudaStream_t st);
 // grid output: out[s][c] = scale * x[s][x_off + c]

@@ -671,9 +671,7 @@ static int pick_sz(int nf, int S) {
 }
 
 template <typename T>
-static cudaError_t mg_attrs() {
-    static bool done = false;  // set once per instantiation and process
-    if (done) return cudaSuccess;
+static cudaError_t mg_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
     if (e == cudaSuccess)
@@ -682,7 +680,13 @@ static cudaError_t mg_attrs() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kUpSSmem * (int)sizeof(T));
-    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+// once per instantiation and process (thread-safe static initialisation)
+template <typename T>
+static cudaError_t mg_attrs() {
+    static const cudaError_t e = mg_set_attrs<T>();
     return e;
 }
 

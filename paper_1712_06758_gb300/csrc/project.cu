@@ -129,6 +129,58 @@ cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_str
     return cudaGetLastError();
 }
 
+// thetaT[c][r] = float(scale * x[cols[r] * x_stride + c]) for the listed columns
+__global__ void k_transpose_cols(int64_t ncell, int R, const int* __restrict__ cols, const double* __restrict__ x,
+                                 int64_t x_stride, double scale, float* __restrict__ thetaT) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int r0 = blockIdx.y * 32;
+    for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+        const int r = r0 + rr;
+        const int64_t c = c0 + threadIdx.x;
+        tile[rr][threadIdx.x] = (r < R && c < ncell) ? (float)(scale * x[(int64_t)cols[r] * x_stride + c]) : 0.0f;
+    }
+    __syncthreads();
+    for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+        const int64_t c = c0 + rr;
+        const int r = r0 + threadIdx.x;
+        if (c < ncell && r < R) thetaT[c * R + r] = tile[threadIdx.x][rr];
+    }
+}
+
+cudaError_t launch_transpose_cols(int64_t ncell, int R, const int* cols, const double* x, int64_t x_stride,
+                                  double scale, float* thetaT, cudaStream_t st) {
+    dim3 grid((unsigned)((ncell + 31) / 32), (unsigned)((R + 31) / 32));
+    k_transpose_cols<<<grid, dim3(32, 8), 0, st>>>(ncell, R, cols, x, x_stride, scale, thetaT);
+    return cudaGetLastError();
+}
+
+// projection with one output pointer per column (same FP32 fmaf order as k_project_*)
+template <typename O>
+__global__ void __launch_bounds__(256) k_project_ptrs(int64_t ntets, int R, const int64_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col, const float* __restrict__ pi,
+                                                      const float* __restrict__ thetaT, int kind,
+                                                      O* const* __restrict__ outs) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntets) return;
+    const int64_t a = rowptr[t], b = rowptr[t + 1];
+    for (int r = 0; r < R; ++r) {
+        float acc = 0.0f;
+        for (int64_t j = a; j < b; ++j) acc = fmaf(pi[j], thetaT[(int64_t)col[j] * R + r], acc);
+        outs[r][t] = out_map<O>(acc, kind);
+    }
+}
+
+cudaError_t launch_project_ptrs(int64_t ntets, int R, const int64_t* rowptr, const int32_t* col, const float* pi,
+                                const float* thetaT, int kind, int out64, void* const* outs, cudaStream_t st) {
+    const unsigned nb = (unsigned)((ntets + 255) / 256);
+    if (out64)
+        k_project_ptrs<double><<<nb, 256, 0, st>>>(ntets, R, rowptr, col, pi, thetaT, kind, (double* const*)outs);
+    else
+        k_project_ptrs<float><<<nb, 256, 0, st>>>(ntets, R, rowptr, col, pi, thetaT, kind, (float* const*)outs);
+    return cudaGetLastError();
+}
+
 __global__ void k_mark_cols(int64_t nnz, const int32_t* __restrict__ col, unsigned char* __restrict__ flag) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x)
         flag[col[j]] = 1;

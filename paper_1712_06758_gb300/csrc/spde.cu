@@ -2,7 +2,13 @@
 // driver (noise -> FP64 iterative refinement around batched MINRES ->
 // projection + exp).  Every numerical step runs in this library's kernels.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -171,6 +177,10 @@ struct Level {
 
 }  // namespace
 
+namespace {
+struct Server;
+}
+
 struct spde_ctx {
     spde_opts opts;
     Profiler prof;
@@ -179,6 +189,7 @@ struct spde_ctx {
     spde_stats stats;
     void* out_tmp = nullptr;
     size_t out_tmp_bytes = 0;
+    Server* srv = nullptr;  // serving engine, started by the first spde_submit
 };
 
 namespace {
@@ -500,6 +511,459 @@ bool is_host_pointer(const void* p) {
 
 }  // namespace
 
+namespace {
+
+// ============================================================================
+// Serving: continuous batching of sample requests.
+//
+// One lane per (level, kappa): its own stream, worker thread and workspace of
+// `cap` columns.  A lane works in rounds; a round is one refinement step of
+// every occupied column (residual -> retire converged columns into their
+// requests' outputs -> one batched inner MINRES solve -> correction).  Free
+// columns take the next queued samples at every round boundary, so requests
+// that arrive while others run join the batch without waiting for it to
+// drain, and lanes of different levels / kappa overlap on the device.  Each
+// column follows exactly the per-column sequence of spde_sample, so a
+// sample's result does not depend on the mix it ran in.
+// ============================================================================
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServeReq {
+    int64_t id = 0;
+    int level = 0, nsamples = 0, out_kind = 0;
+    double kappa = 0.0, sigma = 0.0;
+    uint64_t seed = 0, first = 0;
+    void* out = nullptr;
+    int admitted = 0, finished = 0, dropped = 0;
+    bool cancelled = false, done = false;
+    spde_status status = SPDE_OK;
+    double t_submit = 0.0, t_done = 0.0;
+};
+using ReqPtr = std::shared_ptr<ServeReq>;
+
+struct Lane {
+    struct Slot {
+        ReqPtr req;
+        int j = -1;          // sample index within the request
+        int outer = 0;       // refinement steps done
+        bool used = false;
+        bool fresh = false;  // admitted this round
+        double fnorm2 = 0.0;
+    };
+    Server* srv = nullptr;
+    int level = 0;
+    double kappa = 0.0;
+    int cap = 0;
+    int64_t bytes = 0;
+    cudaStream_t st = nullptr;
+    Workspace ws;
+    std::deque<ReqPtr> queue;  // requests with samples not yet admitted (guarded by Server::mu)
+    std::vector<Slot> slots;
+    uint64_t *d_seed = nullptr, *d_sample = nullptr, *h_seed = nullptr, *h_sample = nullptr;
+    double *d_scale = nullptr, *h_scale = nullptr;
+    int *d_mask = nullptr, *h_mask = nullptr, *d_cols = nullptr, *h_cols = nullptr;
+    int *d_fresh = nullptr, *h_fresh = nullptr;  // separate buffer: its copy may still be pending
+    void **d_outs = nullptr, **h_outs = nullptr;
+    std::thread th;
+    std::condition_variable cv;
+    bool stop = false;
+    bool dead = false;
+};
+
+struct Server {
+    spde_ctx* ctx = nullptr;
+    std::mutex mu;
+    std::map<int64_t, ReqPtr> reqs;
+    std::deque<ReqPtr> pending;  // waiting for a lane (memory budget)
+    std::map<std::pair<int, double>, std::unique_ptr<Lane>> lanes;
+    std::vector<std::unique_ptr<Lane>> graveyard;  // exited lanes, joined outside their thread
+    int64_t next_id = 1;
+    int64_t used_bytes = 0;
+};
+
+int64_t lane_param_bytes(int cap) { return (int64_t)cap * (8 + 8 + 8 + 4 + 4 + 4 + 8) * 2; }
+
+void lane_free(Lane* L) {
+    L->ws.release();
+    dev_free(L->d_seed);
+    dev_free(L->d_sample);
+    dev_free(L->d_scale);
+    dev_free(L->d_mask);
+    dev_free(L->d_fresh);
+    dev_free(L->d_cols);
+    if (L->d_outs) cudaFree(L->d_outs);
+    L->d_outs = nullptr;
+    if (L->h_seed) cudaFreeHost(L->h_seed);
+    if (L->h_sample) cudaFreeHost(L->h_sample);
+    if (L->h_scale) cudaFreeHost(L->h_scale);
+    if (L->h_mask) cudaFreeHost(L->h_mask);
+    if (L->h_fresh) cudaFreeHost(L->h_fresh);
+    if (L->h_cols) cudaFreeHost(L->h_cols);
+    if (L->h_outs) cudaFreeHost(L->h_outs);
+    L->h_seed = L->h_sample = nullptr;
+    L->h_scale = nullptr;
+    L->h_mask = L->h_cols = L->h_fresh = nullptr;
+    L->h_outs = nullptr;
+    if (L->st) cudaStreamDestroy(L->st);
+    L->st = nullptr;
+    cudaGetLastError();
+}
+
+spde_status lane_alloc(Lane* L, int n) {
+    const int cap = L->cap;
+    if (cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPDE_ECUDA, "stream creation failed");
+    }
+    STATUS_TRY(ensure_workspace(L->ws, n, cap, false));
+    STATUS_TRY(dev_alloc(&L->d_seed, cap));
+    STATUS_TRY(dev_alloc(&L->d_sample, cap));
+    STATUS_TRY(dev_alloc(&L->d_scale, cap));
+    STATUS_TRY(dev_alloc(&L->d_mask, cap));
+    STATUS_TRY(dev_alloc(&L->d_fresh, cap));
+    STATUS_TRY(dev_alloc(&L->d_cols, cap));
+    if (cudaMalloc(&L->d_outs, cap * sizeof(void*)) != cudaSuccess ||
+        cudaMallocHost(&L->h_seed, cap * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMallocHost(&L->h_sample, cap * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMallocHost(&L->h_scale, cap * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&L->h_mask, cap * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&L->h_fresh, cap * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&L->h_cols, cap * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&L->h_outs, cap * sizeof(void*)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPDE_ENOMEM, "lane parameter allocation failed");
+    }
+    L->slots.assign(cap, Lane::Slot());
+    return SPDE_OK;
+}
+
+// One refinement step of every occupied column (no lock held).
+spde_status lane_round(Lane* L, std::vector<int>& finished) {
+    spde_ctx* ctx = L->srv->ctx;
+    const spde_opts& o = ctx->opts;
+    Level& LV = ctx->lev[L->level];
+    const int n = LV.n, S = L->cap;
+    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const double kh2 = (L->kappa * LV.h) * (L->kappa * LV.h);
+    Workspace& ws = L->ws;
+    cudaStream_t st = L->st;
+    finished.clear();
+    // fresh columns: noise, zero iterate, ||F||^2
+    bool any_fresh = false, any_old = false;
+    for (int c = 0; c < S; ++c) {
+        const Lane::Slot& sl = L->slots[c];
+        L->h_fresh[c] = (sl.used && sl.fresh) ? 1 : 0;
+        if (sl.used && sl.fresh) {
+            any_fresh = true;
+            L->h_seed[c] = sl.req->seed;
+            L->h_sample[c] = sl.req->first + (uint64_t)sl.j;
+            L->h_scale[c] = -g_half(L->kappa, sl.req->sigma) * LV.h;
+        } else {
+            L->h_seed[c] = 0;
+            L->h_sample[c] = 0;
+            L->h_scale[c] = 0.0;
+        }
+        if (sl.used && !sl.fresh) any_old = true;
+    }
+    if (any_fresh) {
+        CUDA_TRY(cudaMemcpyAsync(L->d_seed, L->h_seed, S * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(L->d_sample, L->h_sample, S * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(L->d_scale, L->h_scale, S * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(L->d_fresh, L->h_fresh, S * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(launch_noise_cols(n3, S, L->d_seed, L->d_sample, L->d_scale, L->d_fresh, ws.F, n3, st));
+        for (int c = 0; c < S; ++c)
+            if (L->h_fresh[c]) CUDA_TRY(cudaMemsetAsync(ws.x64 + (int64_t)c * N4, 0, N4 * sizeof(double), st));
+        const int nb = launch_sumsq(n3, S, ws.F, n3, ws.partR, st);
+        CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv + S, st));
+    }
+    // residual of every occupied column (flux rows exact from theta first)
+    for (int c = 0; c < S; ++c) L->h_mask[c] = L->slots[c].used ? 1 : 0;
+    CUDA_TRY(cudaMemcpyAsync(L->d_mask, L->h_mask, S * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (any_old) CUDA_TRY(launch_flux_from_theta(n, S, ws.x64, N4, ws.tri, st));
+    const int nbr = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, static_cast<float*>(ws.vec[4]), nullptr, ws.partR,
+                                      L->d_mask, st);
+    CUDA_TRY(launch_reduce(S, ws.partR, nbr, ws.colv, st));
+    CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> going;
+    for (int c = 0; c < S; ++c) {
+        Lane::Slot& sl = L->slots[c];
+        if (!sl.used) continue;
+        if (sl.fresh) sl.fnorm2 = ws.h_col[S + c];
+        sl.fresh = false;
+        const double rel = sl.fnorm2 > 0.0 ? std::sqrt(ws.h_col[c] / sl.fnorm2) : 0.0;
+        if (rel <= o.tol || sl.outer >= o.max_outer || sl.req->cancelled) {
+            if (rel > o.tol && !sl.req->cancelled) sl.req->status = SPDE_ENOCONV;
+            finished.push_back(c);
+        } else {
+            going.push_back(c);
+        }
+    }
+    // retire: write each finished column into its request's output
+    const double unscale = 1.0 / std::sqrt(LV.h);
+    for (int pass = 0; pass < 2; ++pass) {  // pass 0: float outputs, pass 1: double outputs
+        int R = 0;
+        int kind_any = -1;
+        for (int c : finished) {
+            const Lane::Slot& sl = L->slots[c];
+            if (sl.req->cancelled) continue;
+            const int kind = sl.req->out_kind & 15;
+            const int out64 = (sl.req->out_kind & SPDE_OUT_F64) ? 1 : 0;
+            if (out64 != pass) continue;
+            const size_t esz = out64 ? 8 : 4;
+            if (kind == SPDE_OUT_GRID_GAUSSIAN) {
+                void* dst = static_cast<char*>(sl.req->out) + (size_t)sl.j * n3 * esz;
+                CUDA_TRY(launch_grid_out(n3, 1, ws.x64 + (int64_t)c * N4 + 3 * n3, N4, unscale, out64, dst, st));
+            } else {
+                // tet outputs are grouped by kind below
+                (void)kind_any;
+            }
+        }
+        for (int kind = 0; kind < 2; ++kind) {
+            R = 0;
+            for (int c : finished) {
+                const Lane::Slot& sl = L->slots[c];
+                if (sl.req->cancelled) continue;
+                const int out64 = (sl.req->out_kind & SPDE_OUT_F64) ? 1 : 0;
+                if (out64 != pass || (sl.req->out_kind & 15) != kind) continue;
+                const size_t esz = out64 ? 8 : 4;
+                L->h_cols[R] = c;
+                L->h_outs[R] = static_cast<char*>(sl.req->out) + (size_t)sl.j * (size_t)LV.mesh.ntets * esz;
+                ++R;
+            }
+            if (R == 0) continue;
+            CUDA_TRY(cudaMemcpyAsync(L->d_cols, L->h_cols, R * sizeof(int), cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(L->d_outs, L->h_outs, R * sizeof(void*), cudaMemcpyHostToDevice, st));
+            CUDA_TRY(launch_transpose_cols(n3, R, L->d_cols, ws.x64 + 3 * n3, N4, unscale, ws.thetaT, st));
+            CUDA_TRY(launch_project_ptrs(LV.mesh.ntets, R, LV.mesh.rowptr, LV.mesh.col, LV.mesh.pi, ws.thetaT,
+                                         kind == SPDE_OUT_LOGNORMAL ? 0 : 1, pass, L->d_outs, st));
+            CUDA_TRY(cudaStreamSynchronize(st));  // host arrays are reused by the next group
+        }
+    }
+    // one inner MINRES solve for the columns still going, then the correction
+    if (!going.empty()) {
+        for (int c = 0; c < S; ++c) L->h_mask[c] = 0;
+        for (int c : going) L->h_mask[c] = 1;
+        CUDA_TRY(cudaMemcpyAsync(L->d_mask, L->h_mask, S * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(launch_set_active(S, L->d_mask, ws.st, st));
+        int its = 0;
+        STATUS_TRY(minres_batch<float>(o, n, kh2, S, ws, o.inner_tol, &its, st));
+        CUDA_TRY(launch_add_theta<float>(n3, S, ws.x64, static_cast<const float*>(ws.vec[0]), ws.st, st));
+        for (int c : going) L->slots[c].outer += 1;
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SPDE_OK;
+}
+
+void server_dispatch(Server* srv);  // lock held
+
+void lane_main(Lane* L) {
+    Server* srv = L->srv;
+    cudaSetDevice(srv->ctx->opts.device);
+    std::vector<int> finished;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            auto any_used = [&] {
+                for (auto& sl : L->slots)
+                    if (sl.used) return true;
+                return false;
+            };
+            if (!any_used() && L->queue.empty()) {
+                L->cv.wait_for(lk, std::chrono::milliseconds(200),
+                               [&] { return L->stop || !L->queue.empty(); });
+                if (!any_used() && L->queue.empty()) {
+                    // idle: give the memory back, let waiting requests use it
+                    L->dead = true;
+                    break;
+                }
+            }
+            if (L->stop && !any_used()) break;
+            // admit queued samples into free columns
+            for (auto& sl : L->slots) {
+                if (sl.used) continue;
+                while (!L->queue.empty() && (L->queue.front()->cancelled ||
+                                             L->queue.front()->admitted >= L->queue.front()->nsamples))
+                    L->queue.pop_front();
+                if (L->queue.empty()) break;
+                ReqPtr r = L->queue.front();
+                sl.req = r;
+                sl.j = r->admitted++;
+                sl.outer = 0;
+                sl.used = true;
+                sl.fresh = true;
+                sl.fnorm2 = 0.0;
+            }
+        }
+        const spde_status s = lane_round(L, finished);
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            const double t = now_s();
+            auto close_req = [&](const ReqPtr& r) {
+                if (!r->done && r->finished + r->dropped >= r->nsamples) {
+                    r->done = true;
+                    r->t_done = t;
+                }
+            };
+            if (s != SPDE_OK) {
+                // a CUDA or allocation failure ends every request in this lane
+                for (auto& sl : L->slots)
+                    if (sl.used) {
+                        sl.req->status = s;
+                        sl.req->dropped += 1;
+                        close_req(sl.req);
+                        sl.used = false;
+                        sl.req.reset();
+                    }
+                for (auto& r : L->queue) {
+                    r->status = s;
+                    r->dropped += r->nsamples - r->admitted;
+                    r->admitted = r->nsamples;
+                    close_req(r);
+                }
+                L->queue.clear();
+                continue;
+            }
+            for (int c : finished) {
+                Lane::Slot& sl = L->slots[c];
+                if (sl.req->cancelled) sl.req->dropped += 1;
+                else sl.req->finished += 1;
+                close_req(sl.req);
+                sl.used = false;
+                sl.req.reset();
+            }
+            for (auto& r : L->queue)
+                if (r->cancelled && r->admitted < r->nsamples) {
+                    r->dropped += r->nsamples - r->admitted;
+                    r->admitted = r->nsamples;
+                    close_req(r);
+                }
+        }
+    }
+    lane_free(L);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->used_bytes -= L->bytes;
+    L->dead = true;
+    auto it = srv->lanes.find({L->level, L->kappa});
+    if (it != srv->lanes.end() && it->second.get() == L) {
+        srv->graveyard.push_back(std::move(it->second));
+        srv->lanes.erase(it);
+    }
+    server_dispatch(srv);
+}
+
+// route pending requests to lanes, creating lanes within the memory budget (lock held)
+void server_dispatch(Server* srv) {
+    spde_ctx* ctx = srv->ctx;
+    const spde_opts& o = ctx->opts;
+    std::deque<ReqPtr> still;
+    while (!srv->pending.empty()) {
+        ReqPtr r = srv->pending.front();
+        srv->pending.pop_front();
+        if (r->cancelled) {
+            r->dropped = r->nsamples - r->finished;
+            r->admitted = r->nsamples;
+            if (!r->done) {
+                r->done = true;
+                r->t_done = now_s();
+            }
+            continue;
+        }
+        auto key = std::make_pair(r->level, r->kappa);
+        auto it = srv->lanes.find(key);
+        if (it != srv->lanes.end() && !it->second->dead) {
+            it->second->queue.push_back(r);
+            it->second->cv.notify_one();
+            continue;
+        }
+        if (it != srv->lanes.end()) {  // exiting lane: its thread releases its memory
+            srv->graveyard.push_back(std::move(it->second));
+            srv->lanes.erase(it);
+        }
+        const int n = ctx->lev[r->level].n;
+        const int64_t per_col = workspace_bytes(n, 1, false);
+        int cap = std::max(1, std::min(o.serve_max_batch, (int)(o.serve_budget_bytes / 4 / std::max<int64_t>(per_col, 1))));
+        while (cap > 1 && srv->used_bytes + workspace_bytes(n, cap, false) + lane_param_bytes(cap) > o.serve_budget_bytes)
+            cap /= 2;
+        const int64_t need = workspace_bytes(n, cap, false) + lane_param_bytes(cap);
+        if (srv->used_bytes + need > o.serve_budget_bytes) {
+            still.push_back(r);  // wait for a lane to free memory
+            continue;
+        }
+        std::unique_ptr<Lane> L(new Lane());
+        L->srv = srv;
+        L->level = r->level;
+        L->kappa = r->kappa;
+        L->cap = cap;
+        L->bytes = need;
+        cudaSetDevice(ctx->opts.device);
+        const spde_status s = lane_alloc(L.get(), n);
+        if (s != SPDE_OK) {
+            lane_free(L.get());
+            still.push_back(r);
+            if (srv->lanes.empty()) {  // nothing can free memory: fail the request
+                still.pop_back();
+                r->status = s;
+                r->dropped = r->nsamples;
+                r->admitted = r->nsamples;
+                r->done = true;
+                r->t_done = now_s();
+            }
+            continue;
+        }
+        srv->used_bytes += need;
+        L->queue.push_back(r);
+        Lane* raw = L.get();
+        srv->lanes[key] = std::move(L);
+        raw->th = std::thread(lane_main, raw);
+    }
+    srv->pending = std::move(still);
+}
+
+void server_reap(Server* srv) {  // join exited lanes (lock not held)
+    std::vector<std::unique_ptr<Lane>> g;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        g.swap(srv->graveyard);
+    }
+    for (auto& L : g)
+        if (L->th.joinable()) L->th.join();
+}
+
+void server_stop(Server* srv) {
+    std::vector<Lane*> ls;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (auto& r : srv->pending) r->cancelled = true;
+        srv->pending.clear();
+        for (auto& kv : srv->lanes) {
+            for (auto& r : kv.second->queue) r->cancelled = true;
+            kv.second->stop = true;
+            kv.second->cv.notify_all();
+            ls.push_back(kv.second.get());
+        }
+    }
+    for (;;) {  // lanes move themselves to the graveyard when they exit
+        server_reap(srv);
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->lanes.empty()) break;
+        for (auto& kv : srv->lanes) kv.second->cv.notify_all();
+        std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+    server_reap(srv);
+}
+
+bool serving_busy(spde_ctx* ctx) {
+    Server* srv = ctx->srv;
+    if (!srv) return false;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    return !srv->lanes.empty() || !srv->pending.empty() || !srv->reqs.empty();
+}
+
+}  // namespace
+
 namespace spde {
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace spde
@@ -520,6 +984,8 @@ spde_status spde_opts_init(spde_opts* o) {
     o->check_every = 8;
     o->device = 0;
     o->use_graphs = 1;
+    o->serve_budget_bytes = (int64_t)120 << 30;
+    o->serve_max_batch = 64;
     return SPDE_OK;
 }
 
@@ -534,6 +1000,8 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
         return fail(SPDE_EINVAL, "bad tolerance or iteration limits");
     if (!(o.omega > 0.0 && o.omega < 1.0)) return fail(SPDE_EINVAL, "omega must lie in (0, 1)");
     if (!(o.schur_c > 0.0) || !(o.flux_diag > 0.0)) return fail(SPDE_EINVAL, "preconditioner weights must be > 0");
+    if (o.serve_budget_bytes <= 0 || o.serve_max_batch < 1 || o.serve_max_batch > 65535)
+        return fail(SPDE_EINVAL, "bad serving budget or batch size");
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (o.device < 0 || o.device >= ndev) return fail(SPDE_EINVAL, "device %d not present", o.device);
@@ -556,6 +1024,7 @@ spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], 
         if (std::fabs((hi[a] - lo[a]) - ext) > 1e-12 * ext) return fail(SPDE_EINVAL, "cells must be cubes");
     }
     std::lock_guard<std::mutex> g(ctx->mu);
+    if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; grids cannot change");
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& L = ctx->lev[level];
     L.mesh.release();
@@ -573,6 +1042,7 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
     if (nverts < 4 || ntets < 1 || !xyz || !tets) return fail(SPDE_EINVAL, "empty mesh");
     if (ntets > (int64_t)1 << 31) return fail(SPDE_EINVAL, "too many tets");
     std::lock_guard<std::mutex> g(ctx->mu);
+    if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; meshes cannot change");
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& L = ctx->lev[level];
     L.mesh.release();
@@ -682,6 +1152,78 @@ spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, do
     return SPDE_OK;
 }
 
+spde_status spde_submit(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, uint64_t seed,
+                        uint64_t first_sample, int out_kind, void* out, int64_t* request) {
+    STATUS_TRY(check_level(ctx, level));
+    STATUS_TRY(check_params(kappa, sigma));
+    if (!request) return fail(SPDE_EINVAL, "null request pointer");
+    *request = 0;
+    if (nsamples < 1) return fail(SPDE_EINVAL, "nsamples must be >= 1");
+    const int kind = out_kind & 15;
+    if (kind > SPDE_OUT_GRID_GAUSSIAN || (out_kind & ~(15 | SPDE_OUT_F64))) return fail(SPDE_EINVAL, "bad out_kind");
+    if (!out) return fail(SPDE_EINVAL, "null output");
+    if (ctx->opts.precision != SPDE_PREC_MIXED) return fail(SPDE_EINVAL, "serving runs the mixed-precision path");
+    if (is_host_pointer(out)) return fail(SPDE_EINVAL, "serving writes device buffers only");
+    if (kind != SPDE_OUT_GRID_GAUSSIAN && !ctx->lev[level].mesh.rowptr)
+        return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!ctx->srv) {
+            ctx->srv = new Server();
+            ctx->srv->ctx = ctx;
+        }
+    }
+    Server* srv = ctx->srv;
+    server_reap(srv);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->reqs.size() >= 100000) return fail(SPDE_EBUSY, "request table full");
+    ReqPtr r = std::make_shared<ServeReq>();
+    r->id = srv->next_id++;
+    r->level = level;
+    r->nsamples = nsamples;
+    r->kappa = kappa;
+    r->sigma = sigma;
+    r->seed = seed;
+    r->first = first_sample;
+    r->out_kind = out_kind;
+    r->out = out;
+    r->t_submit = now_s();
+    srv->reqs[r->id] = r;
+    srv->pending.push_back(r);
+    server_dispatch(srv);
+    *request = r->id;
+    return SPDE_OK;
+}
+
+spde_status spde_poll(spde_ctx* ctx, int64_t request, int* done, double* latency_ms, int* result) {
+    if (!ctx || !done) return fail(SPDE_EINVAL, "null argument");
+    Server* srv = ctx->srv;
+    if (!srv) return fail(SPDE_EINVAL, "unknown request %lld", (long long)request);
+    server_reap(srv);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(request);
+    if (it == srv->reqs.end()) return fail(SPDE_EINVAL, "unknown request %lld", (long long)request);
+    const ReqPtr& r = it->second;
+    *done = r->done ? 1 : 0;
+    if (latency_ms) *latency_ms = r->done ? 1000.0 * (r->t_done - r->t_submit) : 1000.0 * (now_s() - r->t_submit);
+    if (result) *result = r->done ? (r->cancelled ? SPDE_ECANCELED : r->status) : SPDE_OK;
+    if (r->done) srv->reqs.erase(it);  // a finished request is reported once
+    return SPDE_OK;
+}
+
+spde_status spde_cancel(spde_ctx* ctx, int64_t request) {
+    if (!ctx) return fail(SPDE_EINVAL, "null context");
+    Server* srv = ctx->srv;
+    if (!srv) return fail(SPDE_EINVAL, "unknown request %lld", (long long)request);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(request);
+    if (it == srv->reqs.end()) return fail(SPDE_EINVAL, "unknown request %lld", (long long)request);
+    it->second->cancelled = true;
+    server_dispatch(srv);  // drops it if it still waits for a lane
+    for (auto& kv : srv->lanes) kv.second->cv.notify_one();
+    return SPDE_OK;
+}
+
 spde_status spde_query_footprint(spde_ctx* ctx, int level, int nsamples, int64_t* bytes) {
     STATUS_TRY(check_level(ctx, level));
     if (!bytes || nsamples < 0) return fail(SPDE_EINVAL, "bad argument");
@@ -742,6 +1284,11 @@ const char* spde_last_error(void) { return g_err.c_str(); }
 
 spde_status spde_destroy(spde_ctx* ctx) {
     if (!ctx) return SPDE_OK;
+    if (ctx->srv) {
+        server_stop(ctx->srv);
+        delete ctx->srv;
+        ctx->srv = nullptr;
+    }
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         cudaSetDevice(ctx->opts.device);
