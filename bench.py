@@ -36,6 +36,10 @@ WORKLOAD = {"workload": "spde_sampler_128cube_lprism96", "grid_n": 128, "kappa":
             "l2_note": "inputs larger than L2 (solver state ~21 GB per step)"}
 METRIC = "samples/s & p50/p99 latency at 1e-6 rel L2 vs plain FP64 GPU path, 128³ grid"
 
+# serving stream: 4-level hierarchy (grid n, L-prism cubes m), requests as the MLMC driver would send them
+SERVE_LEVELS = [(32, 24), (64, 48), (128, 96), (256, 192)]
+SERVE_KAPPAS = (10.0, 20.0, 40.0)
+
 
 # ---------------------------------------------------------------- host logic
 _T0 = time.time()
@@ -150,6 +154,70 @@ def kernel_traffic(name):
     if hashlib.sha256(blob).hexdigest() != rec["sources_sha256"]:
         return None
     return rec
+
+
+def serve_requests(nreq, rate, seed=7):
+    """Poisson arrivals; level ~ U{0..3}; nsamples = floor(exp(U(0, ln 256))) in [1, 256];
+    kappa in {10, 20, 40}; sigma ~ U(0.5, 2); an independent Philox seed per request."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    out = []
+    for k in range(nreq):
+        ns = int(min(256, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(256.0)))))))
+        out.append({"t": float(t[k]), "level": int(rng.integers(0, 4)), "nsamples": ns,
+                    "kappa": float(SERVE_KAPPAS[int(rng.integers(0, 3))]), "sigma": float(rng.uniform(0.5, 2.0)),
+                    "seed": int(rng.integers(1, 2 ** 62))})
+    return out
+
+
+def run_serving(pkg, smp, outbufs, reqs, poll_sleep=0.0005):
+    """Open-loop submission at the requests' arrival times; latency = submit -> done (library clock)."""
+    import numpy as np
+    t0 = time.perf_counter()
+    pending, lat, statuses = {}, [], []
+    samples = 0
+
+    def poll_all():
+        for rid in list(pending):
+            done, ms, st = pkg.spde_poll(smp.ctx, rid)
+            if done:
+                lat.append(ms)
+                statuses.append(st)
+                del pending[rid]
+
+    for r in reqs:
+        while time.perf_counter() - t0 < r["t"]:
+            poll_all()
+            time.sleep(poll_sleep)
+        rid = pkg.spde_submit(smp.ctx, r["level"], r["nsamples"], r["kappa"], r["sigma"], r["seed"], 0,
+                              pkg.SPDE_OUT_LOGNORMAL, outbufs[r["level"]])
+        pending[rid] = r
+        samples += r["nsamples"]
+    while pending:
+        poll_all()
+        time.sleep(poll_sleep)
+    span = time.perf_counter() - t0
+    lat = np.sort(np.array(lat))
+    return {"requests": len(reqs), "samples": samples, "makespan_s": span, "samples_per_s": samples / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "all_ok": all(st == pkg.SPDE_OK for st in statuses)}
+
+
+def serving_setup(pkg, local):
+    """Sampler with the 4-level hierarchy and per-level shared output buffers (throughput runs
+    overwrite them; serving correctness is covered by the tests)."""
+    import torch
+    from synth import lprism_mesh
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=1e-8, device=local)
+    outbufs = {}
+    for lvl, (n, m) in enumerate(SERVE_LEVELS):
+        xyz, tets = lprism_mesh(m)
+        smp.add_level(lvl, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+        smp.attach_mesh(lvl, xyz, tets)
+        outbufs[lvl] = torch.empty((256, len(tets)), dtype=torch.float32, device="cuda")
+        del xyz, tets
+    return smp, outbufs
 
 
 # ---------------------------------------------------------------- CPU oracle arm
@@ -320,6 +388,16 @@ def run_ours(args):
     e2e = {"value": world * args.steps * S / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": int(S * ntets * 4)}
 
+    # serving: a bounded open-loop stream on the 4-level hierarchy (tol 1e-8)
+    log("serving")
+    smp_s, outbufs = serving_setup(pkg, local)
+    serving = run_serving(pkg, smp_s, outbufs, serve_requests(args.serve_requests, args.serve_rate, seed=7 + rank))
+    serving.update({"rate_req_per_s": args.serve_rate, "levels": [n for n, _ in SERVE_LEVELS],
+                    "meshes": ["L-prism %d^3 cubes" % m for _, m in SERVE_LEVELS], "tol": 1e-8,
+                    "budget_GiB": 120, "note": "open loop, Poisson arrivals; latency = submit to completion"})
+    smp_s.close()
+    del outbufs
+
     line = None
     if rank == 0:
         # plain FP64 path on the same workload (first samples of step 0), and the field difference
@@ -353,6 +431,7 @@ def run_ours(args):
                 "config": dict(W, parallelism="samples sharded over %d rank(s)" % world),
                 "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                "per": "one %d-sample batch call" % S},
+                "serving": serving,
                 "plain_fp64": {"value": plain_rate, "unit": "samples/s", "samples": nplain,
                                "ratio": value / world / plain_rate, "inner_iters": pst["inner_iters"],
                                "max_rel_l2_vs_mixed": float(d.max())},
@@ -370,6 +449,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve_sweep(args):
+    """The serving sweep: rates 10, 30, 100, 300, 1000 req/s, fixed request count per rate."""
+    import torch
+    import paper_1712_06758_gb300 as pkg
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    smp, outbufs = serving_setup(pkg, local)
+    rows = []
+    for rate in (10.0, 30.0, 100.0, 300.0, 1000.0):
+        log("serving at %g req/s" % rate)
+        r = run_serving(pkg, smp, outbufs, serve_requests(args.serve_requests, rate, seed=int(rate)))
+        r["rate_req_per_s"] = rate
+        rows.append(r)
+    smp.close()
+    print(json.dumps({"metric": "serving latency p50/p99 and samples/s vs request rate", "levels":
+                      [n for n, _ in SERVE_LEVELS], "tol": 1e-8, "rows": rows}), flush=True)
+
+
 def main(argv=None):
     import faulthandler
     faulthandler.dump_traceback_later(120, repeat=True, file=sys.stderr)
@@ -381,9 +478,14 @@ def main(argv=None):
     ap.add_argument("--plain-samples", type=int, default=8)
     ap.add_argument("--batch", type=int, default=0, help="override the 64-sample batch (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="headline loop only (profiling runs)")
+    ap.add_argument("--serve-rate", type=float, default=10.0, help="request rate of the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving stream")
+    ap.add_argument("--serve-sweep", action="store_true", help="only the serving sweep over 10..1000 req/s")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_sweep:
+        run_serve_sweep(args)
     else:
         run_ours(args)
 

@@ -7,10 +7,13 @@
 // tau cap c consists of (a) the tet's faces clipped to the cell and (b) the
 // cell's faces clipped to the tet.  With every face polygon oriented
 // outward, 6 V = sum over faces, over fan triangles (v0, vi, vi+1), of
-// v0 . (vi x vi+1).  Polygons are clipped by Sutherland-Hodgman with signed
-// distances snapped to zero within EPS, and a tet face lying on a cell
-// plane with the same outward direction is left to (b), so a shared face is
-// counted once.  Coordinates are cell-local and scaled by 1/h.
+// v0 . (vi x vi+1).  Coordinates are cell-local and scaled by 1/h; tet
+// vertex coordinates within EPS of a cell plane (0 or 1) are first moved
+// onto it, and all sign tests are then exact, so parts (a) and (b) agree on
+// every shared boundary (a face on a cell plane gets an exactly
+// axis-aligned normal and exactly zero distances).  A tet face lying on a
+// cell plane with the same outward direction is left to (b), so a shared
+// face is counted once.
 //
 // Build: per tet, candidate cells from its bounding box -> exclusive scan ->
 // volumes of all candidates -> scan of the nonzero counts -> CSR.
@@ -40,7 +43,7 @@ __device__ __forceinline__ void set_comp(D3& a, int ax, double v) {
 }
 
 constexpr int kPolyMax = 12;
-constexpr double kEps = 1e-12;
+constexpr double kSnap = 1e-12;  // cell units: vertex coordinates this close to 0 or 1 are moved onto the plane
 
 // fan sum of v0 . (vi x vi+1) over a polygon
 __device__ __forceinline__ double fan6(const D3* p, int m) {
@@ -54,9 +57,7 @@ __device__ int clip_axis(const D3* in, int m, D3* out, int ax, double bound, dou
     int k = 0;
     for (int i = 0; i < m; ++i) {
         const D3 a = in[i], b = in[(i + 1) % m];
-        double da = (comp(a, ax) - bound) * sgn, db = (comp(b, ax) - bound) * sgn;
-        if (fabs(da) <= kEps) da = 0.0;
-        if (fabs(db) <= kEps) db = 0.0;
+        const double da = (comp(a, ax) - bound) * sgn, db = (comp(b, ax) - bound) * sgn;
         if (da <= 0.0 && k < kPolyMax) out[k++] = a;
         if ((da < 0.0 && db > 0.0) || (da > 0.0 && db < 0.0)) {
             D3 x = a + (da / (da - db)) * (b - a);
@@ -72,9 +73,7 @@ __device__ int clip_plane(const D3* in, int m, D3* out, D3 n, double d) {
     int k = 0;
     for (int i = 0; i < m; ++i) {
         const D3 a = in[i], b = in[(i + 1) % m];
-        double da = dot3(n, a) - d, db = dot3(n, b) - d;
-        if (fabs(da) <= kEps) da = 0.0;
-        if (fabs(db) <= kEps) db = 0.0;
+        const double da = dot3(n, a) - d, db = dot3(n, b) - d;
         if (da <= 0.0 && k < kPolyMax) out[k++] = a;
         if ((da < 0.0 && db > 0.0) || (da > 0.0 && db < 0.0)) {
             if (k < kPolyMax) out[k++] = a + (da / (da - db)) * (b - a);
@@ -104,8 +103,8 @@ __device__ double tet_unit_cube_volume(const D3 p[4]) {
         for (int ax = 0; ax < 3 && !skip; ++ax) {
             const double na = comp(nv, ax);
             const double ca = comp(a, ax), cb = comp(b, ax), cc = comp(c, ax);
-            if (na > 0.5 && fabs(ca - 1.0) <= kEps && fabs(cb - 1.0) <= kEps && fabs(cc - 1.0) <= kEps) skip = true;
-            if (na < -0.5 && fabs(ca) <= kEps && fabs(cb) <= kEps && fabs(cc) <= kEps) skip = true;
+            if (na > 0.5 && ca == 1.0 && cb == 1.0 && cc == 1.0) skip = true;
+            if (na < -0.5 && ca == 0.0 && cb == 0.0 && cc == 0.0) skip = true;
         }
         if (skip) continue;
         bufA[0] = a;
@@ -243,7 +242,14 @@ __global__ void k_tet_clip(ClipGrid g, const double* __restrict__ xyz, int64_t n
             for (int i = r[0]; i <= r[1]; ++i) {
                 const D3 c0{g.lo[0] + i * g.h, g.lo[1] + j * g.h, g.lo[2] + k * g.h};
                 D3 q[4];
-                for (int v = 0; v < 4; ++v) q[v] = ih * (p[v] - c0);
+                for (int v = 0; v < 4; ++v) {
+                    q[v] = ih * (p[v] - c0);
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const double x = comp(q[v], ax);
+                        if (fabs(x) <= kSnap) set_comp(q[v], ax, 0.0);
+                        else if (fabs(x - 1.0) <= kSnap) set_comp(q[v], ax, 1.0);
+                    }
+                }
                 double v = tet_unit_cube_volume(q);
                 if (!(v > 1e-14)) v = 0.0;
                 else ++cnt;

@@ -185,6 +185,45 @@ def test_clip_matches_oracle(case):
     smp.close()
 
 
+# Tets of the jittered 192^3-cube L-prism (seed 1) around tet 15898757, whose
+# vertices lie within rounding of the 256^3 grid planes z = 0.5 and x = 0.05
+# (on the outer face): a configuration where inconsistent tolerances in the
+# clipping once left a sliver of the intersection surface open.
+NEAR_PLANE_XYZ = [[0.4964294809383716, 0.7293650418560711, 0.49456028756468584], [0.05, 0.734375, 0.4953125],
+                  [0.05355736155541837, 0.734459848836528, 0.4948498762023506],
+                  [0.05852057207050046, 0.7353840591258433, 0.4954273461282783], [0.05, 0.7390625000000001, 0.4953125],
+                  [0.05509514229698885, 0.7382908577087337, 0.495951502032792],
+                  [0.05909978334196638, 0.7388096298173595, 0.49416448731158635],
+                  [0.4950461197617592, 0.7305617978133694, 0.5007409101409984], [0.05, 0.734375, 0.49999999999999994],
+                  [0.055500692284403796, 0.7355042826276564, 0.5008434084846913],
+                  [0.05916945957529681, 0.7348260817433576, 0.5003229827332125],
+                  [0.4943341457401298, 0.7350223236231647, 0.5009075124864458],
+                  [0.49999999999999994, 0.734375, 0.49999999999999994],
+                  [0.05, 0.7390625000000001, 0.49999999999999994],
+                  [0.054071817109563554, 0.7392692841949706, 0.500000417513931],
+                  [0.05925084593838861, 0.7401303576354158, 0.4994870852676509]]
+NEAR_PLANE_TETS = [[1, 2, 5, 14], [1, 2, 14, 9], [1, 4, 14, 5], [1, 4, 13, 14], [1, 8, 9, 14], [1, 8, 14, 13],
+                   [2, 3, 6, 15], [2, 3, 15, 10], [2, 5, 15, 6], [2, 5, 14, 15], [2, 9, 10, 15]]
+
+
+def test_clip_vertices_near_grid_planes():
+    n = 256
+    xyz = np.array(NEAR_PLANE_XYZ)
+    tets = np.array(NEAR_PLANE_TETS, dtype=np.int32)
+    smp = pkg.Sampler()
+    smp.add_level(0, n)
+    smp.attach_mesh(0, xyz, tets)  # the library checks every row sum to 1e-10
+    rowptr, col, g, vol = _gpu_rows(smp, 0)
+    rs = np.add.reduceat(g, rowptr[:-1])
+    assert np.allclose(rs, vol, rtol=1e-13, atol=0)
+    rows = clip.coupling_rows(xyz, tets, n)
+    for t, ref in rows.items():
+        got = dict(zip(col[rowptr[t]:rowptr[t + 1]].tolist(), g[rowptr[t]:rowptr[t + 1]].tolist()))
+        for c in set(ref) | set(got):
+            assert abs(got.get(c, 0.0) - ref.get(c, 0.0)) <= 1e-12 / n ** 3, (t, c)
+    smp.close()
+
+
 def test_clip_column_sums_match_domain_overlap():
     """Sum over tets of G[tau][c] = |c cap D| for the box domain D (closed form)."""
     lo, hi, n = 0.15, 0.85, 16
