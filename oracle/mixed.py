@@ -181,8 +181,8 @@ def solve_dct(n, kappa, sigma, xi, h=None):
     xi = np.asarray(xi, dtype=np.float64)
     batch = xi.reshape(-1, n, n, n)  # [S, z, y, x]
     f = h ** 1.5 * batch
-    th = scipy.fft.idctn(scipy.fft.dctn(f, type=2, norm="ortho", axes=(1, 2, 3)) / lam,
-                         type=2, norm="ortho", axes=(1, 2, 3))
+    th = scipy.fft.idctn(scipy.fft.dctn(f, type=2, norm="ortho", axes=(1, 2, 3), workers=-1) / lam,
+                         type=2, norm="ortho", axes=(1, 2, 3), workers=-1)
     return (g_normaliser(kappa, sigma) * th).reshape(xi.shape)
 
 
