@@ -140,6 +140,21 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
 spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma,
                         uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream);
 
+/* Coupled two-level samples (Sec. 6.2, multilevel sampler): the white noise
+ * is drawn once on the fine level and restricted to the coarse one by
+ * summing the 8 children of every coarse cell (the restricted noise has
+ * exactly the coarse covariance); the coarse level is solved first and the
+ * fine solve starts from its piecewise-constant prolongation.  Sample i is
+ * Philox sample first_sample + i on the FINE grid, so out_fine equals
+ * spde_sample(fine_level, ...) up to the solver tolerance.
+ *   coarse_level must have n_c = n_f / 2 on the same box;
+ *   out_fine   device [nsamples][fine outputs], out_coarse device
+ *   [nsamples][coarse outputs] (layout of out_kind on each level).
+ * Synchronises `stream`; SPDE_ENOCONV as spde_sample. */
+spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level, int nsamples, double kappa,
+                                double sigma, uint64_t seed, uint64_t first_sample, int out_kind, void* out_fine,
+                                void* out_coarse, void* stream);
+
 /* ---- serving (continuous batching) ---------------------------------------
  * Requests for samples from several levels, kappas and sigmas are served
  * concurrently.  Samples of one (level, kappa) run as columns of one batch

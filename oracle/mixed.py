@@ -244,3 +244,30 @@ def neumann_image_variance(x, kappa, sigma, box=1.0, nimg=3):
                 r = math.dist(x, img)
                 tot += math.exp(-kappa * r)
     return sigma ** 2 * tot
+
+
+def restrict_noise(xi_f, n_f):
+    """Coarse normals of a coupled two-level sample (Sec. 6.2).
+
+    The coarse right-hand side is P^T applied to the fine one, f_c = P^T
+    W_f^{1/2} xi_f with P the piecewise-constant prolongation (each coarse
+    cell's value copied to its 8 children).  Written as f_c = W_c^{1/2} xi_c,
+    xi_c = W_c^{-1/2} P^T W_f^{1/2} xi_f.  Input/output flat, x fastest.
+    """
+    n_c = n_f // 2
+    h_f = 1.0 / n_f
+    h_c = 1.0 / n_c
+    f = (h_f ** 1.5) * np.asarray(xi_f, dtype=np.float64).reshape(n_f, n_f, n_f)
+    fc = f.reshape(n_c, 2, n_c, 2, n_c, 2).sum(axis=(1, 3, 5))
+    return (fc / h_c ** 1.5).ravel()
+
+
+def restriction_matrix(n_f):
+    """Dense P^T (coarse x fine) of the piecewise-constant prolongation."""
+    n_c = n_f // 2
+    r = np.zeros((n_c ** 3, n_f ** 3))
+    for k in range(n_f):
+        for j in range(n_f):
+            for i in range(n_f):
+                r[(i // 2) + n_c * ((j // 2) + n_c * (k // 2)), i + n_f * (j + n_f * k)] = 1.0
+    return r

@@ -52,6 +52,8 @@ _SIGS = {
     "spde_mesh_attach": [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int64, _P],
     "spde_sample": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                     ctypes.c_uint64, ctypes.c_int, _P, _P],
+    "spde_sample_coupled": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _P, _P, _P],
     "spde_submit": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                     ctypes.c_uint64, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int64)],
     "spde_poll": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
@@ -157,6 +159,12 @@ def spde_mesh_attach(ctx, level, xyz, tets):
 def spde_sample(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out, stream=None):
     _check(lib().spde_sample(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, _ptr(out),
                              _stream(stream)))
+
+
+def spde_sample_coupled(ctx, fine_level, coarse_level, nsamples, kappa, sigma, seed, first_sample, out_kind,
+                        out_fine, out_coarse, stream=None):
+    _check(lib().spde_sample_coupled(ctx, fine_level, coarse_level, nsamples, kappa, sigma, seed, first_sample,
+                                     out_kind, _ptr(out_fine), _ptr(out_coarse), _stream(stream)))
 
 
 def spde_submit(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out):

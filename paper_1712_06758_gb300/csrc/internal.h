@@ -60,6 +60,11 @@ cudaError_t launch_flux_from_theta(int n, int S, double* x, int64_t col_stride, 
 // x cell block += d ([S][n^3]) for columns whose inner solve ran
 template <typename T>
 cudaError_t launch_add_theta(int64_t n3, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st);
+// two-level coupling: F_c = (1/sqrt 2) sum over children of F_f; theta~_f = theta~_c(parent) / sqrt 2
+cudaError_t launch_restrict_rhs(int nc, int S, const double* Ff, int64_t f_stride, double* Fc, int64_t c_stride,
+                                cudaStream_t st);
+cudaError_t launch_inject_theta(int nc, int S, const double* xc, int64_t c_stride, double* xf, int64_t f_stride,
+                                cudaStream_t st);
 // partial sums of a.a over columns of a strided array; returns nblk
 int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* part, cudaStream_t st);
 // out[s] = sum_b part[s][b] (fixed order)

@@ -352,7 +352,7 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
 // residual in *maxrel.
 template <typename T>
 spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws, double* maxrel, int* outer_out,
-                         int* inner_out, cudaStream_t st) {
+                         int* inner_out, cudaStream_t st, bool warm = false) {
     const spde_opts& o = ctx->opts;
     const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
     // ||F||^2 per column
@@ -362,7 +362,8 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
     prof_begin(PK_OTHER, st);
     CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv + S, st));
     prof_end(st, (double)S * nb * 8.0);
-    CUDA_TRY(cudaMemsetAsync(ws.x64, 0, (size_t)S * N4 * sizeof(double), st));
+    // cold start: x = 0; warm start: the caller filled the cell block of x (flux recomputed below)
+    if (!warm) CUDA_TRY(cudaMemsetAsync(ws.x64, 0, (size_t)S * N4 * sizeof(double), st));
     std::vector<int> mask(S, 1);
     int* d_mask = reinterpret_cast<int*>(ws.colv);  // reuse first S doubles' storage after use
     int outer = 0, inner_total = 0;
@@ -372,7 +373,7 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         // r = [0; F] - A x (FP64) -> r2 (inner type); ||r||^2
         float* r32 = std::is_same<T, float>::value ? reinterpret_cast<float*>(r2) : nullptr;
         double* r64 = std::is_same<T, double>::value ? reinterpret_cast<double*>(r2) : nullptr;
-        if (outer > 0) {
+        if (outer > 0 || warm) {
             // flux rows exact for the current cell field: u = -T^{-1} D1^T theta
             prof_begin(PK_FLUX, st);
             CUDA_TRY(launch_flux_from_theta(n, S, ws.x64, N4, ws.tri, st));
@@ -1221,6 +1222,85 @@ spde_status spde_cancel(spde_ctx* ctx, int64_t request) {
     it->second->cancelled = true;
     server_dispatch(srv);  // drops it if it still waits for a lane
     for (auto& kv : srv->lanes) kv.second->cv.notify_one();
+    return SPDE_OK;
+}
+
+spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level, int nsamples, double kappa,
+                                double sigma, uint64_t seed, uint64_t first_sample, int out_kind, void* out_fine,
+                                void* out_coarse, void* stream) {
+    STATUS_TRY(check_level(ctx, fine_level));
+    STATUS_TRY(check_level(ctx, coarse_level));
+    STATUS_TRY(check_params(kappa, sigma));
+    if (nsamples < 0) return fail(SPDE_EINVAL, "nsamples < 0");
+    const int kind = out_kind & 15;
+    if (kind > SPDE_OUT_GRID_GAUSSIAN || (out_kind & ~(15 | SPDE_OUT_F64))) return fail(SPDE_EINVAL, "bad out_kind");
+    if (nsamples == 0) return SPDE_OK;
+    if (!out_fine || !out_coarse) return fail(SPDE_EINVAL, "null output");
+    if (is_host_pointer(out_fine) || is_host_pointer(out_coarse)) return fail(SPDE_EINVAL, "device outputs only");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& F = ctx->lev[fine_level];
+    Level& C = ctx->lev[coarse_level];
+    if (F.n != 2 * C.n || std::fabs(F.h * 2 - C.h) > 1e-12 * C.h)
+        return fail(SPDE_EINVAL, "coarse grid must be the fine grid coarsened once (n_c = n_f / 2, same box)");
+    for (int a = 0; a < 3; ++a)
+        if (std::fabs(F.lo[a] - C.lo[a]) > 1e-12 * C.h) return fail(SPDE_EINVAL, "levels must share the box");
+    if (kind != SPDE_OUT_GRID_GAUSSIAN && (!F.mesh.rowptr || !C.mesh.rowptr))
+        return fail(SPDE_EINVAL, "both levels need a mesh for tet outputs");
+    ProfScope ps(ctx->prof);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
+    const size_t esz = (out_kind & SPDE_OUT_F64) ? 8 : 4;
+    ctx->stats.outer_iters = 0;
+    ctx->stats.inner_iters = 0;
+    ctx->stats.max_rel_residual = 0.0;
+    int cap = 1;
+    if (!plain) {
+        const int64_t per = workspace_bytes(F.n, 1, false) + workspace_bytes(C.n, 1, false);
+        size_t freeb = 0, totb = 0;
+        if (F.ws.n != F.n || F.ws.S < nsamples || C.ws.n != C.n || C.ws.S < nsamples || F.ws.inner64 != 0 ||
+            C.ws.inner64 != 0) {
+            F.ws.release();
+            C.ws.release();
+            if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) cudaGetLastError();
+            cap = std::max(1, std::min(nsamples, (int)((0.85 * (double)freeb) / (double)std::max<int64_t>(per, 1))));
+        } else {
+            cap = nsamples;
+        }
+    }
+    const int64_t nf3 = (int64_t)F.n * F.n * F.n, nc3 = (int64_t)C.n * C.n * C.n;
+    spde_status worst = SPDE_OK;
+    for (int s0 = 0; s0 < nsamples; s0 += cap) {
+        const int S = std::min(cap, nsamples - s0);
+        STATUS_TRY(ensure_workspace(F.ws, F.n, plain ? 1 : std::min(cap, nsamples), plain));
+        STATUS_TRY(ensure_workspace(C.ws, C.n, plain ? 1 : std::min(cap, nsamples), plain));
+        // fine noise, then its restriction (Sec. 6.2: the same xi drives both levels)
+        CUDA_TRY(launch_noise(nf3, S, seed, first_sample + (uint64_t)s0, -g_half(kappa, sigma) * F.h, F.ws.F, nf3, st));
+        CUDA_TRY(launch_restrict_rhs(C.n, S, F.ws.F, nf3, C.ws.F, nc3, st));
+        double rel = 0.0;
+        int outer = 0, inner = 0;
+        const double khc = (kappa * C.h) * (kappa * C.h), khf = (kappa * F.h) * (kappa * F.h);
+        spde_status sc = plain ? refine_solve<double>(ctx, C.n, khc, S, C.ws, &rel, &outer, &inner, st)
+                               : refine_solve<float>(ctx, C.n, khc, S, C.ws, &rel, &outer, &inner, st);
+        if (sc != SPDE_OK && sc != SPDE_ENOCONV) return sc;
+        if (sc == SPDE_ENOCONV) worst = sc;
+        ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
+        // fine solve started from the coarse field (Sec. 6.2, coarse solution as initial guess)
+        CUDA_TRY(launch_inject_theta(C.n, S, C.ws.x64, 4 * nc3, F.ws.x64, 4 * nf3, st));
+        spde_status sf = plain ? refine_solve<double>(ctx, F.n, khf, S, F.ws, &rel, &outer, &inner, st, true)
+                               : refine_solve<float>(ctx, F.n, khf, S, F.ws, &rel, &outer, &inner, st, true);
+        if (sf != SPDE_OK && sf != SPDE_ENOCONV) return sf;
+        if (sf == SPDE_ENOCONV) worst = sf;
+        ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
+        ctx->stats.inner_iters = std::max(ctx->stats.inner_iters, inner);
+        ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
+        const size_t perf = out_elem_count(F, 1, out_kind), perc = out_elem_count(C, 1, out_kind);
+        STATUS_TRY(write_output(F, S, out_kind, static_cast<char*>(out_fine) + (size_t)s0 * perf * esz, st));
+        STATUS_TRY(write_output(C, S, out_kind, static_cast<char*>(out_coarse) + (size_t)s0 * perc * esz, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->prof.flush();
+    if (worst != SPDE_OK) return fail(worst, "tolerance not reached: %.3e", ctx->stats.max_rel_residual);
     return SPDE_OK;
 }
 

@@ -246,4 +246,67 @@ cudaError_t launch_add_theta(int64_t n3, int S, double* x, const T* d, const Min
 template cudaError_t launch_add_theta<float>(int64_t, int, double*, const float*, const MinresCol*, cudaStream_t);
 template cudaError_t launch_add_theta<double>(int64_t, int, double*, const double*, const MinresCol*, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Two-level coupling (Sec. 6.2): the coarse white-noise right-hand side is the
+// fine one summed over the 8 children of each coarse cell (P^T f; with
+// f = W^{1/2} xi this has exactly the coarse covariance W_c).  In the scaled
+// system (cell rows scaled by h^{-1/2}) that is F_c = (1/sqrt 2) sum F_f.
+// ---------------------------------------------------------------------------
+__global__ void k_restrict_rhs(int nc, const double* __restrict__ Ff, int64_t f_stride, double* __restrict__ Fc,
+                               int64_t c_stride) {
+    const int s = blockIdx.y;
+    const int nf = 2 * nc;
+    const int64_t nc3 = (int64_t)nc * nc * nc;
+    const double* fs = Ff + (int64_t)s * f_stride;
+    double* cs = Fc + (int64_t)s * c_stride;
+    const double w = 0.70710678118654752440;  // 1 / sqrt(2)
+    for (int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; C < nc3; C += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(C % nc), J = (int)((C / nc) % nc), K = (int)(C / ((int64_t)nc * nc));
+        double acc = 0.0;
+        for (int dk = 0; dk < 2; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di)
+                    acc += fs[(2 * I + di) + (int64_t)nf * ((2 * J + dj) + (int64_t)nf * (2 * K + dk))];
+        cs[C] = w * acc;
+    }
+}
+
+cudaError_t launch_restrict_rhs(int nc, int S, const double* Ff, int64_t f_stride, double* Fc, int64_t c_stride,
+                                cudaStream_t st) {
+    const int64_t nc3 = (int64_t)nc * nc * nc;
+    int64_t b = (nc3 + 255) / 256;
+    if (b > 4096) b = 4096;
+    dim3 grid((unsigned)(b < 1 ? 1 : b), S);
+    k_restrict_rhs<<<grid, 256, 0, st>>>(nc, Ff, f_stride, Fc, c_stride);
+    return cudaGetLastError();
+}
+
+// Fine initial cell field = coarse field injected (piecewise-constant P of
+// Sec. 6.1): physical theta_f = theta_c(parent), i.e. scaled
+// theta~_f = theta~_c / sqrt 2 (cell scaling h^{1/2}, H = 2h).  Writes the
+// cell block of xf (stride 4 nf^3); the flux blocks are recomputed later.
+__global__ void k_inject_theta(int nc, const double* __restrict__ xc, int64_t c_stride, double* __restrict__ xf,
+                               int64_t f_stride) {
+    const int s = blockIdx.y;
+    const int nf = 2 * nc;
+    const int64_t nf3 = (int64_t)nf * nf * nf, nc3 = (int64_t)nc * nc * nc;
+    const double* tc = xc + (int64_t)s * c_stride + 3 * nc3;
+    double* tf = xf + (int64_t)s * f_stride + 3 * nf3;
+    const double w = 0.70710678118654752440;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nf3; c += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nf), j = (int)((c / nf) % nf), k = (int)(c / ((int64_t)nf * nf));
+        tf[c] = w * tc[(i >> 1) + (int64_t)nc * ((j >> 1) + (int64_t)nc * (k >> 1))];
+    }
+}
+
+cudaError_t launch_inject_theta(int nc, int S, const double* xc, int64_t c_stride, double* xf, int64_t f_stride,
+                                cudaStream_t st) {
+    const int64_t nf3 = 8LL * nc * nc * nc;
+    int64_t b = (nf3 + 255) / 256;
+    if (b > 4096) b = 4096;
+    dim3 grid((unsigned)b, S);
+    k_inject_theta<<<grid, 256, 0, st>>>(nc, xc, c_stride, xf, f_stride);
+    return cudaGetLastError();
+}
+
 }  // namespace spde

@@ -381,3 +381,27 @@ def test_iteration_cap_reports_enoconv():
     assert ei.value.status == pkg.SPDE_ENOCONV
     assert smp.stats()["max_rel_residual"] > 1e-10
     smp.close()
+
+
+@pytest.mark.parametrize("nf", [32, 64])
+def test_coupled_two_level_sample(nf):
+    """Sec. 6.2 coupled pair: fine field from the fine noise, coarse field from the
+    restricted noise, fine solve warm-started from the coarse field."""
+    nc, kappa, sigma, ns, seed = nf // 2, 20.0, 1.0, 3, 5
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED)
+    smp.add_level(0, nf)
+    smp.add_level(1, nc)
+    kind = pkg.SPDE_OUT_GRID_GAUSSIAN | pkg.SPDE_OUT_F64
+    fine = torch.zeros((ns, nf ** 3), dtype=torch.float64, device=DEV)
+    coarse = torch.zeros((ns, nc ** 3), dtype=torch.float64, device=DEV)
+    pkg.spde_sample_coupled(smp.ctx, 0, 1, ns, kappa, sigma, seed, 4, kind, fine, coarse)
+    warm_iters = smp.stats()["inner_iters"]
+    xi = philox.normals_batch(nf ** 3, seed, 4, ns)
+    ref_f = mixed.solve_dct(nf, kappa, sigma, xi)
+    ref_c = mixed.solve_dct(nc, kappa, sigma, np.stack([mixed.restrict_noise(x, nf) for x in xi]))
+    assert rel(fine.cpu().numpy(), ref_f) <= 1e-8
+    assert rel(coarse.cpu().numpy(), ref_c) <= 1e-8
+    alone = smp.sample(0, ns, kappa, sigma, seed, 4, kind)
+    assert rel(fine.cpu().numpy(), alone.cpu().numpy()) <= 1e-8
+    assert warm_iters <= smp.stats()["inner_iters"]  # the coarse field is a useful start
+    smp.close()

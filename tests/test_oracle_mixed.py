@@ -154,3 +154,25 @@ def test_sample_variance_matches_exact_covariance():
     col = mixed.covariance_column(n, kappa, sigma, 100)
     emp_col = (th * th[:, 100:101]).mean(axis=0)
     assert np.abs(emp_col - col).max() < 5 * math.sqrt(2.0 / ns) * var.max()
+
+
+def test_restricted_noise_has_the_coarse_covariance():
+    """Sec. 6.2: P^T W_f P ... the restricted right-hand side P^T W_f^{1/2} xi has
+    covariance P^T W_f P = W_c exactly (each coarse cell sums 8 disjoint fine cells)."""
+    n_f = 4
+    r = mixed.restriction_matrix(n_f)
+    wf = np.eye(n_f ** 3) * (1.0 / n_f) ** 3
+    wc = np.eye((n_f // 2) ** 3) * (2.0 / n_f) ** 3
+    assert np.allclose(r @ wf @ r.T, wc, rtol=1e-14, atol=0)
+    xi = philox.normals(n_f ** 3, 3, 1)
+    xc = mixed.restrict_noise(xi, n_f)
+    # same as W_c^{-1/2} P^T W_f^{1/2} xi written with the dense matrices
+    assert np.allclose(xc, np.sqrt(np.diag(wc)) ** -1 * (r @ (np.sqrt(np.diag(wf)) * xi)), rtol=1e-14)
+
+
+def test_restricted_noise_is_standard_normal():
+    from scipy import stats
+    xi = philox.normals(64 ** 3, 9, 2)
+    xc = mixed.restrict_noise(xi, 64)
+    assert stats.kstest(xc, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(xc[:-1], xc[1:])[0, 1]) < 5 / np.sqrt(len(xc))
