@@ -67,6 +67,14 @@ enum {
     SPDE_PREC_FP64 = 1   /* plain path: FP64 MINRES + FP64 V-cycle, one sample at a time */
 };
 
+/* inner solver of the refinement */
+enum {
+    SPDE_SOLVER_MINRES = 0,   /* MINRES on the mixed system, block-diagonal preconditioner (default) */
+    SPDE_SOLVER_SCHUR_CG = 1  /* CG on the Schur complement (kappa h)^2 I + D1 T^{-1} D1^T of the cell
+                                 unknowns, T^{-1} by exact line solves, same V-cycle preconditioner;
+                                 same solution */
+};
+
 /* output kinds of spde_sample / spde_project (or-ed with SPDE_OUT_F64) */
 enum {
     SPDE_OUT_LOGNORMAL = 0,     /* exp(theta_h) on the tets, [nsamples][ntets] */
@@ -90,6 +98,7 @@ typedef struct {
     int use_graphs;     /* capture the batched MINRES iteration in CUDA graphs; 1 */
     int64_t serve_budget_bytes; /* device memory the serving lanes may hold; 120 GiB */
     int serve_max_batch;        /* columns per serving lane; 64 */
+    int solver;                 /* SPDE_SOLVER_MINRES (default) or SPDE_SOLVER_SCHUR_CG */
 } spde_opts;
 
 typedef struct {
@@ -207,10 +216,11 @@ spde_status spde_mesh_copy_csr(spde_ctx* ctx, int level, int64_t* row_ptr, int32
  * synchronisation. */
 spde_status spde_profile_enable(spde_ctx* ctx, int enable);
 
-/* Counters of kernel class k (0 <= k < 16, in launch order of the path:
+/* Counters of kernel class k (0 <= k < 18, in launch order of the path:
  * noise, sumsq, residual64, minres_A, alpha, minres_B, mg_down, mg_coarse,
  * mg_up, givens, minres_D, add_correction, transpose_theta, project_exp,
- * flux_from_theta, other (reductions, column flags, MINRES start)):
+ * flux_from_theta, schur_apply, cg_update, other (reductions, column flags,
+ * solver start)):
  * *name its name, *launches its launches, *ms their summed device time,
  * *bytes their summed algorithmic bytes (each launch's inputs read once and
  * outputs written once, for the columns active when it was enqueued).
@@ -283,6 +293,13 @@ spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec,
  *     element it reads). */
 spde_status spde_precond_noalloc(int n, double h, double kappa, int nsamples, int prec,
                                  const spde_opts* opts, const void* r, void* z, void* stream);
+
+/* y = S x with the scaled Schur complement S = (kappa h)^2 I + D1 T^{-1} D1^T of
+ * the cell unknowns (Sec. 4.2: kappa^2 W + B M^{-1} B^T, scaled by h^{-1}),
+ * T^{-1} applied exactly by tridiagonal line solves.  x, y: device
+ * [nsamples][n^3], double (SPDE_PREC_FP64) or float.  Synchronises `stream`. */
+spde_status spde_schur_apply(int n, double h, double kappa, int nsamples, int prec, const void* x, void* y,
+                             void* stream);
 
 /* Solve the scaled system (D A D) X = [0; rhs] for nsamples right-hand sides
  * with the context's precision path (opts given at spde_grid_create).

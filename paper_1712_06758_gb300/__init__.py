@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libspde.so")
 
 SPDE_OK, SPDE_EINVAL, SPDE_ENOMEM, SPDE_EMESH, SPDE_ENOCONV, SPDE_ETIMEOUT, SPDE_ECUDA, SPDE_EBUSY, SPDE_ECANCELED = range(9)
 SPDE_PREC_MIXED, SPDE_PREC_FP64 = 0, 1
+SPDE_SOLVER_MINRES, SPDE_SOLVER_SCHUR_CG = 0, 1
 SPDE_OUT_LOGNORMAL, SPDE_OUT_GAUSSIAN, SPDE_OUT_GRID_GAUSSIAN, SPDE_OUT_F64 = 0, 1, 2, 16
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EMESH", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "EBUSY",
                 8: "ECANCELED"}
@@ -28,7 +29,7 @@ class spde_opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_iter", ctypes.c_int), ("omega", ctypes.c_double),
                 ("schur_c", ctypes.c_double), ("flux_diag", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("device", ctypes.c_int), ("use_graphs", ctypes.c_int), ("serve_budget_bytes", ctypes.c_int64),
-                ("serve_max_batch", ctypes.c_int)]
+                ("serve_max_batch", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class spde_stats(ctypes.Structure):
@@ -74,6 +75,7 @@ _SIGS = {
                      ctypes.POINTER(spde_opts), _P, _P, _P],
     "spde_precond_noalloc": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                              ctypes.POINTER(spde_opts), _P, _P, _P],
+    "spde_schur_apply": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "spde_solve": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "spde_project": [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P],
 }
@@ -217,7 +219,7 @@ def spde_profile_enable(ctx, enable=True):
     _check(lib().spde_profile_enable(ctx, 1 if enable else 0))
 
 
-PROF_CLASSES = 16
+PROF_CLASSES = 18
 
 
 def spde_profile_read(ctx, k):
@@ -265,6 +267,10 @@ def spde_precond_noalloc(n, h, kappa, nsamples, prec, r, z, opts=None, stream=No
     _check(lib().spde_precond_noalloc(n, h, kappa, nsamples, prec,
                                       ctypes.byref(opts) if opts is not None else None, _ptr(r), _ptr(z),
                                       _stream(stream)))
+
+
+def spde_schur_apply(n, h, kappa, nsamples, prec, x, y, stream=None):
+    _check(lib().spde_schur_apply(n, h, kappa, nsamples, prec, _ptr(x), _ptr(y), _stream(stream)))
 
 
 def spde_solve(ctx, level, nsamples, kappa, rhs, x, stream=None):

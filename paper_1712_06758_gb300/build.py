@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspde.so")
-SOURCES = ["noise.cu", "stencil.cu", "krylov.cu", "mg.cu", "clip.cu", "project.cu", "spde.cu", "noalloc.cu"]
+SOURCES = ["noise.cu", "stencil.cu", "krylov.cu", "mg.cu", "clip.cu", "project.cu", "spde.cu", "noalloc.cu", "schur.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -20,6 +20,14 @@ struct MinresCol {
     int d_iter;      // iteration number of the pending update
 };
 
+// Per-column state of the Schur-complement CG (FP64 scalars).
+struct CgCol {
+    double rz, rr0, alpha, beta, tol2;
+    int active;  // column still iterating
+    int iters;
+    int pad0, pad1;
+};
+
 // Multigrid plan of one grid size for a batch of S columns.
 struct MGPlan {
     int n = 0;          // fine cells per axis (power of two)
@@ -105,6 +113,25 @@ size_t mg_scratch_elems(int n, int S);
 void mg_plan_init(MGPlan& plan, int n, double kh2, double c, double omega);
 template <typename T>
 void mg_plan_bind(MGPlan& plan, int S, T* scratch);
+
+// ---- schur.cu (Schur-complement CG on the cell unknowns)
+template <typename T>
+int launch_schur_apply(int n, double kh2, int S, const T* x, T* y, const T* tri, double* dot_part, const CgCol* st,
+                       cudaStream_t stream);
+template <typename T>
+int launch_cg_xr(int64_t n3, int S, T* x, T* r, const T* p, const T* q, double* part, const CgCol* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_p(int64_t n3, int S, T* p, const T* z, const CgCol* st, cudaStream_t s);
+template <typename T>
+int launch_cg_rhs(int64_t n3, int S, const T* mixed_r, T* r, double* part, const CgCol* st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_add(int64_t n3, int S, double* x, const T* d, const CgCol* st, cudaStream_t s);
+cudaError_t launch_cg_alpha(int S, const double* part, int nb, CgCol* st, cudaStream_t s);
+cudaError_t launch_cg_beta(int S, const double* prr, int nrr, const double* prz, int nrz, CgCol* st, int* nactive,
+                           cudaStream_t s);
+cudaError_t launch_cg_init(int S, const double* prz, int nrz, const double* prr, int nrr, double tol, CgCol* st,
+                           int* nactive, cudaStream_t s);
+cudaError_t launch_cg_set_active(int S, const int* mask, CgCol* st, cudaStream_t s);
 
 // ---- clip.cu
 struct ClipResult {

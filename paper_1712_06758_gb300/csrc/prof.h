@@ -25,6 +25,8 @@ enum ProfClass {
     PK_TRANSPOSE,
     PK_PROJECT,
     PK_FLUX,
+    PK_SCHUR_APPLY,
+    PK_CG_UPDATE,
     PK_OTHER,  // small bookkeeping launches (reductions, flags, init)
     PK_NCLASS
 };

@@ -1,0 +1,358 @@
+// Schur-complement variant of the field solve: preconditioned CG on the
+// cell unknowns only, with the identical solution theta.
+//
+// Eliminating the fluxes from the scaled mixed system (first block row
+// T u + D1^T theta = 0) gives S theta = -F with
+//     S = (kappa h)^2 I + D1 T^{-1} D1^T           (symmetric positive definite)
+// (Sec. 4.2: S = kappa^2 W + B M^{-1} B^T in scaled form).  S is applied
+// matrix-free, one axis at a time: along every grid line the face values
+// g = D1^T x are formed, T u = g is solved exactly by Thomas elimination
+// (T = tridiag(1/6, 2/3, 1/6) on the n-1 interior faces), and the line's
+// divergence D1 u is accumulated into the output.  A CTA takes 32 lines into
+// shared memory (coalesced loads; rows padded against bank conflicts), one
+// thread per line walks it.  The preconditioner is the same V-cycle as the
+// MINRES field block.
+#include "device.cuh"
+#include "internal.h"
+
+namespace spde {
+
+constexpr int kLines = 32;  // lines per CTA, one thread each
+
+// One axis of y = S x on the cell arrays x, y ([S][n^3]); mode 0: y = (kappa h)^2 x
+// + this axis' term; mode 1: y += term; mode 2: y += term and partial sums of x.y.
+// A CTA (32 threads) takes L lines (L <= 32, a power of two dividing n): for
+// axis 0 the rows (j, k) g L .. g L + L - 1; for axes 1 and 2 the lines at
+// i = i0 .. i0 + L - 1 for one value of the remaining index.  Threads t >= L idle.
+template <typename T>
+__global__ void __launch_bounds__(kLines) k_schur_axis(int n, int L, int axis, int mode, T kh2, const T* __restrict__ x,
+                                                       T* __restrict__ y, const T* __restrict__ tri,
+                                                       double* __restrict__ dot_part,
+                                                       const CgCol* __restrict__ st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kLines / 32];
+    const int P = n + 1;                     // padded row: no bank conflicts along the line walk
+    T* sx = reinterpret_cast<T*>(smem_raw);  // [L][n + 1]: line values
+    T* su = sx + L * P;                      // [L][n + 1]: face values
+    const int s = blockIdx.y;
+    if (st && !st[s].active) return;
+    const int64_t n3 = (int64_t)n * n * n;
+    const T* xs = x + (int64_t)s * n3;
+    T* ys = y + (int64_t)s * n3;
+    const int t = threadIdx.x;
+    const int ngi = n / L;
+    const int groups = (n / L) * n;  // n^2 lines per axis, L per group
+    const int64_t sa = (axis == 1) ? n : (int64_t)n * n;           // step along a y / z line
+    const int64_t so = (axis == 1) ? (int64_t)n * n : (int64_t)n;  // step of the remaining index
+    T acc = T(0);
+    for (int g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int i0 = (g % ngi) * L, o = g / ngi;
+    if (axis == 0) {
+        const int64_t start = (int64_t)g * L * n;  // L contiguous rows
+        for (int idx = t; idx < L * n; idx += kLines) {
+            const int l = idx / n, e = idx - l * n;
+            sx[l * P + e] = xs[start + idx];
+        }
+    } else if (t < L) {
+        for (int e = 0; e < n; ++e) sx[t * P + e] = xs[i0 + t + so * o + sa * e];
+    }
+    __syncthreads();
+    if (t < L) {
+        // T u = D1^T x along the line, (D1^T x)_f = x_f - x_{f+1}; Thomas elimination
+        const T* xl = sx + t * P;
+        T* ul = su + t * P;
+        const T* cp = tri;
+        const T* inv = tri + (n - 1);
+        const T a = T(1) / T(6);
+        T prev = T(0);
+        for (int f = 0; f < n - 1; ++f) {
+            const T dp = ((xl[f] - xl[f + 1]) - a * prev) * inv[f];
+            ul[f] = dp;
+            prev = dp;
+        }
+        T xn = prev;  // u_{n-2}
+        for (int f = n - 3; f >= 0; --f) {
+            const T xf = ul[f] - cp[f] * xn;
+            ul[f] = xf;
+            xn = xf;
+        }
+        ul[n - 1] = T(0);  // wall face
+    }
+    __syncthreads();
+    // divergence: cell f gains u_f - u_{f-1}
+    if (axis == 0) {
+        const int64_t start = (int64_t)g * L * n;
+        for (int idx = t; idx < L * n; idx += kLines) {
+            const int l = idx / n, e = idx - l * n;
+            const T* ul = su + l * P;
+            const T term = ul[e] - (e > 0 ? ul[e - 1] : T(0));
+            const T xv = sx[l * P + e];
+            const T v = (mode == 0) ? kh2 * xv + term : ys[start + idx] + term;
+            ys[start + idx] = v;
+            if (mode == 2) acc += xv * v;
+        }
+    } else if (t < L) {
+        const T* ul = su + t * P;
+        for (int e = 0; e < n; ++e) {
+            const int64_t gi = i0 + t + so * o + sa * e;
+            const T term = ul[e] - (e > 0 ? ul[e - 1] : T(0));
+            const T xv = sx[t * P + e];
+            const T v = (mode == 0) ? kh2 * xv + term : ys[gi] + term;
+            ys[gi] = v;
+            if (mode == 2) acc += xv * v;
+        }
+    }
+    __syncthreads();  // the next group reuses the shared rows
+    }
+    if (mode == 2 && dot_part) {
+        const double tsum = block_sum<kLines>((double)acc, red);
+        if (t == 0) dot_part[(int64_t)s * kMaxPartials + blockIdx.x] = tsum;
+    }
+}
+
+constexpr size_t kSchurSmemMax = 200 * 1024;
+
+template <typename T>
+static int schur_lines(int n) {
+    int L = kLines;
+    while (L > 1 && (L > n || 2 * (size_t)L * (n + 1) * sizeof(T) > kSchurSmemMax)) L >>= 1;
+    return L;
+}
+
+template <typename T>
+static cudaError_t schur_attrs() {
+    static const cudaError_t e =
+        cudaFuncSetAttribute(k_schur_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSchurSmemMax);
+    return e;
+}
+
+// y = S x for S columns; partial sums of x.y per column into dot_part (nblk returned, or -1)
+template <typename T>
+int launch_schur_apply(int n, double kh2, int S, const T* x, T* y, const T* tri, double* dot_part, const CgCol* st,
+                       cudaStream_t stream) {
+    if (schur_attrs<T>() != cudaSuccess) return -1;
+    const int L = schur_lines<T>(n);
+    const size_t smem = 2 * (size_t)L * (n + 1) * sizeof(T);
+    const int groups = n * n / L;  // n^2 lines per axis
+    const int nb = groups < kMaxPartials ? groups : kMaxPartials;
+    dim3 grid(nb, S);
+    for (int axis = 0; axis < 3; ++axis)
+        k_schur_axis<T><<<grid, kLines, smem, stream>>>(n, L, axis, axis == 0 ? 0 : (axis == 2 ? 2 : 1), (T)kh2, x,
+                                                         y, tri, dot_part, st);
+    return nb;
+}
+
+// ---------------------------------------------------------------------------
+// CG vector updates and per-column scalars
+// ---------------------------------------------------------------------------
+// x += alpha p; r -= alpha q; partial r.r
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_xr(int64_t n3, T* __restrict__ x, T* __restrict__ r,
+                                               const T* __restrict__ p, const T* __restrict__ q,
+                                               double* __restrict__ part, const CgCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    const CgCol& c = st[s];
+    if (!c.active) return;
+    const T al = (T)c.alpha;
+    const int64_t off = (int64_t)s * n3;
+    T acc = T(0);
+    for (int64_t e = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e < n3; e += 4 * (int64_t)gridDim.x * blockDim.x) {
+        V4<T> xv = (c.iters > 0) ? ld4(x + off + e) : zero4<T>();
+        V4<T> rv = ld4(r + off + e);
+        const V4<T> pv = ld4(p + off + e), qv = ld4(q + off + e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            xv.v[k] += al * pv.v[k];
+            rv.v[k] -= al * qv.v[k];
+            acc += rv.v[k] * rv.v[k];
+        }
+        st4(x + off + e, xv);
+        st4(r + off + e, rv);
+    }
+    const double t = block_sum<256>((double)acc, red);
+    if (threadIdx.x == 0) part[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+}
+
+// p = z + beta p (beta = 0 starts the recurrence)
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_p(int64_t n3, T* __restrict__ p, const T* __restrict__ z,
+                                              const CgCol* __restrict__ st) {
+    const int s = blockIdx.y;
+    const CgCol& c = st[s];
+    if (!c.active) return;
+    const T be = (T)c.beta;
+    const bool first = c.iters == 0;
+    const int64_t off = (int64_t)s * n3;
+    for (int64_t e = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e < n3; e += 4 * (int64_t)gridDim.x * blockDim.x) {
+        const V4<T> zv = ld4(z + off + e);
+        V4<T> pv = first ? zero4<T>() : ld4(p + off + e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pv.v[k] = zv.v[k] + be * pv.v[k];
+        st4(p + off + e, pv);
+    }
+}
+
+__device__ __forceinline__ double cg_col_sum(const double* part, int s, int nb, double* red) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(int64_t)s * kMaxPartials + b];
+    return block_sum<256>(acc, red);
+}
+
+// after q = S p: alpha = rz / p.q
+__global__ void __launch_bounds__(256) k_cg_alpha(const double* __restrict__ part, int nb, CgCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    CgCol& c = st[s];
+    if (!c.active) return;
+    const double pq = cg_col_sum(part, s, nb, red);
+    if (threadIdx.x == 0) {
+        c.alpha = (pq > 0.0 && isfinite(pq)) ? c.rz / pq : 0.0;
+        if (!(pq > 0.0) || !isfinite(pq)) c.active = 0;  // breakdown: stop this column
+    }
+}
+
+// after r update and z = M^{-1} r: convergence on ||r||, beta = rz_new / rz
+__global__ void __launch_bounds__(256) k_cg_beta(const double* __restrict__ part_rr, int nrr,
+                                                 const double* __restrict__ part_rz, int nrz, CgCol* __restrict__ st,
+                                                 int* __restrict__ nactive) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    CgCol& c = st[s];
+    if (!c.active) return;
+    const double rr = cg_col_sum(part_rr, s, nrr, red);
+    const double rz = cg_col_sum(part_rz, s, nrz, red);
+    if (threadIdx.x != 0) return;
+    c.iters += 1;
+    c.beta = (c.rz > 0.0) ? rz / c.rz : 0.0;
+    c.rz = rz;
+    const bool done = !(rr > c.tol2 * c.rr0) || !(rz > 0.0) || !isfinite(rz);
+    if (done) c.active = 0;
+    else if (nactive) atomicAdd(nactive, 1);
+}
+
+// start: r = b given, z = M^{-1} r; rz, rr0 from partial sums
+__global__ void __launch_bounds__(256) k_cg_init(const double* __restrict__ part_rz, int nrz,
+                                                 const double* __restrict__ part_rr, int nrr, double tol,
+                                                 CgCol* __restrict__ st, int* __restrict__ nactive) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    CgCol& c = st[s];
+    if (!c.active) return;
+    const double rz = cg_col_sum(part_rz, s, nrz, red);
+    const double rr = cg_col_sum(part_rr, s, nrr, red);
+    if (threadIdx.x != 0) return;
+    c.rz = rz;
+    c.rr0 = rr;
+    c.tol2 = tol * tol;
+    c.alpha = 0.0;
+    c.beta = 0.0;
+    c.iters = 0;
+    c.active = (rr > 0.0 && rz > 0.0 && isfinite(rz)) ? 1 : 0;
+    if (c.active && nactive) atomicAdd(nactive, 1);
+}
+
+// r = -(cell block of the mixed residual), partial r.r
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_rhs(int64_t n3, const T* __restrict__ mixed_r, T* __restrict__ r,
+                                                double* __restrict__ part, const CgCol* __restrict__ st) {
+    __shared__ double red[8];
+    const int s = blockIdx.y;
+    if (!st[s].active) return;
+    const T* src = mixed_r + (int64_t)s * 4 * n3 + 3 * n3;
+    T* dst = r + (int64_t)s * n3;
+    T acc = T(0);
+    for (int64_t e = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e < n3; e += 4 * (int64_t)gridDim.x * blockDim.x) {
+        V4<T> v = ld4(src + e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v.v[k] = -v.v[k];
+            acc += v.v[k] * v.v[k];
+        }
+        st4(dst + e, v);
+    }
+    const double t = block_sum<256>((double)acc, red);
+    if (threadIdx.x == 0) part[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+}
+
+__global__ void k_cg_set_active(int S, const int* __restrict__ mask, CgCol* __restrict__ st) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) {
+        st[s].active = mask ? mask[s] : 1;
+        st[s].iters = 0;
+    }
+}
+
+static inline int cg_blocks(int64_t n3) {
+    int64_t b = (n3 / 4 + 255) / 256;
+    if (b > 2048) b = 2048;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+int launch_cg_xr(int64_t n3, int S, T* x, T* r, const T* p, const T* q, double* part, const CgCol* st, cudaStream_t s) {
+    const int nb = cg_blocks(n3);
+    k_cg_xr<T><<<dim3(nb, S), 256, 0, s>>>(n3, x, r, p, q, part, st);
+    return nb;
+}
+template <typename T>
+cudaError_t launch_cg_p(int64_t n3, int S, T* p, const T* z, const CgCol* st, cudaStream_t s) {
+    k_cg_p<T><<<dim3(cg_blocks(n3), S), 256, 0, s>>>(n3, p, z, st);
+    return cudaGetLastError();
+}
+template <typename T>
+int launch_cg_rhs(int64_t n3, int S, const T* mixed_r, T* r, double* part, const CgCol* st, cudaStream_t s) {
+    const int nb = cg_blocks(n3);
+    k_cg_rhs<T><<<dim3(nb, S), 256, 0, s>>>(n3, mixed_r, r, part, st);
+    return nb;
+}
+cudaError_t launch_cg_alpha(int S, const double* part, int nb, CgCol* st, cudaStream_t s) {
+    k_cg_alpha<<<S, 256, 0, s>>>(part, nb, st);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_beta(int S, const double* prr, int nrr, const double* prz, int nrz, CgCol* st, int* nactive,
+                           cudaStream_t s) {
+    k_cg_beta<<<S, 256, 0, s>>>(prr, nrr, prz, nrz, st, nactive);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_init(int S, const double* prz, int nrz, const double* prr, int nrr, double tol, CgCol* st,
+                           int* nactive, cudaStream_t s) {
+    k_cg_init<<<S, 256, 0, s>>>(prz, nrz, prr, nrr, tol, st, nactive);
+    return cudaGetLastError();
+}
+// x_theta += d (d: [S][n^3]) for columns whose CG ran
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_add(int64_t n3, double* __restrict__ x, const T* __restrict__ d,
+                                                const CgCol* __restrict__ st) {
+    const int s = blockIdx.y;
+    if (st[s].iters == 0) return;
+    double* xs = x + (int64_t)s * 4 * n3 + 3 * n3;
+    const T* ds = d + (int64_t)s * n3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
+        xs[e] += (double)ds[e];
+}
+
+template <typename T>
+cudaError_t launch_cg_add(int64_t n3, int S, double* x, const T* d, const CgCol* st, cudaStream_t s) {
+    int64_t b = (n3 + 1023) / 1024;
+    if (b > 2048) b = 2048;
+    k_cg_add<T><<<dim3((unsigned)(b < 1 ? 1 : b), S), 256, 0, s>>>(n3, x, d, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_set_active(int S, const int* mask, CgCol* st, cudaStream_t s) {
+    k_cg_set_active<<<(S + 127) / 128, 128, 0, s>>>(S, mask, st);
+    return cudaGetLastError();
+}
+
+#define SPDE_SCHUR_INST(T)                                                                                          \
+    template int launch_schur_apply<T>(int, double, int, const T*, T*, const T*, double*, const CgCol*,             \
+                                       cudaStream_t);                                                               \
+    template int launch_cg_xr<T>(int64_t, int, T*, T*, const T*, const T*, double*, const CgCol*, cudaStream_t);   \
+    template cudaError_t launch_cg_p<T>(int64_t, int, T*, const T*, const CgCol*, cudaStream_t);                   \
+    template int launch_cg_rhs<T>(int64_t, int, const T*, T*, double*, const CgCol*, cudaStream_t);                \
+    template cudaError_t launch_cg_add<T>(int64_t, int, double*, const T*, const CgCol*, cudaStream_t);
+SPDE_SCHUR_INST(float)
+SPDE_SCHUR_INST(double)
+
+}  // namespace spde

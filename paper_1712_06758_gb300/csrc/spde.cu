@@ -28,7 +28,7 @@ thread_local Profiler* t_prof = nullptr;
 void set_last_error(const char* msg);
 const char* const kProfNames[PK_NCLASS] = {"noise",   "sumsq",  "residual64", "minres_A",  "alpha",
                                            "minres_B", "mg_down", "mg_coarse",  "mg_up",     "givens",
-                                           "minres_D", "add_correction", "transpose_theta", "project_exp", "flux_from_theta", "other"};
+                                           "minres_D", "add_correction", "transpose_theta", "project_exp", "flux_from_theta", "schur_apply", "cg_update", "other"};
 }  // namespace spde
 
 namespace {
@@ -94,6 +94,8 @@ struct Workspace {
     double* F = nullptr;     // [S][n^3] cell block of the scaled RHS
     void* vec[7] = {};       // inner vectors: d, wA, wB ([S][n^3], cell block only), r1, r2, yA, yB
     double* tri = nullptr;   // Thomas factors of the flux mass matrix T (2n - 2)
+    float* tri32 = nullptr;  // the same in FP32 (Schur-complement operator)
+    CgCol* cg = nullptr;     // Schur-complement CG state [S]
     void* mg = nullptr;      // V-cycle scratch
     double* partA = nullptr; // partial sums [S][kMaxPartials]
     double* partB = nullptr;
@@ -125,6 +127,8 @@ struct Workspace {
         dev_free(nact);
         dev_free(thetaT);
         dev_free(tri);
+        dev_free(tri32);
+        dev_free(cg);
         if (h_nact) cudaFreeHost(h_nact);
         if (h_col) cudaFreeHost(h_col);
         if (h_st) cudaFreeHost(h_st);
@@ -227,6 +231,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
     STATUS_TRY(dev_alloc(&ws.partR, (size_t)S * kMaxPartials));
     STATUS_TRY(dev_alloc(&ws.colv, (size_t)2 * S));
     STATUS_TRY(dev_alloc(&ws.st, (size_t)S));
+    STATUS_TRY(dev_alloc(&ws.cg, (size_t)S));
     STATUS_TRY(dev_alloc(&ws.nact, 1));
     STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
     {
@@ -240,7 +245,10 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
             cprev = tri[f];
         }
         STATUS_TRY(dev_alloc(&ws.tri, tri.size()));
-        if (cudaMemcpy(ws.tri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        STATUS_TRY(dev_alloc(&ws.tri32, tri.size()));
+        std::vector<float> tri32(tri.begin(), tri.end());
+        if (cudaMemcpy(ws.tri32, tri32.data(), tri32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ws.tri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
             ws.release();
             return fail(SPDE_ECUDA, "upload of line-solve factors failed");
@@ -347,6 +355,74 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     return SPDE_OK;
 }
 
+// Schur-complement CG for the columns flagged in cg[].active: S d = -r_theta,
+// r_theta the cell block of the mixed residual in ws.vec[4] (inner type T);
+// d in ws.vec[0] ([S][n^3]).
+template <typename T>
+spde_status cg_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws, double inner_tol, int* iters_out,
+                     cudaStream_t st) {
+    const int64_t n3 = (int64_t)n * n * n;
+    T* x = static_cast<T*>(ws.vec[0]);
+    T* r = static_cast<T*>(ws.vec[1]);
+    T* p = static_cast<T*>(ws.vec[2]);
+    T* q = static_cast<T*>(ws.vec[3]);  // [S][n^3] view of a larger buffer
+    T* z = static_cast<T*>(ws.vec[5]);
+    const T* mixed_r = static_cast<const T*>(ws.vec[4]);
+    const T* tri = std::is_same<T, float>::value ? reinterpret_cast<const T*>(ws.tri32) : reinterpret_cast<const T*>(ws.tri);
+    MGPlan plan;
+    mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
+    mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
+    plan.prof_cols = (double)S;
+    const int act_stride = (int)(sizeof(CgCol) / sizeof(int));
+    const int* act = &ws.cg[0].active;
+    const double w = (double)sizeof(T), n3d = (double)n3;
+    prof_begin(PK_OTHER, st);
+    const int nrr0 = launch_cg_rhs<T>(n3, S, mixed_r, r, ws.partB, ws.cg, st);
+    prof_end(st, (double)S * 2.0 * n3d * w);
+    const int nrz0 = launch_vcycle<T>(plan, S, r, n3, z, n3, ws.partC, act, act_stride, st);
+    if (nrz0 < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
+    CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+    CUDA_TRY(launch_cg_init(S, ws.partC, nrz0, ws.partB, nrr0, inner_tol, ws.cg, ws.nact, st));
+    CUDA_TRY(launch_cg_p<T>(n3, S, p, z, ws.cg, st));
+    CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    int it = 0;
+    int nactive = *ws.h_nact;
+    while (nactive > 0 && it < o.max_iter) {
+        const int chunk = std::min(o.check_every, o.max_iter - it);
+        const double cols = (double)nactive;
+        plan.prof_cols = cols;
+        for (int k = 0; k < chunk; ++k) {
+            prof_begin(PK_SCHUR_APPLY, st);
+            const int nq = launch_schur_apply<T>(n, kh2, S, p, q, tri, ws.partA, ws.cg, st);
+            prof_end(st, cols * 8.0 * n3d * w);  // axis passes: read p, write q; read p, q, write q (x2)
+            if (nq < 0) return fail(SPDE_ECUDA, "Schur operator launch configuration failed");
+            prof_begin(PK_ALPHA, st);
+            CUDA_TRY(launch_cg_alpha(S, ws.partA, nq, ws.cg, st));
+            prof_end(st, cols * nq * 8.0);
+            prof_begin(PK_CG_UPDATE, st);
+            const int nrr = launch_cg_xr<T>(n3, S, x, r, p, q, ws.partB, ws.cg, st);
+            prof_end(st, cols * 6.0 * n3d * w);
+            const int nrz = launch_vcycle<T>(plan, S, r, n3, z, n3, ws.partC, act, act_stride, st);
+            if (k == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+            prof_begin(PK_GIVENS, st);
+            CUDA_TRY(launch_cg_beta(S, ws.partB, nrr, ws.partC, nrz, ws.cg, (k == chunk - 1) ? ws.nact : nullptr, st));
+            prof_end(st, cols * (nrr + nrz) * 8.0);
+            prof_begin(PK_CG_UPDATE, st);
+            CUDA_TRY(launch_cg_p<T>(n3, S, p, z, ws.cg, st));
+            prof_end(st, cols * 3.0 * n3d * w);
+        }
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (t_prof) t_prof->flush();
+        it += chunk;
+        nactive = *ws.h_nact;
+    }
+    *iters_out = it;
+    return SPDE_OK;
+}
+
 // Solve (D A D) x = [0; F] for S columns: FP64 iterative refinement around an
 // inner MINRES of element type T.  F, x64 in ws; returns the max relative
 // residual in *maxrel.
@@ -400,17 +476,22 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         if (nact == 0 || outer >= o.max_outer) break;
         CUDA_TRY(cudaMemcpyAsync(d_mask, mask.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
         prof_begin(PK_OTHER, st);
-        CUDA_TRY(launch_set_active(S, d_mask, ws.st, st));
+        if (o.solver == SPDE_SOLVER_SCHUR_CG) CUDA_TRY(launch_cg_set_active(S, d_mask, ws.cg, st));
+        else CUDA_TRY(launch_set_active(S, d_mask, ws.st, st));
         prof_end(st, (double)S * 4.0);
         // the inner solve only needs to reduce this step's residual by inner_tol (FP32) or
         // to reach the overall tolerance (FP64 inner)
         double itol = o.inner_tol;
         if (std::is_same<T, double>::value) itol = std::max(0.1 * o.tol / std::max(worst, 1e-300), 1e-15);
         int its = 0;
-        STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st));
+        if (o.solver == SPDE_SOLVER_SCHUR_CG) STATUS_TRY(cg_batch<T>(o, n, kh2, S, ws, itol, &its, st));
+        else STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st));
         inner_total += its;
         prof_begin(PK_ADD_CORR, st);
-        CUDA_TRY(launch_add_theta<T>(n3, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.st, st));
+        if (o.solver == SPDE_SOLVER_SCHUR_CG)
+            CUDA_TRY(launch_cg_add<T>(n3, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.cg, st));
+        else
+            CUDA_TRY(launch_add_theta<T>(n3, S, ws.x64, static_cast<const T*>(ws.vec[0]), ws.st, st));
         prof_end(st, (double)nact * (16.0 + sizeof(T)) * (double)n3);
         ++outer;
     }
@@ -987,6 +1068,7 @@ spde_status spde_opts_init(spde_opts* o) {
     o->use_graphs = 1;
     o->serve_budget_bytes = (int64_t)120 << 30;
     o->serve_max_batch = 64;
+    o->solver = SPDE_SOLVER_MINRES;
     return SPDE_OK;
 }
 
@@ -997,6 +1079,7 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
     spde_opts_init(&o);
     if (opts) o = *opts;
     if (o.precision != SPDE_PREC_MIXED && o.precision != SPDE_PREC_FP64) return fail(SPDE_EINVAL, "bad precision");
+    if (o.solver != SPDE_SOLVER_MINRES && o.solver != SPDE_SOLVER_SCHUR_CG) return fail(SPDE_EINVAL, "bad solver");
     if (!(o.tol > 0.0) || !(o.inner_tol > 0.0) || o.max_outer < 1 || o.max_iter < 1 || o.check_every < 1)
         return fail(SPDE_EINVAL, "bad tolerance or iteration limits");
     if (!(o.omega > 0.0 && o.omega < 1.0)) return fail(SPDE_EINVAL, "omega must lie in (0, 1)");
@@ -1475,6 +1558,47 @@ spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, 
             return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
     }
     CUDA_TRY(cudaGetLastError());
+    return SPDE_OK;
+}
+
+spde_status spde_schur_apply(int n, double h, double kappa, int nsamples, int prec, const void* x, void* y,
+                             void* stream) {
+    if (!is_pow2(n) || n < 4 || n > 1024 || nsamples < 0 || !(h > 0.0) || !std::isfinite(kappa) || kappa < 0.0)
+        return fail(SPDE_EINVAL, "bad size or parameters");
+    if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
+    if (prec != SPDE_PREC_FP64 && prec != SPDE_PREC_MIXED) return fail(SPDE_EINVAL, "bad precision");
+    if (nsamples == 0) return SPDE_OK;
+    if (!x || !y) return fail(SPDE_EINVAL, "null buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double kh2 = (kappa * h) * (kappa * h);
+    std::vector<double> tri(2 * (size_t)n - 2);
+    double cprev = 0.0;
+    for (int f = 0; f < n - 1; ++f) {
+        const double piv = 2.0 / 3.0 - (f ? cprev / 6.0 : 0.0);
+        tri[f] = (1.0 / 6.0) / piv;
+        tri[(n - 1) + f] = 1.0 / piv;
+        cprev = tri[f];
+    }
+    void* dtri = nullptr;
+    const size_t tb = tri.size() * (prec == SPDE_PREC_FP64 ? 8 : 4);
+    CUDA_TRY(cudaMalloc(&dtri, tb));
+    cudaError_t e;
+    int nb;
+    if (prec == SPDE_PREC_FP64) {
+        e = cudaMemcpy(dtri, tri.data(), tb, cudaMemcpyHostToDevice);
+        nb = launch_schur_apply<double>(n, kh2, nsamples, static_cast<const double*>(x), static_cast<double*>(y),
+                                        static_cast<const double*>(dtri), nullptr, nullptr, st);
+    } else {
+        std::vector<float> t32(tri.begin(), tri.end());
+        e = cudaMemcpy(dtri, t32.data(), tb, cudaMemcpyHostToDevice);
+        nb = launch_schur_apply<float>(n, kh2, nsamples, static_cast<const float*>(x), static_cast<float*>(y),
+                                       static_cast<const float*>(dtri), nullptr, nullptr, st);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dtri);
+    CUDA_TRY(e);
+    if (nb < 0) return fail(SPDE_ECUDA, "launch configuration failed");
     return SPDE_OK;
 }
 

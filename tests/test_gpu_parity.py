@@ -405,3 +405,34 @@ def test_coupled_two_level_sample(nf):
     assert rel(fine.cpu().numpy(), alone.cpu().numpy()) <= 1e-8
     assert warm_iters <= smp.stats()["inner_iters"]  # the coarse field is a useful start
     smp.close()
+
+
+# ------------------------------------------------ Schur-complement variant
+@pytest.mark.parametrize("n", [4, 8, 32, 128])
+@pytest.mark.parametrize("prec", [pkg.SPDE_PREC_FP64, pkg.SPDE_PREC_MIXED])
+def test_schur_apply_matches_closed_form(n, prec):
+    """Scaled S = h^{-1} S_unscaled is diagonal in the DCT-II basis with eigenvalues Lambda / h."""
+    import scipy.fft
+    h, kappa, ns = 1.0 / n, 20.0, 2
+    x = np.random.default_rng(n).standard_normal((ns, n ** 3))
+    lam = mixed.schur_eigenvalues(n, h, kappa) / h
+    ref = np.stack([scipy.fft.idctn(scipy.fft.dctn(v.reshape(n, n, n), norm="ortho") * lam, norm="ortho").ravel()
+                    for v in x])
+    dt = torch.float64 if prec == pkg.SPDE_PREC_FP64 else torch.float32
+    xt = torch.tensor(x, dtype=dt, device=DEV)
+    yt = torch.full_like(xt, float("nan"))
+    pkg.spde_schur_apply(n, h, kappa, ns, prec, xt, yt)
+    assert rel(yt.cpu().numpy().astype(np.float64), ref) <= (1e-12 if prec == pkg.SPDE_PREC_FP64 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [pkg.SPDE_PREC_MIXED, pkg.SPDE_PREC_FP64])
+@pytest.mark.parametrize("n,ns", [(16, 3), (64, 2), (128, 2)])
+def test_schur_cg_solver_matches_closed_form(prec, n, ns):
+    kappa, sigma = 20.0, 1.0
+    smp = pkg.Sampler(prec, solver=pkg.SPDE_SOLVER_SCHUR_CG)
+    smp.add_level(0, n)
+    grid = smp.sample(0, ns, kappa, sigma, 1, 0, pkg.SPDE_OUT_GRID_GAUSSIAN | pkg.SPDE_OUT_F64)
+    assert smp.stats()["max_rel_residual"] <= 1e-10
+    xi = philox.normals_batch(n ** 3, 1, 0, ns)
+    assert rel(grid.cpu().numpy(), mixed.solve_dct(n, kappa, sigma, xi)) <= 1e-8
+    smp.close()
