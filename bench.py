@@ -20,6 +20,7 @@ the data path).
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -286,6 +287,57 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+
+# ---------------------------------------------------------------- DCT comparison leg
+def dct_ortho(x, dim):
+    """Orthonormal DCT-II along `dim` through one complex FFT of the even/odd reordering (Makhoul)."""
+    import torch
+    n = x.shape[dim]
+    x = x.movedim(dim, -1)
+    v = torch.cat([x[..., ::2], x[..., 1::2].flip(-1)], dim=-1)
+    k = torch.arange(n, device=x.device, dtype=x.dtype)
+    tw = torch.polar(torch.ones_like(k), -math.pi * k / (2 * n))
+    c = 2.0 * (torch.fft.fft(v, dim=-1) * tw).real
+    sc = torch.full_like(k, math.sqrt(0.5 / n))
+    sc[0] = math.sqrt(0.25 / n)
+    return (c * sc).movedim(-1, dim).contiguous()
+
+
+def idct_ortho(y, dim):
+    """Inverse of dct_ortho along `dim` (the orthonormal DCT-III), one complex inverse FFT."""
+    import torch
+    n = y.shape[dim]
+    y = y.movedim(dim, -1)
+    k = torch.arange(n, device=y.device, dtype=y.dtype)
+    sc = torch.full_like(k, math.sqrt(0.5 / n))
+    sc[0] = math.sqrt(0.25 / n)
+    c = y / sc
+    cr = torch.cat([torch.zeros_like(c[..., :1]), c[..., 1:].flip(-1)], dim=-1)
+    v = torch.fft.ifft(torch.polar(torch.ones_like(k), math.pi * k / (2 * n)) * torch.complex(c, -cr) / 2,
+                       dim=-1).real
+    x = torch.empty_like(v)
+    x[..., ::2] = v[..., :(n + 1) // 2]
+    x[..., 1::2] = v[..., (n + 1) // 2:].flip(-1)
+    return x.movedim(-1, dim).contiguous()
+
+
+def dct_field(xi, n, h, kappa, sigma):
+    """Cell field g S^{-1} W^{1/2} xi for constant kappa on the n^3 box, by the DCT-II diagonalisation
+    of the Schur complement (exact there, unlike for a varying kappa(x)); xi is [S][n^3], z slowest."""
+    import torch
+    k = torch.arange(n, device=xi.device, dtype=torch.float64)
+    l1 = 12.0 * torch.sin(math.pi * k / (2 * n)) ** 2 / (2.0 + torch.cos(math.pi * k / n))
+    lam = kappa ** 2 * h ** 3 + h * (l1[:, None, None] + l1[None, :, None] + l1[None, None, :])
+    f = (h ** 1.5) * xi.reshape(-1, n, n, n)
+    for d in (1, 2, 3):
+        f = dct_ortho(f, d)
+    f = f / lam
+    for d in (1, 2, 3):
+        f = idct_ortho(f, d)
+    g = sigma * (4.0 * math.pi) ** 0.75 * math.sqrt(kappa) * math.sqrt(math.gamma(2.0) / math.gamma(0.5))
+    return (g * f).reshape(xi.shape)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -421,6 +473,44 @@ def run_ours(args):
         pst = plain.stats()
         d = (ref_out[:nplain].double() - pout.double()).norm(dim=1) / pout.double().norm(dim=1)
         plain.close()
+        # the Schur-complement CG solver on the same workload and batch (same samples as step 0)
+        log("schur-cg path")
+        sch = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local, solver=pkg.SPDE_SOLVER_SCHUR_CG)
+        sch.add_level(0, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+        sch.attach_mesh(0, xyz, tets)
+        sout = torch.empty((S, ntets), dtype=torch.float32, device="cuda")
+        sch.sample(0, S, W["kappa"], W["sigma"], W["seed"], first_sample(1000, rank, world, S),
+                   pkg.SPDE_OUT_LOGNORMAL, sout, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        sch.sample(0, S, W["kappa"], W["sigma"], W["seed"], first_sample(0, rank, world, S),
+                   pkg.SPDE_OUT_LOGNORMAL, sout, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sch_rate = S / (a.elapsed_time(b) / 1000.0)
+        sst = sch.stats()
+        ds = (ref_out.double() - sout.double()).norm(dim=1) / sout.double().norm(dim=1)
+        sch.close()
+        del sout
+        # direct DCT solve (torch.fft, FP64) between the same noise and projection kernels
+        log("dct path")
+        xi = torch.empty((S, n ** 3), dtype=torch.float64, device="cuda")
+        dout = torch.empty((S, ntets), dtype=torch.float32, device="cuda")
+
+        def dct_step():
+            pkg.spde_noise(n ** 3, S, W["seed"], first_sample(0, rank, world, S), 1.0, xi, stream)
+            th = dct_field(xi, n, 1.0 / n, W["kappa"], W["sigma"])
+            pkg.spde_project(smp.ctx, 0, S, th, pkg.SPDE_OUT_LOGNORMAL, dout, stream)
+
+        dct_step()
+        torch.cuda.synchronize()
+        a.record(stream)
+        dct_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        dct_rate = S / (a.elapsed_time(b) / 1000.0)
+        dd = (ref_out.double() - dout.double()).norm(dim=1) / dout.double().norm(dim=1)
+        del xi, dout
         # the oracle on the host cores, bounded sample
         log("cpu baseline")
         oc = OracleCost(1000)
@@ -435,6 +525,12 @@ def run_ours(args):
                 "plain_fp64": {"value": plain_rate, "unit": "samples/s", "samples": nplain,
                                "ratio": value / world / plain_rate, "inner_iters": pst["inner_iters"],
                                "max_rel_l2_vs_mixed": float(d.max())},
+                "schur_cg": {"value": sch_rate, "unit": "samples/s", "samples": S, "outer_iters": sst["outer_iters"],
+                             "inner_iters": sst["inner_iters"], "max_rel_residual": sst["max_rel_residual"],
+                             "max_rel_l2_vs_minres": float(ds.max())},
+                "dct_direct": {"value": dct_rate, "unit": "samples/s", "samples": S,
+                               "max_rel_l2_vs_minres": float(dd.max()),
+                               "note": "constant kappa only; noise and projection kernels shared, FFTs torch.fft FP64"},
                 "solver": {"outer_iters": iters["outer_iters"], "inner_iters": iters["inner_iters"],
                            "max_rel_residual": iters["max_rel_residual"]},
                 "setup": {"clip_ms": setup["setup_ms"], "nnz": setup["nnz"]},

@@ -2,6 +2,7 @@
 import os
 import socket
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -53,3 +54,17 @@ def test_reduce_max_over_two_gloo_ranks():
     res = sorted(q.get(timeout=10) for _ in range(2))
     assert [m for _, m, _ in res] == [20.0, 20.0]
     assert [f for _, _, f in res] == [3 * 2 * 64, (3 * 2 + 1) * 64]
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_bench_dct_leg_matches_oracle(n):
+    """The bench's torch.fft DCT comparison leg equals the oracle's scipy DCT solve (CPU tensors)."""
+    import torch
+    from oracle import mixed
+    xi = np.random.default_rng(n).standard_normal((3, n ** 3))
+    got = bench.dct_field(torch.tensor(xi), n, 1.0 / n, 20.0, 1.3).numpy()
+    ref = mixed.solve_dct(n, 20.0, 1.3, xi)
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    x = torch.tensor(xi[0].reshape(n, n, n))
+    for d in range(3):
+        assert torch.allclose(bench.idct_ortho(bench.dct_ortho(x, d), d), x, atol=1e-13)
