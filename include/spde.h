@@ -54,8 +54,8 @@ typedef enum {
                           coupling row sum != tet volume); spde_last_error names the tet */
     SPDE_ENOCONV = 4,  /* iteration cap reached before the tolerance; outputs hold
                           the last iterate, spde_get_stats gives the residual */
-    SPDE_ETIMEOUT = 5, /* reserved for bounded waits (no kernel of this library waits
-                          on another CTA, so no current entry point returns it) */
+    SPDE_ETIMEOUT = 5, /* a bounded device wait gave up (a multigrid sweep waited about
+                          one second for a plane copy); that solve's outputs are invalid */
     SPDE_ECUDA = 6,    /* a CUDA runtime call failed */
     SPDE_EBUSY = 7,    /* request table full, or grids / meshes changed while requests are in flight */
     SPDE_ECANCELED = 8 /* (spde_poll result) the request was cancelled */

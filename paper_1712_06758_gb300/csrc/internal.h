@@ -105,6 +105,11 @@ cudaError_t launch_set_active(int S, const int* mask, MinresCol* st_, cudaStream
 cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStream_t st);
 
 // ---- mg.cu
+// the device fault word of the V-cycle sweeps (1: a wait for a plane copy gave up):
+// mg_fault_read enqueues a copy into *host on st (valid once st has synchronised),
+// mg_fault_clear resets it
+cudaError_t mg_fault_read(int* host, cudaStream_t st);
+cudaError_t mg_fault_clear(cudaStream_t st);
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride,
                   double* dot_part, const int* active, int act_stride, cudaStream_t st);

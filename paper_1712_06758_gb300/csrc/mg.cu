@@ -18,6 +18,8 @@
 // smooths, forms the residual and restricts in one pass; an up sweep that
 // prolongs, corrects and post-smooths in one pass).  All levels with
 // n_l <= 16 run inside one CTA per sample in shared memory.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
+
 #include "device.cuh"
 #include "internal.h"
 #include "prof.h"
@@ -31,11 +33,11 @@ constexpr int kMaxTilesPerCol = 2048;
 template <typename T>
 struct LevelCoef {
     T s;         // 2^l
-    T a;         // (kappa h)^2 4^l
     T c;         // Schur weight
     T omega;
-    T invD[7];   // 1 / (s (a + c k)) for k neighbours
-    T D[7];      // s (a + c k)
+    T oi[7];     // omega / D(k), D(k) = s (a + c k), a = (kappa h)^2 4^l, k existing neighbours
+    T ois[7];    // omega s c / D(k)
+    T rcD[7];    // (1/omega - 1) D(k)
 };
 
 template <typename T>
@@ -44,12 +46,13 @@ static LevelCoef<T> level_coef(const MGPlan& p, int l) {
     const double s = (double)(1 << l);
     const double a = p.kh2 * (double)(1ll << (2 * l));
     q.s = (T)s;
-    q.a = (T)a;
     q.c = (T)p.c;
     q.omega = (T)p.omega;
     for (int k = 0; k <= 6; ++k) {
-        q.invD[k] = (T)(1.0 / (s * (a + p.c * k)));
-        q.D[k] = (T)(s * (a + p.c * k));
+        const double D = s * (a + p.c * k);
+        q.oi[k] = (T)(p.omega / D);
+        q.ois[k] = (T)(p.omega * s * p.c / D);
+        q.rcD[k] = (T)((1.0 / p.omega - 1.0) * D);
     }
     return q;
 }
@@ -63,27 +66,32 @@ __device__ __forceinline__ float restrict_w(int a, int I, int nc) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Down sweep at level l: b (fine, n_f^3) -> bc = R (b - A omega D^{-1} b).
-// With x0 = omega D^{-1} b the residual is
-//     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g),
-// so one shared array of x0 on the tile + halo 2 (zero outside the box,
-// which makes the sum run over existing neighbours only) gives r on the
-// tile + halo 1, from which the 4^3-point restriction gathers.
-// Thread block (32, 8): x along threadIdx.x, y along threadIdx.y, loops in z.
-// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool in_range(int i, int n) { return (unsigned)i < (unsigned)n; }
 
-__device__ __forceinline__ bool in_box(int x, int y, int z, int n) {
-    return (unsigned)x < (unsigned)n && (unsigned)y < (unsigned)n && (unsigned)z < (unsigned)n;
+template <typename T>
+struct V2 {
+    T v[2];
+};
+
+template <typename T>
+__device__ __forceinline__ V2<T> ld2(const T* p) {
+    V2<T> r;
+    if constexpr (sizeof(T) == 4) {
+        const float2 f = *reinterpret_cast<const float2*>(p);
+        r.v[0] = f.x;
+        r.v[1] = f.y;
+    } else {
+        const double2 f = *reinterpret_cast<const double2*>(p);
+        r.v[0] = f.x;
+        r.v[1] = f.y;
+    }
+    return r;
 }
 
 template <typename T>
-__device__ __forceinline__ void load_coef(const LevelCoef<T>& q, T* s_invD, T* s_D) {
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    if (tid < 7) {
-        s_invD[tid] = q.invD[tid];
-        s_D[tid] = q.D[tid];
-    }
+__device__ __forceinline__ void st2(T* p, T a, T b) {
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
 // Streaming sweeps: a CTA owns a fine (x, y) tile of SX x SY cells and marches
@@ -91,181 +99,310 @@ __device__ __forceinline__ void load_coef(const LevelCoef<T>& q, T* s_invD, T* s
 // Fine planes are fetched as 16-byte vectors starting 4 cells left of the tile
 // (tiles and grids are multiples of 32, so a vector lies wholly inside or
 // wholly outside the box), one plane ahead into registers, so the loads of
-// plane f+2 are in flight while plane f is computed.
+// plane f+2 are in flight while plane f is computed.  All per-cell work runs
+// on 4-cell x segments (one vector of a plane row): the x neighbours of a
+// segment are its own lanes plus one value on each side, the y and z
+// neighbours are vectors of the adjacent rows and planes.
 constexpr int SX = 32, SY = 16;  // the z extent per CTA (8, 16 or 32 planes) is chosen per launch
-constexpr int PW = SX + 8;               // plane row width in shared memory (x from fx0 - 4)
-constexpr int XH = SY + 4;               // x0 rows, halo 2 (down sweep)
-constexpr int RW = SX + 2, RH = SY + 2;  // residual plane, halo 1
-constexpr int BH = SY + 2;               // b / x rows, halo 1 (up sweep)
-constexpr int CW = SX / 2 + 2, CH = SY / 2 + 2;  // coarse plane with halo 1 (up sweep)
-constexpr int kUpSSmem = 3 * PW * BH + 3 * PW * BH + 3 * CW * CH;
-constexpr int kQ = PW / 4;               // float4 per plane row
+constexpr int PW = SX + 8;       // plane row width in shared memory (x from fx0 - 4)
+constexpr int kQ = PW / 4;       // 4-cell segments per plane row
+constexpr int XH = SY + 4;       // down sweep: x0 rows, y from fy0 - 2
+constexpr int RH = SY + 2;       // down sweep: residual rows, y from fy0 - 1
+constexpr int BH = SY + 2;       // up sweep: b and x rows, y from fy0 - 1
+constexpr int RXY = (SX / 2) * (SY / 2);          // x-y restricted plane (128)
+constexpr int CW = SX / 2 + 6, CH = SY / 2 + 2;   // up sweep: coarse plane, x from cx0 - 3, y from cy0 - 1
+constexpr int kDownSmem = 3 * PW * XH + PW * RH + 4 * RXY;
+constexpr int kUpSmem = 3 * PW * BH + 3 * CW * CH;
 
-__device__ __forceinline__ int ring3(int f) { return (f + 3) % 3; }  // f >= -3
 __device__ __forceinline__ int ring4(int f) { return (f + 4) & 3; }  // f >= -4
 
+// neighbour counts of the 4 cells of a segment in x and y, packed 3 bits each
+__device__ __forceinline__ int kxy_of(int packed, int e) { return (packed >> (3 * e)) & 7; }
+
+// ---------------------------------------------------------------------------
+// Fine planes arrive by TMA: a 4-D tiled tensor map over [S][n][n][n] with a
+// box of PW x rows x 1 x 1 elements (x from fx0 - 4, which keeps the start on a
+// 16-byte boundary); coordinates outside the grid read as zero, which is the
+// "zero outside the box" the sweeps need.  One thread issues the copies into a
+// ring of plane slots, each completing on its own mbarrier.  Every wait is
+// bounded (about one second on the global timer); a wait that gives up sets
+// the CTA's abort flag and the device-wide fault word, later waits return at
+// once and the host reports SPDE_ETIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int kDownStages = 4;
+constexpr int kProducer = kTileThreads - 32;  // issues the plane copies: lane 0 of the last warp, which has no
+                                              // segment work in the residual and prolongation phases
+constexpr int kUpStages = 5;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ int g_mg_fault;
+
 template <typename T>
-struct PlaneRegs {
-    V4<T> v[2];
+__host__ __device__ constexpr int slot_elems(int rows) {  // a plane slot, rounded up to 128 bytes
+    return ((PW * rows * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
+}
+template <typename T>
+__host__ __device__ constexpr int down_smem_bytes() {
+    return 128 + (int)sizeof(T) * (kDownStages * slot_elems<T>(XH) + kDownSmem);
+}
+template <typename T>
+__host__ __device__ constexpr int up_smem_bytes() {
+    return 128 + (int)sizeof(T) * (kUpStages * slot_elems<T>(BH) + kUpSmem);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase of the given parity; false when it gave up
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    return mbar_try(bar, parity) || mbar_wait_slow(bar, parity);
+}
+
+__device__ __forceinline__ void tma_plane(void* dst, const CUtensorMap* map, uint64_t* bar, uint32_t bytes, int x,
+                                          int y, int z, int w) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// The ring of one CTA: plane u of the CTA's sequence (all tiles) lives in slot
+// u % NS and completes phase u / NS of that slot's barrier.
+template <typename T, int NS>
+struct PlaneRing {
+    T* slots;
+    int slot;            // elements per slot
+    uint64_t* bars;
+    volatile int* abort;
+    uint32_t bytes;
+
+    __device__ __forceinline__ T* at(uint32_t u) const { return slots + (int)(u % NS) * slot; }
+    // producer thread only
+    __device__ __forceinline__ void issue(uint32_t u, const CUtensorMap* map, int x, int y, int z, int w) const {
+        if (*abort) return;
+        tma_plane(at(u), map, bars + u % NS, bytes, x, y, z, w);
+    }
+    __device__ __forceinline__ const T* take(uint32_t u) const {
+        if (!*abort && !mbar_wait(bars + u % NS, (u / NS) & 1)) {
+            *abort = 1;
+            atomicExch(&g_mg_fault, 1);
+        }
+        return at(u);
+    }
+    // producer thread, after an abort: bounded wait for copies still in flight
+    __device__ void drain(uint32_t first, uint32_t end) const {
+        for (uint32_t u = first; u < end; ++u) mbar_wait(bars + u % NS, (u / NS) & 1);
+    }
 };
 
-// fetch rows y0 .. y0+rows-1 of plane f (x from x0, PW wide) as vectors; zero outside the box
-template <typename T>
-__device__ __forceinline__ void fetch_plane(PlaneRegs<T>& r, const T* bs, int nf, int64_t plane, int f, int x0,
-                                            int y0, int rows, int tid) {
-    const bool zin = (unsigned)f < (unsigned)nf;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int idx = tid + u * kTileThreads;
-        r.v[u] = zero4<T>();
-        if (idx < kQ * rows && zin) {
-            const int ly = idx / kQ, q4 = idx - ly * kQ;
-            const int gx = x0 + 4 * q4, gy = y0 + ly;
-            if ((unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf)
-                r.v[u] = ld4(bs + gx + (int64_t)nf * gy + plane * f);
-        }
+template <typename T, int NS>
+__device__ __forceinline__ PlaneRing<T, NS> ring_setup(unsigned char* raw, int rows, uint64_t* bars,
+                                                       volatile int* abort, int tid) {
+    PlaneRing<T, NS> r;
+    const uint32_t a = smem_addr(raw);
+    r.slots = reinterpret_cast<T*>(raw + ((128 - (a & 127)) & 127));
+    r.slot = slot_elems<T>(rows);
+    r.bars = bars;
+    r.abort = abort;
+    r.bytes = (uint32_t)(PW * rows * sizeof(T));
+    if (tid == kProducer) {
+        for (int i = 0; i < NS; ++i) mbar_init(bars + i);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    return r;
 }
 
 // ---------------------------------------------------------------------------
 // Down sweep at level l: bc = R (b - A omega D^{-1} b).  With x0 = omega D^{-1} b
 //     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g)
 // (x0 = 0 outside the box, so the sum runs over existing neighbours).
-// Per fine plane f: store the x0 plane f+1, fetch plane f+2, form r on plane
-// f and restrict it in x and y at once (Rxy, 16 x 8 values); every second
-// plane one coarse plane is the 4-tap z combination of four Rxy planes.
-// Each thread's plane positions (offsets, neighbour counts, box tests) are
-// fixed for a tile and computed once before the z-march.
+// Per fine plane f: store the x0 plane f+1 (tile + halo 2), fetch plane f+2,
+// form r on plane f (tile + halo 1) and restrict it in x and y at once (Rxy,
+// 16 x 8 values, two coarse x per thread); every second plane one coarse
+// plane is the 4-tap z combination of four Rxy planes.  Each thread reads
+// back only its own Rxy entries.
 // ---------------------------------------------------------------------------
-constexpr int kRS = (RW * RH + kTileThreads - 1) / kTileThreads;  // r positions per thread (3)
-constexpr int RXY = (SX / 2) * (SY / 2);                            // restricted plane (128)
-constexpr int kDownS2Smem = 3 * PW * XH + RW * RH + 4 * RXY;
-
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads, 4) k_mg_down(int nf, int SZ, LevelCoef<T> q, const T* __restrict__ b,
-                                                             int64_t b_stride, T* __restrict__ bc, int64_t bc_stride,
-                                                             const int* __restrict__ active, int act_stride) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T s_invD[8], s_D[8];
-    T* const Xbase = reinterpret_cast<T*>(smem_raw);  // 3 x0 planes, PW x XH
-    T* const Rp = Xbase + 3 * PW * XH;                 // residual plane, RW x RH
-    T* const Rxy = Rp + RW * RH;                       // 4 x-y restricted planes
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
+    k_mg_down(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
+              int64_t bc_stride, const int* __restrict__ active, int act_stride) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ T s_oi[8], s_rcD[8];
+    __shared__ uint64_t s_bar[kDownStages];
+    __shared__ int s_abort;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
-    load_coef(q, s_invD, s_D);
+    if (*(volatile int*)&g_mg_fault) return;  // an earlier sweep gave up: the host reports it, skip the work
     const int tid = threadIdx.x + 32 * threadIdx.y;
+    const PlaneRing<T, kDownStages> ring = ring_setup<T, kDownStages>(smem_raw, XH, s_bar, &s_abort, tid);
+    T* const Xbase = ring.slots + kDownStages * ring.slot;  // 3 x0 planes, PW x XH
+    T* const Rp = Xbase + 3 * PW * XH;                      // residual plane, PW x RH
+    T* const Rxy = Rp + PW * RH;                            // 4 ring planes of the x-y restricted residual
+    if (tid < 7) {
+        s_oi[tid] = q.oi[tid];
+        s_rcD[tid] = q.rcD[tid];
+    }
     const int nc = nf >> 1;
     const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
     const int ntiles = ntx * nty * ntz;
-    const int64_t plane = (int64_t)nf * nf;
-    const T* bs = b + (int64_t)col * b_stride;
     T* bcs = bc + (int64_t)col * bc_stride;
-    const T rc = (T(1) / q.omega - T(1));
     const T sc = q.s * q.c;
-    const T om = q.omega;
+    const int nplanes = SZ + 4;  // fine planes fz0 - 2 .. fz0 + SZ + 1 per tile
+    uint32_t seq = 0;            // planes of earlier tiles
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
         const int fx0 = tX * SX, fy0 = tY * SY, fz0 = tZ * SZ;
         const int cx0 = fx0 >> 1, cy0 = fy0 >> 1;
+        int issued = 0;  // producer: planes of this tile requested so far
+        auto issue_upto = [&](int jmax) {
+            for (; issued < nplanes && issued <= jmax; ++issued)
+                ring.issue(seq + issued, &bmap, fx0 - 4, fy0 - 2, fz0 - 2 + issued, col);
+        };
+        if (tid == kProducer) issue_upto(kDownStages - 1);
         // --- per-tile slot data
-        // commit: one 4-wide row segment per thread (tid < kQ * XH)
-        int c_off = -1, c_k[4] = {0, 0, 0, 0};
-        if (tid < kQ * XH) {
+        // x0 commit: one segment of the x0 plane (tid < kQ * XH); interior-plane factors cached
+        const bool has_c = tid < kQ * XH;
+        int c_off = 0, c_k = 0;
+        T cI[4];
+        {
             const int ly = tid / kQ, q4 = tid - ly * kQ;
-            const int gy = fy0 - 2 + ly;
-            const int ky = ((unsigned)gy < (unsigned)nf) ? nb_count1(gy, nf) : 0;
+            const int gy = fy0 - 2 + ly, gx0 = fx0 - 4 + 4 * q4;
+            const bool in = has_c && in_range(gy, nf) && in_range(gx0, nf);
             c_off = 4 * q4 + PW * ly;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int gx = fx0 - 4 + 4 * q4 + e;
-                c_k[e] = ky + (((unsigned)gx < (unsigned)nf) ? nb_count1(gx, nf) : 0);
+                const int k = in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
+                c_k |= k << (3 * e);
+                cI[e] = s_oi[k + 2];
             }
         }
-        // residual positions: X offset and kx + ky, or -1 when outside the box in x/y
-        int r_xi[kRS], r_k[kRS];
-#pragma unroll
-        for (int u = 0; u < kRS; ++u) {
-            const int idx = tid + u * kTileThreads;
-            r_xi[u] = 0;
-            r_k[u] = -2;  // -2: no position; -1: outside the box
-            if (idx < RW * RH) {
-                const int ly = idx / RW, lx = idx - ly * RW;
-                const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
-                r_xi[u] = (lx + 3) + PW * (ly + 1);
-                r_k[u] = ((unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf)
-                             ? nb_count1(gx, nf) + nb_count1(gy, nf)
-                             : -1;
-            }
-        }
-        // x-y restriction of one coarse (I, J) per thread (tid < RXY)
-        T wx[4], wy[4];
-        int rb = 0;
+        // residual: one segment of the residual plane (tid < kQ * RH)
+        const bool has_r = tid < kQ * RH;
+        int r_off = 0, r_k = 0;
+        bool r_in = false;
+        T rI[4];
         {
-            const int li = tid & (SX / 2 - 1), lj = (tid / (SX / 2)) & (SY / 2 - 1);
-            const int I = cx0 + li, J = cy0 + lj;
+            const int ly = tid / kQ, q4 = tid - ly * kQ;
+            const int gy = fy0 - 1 + ly, gx0 = fx0 - 4 + 4 * q4;
+            r_in = has_r && in_range(gy, nf) && in_range(gx0, nf);
+            r_off = 4 * q4 + PW * ly;
 #pragma unroll
-            for (int a3 = 0; a3 < 4; ++a3) {
-                wx[a3] = (T)restrict_w(a3, I, nc);
-                wy[a3] = (T)restrict_w(a3, J, nc);
+            for (int e = 0; e < 4; ++e) {
+                const int k = r_in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
+                r_k |= k << (3 * e);
+                rI[e] = s_rcD[k + 2];
             }
-            rb = 2 * li + RW * (2 * lj);
         }
+        // restriction: coarse x pair (cx0 + 2 qm, + 1) of coarse row cy0 + qj (tid < RXY / 2)
+        const bool has_q = tid < RXY / 2;
+        const int qm = tid & 7, qj = (tid >> 3) & 7;
+        T wa[4], wb[4], wy[4];
+#pragma unroll
+        for (int a3 = 0; a3 < 4; ++a3) {
+            wa[a3] = (T)restrict_w(a3, cx0 + 2 * qm, nc);
+            wb[a3] = (T)restrict_w(a3, cx0 + 2 * qm + 1, nc);
+            wy[a3] = (T)restrict_w(a3, cy0 + qj, nc);
+        }
+        const int q_off = 4 * qm + 3 + PW * (2 * qj);  // residual of fine (2I - 1, 2J - 1), I = cx0 + 2 qm
         T* Xm = Xbase;
         T* Xc = Xbase + PW * XH;
         T* Xp = Xbase + 2 * PW * XH;
-        auto commit = [&](const PlaneRegs<T>& r, T* dst, int f) {
-            const int kz = ((unsigned)f < (unsigned)nf) ? nb_count1(f, nf) : 0;
-            if (c_off >= 0) {
+        // x0 plane f (tile plane j) from its b plane in the ring
+        auto commit = [&](int j, T* dst, int f) {
+            const T* raw = ring.take(seq + j);
+            if (has_c) {
+                const bool wall = (f == 0 || f == nf - 1);  // b = 0 off the box, any factor will do
+                const V4<T> bv = ld4(raw + c_off);
                 V4<T> v;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) v.v[e] = om * r.v[0].v[e] * s_invD[c_k[e] + kz];
+                for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * (wall ? s_oi[kxy_of(c_k, e) + 1] : cI[e]);
                 st4(dst + c_off, v);
             }
         };
-        PlaneRegs<T> pr;
-        fetch_plane(pr, bs, nf, plane, fz0 - 2, fx0 - 4, fy0 - 2, XH, tid);
-        commit(pr, Xm, fz0 - 2);
-        fetch_plane(pr, bs, nf, plane, fz0 - 1, fx0 - 4, fy0 - 2, XH, tid);
-        commit(pr, Xc, fz0 - 1);
-        fetch_plane(pr, bs, nf, plane, fz0, fx0 - 4, fy0 - 2, XH, tid);
+        commit(0, Xm, fz0 - 2);
+        commit(1, Xc, fz0 - 1);
         for (int f = fz0 - 1; f <= fz0 + SZ; ++f) {
-            commit(pr, Xp, f + 1);
-            if (f + 2 <= fz0 + SZ + 1) fetch_plane(pr, bs, nf, plane, f + 2, fx0 - 4, fy0 - 2, XH, tid);
+            const int j = f - fz0 + 3;
+            commit(j, Xp, f + 1);
             __syncthreads();
-            {
-                const bool zin = (unsigned)f < (unsigned)nf;
-                const int kz = zin ? nb_count1(f, nf) : 0;
+            if (tid == kProducer) issue_upto(j + kDownStages);  // planes <= j are consumed: their slots are free
+            if (has_r) {
+                V4<T> r = zero4<T>();
+                if (r_in && in_range(f, nf)) {
+                    const bool wall = (f == 0 || f == nf - 1);
+                    const int xo = r_off + PW;  // x0 rows start one row above the residual rows
+                    const V4<T> c = ld4(Xc + xo), u = ld4(Xc + xo - PW), d = ld4(Xc + xo + PW);
+                    const V4<T> m = ld4(Xm + xo), p = ld4(Xp + xo);
+                    const T xl = Xc[xo - 1], xr = Xc[xo + 4];
 #pragma unroll
-                for (int u = 0; u < kRS; ++u) {
-                    if (r_k[u] == -2) continue;
-                    T r = T(0);
-                    if (zin && r_k[u] >= 0) {
-                        const int xi = r_xi[u];
-                        const T nbs = (Xc[xi - 1] + Xc[xi + 1]) + (Xc[xi - PW] + Xc[xi + PW]) + (Xm[xi] + Xp[xi]);
-                        r = rc * s_D[r_k[u] + kz] * Xc[xi] + sc * nbs;
+                    for (int e = 0; e < 4; ++e) {
+                        const T left = (e == 0) ? xl : c.v[e - 1];
+                        const T right = (e == 3) ? xr : c.v[e + 1];
+                        const T nbs = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
+                        r.v[e] = (wall ? s_rcD[kxy_of(r_k, e) + 1] : rI[e]) * c.v[e] + sc * nbs;
                     }
-                    Rp[tid + u * kTileThreads] = r;
                 }
+                st4(Rp + r_off, r);
             }
             __syncthreads();
-            if (tid < RXY) {
-                T acc = T(0);
+            if (has_q) {
+                T acc0 = T(0), acc1 = T(0);
 #pragma unroll
                 for (int b3 = 0; b3 < 4; ++b3) {
-                    const T* row = Rp + rb + RW * b3;
-                    acc += wy[b3] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2] + wx[3] * row[3]);
+                    const T* row = Rp + q_off + PW * b3;
+                    const T a0 = row[0], a5 = row[5];
+                    const V4<T> v = ld4(row + 1);
+                    const T p0 = wa[0] * a0 + wa[1] * v.v[0] + wa[2] * v.v[1] + wa[3] * v.v[2];
+                    const T p1 = wb[0] * v.v[1] + wb[1] * v.v[2] + wb[2] * v.v[3] + wb[3] * a5;
+                    acc0 += wy[b3] * p0;
+                    acc1 += wy[b3] * p1;
                 }
-                Rxy[ring4(f) * RXY + tid] = acc;
+                st2(Rxy + ring4(f) * RXY + 2 * tid, acc0, acc1);
                 if (f >= fz0 + 2 && ((f - fz0) & 1) == 0) {
                     // coarse plane Z = f/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = f-3 .. f
                     const int Z = (f - 2) >> 1;
-                    T z = T(0);
+                    const T w3 = (T)restrict_w(3, Z, nc);
+                    T z0 = w3 * acc0, z1 = w3 * acc1;
 #pragma unroll
-                    for (int c3 = 0; c3 < 4; ++c3)
-                        z += (T)restrict_w(c3, Z, nc) * ((c3 == 3) ? acc : Rxy[ring4(f - 3 + c3) * RXY + tid]);
-                    const int li = tid & (SX / 2 - 1), lj = tid / (SX / 2);
-                    bcs[(cx0 + li) + (int64_t)nc * ((cy0 + lj) + (int64_t)nc * Z)] = z;
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        const V2<T> v = ld2(Rxy + ring4(f - 3 + c3) * RXY + 2 * tid);
+                        const T w = (T)restrict_w(c3, Z, nc);
+                        z0 += w * v.v[0];
+                        z1 += w * v.v[1];
+                    }
+                    st2(bcs + (cx0 + 2 * qm) + (int64_t)nc * ((cy0 + qj) + (int64_t)nc * Z), z0, z1);
                 }
             }
             T* t = Xm;
@@ -274,44 +411,53 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_mg_down(int nf, int SZ, Lev
             Xp = t;
         }
         __syncthreads();
+        if (tid == kProducer && s_abort) ring.drain(seq, seq + issued);
+        seq += nplanes;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x),
+// Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x)
+//     = (1 - omega) x + omega D^{-1} b + omega s c D^{-1} sum_{neighbours} x,
 // optional partial sums of b.y (the MINRES beta^2 contribution).  Per fine
 // plane g: store b(g) and (for even g) coarse plane g/2 + 1, fetch the next
 // ones, form x(g) on the tile + halo 1, then y(g - 1) from x planes g-2 .. g.
-// Per-thread positions, neighbour counts and prolongation offsets are fixed
-// for a tile and computed once before the z-march.
+// The prolongation of a 4-cell segment blends two coarse planes (z), two
+// coarse rows (y) and then the four coarse x values the segment touches.
+// Coarse planes are stored with clamped x and y indices, which is the wall
+// reflection of P.
 // ---------------------------------------------------------------------------
-constexpr int kXS = (RW * BH + kTileThreads - 1) / kTileThreads;  // x positions per thread (3)
-
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads, 3) k_mg_up(int nf, int SZ, LevelCoef<T> q, const T* __restrict__ b,
-                                                           int64_t b_stride, const T* __restrict__ ec,
-                                                           int64_t ec_stride, T* __restrict__ y, int64_t y_stride,
-                                                           double* __restrict__ dot_part,
-                                                           const int* __restrict__ active, int act_stride) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
+    k_mg_up(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
+            int64_t ec_stride, T* __restrict__ y, int64_t y_stride, double* __restrict__ dot_part,
+            const int* __restrict__ active, int act_stride) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
-    __shared__ T s_invD[8], s_D[8];
-    T* const Bbase = reinterpret_cast<T*>(smem_raw);  // 3 b planes, PW x BH
-    T* const Xbase = Bbase + 3 * PW * BH;              // 3 x planes, PW x BH
-    T* const Cbase = Xbase + 3 * PW * BH;              // 3 coarse planes, CW x CH
+    __shared__ T s_oi[8], s_ois[8];
+    __shared__ uint64_t s_bar[kUpStages];
+    __shared__ int s_abort;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
-    load_coef(q, s_invD, s_D);
+    if (*(volatile int*)&g_mg_fault) return;
     const int tid = threadIdx.x + 32 * threadIdx.y;
+    const PlaneRing<T, kUpStages> ring = ring_setup<T, kUpStages>(smem_raw, BH, s_bar, &s_abort, tid);
+    T* const Xbase = ring.slots + kUpStages * ring.slot;  // 3 x planes, PW x BH
+    T* const Cbase = Xbase + 3 * PW * BH;                 // 3 coarse planes, CW x CH
+    if (tid < 7) {
+        s_oi[tid] = q.oi[tid];
+        s_ois[tid] = q.ois[tid];
+    }
     const int nc = nf >> 1;
     const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
     const int ntiles = ntx * nty * ntz;
     const int64_t plane = (int64_t)nf * nf, cplane = (int64_t)nc * nc;
-    const T* bs = b + (int64_t)col * b_stride;
     const T* es = ec + (int64_t)col * ec_stride;
     T* ys = y + (int64_t)col * y_stride;
-    const T om = q.omega;
+    const T om1 = T(1) - q.omega;
     const T w0 = T(0.75), w1 = T(0.25);
+    const int nplanes = SZ + 2;  // b planes fz0 - 1 .. fz0 + SZ per tile
+    uint32_t seq = 0;
     T dacc = T(0);  // per-thread partial of b.y in the element type; FP64 across threads
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -319,53 +465,54 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_mg_up(int nf, int SZ, Level
         const int fx0 = tX * SX, fy0 = tY * SY, fz0 = tZ * SZ;
         const int cx0 = fx0 >> 1, cy0 = fy0 >> 1;
         const int cz0 = fz0 >> 1;
+        int issued = 0;
+        auto issue_upto = [&](int jmax) {
+            for (; issued < nplanes && issued <= jmax; ++issued)
+                ring.issue(seq + issued, &bmap, fx0 - 4, fy0 - 1, fz0 - 1 + issued, col);
+        };
+        if (tid == kProducer) issue_upto(kUpStages - 1);
         // --- per-tile slot data
         int c_src = -1;  // coarse plane element of this thread (clamped x, y), or -1
         if (tid < CW * CH) {
             const int ly = tid / CW, lx = tid - ly * CW;
-            const int gx = min(max(cx0 - 1 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
+            const int gx = min(max(cx0 - 3 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
             c_src = gx + nc * gy;
         }
-        int x_xi[kXS], x_k[kXS], x_c00[kXS], x_c10[kXS], x_c01[kXS], x_c11[kXS];
+        // prolongation: one segment of the x plane (tid < kQ * BH)
+        const bool has_x = tid < kQ * BH;
+        int x_off = 0, x_k = 0, p_r0 = 0, p_r1 = 0;
+        bool x_in = false;
+        T xI[4];
+        {
+            const int ly = tid / kQ, q4 = tid - ly * kQ;
+            const int gy = fy0 - 1 + ly, gx0 = fx0 - 4 + 4 * q4;
+            x_in = has_x && in_range(gy, nf) && in_range(gx0, nf);
+            x_off = 4 * q4 + PW * ly;
+            if (x_in) {
+                // coarse rows (gy >> 1) and its other neighbour; coarse x gx0/2 - 1 .. gx0/2 + 2
+                p_r0 = ((gy >> 1) - (cy0 - 1)) * CW + 2 * q4;
+                p_r1 = p_r0 + ((gy & 1) ? CW : -CW);
+            }
 #pragma unroll
-        for (int u = 0; u < kXS; ++u) {
-            const int idx = tid + u * kTileThreads;
-            x_xi[u] = 0;
-            x_k[u] = -2;
-            x_c00[u] = x_c10[u] = x_c01[u] = x_c11[u] = 0;
-            if (idx < RW * BH) {
-                const int ly = idx / RW, lx = idx - ly * RW;
-                const int gx = fx0 - 1 + lx, gy = fy0 - 1 + ly;
-                x_xi[u] = (lx + 3) + PW * ly;
-                if ((unsigned)gx < (unsigned)nf && (unsigned)gy < (unsigned)nf) {
-                    x_k[u] = nb_count1(gx, nf) + nb_count1(gy, nf);
-                    const int Ix = gx >> 1, Iy = gy >> 1;
-                    const int px0 = Ix - (cx0 - 1);
-                    const int px1 = min(max((gx & 1) ? Ix + 1 : Ix - 1, 0), nc - 1) - (cx0 - 1);
-                    const int py0 = Iy - (cy0 - 1);
-                    const int py1 = min(max((gy & 1) ? Iy + 1 : Iy - 1, 0), nc - 1) - (cy0 - 1);
-                    x_c00[u] = px0 + CW * py0;
-                    x_c10[u] = px1 + CW * py0;
-                    x_c01[u] = px0 + CW * py1;
-                    x_c11[u] = px1 + CW * py1;
-                } else {
-                    x_k[u] = -1;
-                }
+            for (int e = 0; e < 4; ++e) {
+                const int k = x_in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
+                x_k |= k << (3 * e);
+                xI[e] = s_oi[k + 2];
             }
         }
-        // output: 4 consecutive cells per thread (tid < SX * SY / 4)
-        const int oy = tid / (SX / 4), ox0 = 4 * (tid - oy * (SX / 4));
+        // output: one segment of the tile (tid < SX * SY / 4)
         const bool has_out = tid < SX * SY / 4;
+        const int oy = tid / (SX / 4), ox0 = 4 * (tid - oy * (SX / 4));
         const int o_xi = (ox0 + 4) + PW * (oy + 1);
-        int o_k[4];
-        {
-            const int ky = has_out ? nb_count1(fy0 + oy, nf) : 0;
+        int o_k = 0;
+        T oI[4], sI[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) o_k[e] = ky + (has_out ? nb_count1(fx0 + ox0 + e, nf) : 0);
+        for (int e = 0; e < 4; ++e) {
+            const int k = has_out ? nb_count1(fy0 + oy, nf) + nb_count1(fx0 + ox0 + e, nf) : 0;
+            o_k |= k << (3 * e);
+            oI[e] = s_oi[k + 2];
+            sI[e] = s_ois[k + 2];
         }
-        T* Bm = Bbase;  // b planes g-2, g-1, g (rotating)
-        T* Bc = Bbase + PW * BH;
-        T* Bp = Bbase + 2 * PW * BH;
         T* Xm = Xbase;  // x planes g-2, g-1, g (rotating)
         T* Xc = Xbase + PW * BH;
         T* Xp = Xbase + 2 * PW * BH;
@@ -375,47 +522,46 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_mg_up(int nf, int SZ, Level
         auto fetch_c = [&](int Z) -> T {
             return (c_src >= 0) ? es[c_src + cplane * min(max(Z, 0), nc - 1)] : T(0);
         };
-        auto commit_b = [&](const PlaneRegs<T>& r, T* dst) {
-            if (tid < kQ * BH) st4(dst + 4 * tid, r.v[0]);
-        };
+        // x(g) on the tile + halo 1 from b(g) and the coarse planes Iz (C0, weight 3/4) and its z neighbour (C1)
         auto make_x = [&](int g, const T* Bg, T* Xg, const T* C0, const T* C1) {
-            const bool zin = (unsigned)g < (unsigned)nf;
-            const int kz = zin ? nb_count1(g, nf) : 0;
+            if (!has_x) return;
+            V4<T> v = zero4<T>();
+            if (x_in && in_range(g, nf)) {
+                const bool wall = (g == 0 || g == nf - 1);
+                const V2<T> a0 = ld2(C0 + p_r0), a1 = ld2(C0 + p_r0 + 2);
+                const V2<T> b0 = ld2(C0 + p_r1), b1 = ld2(C0 + p_r1 + 2);
+                const V2<T> c0 = ld2(C1 + p_r0), c1 = ld2(C1 + p_r0 + 2);
+                const V2<T> d0 = ld2(C1 + p_r1), d1 = ld2(C1 + p_r1 + 2);
+                const T ar[4] = {a0.v[0], a0.v[1], a1.v[0], a1.v[1]};
+                const T br[4] = {b0.v[0], b0.v[1], b1.v[0], b1.v[1]};
+                const T cr[4] = {c0.v[0], c0.v[1], c1.v[0], c1.v[1]};
+                const T dr[4] = {d0.v[0], d0.v[1], d1.v[0], d1.v[1]};
+                T cy[4];
 #pragma unroll
-            for (int u = 0; u < kXS; ++u) {
-                if (x_k[u] == -2) continue;
-                T v = T(0);
-                if (zin && x_k[u] >= 0) {
-                    const T a00 = w0 * C0[x_c00[u]] + w1 * C0[x_c10[u]];
-                    const T a10 = w0 * C0[x_c01[u]] + w1 * C0[x_c11[u]];
-                    const T a01 = w0 * C1[x_c00[u]] + w1 * C1[x_c10[u]];
-                    const T a11 = w0 * C1[x_c01[u]] + w1 * C1[x_c11[u]];
-                    const T pe = w0 * (w0 * a00 + w1 * a10) + w1 * (w0 * a01 + w1 * a11);
-                    v = om * Bg[x_xi[u]] * s_invD[x_k[u] + kz] + pe;
-                }
-                Xg[x_xi[u]] = v;
+                for (int p = 0; p < 4; ++p)
+                    cy[p] = w0 * (w0 * ar[p] + w1 * cr[p]) + w1 * (w0 * br[p] + w1 * dr[p]);
+                const T pe[4] = {w0 * cy[1] + w1 * cy[0], w0 * cy[1] + w1 * cy[2], w0 * cy[2] + w1 * cy[1],
+                                 w0 * cy[2] + w1 * cy[3]};
+                const V4<T> bb = ld4(Bg + x_off);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    v.v[e] = (wall ? s_oi[kxy_of(x_k, e) + 1] : xI[e]) * bb.v[e] + pe[e];
             }
+            st4(Xg + x_off, v);
         };
-        PlaneRegs<T> pb;
         // prologue: coarse planes cz0-1 (Cc role for g = fz0-1 -> Iz = cz0-1) and cz0
         if (c_src >= 0) {
             Cc[tid] = fetch_c(cz0 - 1);
             Cp[tid] = fetch_c(cz0);
         }
-        fetch_plane(pb, bs, nf, plane, fz0 - 1, fx0 - 4, fy0 - 1, BH, tid);
-        commit_b(pb, Bp);
+        const T* Bprev = ring.take(seq);
         __syncthreads();
-        make_x(fz0 - 1, Bp, Xp, Cc, Cp);  // odd g: planes Iz and Iz + 1
-        fetch_plane(pb, bs, nf, plane, fz0, fx0 - 4, fy0 - 1, BH, tid);
+        make_x(fz0 - 1, Bprev, Xp, Cc, Cp);  // odd g: planes Iz and Iz + 1
         T pc = fetch_c(cz0 + 1);
         for (int g = fz0; g <= fz0 + SZ; ++g) {
-            // rotate roles: plane g goes to the freed slot
+            const int j = g - fz0 + 1;
             {
-                T* t = Bm;
-                Bm = Bc;
-                Bc = Bp;
-                Bp = t;
-                t = Xm;
+                T* t = Xm;
                 Xm = Xc;
                 Xc = Xp;
                 Xp = t;
@@ -427,34 +573,39 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_mg_up(int nf, int SZ, Level
                 Cp = t;
                 if (c_src >= 0) Cp[tid] = pc;
             }
-            commit_b(pb, Bp);
-            if (g + 1 <= fz0 + SZ) {
-                fetch_plane(pb, bs, nf, plane, g + 1, fx0 - 4, fy0 - 1, BH, tid);
-                if (((g + 1) & 1) == 0) pc = fetch_c(((g + 1) >> 1) + 1);
-            }
+            const T* Bcur = ring.take(seq + j);
+            if (g + 1 <= fz0 + SZ && ((g + 1) & 1) == 0) pc = fetch_c(((g + 1) >> 1) + 1);
             __syncthreads();
-            if ((g & 1) == 0) make_x(g, Bp, Xp, Cc, Cm);  // even g: planes Iz and Iz - 1
-            else make_x(g, Bp, Xp, Cc, Cp);               // odd g: planes Iz and Iz + 1
+            if (tid == kProducer) issue_upto(j - 2 + kUpStages);  // planes <= j - 2 are consumed: their slots are free
+            if ((g & 1) == 0) make_x(g, Bcur, Xp, Cc, Cm);  // even g: planes Iz and Iz - 1
+            else make_x(g, Bcur, Xp, Cc, Cp);               // odd g: planes Iz and Iz + 1
             __syncthreads();
-            const int f = g - 1;  // output plane: x planes f-1, f, f+1 = Xm, Xc, Xp; b(f) = Bc
+            const int f = g - 1;  // output plane: x planes f-1, f, f+1 = Xm, Xc, Xp; b(f) = Bprev
             if (f >= fz0 && has_out) {
-                const int kz = nb_count1(f, nf);
+                const bool wall = (f == 0 || f == nf - 1);
+                const V4<T> c = ld4(Xc + o_xi), u = ld4(Xc + o_xi - PW), d = ld4(Xc + o_xi + PW);
+                const V4<T> m = ld4(Xm + o_xi), p = ld4(Xp + o_xi), bb = ld4(Bprev + o_xi);
+                const T xl = Xc[o_xi - 1], xr = Xc[o_xi + 4];
                 V4<T> out;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int xi = o_xi + e;
-                    const T x0 = Xc[xi];
-                    const T nbs = (Xc[xi - 1] + Xc[xi + 1]) + (Xc[xi - PW] + Xc[xi + PW]) + (Xm[xi] + Xp[xi]);
-                    const int k0 = o_k[e] + kz;
-                    const T bv = Bc[xi];
-                    const T yv = x0 + om * s_invD[k0] * (bv - q.s * (q.a * x0 + q.c * ((T)k0 * x0 - nbs)));
+                    const T left = (e == 0) ? xl : c.v[e - 1];
+                    const T right = (e == 3) ? xr : c.v[e + 1];
+                    const T nbs = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
+                    const int kw = kxy_of(o_k, e) + 1;
+                    const T oi = wall ? s_oi[kw] : oI[e];
+                    const T ois = wall ? s_ois[kw] : sI[e];
+                    const T yv = om1 * c.v[e] + oi * bb.v[e] + ois * nbs;
                     out.v[e] = yv;
-                    dacc += bv * yv;
+                    dacc += bb.v[e] * yv;
                 }
                 st4(ys + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f, out);
             }
+            Bprev = Bcur;
         }
         __syncthreads();
+        if (tid == kProducer && s_abort) ring.drain(seq, seq + issued);
+        seq += nplanes;
     }
     if (dot_part) {
         const double tsum = block_sum<kTileThreads>((double)dacc, red);
@@ -500,7 +651,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
                                                               T* __restrict__ eout, int64_t e_stride,
                                                               double* __restrict__ dot_part,
                                                               const int* __restrict__ active, int act_stride) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kCoarseThreads / 32];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int col = blockIdx.x;
@@ -675,12 +826,56 @@ static cudaError_t mg_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mg_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kDownS2Smem * (int)sizeof(T));
+        e = cudaFuncSetAttribute(k_mg_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kUpSSmem * (int)sizeof(T));
+        e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_smem_bytes<T>());
     return e;
+}
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// tensor map of S stacked n^3 grids (column stride col_stride elements), box PW x rows x 1 x 1
+template <typename T>
+static bool plane_map(CUtensorMap* m, const T* base, int n, int S, int64_t col_stride, int rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    const size_t es = sizeof(T);
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || ((col_stride * es) & 15) || ((n * es) & 15)) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)S};
+    const cuuint64_t strides[3] = {(cuuint64_t)n * es, (cuuint64_t)n * n * es, (cuuint64_t)col_stride * es};
+    const cuuint32_t box[4] = {(cuuint32_t)PW, (cuuint32_t)rows, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+              const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t mg_fault_read(int* host, cudaStream_t st) {
+    return cudaMemcpyFromSymbolAsync(host, g_mg_fault, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+}
+
+cudaError_t mg_fault_clear(cudaStream_t st) {
+    static const int zero = 0;
+    const cudaError_t e = cudaMemcpyToSymbolAsync(g_mg_fault, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
 }
 
 // once per instantiation and process (thread-safe static initialisation)
@@ -721,9 +916,11 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const int ntiles = (nf / SX) * (nf / SY) * (nf / sz);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
+        CUtensorMap map;
+        if (!plane_map<T>(&map, in, nf, S, in_stride, XH)) return -1;
         prof_begin(PK_MG_DOWN, st);
-        k_mg_down<T><<<grid, dim3(32, 8), kDownS2Smem * sizeof(T), st>>>(nf, sz, level_coef<T>(plan, l), in, in_stride, out,
-                                                    (int64_t)nc * nc * nc, active, act_stride);
+        k_mg_down<T><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(map, nf, sz, level_coef<T>(plan, l), out,
+                                                                      (int64_t)nc * nc * nc, active, act_stride);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
         in = out;
         in_stride = (int64_t)nc * nc * nc;
@@ -747,10 +944,13 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const int64_t bls = (l == 0) ? b_stride : (int64_t)nf * nf * nf;
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
         const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
+        CUtensorMap map;
+        if (!plane_map<T>(&map, bl, nf, S, bls, BH)) return -1;
         prof_begin(PK_MG_UP, st);
-        k_mg_up<T><<<grid, dim3(32, 8), kUpSSmem * sizeof(T), st>>>(nf, sz, level_coef<T>(plan, l), bl, bls,
-                                                  static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
-                                                  yls, (l == 0) ? dot_part : nullptr, active, act_stride);
+        k_mg_up<T><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(map, nf, sz, level_coef<T>(plan, l),
+                                                                  static_cast<const T*>(plan.e[l + 1]),
+                                                                  (int64_t)nc * nc * nc, yl, yls,
+                                                                  (l == 0) ? dot_part : nullptr, active, act_stride);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);
         if (l == 0) nblk0 = nb;
     }

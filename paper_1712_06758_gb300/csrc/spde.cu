@@ -423,6 +423,14 @@ spde_status cg_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws
     return SPDE_OK;
 }
 
+// a V-cycle sweep that gave up waiting for a plane copy leaves the columns of
+// that solve invalid: report it (and reset the fault word for later calls)
+static spde_status fault_status(int fault, cudaStream_t st) {
+    if (!fault) return SPDE_OK;
+    CUDA_TRY(mg_fault_clear(st));
+    return fail(SPDE_ETIMEOUT, "a multigrid sweep gave up waiting for a plane copy; this solve's results are invalid");
+}
+
 // Solve (D A D) x = [0; F] for S columns: FP64 iterative refinement around an
 // inner MINRES of element type T.  F, x64 in ws; returns the max relative
 // residual in *maxrel.
@@ -463,7 +471,10 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, st));
         prof_end(st, (double)S * nb * 8.0);
         CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        int fault = 0;
+        CUDA_TRY(mg_fault_read(&fault, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        STATUS_TRY(fault_status(fault, st));
         int nact = 0;
         worst = 0.0;
         for (int s = 0; s < S; ++s) {
@@ -768,7 +779,10 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
                                       L->d_mask, st);
     CUDA_TRY(launch_reduce(S, ws.partR, nbr, ws.colv, st));
     CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int fault = 0;
+    CUDA_TRY(mg_fault_read(&fault, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    STATUS_TRY(fault_status(fault, st));
     std::vector<int> going;
     for (int c = 0; c < S; ++c) {
         Lane::Slot& sl = L->slots[c];
