@@ -14,11 +14,34 @@ struct MinresCol {
     double tol;      // stop when phibar <= tol * beta1
     // coefficients of the pending w/x update (saved by the Givens step)
     double d_oldb, d_oldeps, d_delta, d_gamma, d_phi;
+    // the per-column factors the vector passes use, computed once by the scalar
+    // steps (FP64, and rounded to FP32 for the FP32 passes) so that no thread of
+    // a vector pass divides in FP64
+    double kd[8];
+    float kf[8];
     int active;      // column still iterating
     int upd;         // a w/x update is pending (consumed by the next fused pass or the final D)
     int iters;
     int d_iter;      // iteration number of the pending update
 };
+
+// indices of MinresCol::kd / kf
+enum {
+    KC_IB = 0,    // 1 / beta            (Lanczos pass)
+    KC_COEF = 1,  // beta / oldb, 0 in the first iteration
+    KC_F = 2,     // alpha / beta        (second Lanczos pass)
+    KC_IV = 3,    // 1 / d_oldb          (w/x update)
+    KC_OE = 4,    // d_oldeps
+    KC_DE = 5,    // d_delta
+    KC_IG = 6,    // 1 / d_gamma
+    KC_PH = 7     // d_phi
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ T col_coef(const MinresCol& c, int k) {
+    if constexpr (sizeof(T) == 4) return c.kf[k];
+    else return c.kd[k];
+}
 
 // Per-column state of the Schur-complement CG (FP64 scalars).
 struct CgCol {

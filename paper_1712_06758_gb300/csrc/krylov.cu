@@ -35,6 +35,11 @@ static inline int cell_blocks(int64_t n3) {
 //                             x += phi w'   (cell block, [S][n^3] arrays)
 // The D coefficients were saved by the Givens step in MinresCol (d_* fields)
 // because beta / oldb have already advanced for the A part.
+__device__ __forceinline__ void set_coef(MinresCol& c, int k, double v) {
+    c.kd[k] = v;
+    c.kf[k] = (float)v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n, T kh2, const T* __restrict__ y, T* __restrict__ r1,
                                                      double* __restrict__ partA, const MinresCol* __restrict__ st,
@@ -54,8 +59,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n,
     T* rs = r1 + off;
     T acc = T(0);
     if (doA) {
-        const T ib = (T)(1.0 / cs.beta);
-        const T coef = (T)(cs.oldb > 0.0 ? cs.beta / cs.oldb : 0.0);
+        const T ib = col_coef<T>(cs, KC_IB);
+        const T coef = col_coef<T>(cs, KC_COEF);
         // r1 holds no data before the second iteration (coef == 0): do not read it
         const bool use_r1 = coef != T(0);
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -88,8 +93,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n,
         }
     }
     if (doD) {
-        const T iv = (T)(1.0 / cs.d_oldb);
-        const T oe = (T)cs.d_oldeps, de = (T)cs.d_delta, ig = (T)(1.0 / cs.d_gamma), ph = (T)cs.d_phi;
+        const T iv = col_coef<T>(cs, KC_IV), oe = col_coef<T>(cs, KC_OE), de = col_coef<T>(cs, KC_DE);
+        const T ig = col_coef<T>(cs, KC_IG), ph = col_coef<T>(cs, KC_PH);
         const int it = cs.d_iter;
         const T* yc = yprev + off + 3 * (int64_t)n3;
         const int64_t o3 = (int64_t)s * n3;
@@ -119,7 +124,7 @@ template <typename T>
 int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, const T* yprev,
                     T* w1, const T* w2, T* xd, cudaStream_t st) {
     const int64_t n3 = (int64_t)n * n * n;
-    const int nb = cell_blocks(n3 / 4);
+    const int nb = cell_blocks(n3 / 16);  // four quads per thread: one reduction per 1024 quads
     dim3 grid(nb, S);
     k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, r1, partA, st_, yprev, w1, w2, xd);
     return nb;
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(256) k_minres_B(int64_t N4, int64_t n3u, T* __
     const int s = blockIdx.y;
     const MinresCol& cs = st[s];
     if (!cs.active) return;
-    const T f = (T)(cs.alpha / cs.beta);
+    const T f = col_coef<T>(cs, KC_F);
     const int64_t off = (int64_t)s * N4;
     T acc = T(0);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x) {
@@ -196,7 +201,10 @@ __global__ void __launch_bounds__(256) k_alpha(const double* __restrict__ partA,
     const int s = blockIdx.x;
     if (!st[s].active) return;
     const double a = col_sum(partA, s, nA, red);
-    if (threadIdx.x == 0) st[s].alpha = a;
+    if (threadIdx.x == 0) {
+        st[s].alpha = a;
+        set_coef(st[s], KC_F, a / st[s].beta);
+    }
 }
 
 cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cudaStream_t st) {
@@ -242,6 +250,13 @@ __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB
     c.d_gamma = gamma;
     c.d_phi = c.phi;
     c.d_iter = c.iters;
+    set_coef(c, KC_IB, 1.0 / beta);
+    set_coef(c, KC_COEF, c.oldb > 0.0 ? beta / c.oldb : 0.0);
+    set_coef(c, KC_IV, 1.0 / c.d_oldb);
+    set_coef(c, KC_OE, c.d_oldeps);
+    set_coef(c, KC_DE, c.d_delta);
+    set_coef(c, KC_IG, 1.0 / c.d_gamma);
+    set_coef(c, KC_PH, c.d_phi);
     const bool done = !(beta2 > 0.0) || !isfinite(beta) || c.phibar <= c.tol * c.beta1;
     if (done) c.active = 0;
     else if (nactive) atomicAdd(nactive, 1);
@@ -284,6 +299,8 @@ __global__ void __launch_bounds__(256) k_minres_init(const double* __restrict__ 
     c.tol = tol;
     c.upd = 0;
     c.iters = 0;
+    set_coef(c, KC_IB, 1.0 / beta1);
+    set_coef(c, KC_COEF, 0.0);
     c.active = (beta2 > 0.0 && isfinite(beta1)) ? 1 : 0;
     if (c.active && nactive) atomicAdd(nactive, 1);
 }
@@ -303,8 +320,8 @@ __global__ void __launch_bounds__(256) k_minres_D(int64_t n3, const T* __restric
     const int s = blockIdx.y;
     const MinresCol& c = st[s];
     if (!c.upd) return;
-    const T iv = (T)(1.0 / c.d_oldb);
-    const T oe = (T)c.d_oldeps, de = (T)c.d_delta, ig = (T)(1.0 / c.d_gamma), ph = (T)c.d_phi;
+    const T iv = col_coef<T>(c, KC_IV), oe = col_coef<T>(c, KC_OE), de = col_coef<T>(c, KC_DE);
+    const T ig = col_coef<T>(c, KC_IG), ph = col_coef<T>(c, KC_PH);
     const T* ys = ycur + (int64_t)s * 4 * n3 + 3 * n3;
     const int64_t off = (int64_t)s * n3;
     // iteration 1: w1 = w2 = 0 and x = 0; iteration 2: w1 = 0 (buffers hold no data yet)
