@@ -95,14 +95,13 @@ __device__ __forceinline__ void st2(T* p, T a, T b) {
 }
 
 // Streaming sweeps: a CTA owns a fine (x, y) tile of SX x SY cells and marches
-// along z through SZ fine planes, keeping a few planes in shared-memory rings.
-// Fine planes are fetched as 16-byte vectors starting 4 cells left of the tile
-// (tiles and grids are multiples of 32, so a vector lies wholly inside or
-// wholly outside the box), one plane ahead into registers, so the loads of
-// plane f+2 are in flight while plane f is computed.  All per-cell work runs
-// on 4-cell x segments (one vector of a plane row): the x neighbours of a
-// segment are its own lanes plus one value on each side, the y and z
-// neighbours are vectors of the adjacent rows and planes.
+// along z through SZ fine planes, keeping a few planes in shared-memory rings
+// (tiles and grids are multiples of 32, so a 4-cell vector of a plane row lies
+// wholly inside or wholly outside the box).  All per-cell work runs on 4-cell x
+// segments: the x neighbours of a segment are its own lanes plus one value on
+// each side, the y and z neighbours are vectors of the adjacent rows and
+// planes.  The marches are software-pipelined: each step works on three planes
+// at different stages, on different warps, with one barrier per step.
 constexpr int SX = 32, SY = 16;  // the z extent per CTA (8, 16 or 32 planes) is chosen per launch
 constexpr int PW = SX + 8;       // plane row width in shared memory (x from fx0 - 4)
 constexpr int kQ = PW / 4;       // 4-cell segments per plane row
@@ -111,8 +110,8 @@ constexpr int RH = SY + 2;       // down sweep: residual rows, y from fy0 - 1
 constexpr int BH = SY + 2;       // up sweep: b and x rows, y from fy0 - 1
 constexpr int RXY = (SX / 2) * (SY / 2);          // x-y restricted plane (128)
 constexpr int CW = SX / 2 + 6, CH = SY / 2 + 2;   // up sweep: coarse plane, x from cx0 - 3, y from cy0 - 1
-constexpr int kDownSmem = 3 * PW * XH + PW * RH + 4 * RXY;
-constexpr int kUpSmem = 3 * PW * BH + 3 * CW * CH;
+constexpr int kDownSmem = 4 * PW * XH + 2 * PW * RH + 4 * RXY;
+constexpr int kUpSmem = 4 * PW * BH + 3 * CW * CH;
 
 __device__ __forceinline__ int ring4(int f) { return (f + 4) & 3; }  // f >= -4
 
@@ -132,7 +131,7 @@ __device__ __forceinline__ int kxy_of(int packed, int e) { return (packed >> (3 
 constexpr int kDownStages = 4;
 constexpr int kProducer = kTileThreads - 32;  // issues the plane copies: lane 0 of the last warp, which has no
                                               // segment work in the residual and prolongation phases
-constexpr int kUpStages = 5;
+constexpr int kUpStages = 6;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
 __device__ int g_mg_fault;
@@ -247,12 +246,15 @@ __device__ __forceinline__ PlaneRing<T, NS> ring_setup(unsigned char* raw, int r
 // Down sweep at level l: bc = R (b - A omega D^{-1} b).  With x0 = omega D^{-1} b
 //     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g)
 // (x0 = 0 outside the box, so the sum runs over existing neighbours).
-// Per fine plane f: store the x0 plane f+1 (tile + halo 2), fetch plane f+2,
-// form r on plane f (tile + halo 1) and restrict it in x and y at once (Rxy,
-// 16 x 8 values, two coarse x per thread); every second plane one coarse
-// plane is the 4-tap z combination of four Rxy planes.  Each thread reads
-// back only its own Rxy entries.
+// Step f: warps 0-6 store the x0 plane f+2 (tile + halo 2) from its b plane,
+// warps 0-5 form r on plane f (tile + halo 1) from x0 planes f-1 .. f+1, and
+// warps 6-7 restrict r(f-1) in x and y at once (Rxy, 16 x 8 values, two coarse
+// x per thread); every second step one coarse plane is the 4-tap z
+// combination of four Rxy planes (each thread reads back only its own Rxy
+// entries).  x0 planes live in 4 slots, r planes in 2.
 // ---------------------------------------------------------------------------
+constexpr int kRestrictBase = kTileThreads - RXY / 2;  // the restriction threads: the last two warps
+
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
     k_mg_down(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
@@ -266,9 +268,11 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
     if (*(volatile int*)&g_mg_fault) return;  // an earlier sweep gave up: the host reports it, skip the work
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const PlaneRing<T, kDownStages> ring = ring_setup<T, kDownStages>(smem_raw, XH, s_bar, &s_abort, tid);
-    T* const Xbase = ring.slots + kDownStages * ring.slot;  // 3 x0 planes, PW x XH
-    T* const Rp = Xbase + 3 * PW * XH;                      // residual plane, PW x RH
-    T* const Rxy = Rp + PW * RH;                            // 4 ring planes of the x-y restricted residual
+    T* const Xbase = ring.slots + kDownStages * ring.slot;  // 4 x0 plane slots, PW x XH
+    T* const Rbase = Xbase + 4 * PW * XH;                   // 2 residual plane slots, PW x RH
+    T* const Rxy = Rbase + 2 * PW * RH;                     // 4 ring planes of the x-y restricted residual
+    auto Xs = [&](int f) { return Xbase + ((f + 4) & 3) * (PW * XH); };  // f >= -4
+    auto Rs = [&](int f) { return Rbase + (f & 1) * (PW * RH); };
     if (tid < 7) {
         s_oi[tid] = q.oi[tid];
         s_rcD[tid] = q.rcD[tid];
@@ -325,9 +329,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
                 rI[e] = s_rcD[k + 2];
             }
         }
-        // restriction: coarse x pair (cx0 + 2 qm, + 1) of coarse row cy0 + qj (tid < RXY / 2)
-        const bool has_q = tid < RXY / 2;
-        const int qm = tid & 7, qj = (tid >> 3) & 7;
+        // restriction: coarse x pair (cx0 + 2 qm, + 1) of coarse row cy0 + qj
+        const int qt = tid - kRestrictBase;
+        const bool has_q = qt >= 0;
+        const int qm = qt & 7, qj = (qt >> 3) & 7;
         T wa[4], wb[4], wy[4];
 #pragma unroll
         for (int a3 = 0; a3 < 4; ++a3) {
@@ -336,49 +341,61 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
             wy[a3] = (T)restrict_w(a3, cy0 + qj, nc);
         }
         const int q_off = 4 * qm + 3 + PW * (2 * qj);  // residual of fine (2I - 1, 2J - 1), I = cx0 + 2 qm
-        T* Xm = Xbase;
-        T* Xc = Xbase + PW * XH;
-        T* Xp = Xbase + 2 * PW * XH;
-        // x0 plane f (tile plane j) from its b plane in the ring
-        auto commit = [&](int j, T* dst, int f) {
-            const T* raw = ring.take(seq + j);
+        T* const Rxq = Rxy + 2 * (qt & (RXY / 2 - 1));
+        // x0 plane f (tile plane j = f - fz0 + 2) from its b plane in the ring
+        auto commit = [&](int f) {
+            const T* raw = ring.take(seq + (f - fz0 + 2));
             if (has_c) {
                 const bool wall = (f == 0 || f == nf - 1);  // b = 0 off the box, any factor will do
                 const V4<T> bv = ld4(raw + c_off);
                 V4<T> v;
+                if (!wall) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * (wall ? s_oi[kxy_of(c_k, e) + 1] : cI[e]);
-                st4(dst + c_off, v);
+                    for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * cI[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * s_oi[kxy_of(c_k, e) + 1];
+                }
+                st4(Xs(f) + c_off, v);
             }
         };
-        commit(0, Xm, fz0 - 2);
-        commit(1, Xc, fz0 - 1);
-        for (int f = fz0 - 1; f <= fz0 + SZ; ++f) {
-            const int j = f - fz0 + 3;
-            commit(j, Xp, f + 1);
-            __syncthreads();
-            if (tid == kProducer) issue_upto(j + kDownStages);  // planes <= j are consumed: their slots are free
-            if (has_r) {
+        commit(fz0 - 2);
+        commit(fz0 - 1);
+        commit(fz0);
+        __syncthreads();
+        if (tid == kProducer) issue_upto(2 + kDownStages);  // planes 0 .. 2 are consumed
+        for (int f = fz0 - 1; f <= fz0 + SZ + 1; ++f) {
+            if (f + 2 <= fz0 + SZ + 1) commit(f + 2);
+            if (has_r && f <= fz0 + SZ) {
                 V4<T> r = zero4<T>();
                 if (r_in && in_range(f, nf)) {
                     const bool wall = (f == 0 || f == nf - 1);
                     const int xo = r_off + PW;  // x0 rows start one row above the residual rows
+                    const T* Xc = Xs(f);
                     const V4<T> c = ld4(Xc + xo), u = ld4(Xc + xo - PW), d = ld4(Xc + xo + PW);
-                    const V4<T> m = ld4(Xm + xo), p = ld4(Xp + xo);
+                    const V4<T> m = ld4(Xs(f - 1) + xo), p = ld4(Xs(f + 1) + xo);
                     const T xl = Xc[xo - 1], xr = Xc[xo + 4];
+                    T nbs[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const T left = (e == 0) ? xl : c.v[e - 1];
                         const T right = (e == 3) ? xr : c.v[e + 1];
-                        const T nbs = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
-                        r.v[e] = (wall ? s_rcD[kxy_of(r_k, e) + 1] : rI[e]) * c.v[e] + sc * nbs;
+                        nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
+                    }
+                    if (!wall) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) r.v[e] = rI[e] * c.v[e] + sc * nbs[e];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) r.v[e] = s_rcD[kxy_of(r_k, e) + 1] * c.v[e] + sc * nbs[e];
                     }
                 }
-                st4(Rp + r_off, r);
+                st4(Rs(f) + r_off, r);
             }
-            __syncthreads();
-            if (has_q) {
+            const int fr = f - 1;  // plane restricted in this step
+            if (has_q && fr >= fz0 - 1) {
                 T acc0 = T(0), acc1 = T(0);
+                const T* Rp = Rs(fr);
 #pragma unroll
                 for (int b3 = 0; b3 < 4; ++b3) {
                     const T* row = Rp + q_off + PW * b3;
@@ -389,15 +406,15 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
                     acc0 += wy[b3] * p0;
                     acc1 += wy[b3] * p1;
                 }
-                st2(Rxy + ring4(f) * RXY + 2 * tid, acc0, acc1);
-                if (f >= fz0 + 2 && ((f - fz0) & 1) == 0) {
-                    // coarse plane Z = f/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = f-3 .. f
-                    const int Z = (f - 2) >> 1;
+                st2(Rxq + ring4(fr) * RXY, acc0, acc1);
+                if (fr >= fz0 + 2 && ((fr - fz0) & 1) == 0) {
+                    // coarse plane Z = fr/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = fr-3 .. fr
+                    const int Z = (fr - 2) >> 1;
                     const T w3 = (T)restrict_w(3, Z, nc);
                     T z0 = w3 * acc0, z1 = w3 * acc1;
 #pragma unroll
                     for (int c3 = 0; c3 < 3; ++c3) {
-                        const V2<T> v = ld2(Rxy + ring4(f - 3 + c3) * RXY + 2 * tid);
+                        const V2<T> v = ld2(Rxq + ring4(fr - 3 + c3) * RXY);
                         const T w = (T)restrict_w(c3, Z, nc);
                         z0 += w * v.v[0];
                         z1 += w * v.v[1];
@@ -405,12 +422,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
                     st2(bcs + (cx0 + 2 * qm) + (int64_t)nc * ((cy0 + qj) + (int64_t)nc * Z), z0, z1);
                 }
             }
-            T* t = Xm;
-            Xm = Xc;
-            Xc = Xp;
-            Xp = t;
+            __syncthreads();
+            // planes up to f + 2 (tile plane f - fz0 + 4) are consumed: their slots are free
+            if (tid == kProducer) issue_upto(f - fz0 + 4 + kDownStages);
         }
-        __syncthreads();
         if (tid == kProducer && s_abort) ring.drain(seq, seq + issued);
         seq += nplanes;
     }
@@ -419,14 +434,16 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
 // ---------------------------------------------------------------------------
 // Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x)
 //     = (1 - omega) x + omega D^{-1} b + omega s c D^{-1} sum_{neighbours} x,
-// optional partial sums of b.y (the MINRES beta^2 contribution).  Per fine
-// plane g: store b(g) and (for even g) coarse plane g/2 + 1, fetch the next
-// ones, form x(g) on the tile + halo 1, then y(g - 1) from x planes g-2 .. g.
-// The prolongation of a 4-cell segment blends two coarse planes (z), two
-// coarse rows (y) and then the four coarse x values the segment touches.
-// Coarse planes are stored with clamped x and y indices, which is the wall
-// reflection of P.
+// optional partial sums of b.y (the MINRES beta^2 contribution).  Step g:
+// warps 0-5 form x(g+1) on the tile + halo 1 from b(g+1) and two coarse planes,
+// warps 4-7 form y(g-1) from x planes g-2 .. g and b(g-1).  The prolongation of
+// a 4-cell segment blends two coarse planes (z), two coarse rows (y) and then
+// the four coarse x values the segment touches.  Coarse planes are stored
+// with clamped x and y indices, which is the wall reflection of P; coarse
+// plane Z lives in slot Z mod 3, x planes in 4 slots.
 // ---------------------------------------------------------------------------
+constexpr int kOutBase = kTileThreads - SX * SY / 4;  // the output threads: the last four warps
+
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     k_mg_up(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
@@ -442,8 +459,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     if (*(volatile int*)&g_mg_fault) return;
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const PlaneRing<T, kUpStages> ring = ring_setup<T, kUpStages>(smem_raw, BH, s_bar, &s_abort, tid);
-    T* const Xbase = ring.slots + kUpStages * ring.slot;  // 3 x planes, PW x BH
-    T* const Cbase = Xbase + 3 * PW * BH;                 // 3 coarse planes, CW x CH
+    T* const Xbase = ring.slots + kUpStages * ring.slot;  // 4 x plane slots, PW x BH
+    T* const Cbase = Xbase + 4 * PW * BH;                 // 3 coarse plane slots, CW x CH
+    auto Xs = [&](int g) { return Xbase + ((g + 4) & 3) * (PW * BH); };   // g >= -4
+    auto Cs = [&](int Z) { return Cbase + ((Z + 3) % 3) * (CW * CH); };  // Z >= -3
     if (tid < 7) {
         s_oi[tid] = q.oi[tid];
         s_ois[tid] = q.ois[tid];
@@ -500,9 +519,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 xI[e] = s_oi[k + 2];
             }
         }
-        // output: one segment of the tile (tid < SX * SY / 4)
-        const bool has_out = tid < SX * SY / 4;
-        const int oy = tid / (SX / 4), ox0 = 4 * (tid - oy * (SX / 4));
+        // output: one segment of the tile
+        const int ot = tid - kOutBase;
+        const bool has_out = ot >= 0;
+        const int oy = (ot & (SX * SY / 4 - 1)) / (SX / 4), ox0 = 4 * (ot & (SX / 4 - 1));
         const int o_xi = (ox0 + 4) + PW * (oy + 1);
         int o_k = 0;
         T oI[4], sI[4];
@@ -513,21 +533,20 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
             oI[e] = s_oi[k + 2];
             sI[e] = s_ois[k + 2];
         }
-        T* Xm = Xbase;  // x planes g-2, g-1, g (rotating)
-        T* Xc = Xbase + PW * BH;
-        T* Xp = Xbase + 2 * PW * BH;
-        T* Cm = Cbase;  // coarse planes Z-1, Z, Z+1 with Z = g >> 1 (rotating at even g)
-        T* Cc = Cbase + CW * CH;
-        T* Cp = Cbase + 2 * CW * CH;
         auto fetch_c = [&](int Z) -> T {
             return (c_src >= 0) ? es[c_src + cplane * min(max(Z, 0), nc - 1)] : T(0);
         };
-        // x(g) on the tile + halo 1 from b(g) and the coarse planes Iz (C0, weight 3/4) and its z neighbour (C1)
-        auto make_x = [&](int g, const T* Bg, T* Xg, const T* C0, const T* C1) {
+        // x(g) on the tile + halo 1 from b(g) (tile plane g - fz0 + 1) and the coarse planes Iz = g >> 1
+        // (weight 3/4) and its z neighbour (Iz - 1 for even g, Iz + 1 for odd g)
+        auto make_x = [&](int g) {
+            const T* Bg = ring.take(seq + (g - fz0 + 1));
             if (!has_x) return;
             V4<T> v = zero4<T>();
             if (x_in && in_range(g, nf)) {
                 const bool wall = (g == 0 || g == nf - 1);
+                const int Iz = g >> 1;
+                const T* C0 = Cs(Iz);
+                const T* C1 = Cs((g & 1) ? Iz + 1 : Iz - 1);
                 const V2<T> a0 = ld2(C0 + p_r0), a1 = ld2(C0 + p_r0 + 2);
                 const V2<T> b0 = ld2(C0 + p_r1), b1 = ld2(C0 + p_r1 + 2);
                 const V2<T> c0 = ld2(C1 + p_r0), c1 = ld2(C1 + p_r0 + 2);
@@ -543,67 +562,72 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 const T pe[4] = {w0 * cy[1] + w1 * cy[0], w0 * cy[1] + w1 * cy[2], w0 * cy[2] + w1 * cy[1],
                                  w0 * cy[2] + w1 * cy[3]};
                 const V4<T> bb = ld4(Bg + x_off);
+                if (!wall) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    v.v[e] = (wall ? s_oi[kxy_of(x_k, e) + 1] : xI[e]) * bb.v[e] + pe[e];
+                    for (int e = 0; e < 4; ++e) v.v[e] = xI[e] * bb.v[e] + pe[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v.v[e] = s_oi[kxy_of(x_k, e) + 1] * bb.v[e] + pe[e];
+                }
             }
-            st4(Xg + x_off, v);
+            st4(Xs(g) + x_off, v);
         };
-        // prologue: coarse planes cz0-1 (Cc role for g = fz0-1 -> Iz = cz0-1) and cz0
+        // prologue: coarse planes cz0-1 .. cz0+1, then x(fz0 - 1) and x(fz0)
         if (c_src >= 0) {
-            Cc[tid] = fetch_c(cz0 - 1);
-            Cp[tid] = fetch_c(cz0);
+            Cs(cz0 - 1)[tid] = fetch_c(cz0 - 1);
+            Cs(cz0)[tid] = fetch_c(cz0);
+            Cs(cz0 + 1)[tid] = fetch_c(cz0 + 1);
         }
-        const T* Bprev = ring.take(seq);
+        T pc = fetch_c(cz0 + 2);  // stored while x(fz0 + 2) is formed, first used by x(fz0 + 3)
         __syncthreads();
-        make_x(fz0 - 1, Bprev, Xp, Cc, Cp);  // odd g: planes Iz and Iz + 1
-        T pc = fetch_c(cz0 + 1);
+        make_x(fz0 - 1);
+        make_x(fz0);
+        __syncthreads();
+        if (tid == kProducer) issue_upto(kUpStages);  // plane 0 (b(fz0 - 1)) is consumed
         for (int g = fz0; g <= fz0 + SZ; ++g) {
-            const int j = g - fz0 + 1;
-            {
-                T* t = Xm;
-                Xm = Xc;
-                Xc = Xp;
-                Xp = t;
+            const int gn = g + 1;  // x plane formed in this step
+            if (gn <= fz0 + SZ) {
+                if ((gn & 1) == 0) {
+                    // coarse plane gn/2 + 1 (slot of gn/2 - 2, no longer read) for x(gn + 1) onwards
+                    if (c_src >= 0) Cs((gn >> 1) + 1)[tid] = pc;
+                    if (gn + 2 <= fz0 + SZ) pc = fetch_c((gn >> 1) + 2);
+                }
+                make_x(gn);
             }
-            if ((g & 1) == 0) {  // Z = g/2: coarse roles become (Z-1, Z, Z+1)
-                T* t = Cm;
-                Cm = Cc;
-                Cc = Cp;
-                Cp = t;
-                if (c_src >= 0) Cp[tid] = pc;
-            }
-            const T* Bcur = ring.take(seq + j);
-            if (g + 1 <= fz0 + SZ && ((g + 1) & 1) == 0) pc = fetch_c(((g + 1) >> 1) + 1);
-            __syncthreads();
-            if (tid == kProducer) issue_upto(j - 2 + kUpStages);  // planes <= j - 2 are consumed: their slots are free
-            if ((g & 1) == 0) make_x(g, Bcur, Xp, Cc, Cm);  // even g: planes Iz and Iz - 1
-            else make_x(g, Bcur, Xp, Cc, Cp);               // odd g: planes Iz and Iz + 1
-            __syncthreads();
-            const int f = g - 1;  // output plane: x planes f-1, f, f+1 = Xm, Xc, Xp; b(f) = Bprev
+            const int f = g - 1;  // output plane: x planes f-1, f, f+1 and b(f)
             if (f >= fz0 && has_out) {
                 const bool wall = (f == 0 || f == nf - 1);
+                const T* Xc = Xs(f);
+                const T* Bf = ring.at(seq + (f - fz0 + 1));
                 const V4<T> c = ld4(Xc + o_xi), u = ld4(Xc + o_xi - PW), d = ld4(Xc + o_xi + PW);
-                const V4<T> m = ld4(Xm + o_xi), p = ld4(Xp + o_xi), bb = ld4(Bprev + o_xi);
+                const V4<T> m = ld4(Xs(f - 1) + o_xi), p = ld4(Xs(f + 1) + o_xi), bb = ld4(Bf + o_xi);
                 const T xl = Xc[o_xi - 1], xr = Xc[o_xi + 4];
-                V4<T> out;
+                T nbs[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const T left = (e == 0) ? xl : c.v[e - 1];
                     const T right = (e == 3) ? xr : c.v[e + 1];
-                    const T nbs = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
-                    const int kw = kxy_of(o_k, e) + 1;
-                    const T oi = wall ? s_oi[kw] : oI[e];
-                    const T ois = wall ? s_ois[kw] : sI[e];
-                    const T yv = om1 * c.v[e] + oi * bb.v[e] + ois * nbs;
-                    out.v[e] = yv;
-                    dacc += bb.v[e] * yv;
+                    nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
                 }
+                V4<T> out;
+                if (!wall) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) out.v[e] = om1 * c.v[e] + oI[e] * bb.v[e] + sI[e] * nbs[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int kw = kxy_of(o_k, e) + 1;
+                        out.v[e] = om1 * c.v[e] + s_oi[kw] * bb.v[e] + s_ois[kw] * nbs[e];
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dacc += bb.v[e] * out.v[e];
                 st4(ys + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f, out);
             }
-            Bprev = Bcur;
+            __syncthreads();
+            // b planes up to f (tile plane g - fz0) are consumed: their slots are free
+            if (tid == kProducer) issue_upto(g - fz0 + kUpStages);
         }
-        __syncthreads();
         if (tid == kProducer && s_abort) ring.drain(seq, seq + issued);
         seq += nplanes;
     }
