@@ -273,10 +273,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
     T* const Rxy = Rbase + 2 * PW * RH;                     // 4 ring planes of the x-y restricted residual
     auto Xs = [&](int f) { return Xbase + ((f + 4) & 3) * (PW * XH); };  // f >= -4
     auto Rs = [&](int f) { return Rbase + (f & 1) * (PW * RH); };
-    if (tid < 7) {
-        s_oi[tid] = q.oi[tid];
-        s_rcD[tid] = q.rcD[tid];
-    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k)  // constant indices: the parameter struct stays in the constant bank
+        if (tid == k) {
+            s_oi[k] = q.oi[k];
+            s_rcD[k] = q.rcD[k];
+        }
     const int nc = nf >> 1;
     const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
     const int ntiles = ntx * nty * ntz;
@@ -463,10 +465,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     T* const Cbase = Xbase + 4 * PW * BH;                 // 3 coarse plane slots, CW x CH
     auto Xs = [&](int g) { return Xbase + ((g + 4) & 3) * (PW * BH); };   // g >= -4
     auto Cs = [&](int Z) { return Cbase + ((Z + 3) % 3) * (CW * CH); };  // Z >= -3
-    if (tid < 7) {
-        s_oi[tid] = q.oi[tid];
-        s_ois[tid] = q.ois[tid];
-    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        if (tid == k) {
+            s_oi[k] = q.oi[k];
+            s_ois[k] = q.ois[k];
+        }
     const int nc = nf >> 1;
     const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
     const int ntiles = ntx * nty * ntz;

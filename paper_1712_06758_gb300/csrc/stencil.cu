@@ -46,7 +46,12 @@ cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_
 template cudaError_t launch_apply<float>(int, double, int, const float*, float*, cudaStream_t);
 template cudaError_t launch_apply<double>(int, double, int, const double*, double*, cudaStream_t);
 
-// r = [0; F] - A x in FP64; optional float and double copies; partial r.r
+// r = [0; F] - A x in FP64; optional float and double copies; partial r.r.
+// Every caller forms the flux of x exactly from its cell field first
+// (u = -T^{-1} D1^T theta by FP64 line solves, or x = 0), so the flux rows of
+// r vanish up to the rounding of those solves: they are written as zeros and
+// only the cell row  F - (D1 u - (kappa h)^2 theta)  is formed (the FP64
+// arithmetic, the rate-limiting unit here, drops to a third).
 __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const double* __restrict__ F, int64_t F_stride,
                                                     const double* __restrict__ x, float* __restrict__ r32,
                                                     double* __restrict__ r64, double* __restrict__ part,
@@ -58,42 +63,53 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
     const int n3 = 1 << (3 * logn);
     const int64_t off = (int64_t)s * 4 * n3;
     const double* xs = x + off;
+    const double* ux = xs;
+    const double* uy = xs + n3;
+    const double* uz = xs + 2 * n3;
+    const double* th = xs + 3 * n3;
     const double* Fs = F + (int64_t)s * F_stride;
+    const int sy = n, sz = n << logn;
     double acc = 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (n3 >> 2); q += gridDim.x * blockDim.x) {
         const QuadPos p = quad_pos(q, logn);
-        V4<double> a, b, c, d;
-        apply_quad<double, double>(xs, n, logn, p, kh2, a.v, b.v, c.v, d.v);
-        const V4<double> f = ld4(Fs + p.c);
+        const int c = p.c;
+        const bool jl = p.j > 0, jh = p.j < n - 1;
+        const bool kl = p.k > 0, kh = p.k < n - 1;
+        const V4<double> ux4 = ld4(ux + c), uy4 = ld4(uy + c), uz4 = ld4(uz + c), th4 = ld4(th + c);
+        const V4<double> uyM = jl ? ld4(uy + c - sy) : zero4<double>();
+        const V4<double> uzM = kl ? ld4(uz + c - sz) : zero4<double>();
+        const double uxL = (p.i0 > 0) ? ux[c - 1] : 0.0;
+        const V4<double> f = ld4(Fs + c);
+        V4<double> d;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            a.v[e] = -a.v[e];
-            b.v[e] = -b.v[e];
-            c.v[e] = -c.v[e];
-            d.v[e] = f.v[e] - d.v[e];
-            acc += a.v[e] * a.v[e] + b.v[e] * b.v[e] + c.v[e] * c.v[e] + d.v[e] * d.v[e];
+            const int i = p.i0 + e;
+            const double ux0 = (i < n - 1) ? ux4.v[e] : 0.0;
+            const double uxm = (e > 0) ? ux4.v[e - 1] : uxL;
+            const double uy0 = jh ? uy4.v[e] : 0.0;
+            const double uz0 = kh ? uz4.v[e] : 0.0;
+            const double yt = (ux0 - uxm) + (uy0 - uyM.v[e]) + (uz0 - uzM.v[e]) - kh2 * th4.v[e];
+            d.v[e] = f.v[e] - yt;
+            acc += d.v[e] * d.v[e];
         }
         if (r32) {
             float* o = r32 + off;
-            V4<float> fa, fb, fc, fd;
+            const V4<float> z = zero4<float>();
+            V4<float> fd;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                fa.v[e] = (float)a.v[e];
-                fb.v[e] = (float)b.v[e];
-                fc.v[e] = (float)c.v[e];
-                fd.v[e] = (float)d.v[e];
-            }
-            st4(o + p.c, fa);
-            st4(o + n3 + p.c, fb);
-            st4(o + 2 * n3 + p.c, fc);
-            st4(o + 3 * n3 + p.c, fd);
+            for (int e = 0; e < 4; ++e) fd.v[e] = (float)d.v[e];
+            st4(o + c, z);
+            st4(o + n3 + c, z);
+            st4(o + 2 * n3 + c, z);
+            st4(o + 3 * n3 + c, fd);
         }
         if (r64) {
             double* o = r64 + off;
-            st4(o + p.c, a);
-            st4(o + n3 + p.c, b);
-            st4(o + 2 * n3 + p.c, c);
-            st4(o + 3 * n3 + p.c, d);
+            const V4<double> z = zero4<double>();
+            st4(o + c, z);
+            st4(o + n3 + c, z);
+            st4(o + 2 * n3 + c, z);
+            st4(o + 3 * n3 + c, d);
         }
     }
     const double t = block_sum<256>(acc, red);
