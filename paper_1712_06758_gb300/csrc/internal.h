@@ -102,13 +102,16 @@ int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* 
 cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cudaStream_t st);
 
 // ---- krylov.cu
-// A(k+1) fused with the pending D(k) when yprev != null (see krylov.cu)
+// A(k+1) fused with the pending D(k) when yprev != null (see krylov.cu).  The
+// preconditioned Lanczos vector is fd * u on the flux blocks and y's cell block.
 template <typename T>
-int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, const T* yprev,
-                    T* w1, const T* w2, T* xd, cudaStream_t st);
+int launch_minres_A(int n, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
+                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st);
+// r1 -= (alpha / beta) r2 and the flux part of the next beta^2 (the flux block of
+// the next preconditioned vector is fd * r1 and is not stored)
 template <typename T>
-int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, T* ynext, double fd, double* partB,
-                    MinresCol* st_, cudaStream_t st);
+int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, double fd, double* partB, MinresCol* st_,
+                    cudaStream_t st);
 template <typename T>
 int launch_precond_u(int64_t N4, int n3, int S, const T* r, T* y, double fd, double* part,
                      const MinresCol* st_, cudaStream_t st);

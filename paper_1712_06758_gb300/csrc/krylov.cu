@@ -40,8 +40,59 @@ __device__ __forceinline__ void set_coef(MinresCol& c, int k, double v) {
     c.kf[k] = (float)v;
 }
 
+// y = A v on a quad for a preconditioned Lanczos vector v whose flux blocks
+// are fd * u (the flux block of the preconditioner is fd I, so they are never
+// stored) and whose cell block is th; fd multiplies each flux sum once.  The
+// unscaled flux centre values and the cell centre values come back in vc (the
+// caller scales the flux part of its inner product by fd); wall fluxes are
+// masked by index.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n, T kh2, const T* __restrict__ y, T* __restrict__ r1,
+__device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T* __restrict__ th, T fd, int n,
+                                              int logn, const QuadPos& p, T kh2, T yu[4], T yv[4], T yw[4], T yt[4],
+                                              V4<T> vc[4]) {
+    const int n3 = 1 << (3 * logn);
+    const int sy = n, sz = n << logn;
+    const T* ux = us;
+    const T* uy = us + n3;
+    const T* uz = us + 2 * n3;
+    const int c = p.c;
+    const V4<T> ux4 = ld4(ux + c), uy4 = ld4(uy + c), uz4 = ld4(uz + c), th4 = ld4(th + c);
+    const bool jl = p.j > 0, jh = p.j < n - 1, jhh = p.j + 1 < n - 1;
+    const bool kl = p.k > 0, kh = p.k < n - 1, khh = p.k + 1 < n - 1;
+    const V4<T> uyM = jl ? ld4(uy + c - sy) : zero4<T>();
+    const V4<T> uyP = jhh ? ld4(uy + c + sy) : zero4<T>();
+    const V4<T> uzM = kl ? ld4(uz + c - sz) : zero4<T>();
+    const V4<T> uzP = khh ? ld4(uz + c + sz) : zero4<T>();
+    const V4<T> thY = jh ? ld4(th + c + sy) : zero4<T>();
+    const V4<T> thZ = kh ? ld4(th + c + sz) : zero4<T>();
+    const T uxL = (p.i0 > 0) ? ux[c - 1] : T(0);
+    const T uxR = (p.i0 + 4 < n - 1) ? ux[c + 4] : T(0);
+    const T thR = (p.i0 + 4 < n) ? th[c + 4] : T(0);
+    const T a6 = T(1) / T(6), a23 = T(2) / T(3);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = p.i0 + e;
+        const T t0 = th4.v[e];
+        const T ux0 = (i < n - 1) ? ux4.v[e] : T(0);
+        const T uxm = (e > 0) ? ((i - 1 < n - 1) ? ux4.v[e - 1] : T(0)) : uxL;
+        const T uxp = (e < 3) ? ((i + 1 < n - 1) ? ux4.v[e + 1] : T(0)) : uxR;
+        const T thx = (e < 3) ? th4.v[e + 1] : thR;
+        const T uy0 = jh ? uy4.v[e] : T(0);
+        const T uz0 = kh ? uz4.v[e] : T(0);
+        const T uym = uyM.v[e], uzm = uzM.v[e];
+        yu[e] = (i < n - 1) ? fd * (a23 * ux0 + a6 * (uxm + uxp)) + (t0 - thx) : T(0);
+        yv[e] = jh ? fd * (a23 * uy0 + a6 * (uym + uyP.v[e])) + (t0 - thY.v[e]) : T(0);
+        yw[e] = kh ? fd * (a23 * uz0 + a6 * (uzm + uzP.v[e])) + (t0 - thZ.v[e]) : T(0);
+        yt[e] = fd * ((ux0 - uxm) + (uy0 - uym) + (uz0 - uzm)) - kh2 * t0;
+    }
+    vc[0] = ux4;
+    vc[1] = uy4;
+    vc[2] = uz4;
+    vc[3] = th4;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n, T kh2, const T* __restrict__ y, const T* __restrict__ u, T fd, T* __restrict__ r1,
                                                      double* __restrict__ partA, const MinresCol* __restrict__ st,
                                                      const T* __restrict__ yprev, T* __restrict__ w1,
                                                      const T* __restrict__ w2, T* __restrict__ xd) {
@@ -55,7 +106,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n,
     const int n3 = 1 << (3 * logn);
     const int nq = n3 >> 2;
     const int64_t off = (int64_t)s * 4 * n3;
-    const T* ys = y + off;
+    const T* ys = y + off;   // only its cell block is read
+    const T* us = u + off;   // flux blocks of the Lanczos vector: y's are fd times these
     T* rs = r1 + off;
     T acc = T(0);
     if (doA) {
@@ -66,9 +118,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n,
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
             const QuadPos p = quad_pos(q, logn);
             T yu[4], yv[4], yw[4], yt[4];
-            apply_quad<T, T>(ys, n, logn, p, kh2, yu, yv, yw, yt);
-            const V4<T> v0 = ld4(ys + p.c), v1 = ld4(ys + n3 + p.c), v2 = ld4(ys + 2 * n3 + p.c),
-                        v3 = ld4(ys + 3 * n3 + p.c);
+            V4<T> vc[4];
+            apply_quad_fd<T>(us, ys + 3 * n3, fd, n, logn, p, kh2, yu, yv, yw, yt, vc);
+            const V4<T> v0 = vc[0], v1 = vc[1], v2 = vc[2], v3 = vc[3];
             V4<T> z0, z1, z2, z3;
             if (use_r1) {
                 z0 = ld4(rs + p.c);
@@ -84,7 +136,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n,
                 z1.v[e] = yv[e] * ib - coef * z1.v[e];
                 z2.v[e] = yw[e] * ib - coef * z2.v[e];
                 z3.v[e] = yt[e] * ib - coef * z3.v[e];
-                acc += (v0.v[e] * z0.v[e] + v1.v[e] * z1.v[e] + v2.v[e] * z2.v[e] + v3.v[e] * z3.v[e]) * ib;
+                acc += (fd * (v0.v[e] * z0.v[e] + v1.v[e] * z1.v[e] + v2.v[e] * z2.v[e]) + v3.v[e] * z3.v[e]) * ib;
             }
             st4(rs + p.c, z0);
             st4(rs + n3 + p.c, z1);
@@ -121,19 +173,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_minres_A(int n,
 }
 
 template <typename T>
-int launch_minres_A(int n, double kh2, int S, const T* y, T* r1, double* partA, MinresCol* st_, const T* yprev,
-                    T* w1, const T* w2, T* xd, cudaStream_t st) {
+int launch_minres_A(int n, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
+                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st) {
     const int64_t n3 = (int64_t)n * n * n;
     const int nb = cell_blocks(n3 / 16);  // four quads per thread: one reduction per 1024 quads
     dim3 grid(nb, S);
-    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, r1, partA, st_, yprev, w1, w2, xd);
+    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd);
     return nb;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_minres_B(int64_t N4, int64_t n3u, T* __restrict__ r1, const T* __restrict__ r2,
-                                                  T* __restrict__ ynext, T fd, double* __restrict__ partB,
-                                                  const MinresCol* __restrict__ st) {
+                                                  T fd, double* __restrict__ partB, const MinresCol* __restrict__ st) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     const MinresCol& cs = st[s];
@@ -144,22 +195,18 @@ __global__ void __launch_bounds__(256) k_minres_B(int64_t N4, int64_t n3u, T* __
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x) {
         const T z = r1[off + e] - f * r2[off + e];
         r1[off + e] = z;
-        if (e < n3u) {
-            const T yv = fd * z;
-            ynext[off + e] = yv;
-            acc += z * yv;
-        }
+        if (e < n3u) acc += z * (fd * z);  // flux block of the next preconditioned vector, never stored
     }
     const double t = block_sum<256>((double)acc, red);
     if (threadIdx.x == 0) partB[(int64_t)s * kMaxPartials + blockIdx.x] = t;
 }
 
 template <typename T>
-int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, T* ynext, double fd, double* partB,
-                    MinresCol* st_, cudaStream_t st) {
+int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, double fd, double* partB, MinresCol* st_,
+                    cudaStream_t st) {
     const int nb = elem_blocks(N4);
     dim3 grid(nb, S);
-    k_minres_B<T><<<grid, 256, 0, st>>>(N4, 3 * (int64_t)n3, r1, r2, ynext, (T)fd, partB, st_);
+    k_minres_B<T><<<grid, 256, 0, st>>>(N4, 3 * (int64_t)n3, r1, r2, (T)fd, partB, st_);
     return nb;
 }
 
@@ -363,10 +410,9 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 }
 
 #define SPDE_KRYLOV_INST(T)                                                                                        \
-    template int launch_minres_A<T>(int, double, int, const T*, T*, double*, MinresCol*, const T*, T*, const T*, \
-                                    T*, cudaStream_t);                                                             \
-    template int launch_minres_B<T>(int64_t, int, int, T*, const T*, T*, double, double*, MinresCol*,             \
-                                    cudaStream_t);                                                                 \
+    template int launch_minres_A<T>(int, double, int, const T*, const T*, double, T*, double*, MinresCol*,        \
+                                    const T*, T*, const T*, T*, cudaStream_t);                                     \
+    template int launch_minres_B<T>(int64_t, int, int, T*, const T*, double, double*, MinresCol*, cudaStream_t);   \
     template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \
                                      cudaStream_t);                                                                \
     template cudaError_t launch_minres_D<T>(int64_t, int, const T*, T*, const T*, T*, const MinresCol*,          \

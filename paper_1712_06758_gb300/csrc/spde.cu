@@ -315,8 +315,8 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             const int itn = it + q + 1;  // 1-based iteration of the columns that started together
             // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
-            const int nA = launch_minres_A<T>(n, kh2, S, ycur, r1, ws.partA, ws.st, pending ? yprev : nullptr, w1,
-                                              w2, d, st);
+            const int nA = launch_minres_A<T>(n, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
+                                              pending ? yprev : nullptr, w1, w2, d, st);
             prof_end(st, cols * (itn >= 2 ? 12.0 : 8.0) * n3d * w +
                              (pending ? cols * (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0));
             if (pending) std::swap(w1, w2);
@@ -324,8 +324,8 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, st));
             prof_end(st, cols * nA * 8.0);
             prof_begin(PK_MINRES_B, st);
-            const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, ynext, o.flux_diag, ws.partB, ws.st, st);
-            prof_end(st, cols * 15.0 * n3d * w);
+            const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, o.flux_diag, ws.partB, ws.st, st);
+            prof_end(st, cols * 12.0 * n3d * w);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
             if (q == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
             prof_begin(PK_GIVENS, st);

@@ -229,13 +229,69 @@ __global__ void __launch_bounds__(256) k_flux_lines(int n, int logn, int axis, c
     }
 }
 
+// Lines along x are contiguous rows: a CTA stages kRowLines(n) consecutive rows
+// of theta in shared memory (coalesced), each thread solves one row in place
+// there, and the tile goes back to the ux block coalesced.
+constexpr int kRowTileElems = 8192;  // doubles of one staged tile (64 KB)
+static inline int row_lines(int n) {
+    const int lr = n >= kRowTileElems / 32 ? kRowTileElems / n : 32;
+    return lr < n * n ? lr : n * n;  // n = 4 has only 16 rows
+}
+
+__global__ void __launch_bounds__(128) k_flux_rows(int n, int logn, int lines_per_cta, const double* __restrict__ x,
+                                                   double* __restrict__ xu, int64_t col_stride,
+                                                   const double* __restrict__ tri) {
+    extern __shared__ double srow[];  // lines_per_cta rows of n + 1 (padded against bank conflicts)
+    const int64_t off = (int64_t)blockIdx.y * col_stride;
+    const int n3 = 1 << (3 * logn);
+    const int64_t row0 = (int64_t)blockIdx.x * lines_per_cta;  // first (j, k) row of the tile
+    const double* th = x + off + 3 * (int64_t)n3 + (row0 << logn);
+    double* u = xu + off + (row0 << logn);
+    const int tile = lines_per_cta << logn;
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) srow[(e >> logn) * (n + 1) + (e & (n - 1))] = th[e];
+    __syncthreads();
+    const double* cp = tri;
+    const double* inv = tri + (n - 1);
+    const double a = 1.0 / 6.0;
+    for (int L = threadIdx.x; L < lines_per_cta; L += blockDim.x) {
+        double* r = srow + L * (n + 1);
+        // forward elimination of T u = theta_{f+1} - theta_f, in place (theta_f is dead once dp_f exists)
+        double prev = 0.0, tcur = r[0];
+        for (int f = 0; f < n - 1; ++f) {
+            const double tnext = r[f + 1];
+            const double dp = ((tnext - tcur) - a * prev) * inv[f];
+            r[f] = dp;
+            prev = dp;
+            tcur = tnext;
+        }
+        r[n - 1] = 0.0;  // wall flux
+        double xn = prev;
+        for (int f = n - 3; f >= 0; --f) {
+            const double xf = r[f] - cp[f] * xn;
+            r[f] = xf;
+            xn = xf;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tile; e += blockDim.x) u[e] = srow[(e >> logn) * (n + 1) + (e & (n - 1))];
+}
+
+static cudaError_t flux_rows_attr() {
+    static const cudaError_t e = cudaFuncSetAttribute(k_flux_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (kRowTileElems + 64) * (int)sizeof(double));
+    return e;
+}
+
 cudaError_t launch_flux_from_theta(int n, int S, double* x, int64_t col_stride, const double* tri, cudaStream_t st) {
     const int logn = 31 - __builtin_clz(n);
     const int lines = n * n;
+    const int lr = row_lines(n);
+    const cudaError_t ea = flux_rows_attr();
+    if (ea != cudaSuccess) return ea;
+    dim3 grow(lines / lr, S);
+    k_flux_rows<<<grow, 128, (size_t)lr * (n + 1) * sizeof(double), st>>>(n, logn, lr, x, x, col_stride, tri);
     dim3 grid((lines + 255) / 256, S);
-    for (int axis = 0; axis < 3; ++axis) {
-        k_flux_lines<<<grid, 256, 0, st>>>(n, logn, axis, x, x, col_stride, tri);
-    }
+    for (int axis = 1; axis < 3; ++axis) k_flux_lines<<<grid, 256, 0, st>>>(n, logn, axis, x, x, col_stride, tri);
     return cudaGetLastError();
 }
 
