@@ -27,6 +27,15 @@ module (its own; unrelated to any device layout):
 RT0 degree of freedom = the normal component u.e_axis on the face (the
 paper fixes no scaling; theta does not depend on it).  Boundary faces carry
 the essential condition u.n = 0 and are eliminated.
+
+Space-dependent parameters (Sec. 1 states that the method, unlike circulant
+embedding, admits correlation and marginal-variance functions that vary in
+space; the paper gives no formula).  Reading taken here: kappa and sigma are
+constant per cell of the embedding grid.  Then the reaction block is
+diag(kappa_c^2) W and the noise of cell c carries the normaliser of Sec. 4
+evaluated with that cell's kappa_c, sigma_c.  Every routine below that takes
+`kappa` / `sigma` accepts either a number or an array of the n^3 cell values
+(cell order i + n (j + n k)).
 """
 import math
 
@@ -134,18 +143,20 @@ class MixedSystem:
         self.W = sp.identity(self.Nt, format="csr") * h ** 3
 
     def matrix(self, kappa):
-        return sp.bmat([[self.M, self.B.T], [self.B, -kappa ** 2 * self.W]], format="csc")
+        k2 = np.broadcast_to(np.asarray(kappa, dtype=np.float64) ** 2, (self.Nt,))
+        return sp.bmat([[self.M, self.B.T], [self.B, -(sp.diags(k2) @ self.W)]], format="csc")
 
     def apply(self, kappa, u, theta):
         """y = A [u; theta] with the assembled blocks."""
         yu = self.M @ u + self.B.T @ theta
-        yt = self.B @ u - kappa ** 2 * (self.W @ theta)
+        yt = self.B @ u - np.asarray(kappa, dtype=np.float64) ** 2 * (self.W @ theta)
         return yu, yt
 
     def rhs(self, kappa, sigma, xi):
-        """F = [0; -g f], f = W^{1/2} xi (Sec. 4.2)."""
+        """F = [0; -g f], f = W^{1/2} xi (Sec. 4.2); g per cell for cell-wise kappa, sigma."""
         f = np.sqrt(self.W.diagonal()) * xi
-        return np.concatenate([np.zeros(self.Nu), -g_normaliser(kappa, sigma) * f])
+        g = g_normaliser(np.asarray(kappa, dtype=np.float64), np.asarray(sigma, dtype=np.float64))
+        return np.concatenate([np.zeros(self.Nu), -g * f])
 
     def solve_sparse(self, kappa, sigma, xi):
         """Sparse direct (SuperLU) solve of the full saddle-point system."""

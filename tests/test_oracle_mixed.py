@@ -176,3 +176,65 @@ def test_restricted_noise_is_standard_normal():
     xc = mixed.restrict_noise(xi, 64)
     assert stats.kstest(xc, "norm").pvalue > 1e-3
     assert abs(np.corrcoef(xc[:-1], xc[1:])[0, 1]) < 5 / np.sqrt(len(xc))
+
+
+# ------------------------------------------------ cell-wise kappa(x), sigma(x)
+def _mixed_line(kappa_line, g_line, eta, h):
+    """The mixed RT0 x P0 method on one line of n cells, written from scratch for a
+    field that does not vary across the line: x-face mass h^3 tridiag(1/6, 2/3, 1/6)
+    over the n-1 inner faces; the integral of the divergence of the face-f function
+    is +h^2 over cell f and -h^2 over cell f+1 (matrix h^2 D); reaction block
+    h^3 diag(kappa^2); right-hand side -g h^{3/2} eta.  Solved densely."""
+    n = len(kappa_line)
+    T = np.diag(np.full(n - 1, 2.0 / 3.0)) + np.diag(np.full(n - 2, 1.0 / 6.0), 1) + np.diag(np.full(n - 2, 1.0 / 6.0), -1)
+    D = np.zeros((n, n - 1))
+    for f in range(n - 1):
+        D[f, f] = 1.0       # face f is the right face of cell f (outward normal +x)
+        D[f + 1, f] = -1.0  # and the left face of cell f + 1
+    A = np.block([[h ** 3 * T, h ** 2 * D.T], [h ** 2 * D, -h ** 3 * np.diag(np.asarray(kappa_line) ** 2)]])
+    b = np.concatenate([np.zeros(n - 1), -np.asarray(g_line) * h ** 1.5 * eta])
+    return np.linalg.solve(A, b)[n - 1:]
+
+
+def test_fields_constant_arrays_equal_scalar():
+    n = 4
+    ms = mixed.MixedSystem(n)
+    xi = np.random.default_rng(11).standard_normal(n ** 3)
+    _, t1 = ms.solve_sparse(20.0, 1.3, xi)
+    _, t2 = ms.solve_sparse(np.full(n ** 3, 20.0), np.full(n ** 3, 1.3), xi)
+    assert np.array_equal(t1, t2)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_fields_sigma_only_is_rescaled_noise(n):
+    """With kappa constant, a cell-wise sigma only rescales the noise cell by cell, so the
+    DCT closed form of the constant-kappa Schur complement gives the exact field."""
+    rng = np.random.default_rng(n)
+    sig = rng.uniform(0.5, 2.0, n ** 3)
+    xi = rng.standard_normal(n ** 3)
+    _, th = mixed.MixedSystem(n).solve_sparse(20.0, sig, xi)
+    ref = mixed.solve_dct(n, 20.0, 1.0, sig * xi)
+    assert np.linalg.norm(th - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_fields_layered_kappa_reduces_to_one_line(axis):
+    """kappa and the noise vary along one axis only: the 3-D field is constant across
+    the other two axes and equals the 1-D mixed solution on every line."""
+    n, h = 8, 1.0 / 8
+    rng = np.random.default_rng(3 + axis)
+    k_line = rng.uniform(5.0, 40.0, n)
+    s_line = rng.uniform(0.5, 2.0, n)
+    eta = rng.standard_normal(n)
+    idx = np.indices((n, n, n))  # [0] = k (z), [1] = j (y), [2] = i (x) in the C-order flat index i + n (j + n k)
+    pos = idx[2] if axis == 0 else idx[0]
+    kap, sig, xi = k_line[pos].ravel(), s_line[pos].ravel(), eta[pos].ravel()
+    _, th = mixed.MixedSystem(n).solve_sparse(kap, sig, xi)
+    th = th.reshape(n, n, n)
+    line = th[0, 0, :] if axis == 0 else th[:, 0, 0]
+    g_line = np.array([mixed.g_normaliser(k, s) for k, s in zip(k_line, s_line)])
+    ref = _mixed_line(k_line, g_line, eta, h)
+    assert np.allclose(line, ref, rtol=1e-11, atol=1e-14 * np.abs(ref).max())
+    # constant across the other two axes
+    full = np.broadcast_to(line[None, None, :] if axis == 0 else line[:, None, None], (n, n, n))
+    assert np.allclose(th, full, rtol=1e-11, atol=1e-14 * np.abs(ref).max())
