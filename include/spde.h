@@ -149,6 +149,29 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
 spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma,
                         uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream);
 
+/* Spatially varying kappa(x) and sigma(x) on `level` (Sec. 1: the sampler,
+ * unlike circulant embedding, admits correlation lengths and marginal
+ * variances that vary in space).  The values are constant per cell of the
+ * level's embedding grid: host arrays of n^3 doubles, x fastest
+ * (i + n (j + n k)), every kappa and sigma finite and > 0 (else SPDE_EINVAL
+ * naming the cell).  The reaction block becomes diag(kappa_c^2) W and the
+ * noise of cell c is scaled by g_c = sigma_c sqrt(8 pi kappa_c) (the nu = 1/2,
+ * d = 3 normaliser of Sec. 4 evaluated cell by cell).  The arrays are copied
+ * to the device (3 n^3 words); two null pointers clear the fields; the level
+ * keeps them until then or until spde_level_add redefines it.  SPDE_EBUSY
+ * while serving requests are in flight. */
+spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_cells,
+                                  const double* sigma_cells);
+
+/* spde_sample with the fields of spde_level_set_fields in place of one kappa
+ * and sigma.  The mixed operator and the FP64 residual take kappa_c per
+ * cell; the multigrid preconditioner uses the mean of (kappa_c h)^2, so the
+ * field is exact to the tolerance and only the iteration count depends on
+ * how strongly kappa varies.  MINRES solver only (SPDE_EINVAL with
+ * SPDE_SOLVER_SCHUR_CG); SPDE_EINVAL when the level has no fields. */
+spde_status spde_sample_fields(spde_ctx* ctx, int level, int nsamples, uint64_t seed,
+                               uint64_t first_sample, int out_kind, void* out, void* stream);
+
 /* Coupled two-level samples (Sec. 6.2, multilevel sampler): the white noise
  * is drawn once on the fine level and restricted to the coarse one by
  * summing the 8 children of every coarse cell (the restricted noise has

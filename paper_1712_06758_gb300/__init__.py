@@ -53,6 +53,8 @@ _SIGS = {
     "spde_mesh_attach": [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int64, _P],
     "spde_sample": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                     ctypes.c_uint64, ctypes.c_int, _P, _P],
+    "spde_level_set_fields": [_P, ctypes.c_int, _P, _P],
+    "spde_sample_fields": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _P, _P],
     "spde_sample_coupled": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                             ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _P, _P, _P],
     "spde_submit": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
@@ -161,6 +163,21 @@ def spde_mesh_attach(ctx, level, xyz, tets):
 def spde_sample(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out, stream=None):
     _check(lib().spde_sample(ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, _ptr(out),
                              _stream(stream)))
+
+
+def spde_level_set_fields(ctx, level, kappa_cells, sigma_cells):
+    """kappa_cells, sigma_cells: the level's n^3 cell values (x fastest) on the host,
+    or both None to clear.  The library reads n^3 values from each: pass arrays of
+    exactly that length (Sampler.set_fields checks it)."""
+    import numpy as np
+    k = None if kappa_cells is None else np.ascontiguousarray(kappa_cells, dtype=np.float64).ravel()
+    s = None if sigma_cells is None else np.ascontiguousarray(sigma_cells, dtype=np.float64).ravel()
+    _check(lib().spde_level_set_fields(ctx, level, None if k is None else k.ctypes.data,
+                                       None if s is None else s.ctypes.data))
+
+
+def spde_sample_fields(ctx, level, nsamples, seed, first_sample, out_kind, out, stream=None):
+    _check(lib().spde_sample_fields(ctx, level, nsamples, seed, first_sample, out_kind, _ptr(out), _stream(stream)))
 
 
 def spde_sample_coupled(ctx, fine_level, coarse_level, nsamples, kappa, sigma, seed, first_sample, out_kind,
@@ -312,6 +329,25 @@ class Sampler:
             dt = torch.float64 if out_kind & SPDE_OUT_F64 else torch.float32
             out = torch.empty((nsamples, per), dtype=dt, device="cuda")
         spde_sample(self.ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out, stream)
+        return out
+
+    def set_fields(self, level, kappa_cells, sigma_cells):
+        import numpy as np
+        n = self.levels[level][0]
+        for a in (kappa_cells, sigma_cells):
+            if a is not None and np.size(a) != n ** 3:
+                raise ValueError("fields of level %d need %d cell values" % (level, n ** 3))
+        spde_level_set_fields(self.ctx, level, kappa_cells, sigma_cells)
+
+    def sample_fields(self, level, nsamples, seed, first_sample=0, out_kind=SPDE_OUT_LOGNORMAL, out=None,
+                      stream=None):
+        import torch
+        if out is None:
+            n = self.levels[level][0]
+            per = n ** 3 if (out_kind & 15) == SPDE_OUT_GRID_GAUSSIAN else self.ntets(level)
+            dt = torch.float64 if out_kind & SPDE_OUT_F64 else torch.float32
+            out = torch.empty((nsamples, per), dtype=dt, device="cuda")
+        spde_sample_fields(self.ctx, level, nsamples, seed, first_sample, out_kind, out, stream)
         return out
 
     def stats(self):

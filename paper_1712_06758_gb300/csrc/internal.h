@@ -81,7 +81,13 @@ cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_
 // r = [0; F] - A x (FP64), written to r32 (float, may be null) and r64 (double, may be
 // null); partial sums of r.r per column into part [S][nblk]; returns nblk
 int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x,
-                      float* r32, double* r64, double* part, const int* active, cudaStream_t st);
+                      float* r32, double* r64, double* part, const int* active, cudaStream_t st,
+                      const double* kh2c = nullptr);
+// F[s][e] *= c[e] (per-cell noise factor of a level with fields)
+cudaError_t launch_scale_cells(int64_t n3, int S, double* F, int64_t stride, const double* c, cudaStream_t st);
+// (kappa h)^2 (FP64, FP32) and -g h per cell from cell-wise kappa, sigma (device arrays)
+cudaError_t launch_field_coefs(int64_t n3, double h, const double* kappa, const double* sigma, double* kh2_64,
+                               float* kh2_32, double* gh, cudaStream_t st);
 // x += d (double += float) on active columns
 cudaError_t launch_add_correction(int64_t nelem, int S, double* x, const float* d, const int* active,
                                   cudaStream_t st);
@@ -106,7 +112,8 @@ cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cuda
 // preconditioned Lanczos vector is fd * u on the flux blocks and y's cell block.
 template <typename T>
 int launch_minres_A(int n, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
-                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st);
+                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st,
+                    const T* kh2c = nullptr);
 // r1 -= (alpha / beta) r2 and the flux part of the next beta^2 (the flux block of
 // the next preconditioned vector is fd * r1 and is not stored)
 template <typename T>

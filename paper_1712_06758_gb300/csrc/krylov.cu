@@ -48,8 +48,8 @@ __device__ __forceinline__ void set_coef(MinresCol& c, int k, double v) {
 // masked by index.
 template <typename T>
 __device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T* __restrict__ th, T fd, int n,
-                                              int logn, const QuadPos& p, T kh2, T yu[4], T yv[4], T yw[4], T yt[4],
-                                              V4<T> vc[4]) {
+                                              int logn, const QuadPos& p, const V4<T>& kh2, T yu[4], T yv[4],
+                                              T yw[4], T yt[4], V4<T> vc[4]) {
     const int n3 = 1 << (3 * logn);
     const int sy = n, sz = n << logn;
     const T* ux = us;
@@ -83,7 +83,7 @@ __device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T*
         yu[e] = (i < n - 1) ? fd * (a23 * ux0 + a6 * (uxm + uxp)) + (t0 - thx) : T(0);
         yv[e] = jh ? fd * (a23 * uy0 + a6 * (uym + uyP.v[e])) + (t0 - thY.v[e]) : T(0);
         yw[e] = kh ? fd * (a23 * uz0 + a6 * (uzm + uzP.v[e])) + (t0 - thZ.v[e]) : T(0);
-        yt[e] = fd * ((ux0 - uxm) + (uy0 - uym) + (uz0 - uzm)) - kh2 * t0;
+        yt[e] = fd * ((ux0 - uxm) + (uy0 - uym) + (uz0 - uzm)) - kh2.v[e] * t0;
     }
     vc[0] = ux4;
     vc[1] = uy4;
@@ -95,7 +95,8 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n, T kh2, const T* __restrict__ y, const T* __restrict__ u, T fd, T* __restrict__ r1,
                                                      double* __restrict__ partA, const MinresCol* __restrict__ st,
                                                      const T* __restrict__ yprev, T* __restrict__ w1,
-                                                     const T* __restrict__ w2, T* __restrict__ xd) {
+                                                     const T* __restrict__ w2, T* __restrict__ xd,
+                                                     const T* __restrict__ kh2c) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     const MinresCol& cs = st[s];
@@ -119,7 +120,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
             const QuadPos p = quad_pos(q, logn);
             T yu[4], yv[4], yw[4], yt[4];
             V4<T> vc[4];
-            apply_quad_fd<T>(us, ys + 3 * n3, fd, n, logn, p, kh2, yu, yv, yw, yt, vc);
+            V4<T> k4;  // (kappa h)^2 per cell: one value, or the level's field
+            if (kh2c) k4 = ld4(kh2c + p.c);
+            else
+#pragma unroll
+                for (int e = 0; e < 4; ++e) k4.v[e] = kh2;
+            apply_quad_fd<T>(us, ys + 3 * n3, fd, n, logn, p, k4, yu, yv, yw, yt, vc);
             const V4<T> v0 = vc[0], v1 = vc[1], v2 = vc[2], v3 = vc[3];
             V4<T> z0, z1, z2, z3;
             if (use_r1) {
@@ -174,11 +180,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
 
 template <typename T>
 int launch_minres_A(int n, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
-                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st) {
+                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st, const T* kh2c) {
     const int64_t n3 = (int64_t)n * n * n;
     const int nb = cell_blocks(n3 / 16);  // four quads per thread: one reduction per 1024 quads
     dim3 grid(nb, S);
-    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd);
+    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c);
     return nb;
 }
 
@@ -411,7 +417,7 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 
 #define SPDE_KRYLOV_INST(T)                                                                                        \
     template int launch_minres_A<T>(int, double, int, const T*, const T*, double, T*, double*, MinresCol*,        \
-                                    const T*, T*, const T*, T*, cudaStream_t);                                     \
+                                    const T*, T*, const T*, T*, cudaStream_t, const T*);                           \
     template int launch_minres_B<T>(int64_t, int, int, T*, const T*, double, double*, MinresCol*, cudaStream_t);   \
     template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \
                                      cudaStream_t);                                                                \

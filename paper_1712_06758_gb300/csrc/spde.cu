@@ -170,6 +170,23 @@ struct Mesh {
     }
 };
 
+// Cell-wise kappa(x), sigma(x) of a level (spde_level_set_fields), as the
+// coefficients the kernels use.
+struct Fields {
+    bool set = false;
+    double* kh2_64 = nullptr;  // (kappa_c h)^2
+    float* kh2_32 = nullptr;
+    double* gh = nullptr;      // -g_c h, the per-cell factor of the scaled right-hand side
+    double kh2_mean = 0.0;     // mean (kappa_c h)^2: the one coefficient of the V-cycle preconditioner
+    void release() {
+        dev_free(kh2_64);
+        dev_free(kh2_32);
+        dev_free(gh);
+        set = false;
+        kh2_mean = 0.0;
+    }
+};
+
 struct Level {
     bool defined = false;
     int n = 0;
@@ -177,6 +194,7 @@ struct Level {
     double lo[3] = {0, 0, 0};
     Mesh mesh;
     Workspace ws;
+    Fields fields;
 };
 
 }  // namespace
@@ -271,7 +289,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
 // st[].active; right-hand sides in r2 (inner type T), solution in d.
 template <typename T>
 spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws, double inner_tol,
-                         int* iters_out, cudaStream_t st) {
+                         int* iters_out, cudaStream_t st, const T* kh2c = nullptr) {
     const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
     T* d = static_cast<T*>(ws.vec[0]);
     T* w1 = static_cast<T*>(ws.vec[1]);
@@ -316,8 +334,8 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
             const int nA = launch_minres_A<T>(n, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
-                                              pending ? yprev : nullptr, w1, w2, d, st);
-            prof_end(st, cols * (itn >= 2 ? 12.0 : 8.0) * n3d * w +
+                                              pending ? yprev : nullptr, w1, w2, d, st, kh2c);
+            prof_end(st, cols * ((itn >= 2 ? 12.0 : 8.0) + (kh2c ? 1.0 : 0.0)) * n3d * w +
                              (pending ? cols * (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0));
             if (pending) std::swap(w1, w2);
             prof_begin(PK_ALPHA, st);
@@ -436,7 +454,7 @@ static spde_status fault_status(int fault, cudaStream_t st) {
 // residual in *maxrel.
 template <typename T>
 spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws, double* maxrel, int* outer_out,
-                         int* inner_out, cudaStream_t st, bool warm = false) {
+                         int* inner_out, cudaStream_t st, bool warm = false, const Fields* fl = nullptr) {
     const spde_opts& o = ctx->opts;
     const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
     // ||F||^2 per column
@@ -464,8 +482,8 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
             prof_end(st, (double)S * 96.0 * (double)n3);
         }
         prof_begin(PK_RESIDUAL, st);
-        nb = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st);
-        prof_end(st, (double)S * (40.0 + 4.0 * sizeof(T)) * (double)n3);
+        nb = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st, fl ? fl->kh2_64 : nullptr);
+        prof_end(st, (double)S * (40.0 + 4.0 * sizeof(T) + (fl ? 8.0 : 0.0)) * (double)n3);
         CUDA_TRY(cudaGetLastError());
         prof_begin(PK_OTHER, st);
         CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, st));
@@ -496,7 +514,14 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         if (std::is_same<T, double>::value) itol = std::max(0.1 * o.tol / std::max(worst, 1e-300), 1e-15);
         int its = 0;
         if (o.solver == SPDE_SOLVER_SCHUR_CG) STATUS_TRY(cg_batch<T>(o, n, kh2, S, ws, itol, &its, st));
-        else STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st));
+        else {
+            const T* kh2c = nullptr;
+            if (fl) {
+                if constexpr (sizeof(T) == 4) kh2c = fl->kh2_32;
+                else kh2c = fl->kh2_64;
+            }
+            STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st, kh2c));
+        }
         inner_total += its;
         prof_begin(PK_ADD_CORR, st);
         if (o.solver == SPDE_SOLVER_SCHUR_CG)
@@ -538,20 +563,23 @@ int batch_capacity(int n, int S, bool inner64) {
 }
 
 // Draw `S` samples starting at `first` into ws.x64 (scaled solution).
+// With fl (a level with fields), kappa and sigma are ignored: the right-hand side
+// is -g_c h xi_c cell by cell and the operator takes (kappa_c h)^2 per cell.
 spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double sigma, uint64_t seed, uint64_t first,
-                          cudaStream_t st) {
+                          cudaStream_t st, const Fields* fl = nullptr) {
     const int n = L.n;
     const int64_t n3 = (int64_t)n * n * n;
-    const double kh2 = (kappa * L.h) * (kappa * L.h);
+    const double kh2 = fl ? fl->kh2_mean : (kappa * L.h) * (kappa * L.h);
     // scaled RHS cell block: h^{-1/2} (-g h^{3/2} xi) = -g h xi
     prof_begin(PK_NOISE, st);
-    CUDA_TRY(launch_noise(n3, S, seed, first, -g_half(kappa, sigma) * L.h, L.ws.F, n3, st));
-    prof_end(st, (double)S * 8.0 * (double)n3);
+    CUDA_TRY(launch_noise(n3, S, seed, first, fl ? 1.0 : -g_half(kappa, sigma) * L.h, L.ws.F, n3, st));
+    if (fl) CUDA_TRY(launch_scale_cells(n3, S, L.ws.F, n3, fl->gh, st));
+    prof_end(st, (double)S * (fl ? 24.0 : 8.0) * (double)n3);
     double rel = 0.0;
     int outer = 0, inner = 0;
     spde_status s;
-    if (L.ws.inner64 == 1) s = refine_solve<double>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st);
-    else s = refine_solve<float>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st);
+    if (L.ws.inner64 == 1) s = refine_solve<double>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st, false, fl);
+    else s = refine_solve<float>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st, false, fl);
     ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
     ctx->stats.inner_iters = std::max(ctx->stats.inner_iters, inner);
     ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
@@ -1127,6 +1155,7 @@ spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], 
     Level& L = ctx->lev[level];
     L.mesh.release();
     L.ws.release();
+    L.fields.release();
     L.defined = true;
     L.n = n;
     L.h = ext / n;
@@ -1189,10 +1218,73 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
     return SPDE_OK;
 }
 
+namespace {
+spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, bool use_fields,
+                        uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream);
+}
+
 spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, uint64_t seed,
                         uint64_t first_sample, int out_kind, void* out, void* stream) {
     STATUS_TRY(check_level(ctx, level));
     STATUS_TRY(check_params(kappa, sigma));
+    return sample_impl(ctx, level, nsamples, kappa, sigma, false, seed, first_sample, out_kind, out, stream);
+}
+
+spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_cells, const double* sigma_cells) {
+    STATUS_TRY(check_level(ctx, level));
+    if ((kappa_cells == nullptr) != (sigma_cells == nullptr))
+        return fail(SPDE_EINVAL, "give both kappa and sigma, or neither (to clear the fields)");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; fields cannot change");
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    Level& L = ctx->lev[level];
+    L.fields.release();
+    if (!kappa_cells) return SPDE_OK;
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    double sum = 0.0;
+    for (int64_t e = 0; e < n3; ++e) {
+        const double k = kappa_cells[e], sg = sigma_cells[e];
+        if (!(k > 0.0) || !std::isfinite(k)) return fail(SPDE_EINVAL, "kappa must be finite and > 0 (cell %lld)", (long long)e);
+        if (!(sg > 0.0) || !std::isfinite(sg)) return fail(SPDE_EINVAL, "sigma must be finite and > 0 (cell %lld)", (long long)e);
+        sum += (k * L.h) * (k * L.h);
+    }
+    Fields& f = L.fields;
+    double* dk = nullptr;
+    double* ds = nullptr;
+    spde_status st = dev_alloc(&f.kh2_64, (size_t)n3);
+    if (st == SPDE_OK) st = dev_alloc(&f.kh2_32, (size_t)n3);
+    if (st == SPDE_OK) st = dev_alloc(&f.gh, (size_t)n3);
+    if (st == SPDE_OK) st = dev_alloc(&dk, (size_t)n3);
+    if (st == SPDE_OK) st = dev_alloc(&ds, (size_t)n3);
+    cudaError_t e = cudaSuccess;
+    if (st == SPDE_OK) e = cudaMemcpy(dk, kappa_cells, (size_t)n3 * sizeof(double), cudaMemcpyHostToDevice);
+    if (st == SPDE_OK && e == cudaSuccess)
+        e = cudaMemcpy(ds, sigma_cells, (size_t)n3 * sizeof(double), cudaMemcpyHostToDevice);
+    if (st == SPDE_OK && e == cudaSuccess) e = launch_field_coefs(n3, L.h, dk, ds, f.kh2_64, f.kh2_32, f.gh, 0);
+    if (st == SPDE_OK && e == cudaSuccess) e = cudaDeviceSynchronize();
+    dev_free(dk);
+    dev_free(ds);
+    if (st != SPDE_OK || e != cudaSuccess) {
+        f.release();
+        if (st != SPDE_OK) return st;
+        CUDA_TRY(e);
+    }
+    f.kh2_mean = sum / (double)n3;
+    f.set = true;
+    return SPDE_OK;
+}
+
+spde_status spde_sample_fields(spde_ctx* ctx, int level, int nsamples, uint64_t seed, uint64_t first_sample,
+                               int out_kind, void* out, void* stream) {
+    STATUS_TRY(check_level(ctx, level));
+    if (!ctx->lev[level].fields.set) return fail(SPDE_EINVAL, "level %d has no fields (spde_level_set_fields)", level);
+    if (ctx->opts.solver != SPDE_SOLVER_MINRES) return fail(SPDE_EINVAL, "fields need the MINRES solver");
+    return sample_impl(ctx, level, nsamples, 0.0, 0.0, true, seed, first_sample, out_kind, out, stream);
+}
+
+namespace {
+spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, bool use_fields,
+                        uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream) {
     if (nsamples < 0) return fail(SPDE_EINVAL, "nsamples < 0");
     const int kind = out_kind & 15;
     if (kind > SPDE_OUT_GRID_GAUSSIAN || (out_kind & ~(15 | SPDE_OUT_F64))) return fail(SPDE_EINVAL, "bad out_kind");
@@ -1223,7 +1315,8 @@ spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, do
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
         STATUS_TRY(ensure_workspace(L.ws, L.n, plain ? 1 : std::min(cap, nsamples), plain));
-        spde_status s = solve_samples(ctx, L, S, kappa, sigma, seed, first_sample + (uint64_t)s0, st);
+        spde_status s = solve_samples(ctx, L, S, kappa, sigma, seed, first_sample + (uint64_t)s0, st,
+                                      use_fields ? &L.fields : nullptr);
         if (s != SPDE_OK && s != SPDE_ENOCONV) return s;
         if (s == SPDE_ENOCONV) worst = s;
         const size_t per = out_elem_count(L, 1, out_kind);
@@ -1249,6 +1342,7 @@ spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, do
         return fail(worst, "tolerance not reached: relative residual %.3e", ctx->stats.max_rel_residual);
     return SPDE_OK;
 }
+}  // namespace
 
 spde_status spde_submit(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, uint64_t seed,
                         uint64_t first_sample, int out_kind, void* out, int64_t* request) {
@@ -1472,6 +1566,7 @@ spde_status spde_destroy(spde_ctx* ctx) {
         for (auto& L : ctx->lev) {
             L.mesh.release();
             L.ws.release();
+            L.fields.release();
         }
         if (ctx->out_tmp) cudaFree(ctx->out_tmp);
     }

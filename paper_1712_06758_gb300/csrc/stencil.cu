@@ -55,7 +55,7 @@ template cudaError_t launch_apply<double>(int, double, int, const double*, doubl
 __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const double* __restrict__ F, int64_t F_stride,
                                                     const double* __restrict__ x, float* __restrict__ r32,
                                                     double* __restrict__ r64, double* __restrict__ part,
-                                                    const int* __restrict__ active) {
+                                                    const int* __restrict__ active, const double* __restrict__ kh2c) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     if (active && !active[s]) return;
@@ -80,6 +80,11 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
         const V4<double> uzM = kl ? ld4(uz + c - sz) : zero4<double>();
         const double uxL = (p.i0 > 0) ? ux[c - 1] : 0.0;
         const V4<double> f = ld4(Fs + c);
+        V4<double> k4;  // (kappa h)^2 per cell: one value, or the level's field
+        if (kh2c) k4 = ld4(kh2c + c);
+        else
+#pragma unroll
+            for (int e = 0; e < 4; ++e) k4.v[e] = kh2;
         V4<double> d;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
             const double uxm = (e > 0) ? ux4.v[e - 1] : uxL;
             const double uy0 = jh ? uy4.v[e] : 0.0;
             const double uz0 = kh ? uz4.v[e] : 0.0;
-            const double yt = (ux0 - uxm) + (uy0 - uyM.v[e]) + (uz0 - uzM.v[e]) - kh2 * th4.v[e];
+            const double yt = (ux0 - uxm) + (uy0 - uyM.v[e]) + (uz0 - uzM.v[e]) - k4.v[e] * th4.v[e];
             d.v[e] = f.v[e] - yt;
             acc += d.v[e] * d.v[e];
         }
@@ -117,12 +122,49 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
 }
 
 int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x, float* r32,
-                      double* r64, double* part, const int* active, cudaStream_t st) {
+                      double* r64, double* part, const int* active, cudaStream_t st, const double* kh2c) {
     const int64_t n3 = (int64_t)n * n * n;
     const int nb = stencil_blocks(n3 / 4);
     dim3 grid(nb, S);
-    k_residual64<<<grid, 256, 0, st>>>(n, kh2, F, F_stride, x, r32, r64, part, active);
+    k_residual64<<<grid, 256, 0, st>>>(n, kh2, F, F_stride, x, r32, r64, part, active, kh2c);
     return nb;
+}
+
+// F[s][e] *= c[e]: the per-cell noise factor -g(x) h of a level with fields
+__global__ void __launch_bounds__(256) k_scale_cells(int64_t n3, double* __restrict__ F, int64_t stride,
+                                                     const double* __restrict__ c) {
+    double* Fs = F + (int64_t)blockIdx.y * stride;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
+        Fs[e] *= c[e];
+}
+
+cudaError_t launch_scale_cells(int64_t n3, int S, double* F, int64_t stride, const double* c, cudaStream_t st) {
+    int64_t b = (n3 + 1023) / 1024;
+    if (b > 4096) b = 4096;
+    dim3 grid((unsigned)(b < 1 ? 1 : b), S);
+    k_scale_cells<<<grid, 256, 0, st>>>(n3, F, stride, c);
+    return cudaGetLastError();
+}
+
+// per-cell coefficients of a level with fields: (kappa h)^2 in FP64 and FP32, and
+// the noise factor -g h with g = sigma sqrt(8 pi kappa) (the nu = 1/2, d = 3 normaliser)
+__global__ void __launch_bounds__(256) k_field_coefs(int64_t n3, double h, const double* __restrict__ kappa,
+                                                     const double* __restrict__ sigma, double* __restrict__ kh2_64,
+                                                     float* __restrict__ kh2_32, double* __restrict__ gh) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
+        const double kh = kappa[e] * h;
+        kh2_64[e] = kh * kh;
+        kh2_32[e] = (float)(kh * kh);
+        gh[e] = -sigma[e] * sqrt(8.0 * 3.14159265358979323846 * kappa[e]) * h;
+    }
+}
+
+cudaError_t launch_field_coefs(int64_t n3, double h, const double* kappa, const double* sigma, double* kh2_64,
+                               float* kh2_32, double* gh, cudaStream_t st) {
+    int64_t b = (n3 + 1023) / 1024;
+    if (b > 4096) b = 4096;
+    k_field_coefs<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(n3, h, kappa, sigma, kh2_64, kh2_32, gh);
+    return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_add_correction(int64_t nelem, double* __restrict__ x,
