@@ -317,6 +317,16 @@ spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec,
 spde_status spde_precond_noalloc(int n, double h, double kappa, int nsamples, int prec,
                                  const spde_opts* opts, const void* r, void* z, void* stream);
 
+/* Self-check of the bounded device waits (no paper counterpart: a safety
+ * property of this implementation).  The multigrid sweeps wait on mbarriers
+ * for their plane copies; every such wait gives up after about one second,
+ * raises a device fault word and returns, and the solve then reports
+ * SPDE_ETIMEOUT.  This call launches one CTA whose barrier never completes
+ * and checks that path on `device`: SPDE_OK when the wait gave up and the
+ * fault word was raised (then cleared), *waited_ms the time the wait took
+ * (about 1000); the context stays usable.  Synchronises the device. */
+spde_status spde_check_wait_limit(int device, double* waited_ms);
+
 /* y = S x with the scaled Schur complement S = (kappa h)^2 I + D1 T^{-1} D1^T of
  * the cell unknowns (Sec. 4.2: kappa^2 W + B M^{-1} B^T, scaled by h^{-1}),
  * T^{-1} applied exactly by tridiagonal line solves.  x, y: device

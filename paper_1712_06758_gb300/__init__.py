@@ -53,6 +53,7 @@ _SIGS = {
     "spde_mesh_attach": [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int64, _P],
     "spde_sample": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                     ctypes.c_uint64, ctypes.c_int, _P, _P],
+    "spde_check_wait_limit": [ctypes.c_int, _P],
     "spde_level_set_fields": [_P, ctypes.c_int, _P, _P],
     "spde_sample_fields": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _P, _P],
     "spde_sample_coupled": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -174,6 +175,13 @@ def spde_level_set_fields(ctx, level, kappa_cells, sigma_cells):
     s = None if sigma_cells is None else np.ascontiguousarray(sigma_cells, dtype=np.float64).ravel()
     _check(lib().spde_level_set_fields(ctx, level, None if k is None else k.ctypes.data,
                                        None if s is None else s.ctypes.data))
+
+
+def spde_check_wait_limit(device=0):
+    """Runs the bounded-wait self-check; returns the time the probe's wait took (ms)."""
+    ms = ctypes.c_double(0.0)
+    _check(lib().spde_check_wait_limit(device, ctypes.byref(ms)))
+    return ms.value
 
 
 def spde_sample_fields(ctx, level, nsamples, seed, first_sample, out_kind, out, stream=None):

@@ -123,6 +123,8 @@ template <typename T>
 int launch_precond_u(int64_t N4, int n3, int S, const T* r, T* y, double fd, double* part,
                      const MinresCol* st_, cudaStream_t st);
 cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cudaStream_t st);
+// nactive (optional, two ints): [0] += columns still active after this step,
+// [1] += columns whose w/x update this step left pending
 cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC,
                           MinresCol* st_, int* nactive, cudaStream_t st);
 cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC,
@@ -142,6 +144,8 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 // mg_fault_read enqueues a copy into *host on st (valid once st has synchronised),
 // mg_fault_clear resets it
 cudaError_t mg_fault_read(int* host, cudaStream_t st);
+// launches the bounded-wait self-check (one CTA whose wait must give up); its wait time goes to *elapsed_ns_dev
+cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, cudaStream_t st);
 cudaError_t mg_fault_clear(cudaStream_t st);
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride,

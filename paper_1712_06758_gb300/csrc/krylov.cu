@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB
     set_coef(c, KC_IG, 1.0 / c.d_gamma);
     set_coef(c, KC_PH, c.d_phi);
     const bool done = !(beta2 > 0.0) || !isfinite(beta) || c.phibar <= c.tol * c.beta1;
+    if (nactive) atomicAdd(nactive + 1, 1);  // this column's update is pending
     if (done) c.active = 0;
     else if (nactive) atomicAdd(nactive, 1);
 }

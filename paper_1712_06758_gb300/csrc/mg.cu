@@ -896,6 +896,27 @@ static bool plane_map(CUtensorMap* m, const T* base, int n, int S, int64_t col_s
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Self-check of the bounded wait: one CTA waits on an mbarrier that is set up
+// for one arrival which never comes, so phase 0 never completes; every thread
+// must give up after the limit, raise the fault word and return.
+__global__ void k_wait_probe(unsigned long long* elapsed_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned long long t0 = global_ns();
+    if (!mbar_wait(&bar, 0)) atomicExch(&g_mg_fault, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) *elapsed_ns = global_ns() - t0;
+}
+
+cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(elapsed_ns_dev);
+    return cudaGetLastError();
+}
+
 cudaError_t mg_fault_read(int* host, cudaStream_t st) {
     return cudaMemcpyFromSymbolAsync(host, g_mg_fault, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
 }

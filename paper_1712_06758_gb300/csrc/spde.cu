@@ -250,7 +250,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
     STATUS_TRY(dev_alloc(&ws.colv, (size_t)2 * S));
     STATUS_TRY(dev_alloc(&ws.st, (size_t)S));
     STATUS_TRY(dev_alloc(&ws.cg, (size_t)S));
-    STATUS_TRY(dev_alloc(&ws.nact, 1));
+    STATUS_TRY(dev_alloc(&ws.nact, 2));  // [0] columns still active, [1] columns with an update pending
     STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
     {
         // Thomas factors of tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of a line
@@ -272,7 +272,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
             return fail(SPDE_ECUDA, "upload of line-solve factors failed");
         }
     }
-    if (cudaMallocHost(&ws.h_nact, sizeof(int)) != cudaSuccess ||
+    if (cudaMallocHost(&ws.h_nact, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ws.h_col, 2 * S * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&ws.h_st, S * sizeof(MinresCol)) != cudaSuccess) {
         cudaGetLastError();
@@ -323,6 +323,7 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     bool pending = false;  // a w/x update of the last iteration waits for the next pass
     int last_itn = 0;
     double last_cols = (double)S;
+    int last_upd = S;  // columns whose last update waits for the final pass
     T* yprev = nullptr;
     while (nactive > 0 && it < o.max_iter) {
         const int chunk = std::min(o.check_every, o.max_iter - it);
@@ -345,7 +346,7 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, o.flux_diag, ws.partB, ws.st, st);
             prof_end(st, cols * 12.0 * n3d * w);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
-            if (q == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
+            if (q == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, 2 * sizeof(int), st));
             prof_begin(PK_GIVENS, st);
             CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, (q == chunk - 1) ? ws.nact : nullptr, st));
             prof_end(st, cols * (nB + nC) * 8.0);
@@ -357,16 +358,17 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             std::swap(ycur, ynext);
         }
         CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         if (t_prof) t_prof->flush();
         it += chunk;
-        nactive = *ws.h_nact;
+        nactive = ws.h_nact[0];
+        last_upd = ws.h_nact[1];
     }
     if (pending) {
         prof_begin(PK_MINRES_D, st);
         CUDA_TRY(launch_minres_D<T>(n3, S, yprev, w1, w2, d, ws.st, st));
-        prof_end(st, last_cols * (last_itn >= 3 ? 6.0 : (last_itn == 2 ? 5.0 : 3.0)) * n3d * w);
+        prof_end(st, (double)last_upd * (last_itn >= 3 ? 6.0 : (last_itn == 2 ? 5.0 : 3.0)) * n3d * w);
         std::swap(w1, w2);
     }
     *iters_out = it;
@@ -1667,6 +1669,29 @@ spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, 
             return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
     }
     CUDA_TRY(cudaGetLastError());
+    return SPDE_OK;
+}
+
+spde_status spde_check_wait_limit(int device, double* waited_ms) {
+    if (!waited_ms) return fail(SPDE_EINVAL, "null argument");
+    *waited_ms = 0.0;
+    CUDA_TRY(cudaSetDevice(device));
+    unsigned long long* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long)));
+    unsigned long long ns = 0;
+    int fault = 0;
+    cudaError_t e = mg_fault_read(&fault, 0);  // a fault left by an earlier call is not this probe's
+    if (e == cudaSuccess && fault) e = mg_fault_clear(0);
+    if (e == cudaSuccess) e = mg_wait_probe(d, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&ns, d, sizeof(ns), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = mg_fault_read(&fault, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e == cudaSuccess && fault) e = mg_fault_clear(0);
+    cudaFree(d);
+    CUDA_TRY(e);
+    *waited_ms = 1e-6 * (double)ns;
+    if (!fault) return fail(SPDE_ECUDA, "the probe's wait did not give up (fault word not raised)");
     return SPDE_OK;
 }
 
