@@ -93,7 +93,7 @@ typedef struct {
     double omega;       /* damped-Jacobi weight of the V-cycle smoother; 0.8 */
     double schur_c;     /* weight c of the 7-point Schur approximation kappa^2 h^2 I + c L; 1.0 */
     double flux_diag;   /* flux-block preconditioner, a multiple of the identity; 1.5 = diag(T)^{-1} */
-    int check_every;    /* MINRES iterations between host convergence checks; 8 */
+    int check_every;    /* MINRES iterations between host convergence checks; 8 (at most 64 are used) */
     int device;         /* CUDA device ordinal; 0 */
     int use_graphs;     /* capture the batched MINRES iteration in CUDA graphs; 1 */
     int64_t serve_budget_bytes; /* device memory the serving lanes may hold; 120 GiB */

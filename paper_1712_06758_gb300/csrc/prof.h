@@ -68,6 +68,15 @@ struct Profiler {
         cur.bytes = b;
         pending.push_back(cur);
     }
+    // records not yet flushed: their byte counts can still be set once the
+    // number of columns a launch really processed is known
+    size_t mark() const { return pending.size(); }
+    void scale(size_t i0, size_t i1, double f) {
+        for (size_t i = i0; i < i1 && i < pending.size(); ++i) pending[i].bytes *= f;
+    }
+    void set_bytes(size_t i, double b) {
+        if (i < pending.size()) pending[i].bytes = b;
+    }
     // call after the stream is synchronised
     void flush() {
         for (auto& r : pending) {

@@ -66,6 +66,9 @@ spde_status fail(spde_status s, const char* fmt, ...) {
 // (4 pi)^{3/4} kappa^{1/2} sqrt(Gamma(2) / Gamma(1/2)) sigma = sqrt(8 pi kappa) sigma
 double g_half(double kappa, double sigma) { return sigma * std::sqrt(8.0 * M_PI * kappa); }
 
+// MINRES iterations between two host checks of the active columns at most
+constexpr int kMaxChunk = 64;
+
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 template <typename T>
@@ -250,7 +253,8 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
     STATUS_TRY(dev_alloc(&ws.colv, (size_t)2 * S));
     STATUS_TRY(dev_alloc(&ws.st, (size_t)S));
     STATUS_TRY(dev_alloc(&ws.cg, (size_t)S));
-    STATUS_TRY(dev_alloc(&ws.nact, 2));  // [0] columns still active, [1] columns with an update pending
+    // per MINRES iteration of a chunk: [2q] columns still active after it, [2q+1] columns it left an update pending
+    STATUS_TRY(dev_alloc(&ws.nact, 2 * kMaxChunk));
     STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
     {
         // Thomas factors of tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of a line
@@ -272,7 +276,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
             return fail(SPDE_ECUDA, "upload of line-solve factors failed");
         }
     }
-    if (cudaMallocHost(&ws.h_nact, 2 * sizeof(int)) != cudaSuccess ||
+    if (cudaMallocHost(&ws.h_nact, 2 * kMaxChunk * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ws.h_col, 2 * S * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&ws.h_st, S * sizeof(MinresCol)) != cudaSuccess) {
         cudaGetLastError();
@@ -322,48 +326,59 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     int nactive = *ws.h_nact;
     bool pending = false;  // a w/x update of the last iteration waits for the next pass
     int last_itn = 0;
-    double last_cols = (double)S;
-    int last_upd = S;  // columns whose last update waits for the final pass
+    int last_upd = 0;  // columns whose last update waits for the next pass
     T* yprev = nullptr;
     while (nactive > 0 && it < o.max_iter) {
-        const int chunk = std::min(o.check_every, o.max_iter - it);
-        // bytes are counted for the columns active at the start of the chunk
-        const double cols = (double)nactive;
-        plan.prof_cols = cols;
+        const int chunk = std::min(std::min(o.check_every, o.max_iter - it), kMaxChunk);
+        // the profiler's byte counts are recorded per column and scaled after the chunk's
+        // synchronisation by the columns each iteration really processed
+        CUDA_TRY(cudaMemsetAsync(ws.nact, 0, 2 * chunk * sizeof(int), st));
+        plan.prof_cols = 1.0;
+        size_t rec[kMaxChunk + 1];
+        double a_bytes[kMaxChunk], d_bytes[kMaxChunk];
         for (int q = 0; q < chunk; ++q) {
             const int itn = it + q + 1;  // 1-based iteration of the columns that started together
+            rec[q] = t_prof ? t_prof->mark() : 0;
             // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
             const int nA = launch_minres_A<T>(n, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
                                               pending ? yprev : nullptr, w1, w2, d, st, kh2c);
-            prof_end(st, cols * ((itn >= 2 ? 12.0 : 8.0) + (kh2c ? 1.0 : 0.0)) * n3d * w +
-                             (pending ? cols * (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0));
+            a_bytes[q] = ((itn >= 2 ? 12.0 : 8.0) + (kh2c ? 1.0 : 0.0)) * n3d * w;
+            d_bytes[q] = pending ? (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0;
+            prof_end(st, 0.0);
             if (pending) std::swap(w1, w2);
             prof_begin(PK_ALPHA, st);
             CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, st));
-            prof_end(st, cols * nA * 8.0);
+            prof_end(st, nA * 8.0);
             prof_begin(PK_MINRES_B, st);
             const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, o.flux_diag, ws.partB, ws.st, st);
-            prof_end(st, cols * 12.0 * n3d * w);
+            prof_end(st, 12.0 * n3d * w);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
-            if (q == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, 2 * sizeof(int), st));
             prof_begin(PK_GIVENS, st);
-            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, (q == chunk - 1) ? ws.nact : nullptr, st));
-            prof_end(st, cols * (nB + nC) * 8.0);
+            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, ws.nact + 2 * q, st));
+            prof_end(st, (nB + nC) * 8.0);
             pending = true;
             last_itn = itn;
-            last_cols = cols;
             yprev = ycur;
             std::swap(r1, r2);
             std::swap(ycur, ynext);
         }
+        rec[chunk] = t_prof ? t_prof->mark() : 0;
         CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, 2 * chunk * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        if (t_prof) t_prof->flush();
+        if (t_prof) {
+            for (int q = 0; q < chunk; ++q) {
+                const double on = q == 0 ? (double)nactive : (double)ws.h_nact[2 * (q - 1)];
+                const double upd = q == 0 ? (double)last_upd : (double)ws.h_nact[2 * (q - 1) + 1];
+                t_prof->scale(rec[q], rec[q + 1], on);
+                t_prof->set_bytes(rec[q], a_bytes[q] * on + d_bytes[q] * upd);
+            }
+            t_prof->flush();
+        }
         it += chunk;
-        nactive = ws.h_nact[0];
-        last_upd = ws.h_nact[1];
+        nactive = ws.h_nact[2 * (chunk - 1)];
+        last_upd = ws.h_nact[2 * (chunk - 1) + 1];
     }
     if (pending) {
         prof_begin(PK_MINRES_D, st);
