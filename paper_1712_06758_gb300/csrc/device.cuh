@@ -52,6 +52,31 @@ __device__ __forceinline__ double block_sum(double v, double* smem /* >= BLOCK/3
     return s;
 }
 
+// Block sum of per-thread partials of the element type: FP32 partials are
+// summed in FP32 within a warp (fixed shuffle tree) and the warps' sums in
+// FP64; FP64 partials go through block_sum.  Deterministic for a fixed block.
+template <int BLOCK, typename T>
+__device__ __forceinline__ double block_sum_t(T v, double* smem /* >= BLOCK/32 */) {
+    if constexpr (sizeof(T) == 8) {
+        return block_sum<BLOCK>((double)v, smem);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+        const int lane = tid & 31, warp = tid >> 5;
+        if (lane == 0) smem[warp] = (double)v;
+        __syncthreads();
+        double s = 0.0;
+        if (tid < 32) {
+            s = (tid < BLOCK / 32) ? smem[tid] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        }
+        __syncthreads();
+        return s;
+    }
+}
+
 // number of existing neighbours of cell i along one axis of length n
 __device__ __forceinline__ int nb_count1(int i, int n) { return (i > 0) + (i < n - 1); }
 

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
         }
     }
     if (doA) {
-        const double t = block_sum<256>((double)acc, red);
+        const double t = block_sum_t<256, T>(acc, red);
         if (threadIdx.x == 0) partA[(int64_t)s * kMaxPartials + blockIdx.x] = t;
     }
 }
@@ -197,20 +197,26 @@ __global__ void __launch_bounds__(256) k_minres_B(int64_t N4, int64_t n3u, T* __
     if (!cs.active) return;
     const T f = col_coef<T>(cs, KC_F);
     const int64_t off = (int64_t)s * N4;
+    const int64_t nq = N4 >> 2, nqu = n3u >> 2;  // 4-vectors; the flux blocks end on a vector boundary
     T acc = T(0);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N4; e += (int64_t)gridDim.x * blockDim.x) {
-        const T z = r1[off + e] - f * r2[off + e];
-        r1[off + e] = z;
-        if (e < n3u) acc += z * (fd * z);  // flux block of the next preconditioned vector, never stored
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        V4<T> z = ld4(r1 + off + 4 * q);
+        const V4<T> p = ld4(r2 + off + 4 * q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z.v[e] = z.v[e] - f * p.v[e];
+        st4(r1 + off + 4 * q, z);
+        if (q < nqu)  // flux block of the next preconditioned vector, never stored
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc += z.v[e] * (fd * z.v[e]);
     }
-    const double t = block_sum<256>((double)acc, red);
+    const double t = block_sum_t<256, T>(acc, red);
     if (threadIdx.x == 0) partB[(int64_t)s * kMaxPartials + blockIdx.x] = t;
 }
 
 template <typename T>
 int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, double fd, double* partB, MinresCol* st_,
                     cudaStream_t st) {
-    const int nb = elem_blocks(N4);
+    const int nb = elem_blocks(N4 / 16);  // sixteen 4-vectors per thread at n = 128: one reduction per 4096 values
     dim3 grid(nb, S);
     k_minres_B<T><<<grid, 256, 0, st>>>(N4, 3 * (int64_t)n3, r1, r2, (T)fd, partB, st_);
     return nb;

@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         seq += nplanes;
     }
     if (dot_part) {
-        const double tsum = block_sum<kTileThreads>((double)dacc, red);
+        const double tsum = block_sum_t<kTileThreads, T>(dacc, red);
         if (tid == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
     }
 }
