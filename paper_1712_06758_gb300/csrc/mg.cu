@@ -20,6 +20,8 @@
 // n_l <= 16 run inside one CTA per sample in shared memory.
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 
+#include <type_traits>
+
 #include "device.cuh"
 #include "internal.h"
 #include "prof.h"
@@ -111,7 +113,7 @@ constexpr int BH = SY + 2;       // up sweep: b and x rows, y from fy0 - 1
 constexpr int RXY = (SX / 2) * (SY / 2);          // x-y restricted plane (128)
 constexpr int CW = SX / 2 + 6, CH = SY / 2 + 2;   // up sweep: coarse plane, x from cx0 - 3, y from cy0 - 1
 constexpr int kDownSmem = 4 * PW * XH + 2 * PW * RH + 4 * RXY;
-constexpr int kUpSmem = 4 * PW * BH + 3 * CW * CH;
+constexpr int kUpSmem = 4 * PW * BH + 4 * CW * CH;
 
 __device__ __forceinline__ int ring4(int f) { return (f + 4) & 3; }  // f >= -4
 
@@ -128,10 +130,11 @@ __device__ __forceinline__ int kxy_of(int packed, int e) { return (packed >> (3 
 // the CTA's abort flag and the device-wide fault word, later waits return at
 // once and the host reports SPDE_ETIMEOUT.
 // ---------------------------------------------------------------------------
-constexpr int kDownStages = 4;
+constexpr int kRing = 4;  // plane slots of the TMA ring (both sweeps): the z-march is unrolled by 4
+template <int K>
+using IC = std::integral_constant<int, K>;
 constexpr int kProducer = kTileThreads - 32;  // issues the plane copies: lane 0 of the last warp, which has no
                                               // segment work in the residual and prolongation phases
-constexpr int kUpStages = 6;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
 __device__ int g_mg_fault;
@@ -142,11 +145,11 @@ __host__ __device__ constexpr int slot_elems(int rows) {  // a plane slot, round
 }
 template <typename T>
 __host__ __device__ constexpr int down_smem_bytes() {
-    return 128 + (int)sizeof(T) * (kDownStages * slot_elems<T>(XH) + kDownSmem);
+    return 128 + (int)sizeof(T) * (kRing * slot_elems<T>(XH) + kDownSmem);
 }
 template <typename T>
 __host__ __device__ constexpr int up_smem_bytes() {
-    return 128 + (int)sizeof(T) * (kUpStages * slot_elems<T>(BH) + kUpSmem);
+    return 128 + (int)sizeof(T) * (kRing * slot_elems<T>(BH) + kUpSmem);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -195,8 +198,10 @@ __device__ __forceinline__ void tma_plane(void* dst, const CUtensorMap* map, uin
         : "memory");
 }
 
-// The ring of one CTA: plane u of the CTA's sequence (all tiles) lives in slot
-// u % NS and completes phase u / NS of that slot's barrier.
+// The ring of one CTA.  Within a tile, tile plane j lives in slot j mod NS; the
+// tile's planes are all issued and consumed before the next tile starts.  Every
+// thread tracks, per slot, the parity of the next completion it waits for; the
+// producer also tracks the slots whose copy it has not yet seen complete.
 template <typename T, int NS>
 struct PlaneRing {
     T* slots;
@@ -204,23 +209,35 @@ struct PlaneRing {
     uint64_t* bars;
     volatile int* abort;
     uint32_t bytes;
+    uint32_t ph = 0;     // bit s: parity of slot s's next completion
+    uint32_t pend = 0;   // producer: bit s set while a copy into slot s is unobserved
 
-    __device__ __forceinline__ T* at(uint32_t u) const { return slots + (int)(u % NS) * slot; }
-    // producer thread only
-    __device__ __forceinline__ void issue(uint32_t u, const CUtensorMap* map, int x, int y, int z, int w) const {
-        if (*abort) return;
-        tma_plane(at(u), map, bars + u % NS, bytes, x, y, z, w);
+    __device__ __forceinline__ T* at(int s) const { return slots + s * slot; }
+    // producer thread only; false once the CTA has given up
+    __device__ __forceinline__ bool issue(int s, const CUtensorMap* map, int x, int y, int z, int w) {
+        if (*abort) return false;
+        tma_plane(at(s), map, bars + s, bytes, x, y, z, w);
+        pend |= 1u << s;
+        return true;
     }
-    __device__ __forceinline__ const T* take(uint32_t u) const {
-        if (!*abort && !mbar_wait(bars + u % NS, (u / NS) & 1)) {
-            *abort = 1;
-            atomicExch(&g_mg_fault, 1);
+    __device__ __forceinline__ const T* take(int s) {
+        const uint32_t par = (ph >> s) & 1u;
+        ph ^= 1u << s;
+        if (!*abort) {
+            if (mbar_wait(bars + s, par)) pend &= ~(1u << s);
+            else {
+                *abort = 1;
+                atomicExch(&g_mg_fault, 1);
+            }
         }
-        return at(u);
+        return at(s);
     }
-    // producer thread, after an abort: bounded wait for copies still in flight
-    __device__ void drain(uint32_t first, uint32_t end) const {
-        for (uint32_t u = first; u < end; ++u) mbar_wait(bars + u % NS, (u / NS) & 1);
+    // producer thread, after an abort: bounded wait for copies still in flight (their
+    // slots were taken without waiting, so each awaits the phase before the current one)
+    __device__ void drain() {
+        for (int s = 0; s < NS; ++s)
+            if ((pend >> s) & 1u) mbar_wait(bars + s, ((ph >> s) & 1u) ^ 1u);
+        pend = 0;
     }
 };
 
@@ -246,33 +263,33 @@ __device__ __forceinline__ PlaneRing<T, NS> ring_setup(unsigned char* raw, int r
 // Down sweep at level l: bc = R (b - A omega D^{-1} b).  With x0 = omega D^{-1} b
 //     r(f) = (1/omega - 1) D(f) x0(f) + s c sum_{neighbours g} x0(g)
 // (x0 = 0 outside the box, so the sum runs over existing neighbours).
-// Step f: warps 0-6 store the x0 plane f+2 (tile + halo 2) from its b plane,
-// warps 0-5 form r on plane f (tile + halo 1) from x0 planes f-1 .. f+1, and
-// warps 6-7 restrict r(f-1) in x and y at once (Rxy, 16 x 8 values, two coarse
-// x per thread); every second step one coarse plane is the 4-tap z
-// combination of four Rxy planes (each thread reads back only its own Rxy
-// entries).  x0 planes live in 4 slots, r planes in 2.
+// Step t (fine plane f = fz0 - 1 + t): warps 0-6 store the x0 plane f+2 (tile +
+// halo 2) from its b plane, warps 0-5 form r on plane f (tile + halo 1) from
+// x0 planes f-1 .. f+1, and warps 6-7 restrict r(f-1) in x and y at once (Rxy,
+// 16 x 8 values, two coarse x per thread); every second step one coarse plane
+// is the 4-tap z combination of four Rxy planes (each thread reads back only
+// its own Rxy entries).  x0 planes live in 4 slots, r planes in 2, Rxy in 4:
+// with tiles starting on multiples of 4 planes, the z-march unrolled by 4 has
+// every slot index fixed at compile time.
 // ---------------------------------------------------------------------------
 constexpr int kRestrictBase = kTileThreads - RXY / 2;  // the restriction threads: the last two warps
 
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
     k_mg_down(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
               int64_t bc_stride, const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_oi[8], s_rcD[8];
-    __shared__ uint64_t s_bar[kDownStages];
+    __shared__ uint64_t s_bar[kRing];
     __shared__ int s_abort;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
     if (*(volatile int*)&g_mg_fault) return;  // an earlier sweep gave up: the host reports it, skip the work
     const int tid = threadIdx.x + 32 * threadIdx.y;
-    const PlaneRing<T, kDownStages> ring = ring_setup<T, kDownStages>(smem_raw, XH, s_bar, &s_abort, tid);
-    T* const Xbase = ring.slots + kDownStages * ring.slot;  // 4 x0 plane slots, PW x XH
-    T* const Rbase = Xbase + 4 * PW * XH;                   // 2 residual plane slots, PW x RH
-    T* const Rxy = Rbase + 2 * PW * RH;                     // 4 ring planes of the x-y restricted residual
-    auto Xs = [&](int f) { return Xbase + ((f + 4) & 3) * (PW * XH); };  // f >= -4
-    auto Rs = [&](int f) { return Rbase + (f & 1) * (PW * RH); };
+    PlaneRing<T, kRing> ring = ring_setup<T, kRing>(smem_raw, XH, s_bar, &s_abort, tid);
+    T* const Xbase = ring.slots + kRing * ring.slot;  // 4 x0 plane slots, PW x XH
+    T* const Rbase = Xbase + 4 * PW * XH;             // 2 residual plane slots, PW x RH
+    T* const Rxy = Rbase + 2 * PW * RH;               // 4 ring planes of the x-y restricted residual
 #pragma unroll
     for (int k = 0; k < 7; ++k)  // constant indices: the parameter struct stays in the constant bank
         if (tid == k) {
@@ -285,7 +302,6 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
     T* bcs = bc + (int64_t)col * bc_stride;
     const T sc = q.s * q.c;
     const int nplanes = SZ + 4;  // fine planes fz0 - 2 .. fz0 + SZ + 1 per tile
-    uint32_t seq = 0;            // planes of earlier tiles
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
@@ -294,9 +310,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
         int issued = 0;  // producer: planes of this tile requested so far
         auto issue_upto = [&](int jmax) {
             for (; issued < nplanes && issued <= jmax; ++issued)
-                ring.issue(seq + issued, &bmap, fx0 - 4, fy0 - 2, fz0 - 2 + issued, col);
+                if (!ring.issue(issued & (kRing - 1), &bmap, fx0 - 4, fy0 - 2, fz0 - 2 + issued, col)) break;
         };
-        if (tid == kProducer) issue_upto(kDownStages - 1);
+        if (tid == kProducer) issue_upto(kRing - 1);
         // --- per-tile slot data
         // x0 commit: one segment of the x0 plane (tid < kQ * XH); interior-plane factors cached
         const bool has_c = tid < kQ * XH;
@@ -344,9 +360,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
         }
         const int q_off = 4 * qm + 3 + PW * (2 * qj);  // residual of fine (2I - 1, 2J - 1), I = cx0 + 2 qm
         T* const Rxq = Rxy + 2 * (qt & (RXY / 2 - 1));
-        // x0 plane f (tile plane j = f - fz0 + 2) from its b plane in the ring
-        auto commit = [&](int f) {
-            const T* raw = ring.take(seq + (f - fz0 + 2));
+        // x0 plane f = fz0 - 2 + j from tile plane j (ring slot JS = j mod 4; x0 slot (j + 2) mod 4)
+        auto commit = [&](auto js, int f) {
+            constexpr int JS = decltype(js)::value;
+            const T* raw = ring.take(JS);
             if (has_c) {
                 const bool wall = (f == 0 || f == nf - 1);  // b = 0 off the box, any factor will do
                 const V4<T> bv = ld4(raw + c_off);
@@ -358,24 +375,24 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * s_oi[kxy_of(c_k, e) + 1];
                 }
-                st4(Xs(f) + c_off, v);
+                st4(Xbase + ((JS + 2) & 3) * (PW * XH) + c_off, v);
             }
         };
-        commit(fz0 - 2);
-        commit(fz0 - 1);
-        commit(fz0);
-        __syncthreads();
-        if (tid == kProducer) issue_upto(2 + kDownStages);  // planes 0 .. 2 are consumed
-        for (int f = fz0 - 1; f <= fz0 + SZ + 1; ++f) {
-            if (f + 2 <= fz0 + SZ + 1) commit(f + 2);
-            if (has_r && f <= fz0 + SZ) {
+        // step t: commit plane f + 2 (tile plane t + 3), residual of f, restriction of f - 1
+        auto step = [&](auto kc, int t) {
+            constexpr int K = decltype(kc)::value;  // t mod 4
+            const int f = fz0 - 1 + t;
+            if (t <= SZ) commit(IC<(K + 3) & 3>{}, f + 2);
+            if (has_r && t <= SZ + 1) {
                 V4<T> r = zero4<T>();
                 if (r_in && in_range(f, nf)) {
                     const bool wall = (f == 0 || f == nf - 1);
                     const int xo = r_off + PW;  // x0 rows start one row above the residual rows
-                    const T* Xc = Xs(f);
+                    const T* Xc = Xbase + ((K + 3) & 3) * (PW * XH);
+                    const T* Xm = Xbase + ((K + 2) & 3) * (PW * XH);
+                    const T* Xp = Xbase + (K & 3) * (PW * XH);
                     const V4<T> c = ld4(Xc + xo), u = ld4(Xc + xo - PW), d = ld4(Xc + xo + PW);
-                    const V4<T> m = ld4(Xs(f - 1) + xo), p = ld4(Xs(f + 1) + xo);
+                    const V4<T> m = ld4(Xm + xo), p = ld4(Xp + xo);
                     const T xl = Xc[xo - 1], xr = Xc[xo + 4];
                     T nbs[4];
 #pragma unroll
@@ -392,12 +409,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
                         for (int e = 0; e < 4; ++e) r.v[e] = s_rcD[kxy_of(r_k, e) + 1] * c.v[e] + sc * nbs[e];
                     }
                 }
-                st4(Rs(f) + r_off, r);
+                st4(Rbase + ((K + 1) & 1) * (PW * RH) + r_off, r);
             }
-            const int fr = f - 1;  // plane restricted in this step
-            if (has_q && fr >= fz0 - 1) {
+            if (has_q && t >= 1) {
+                const int fr = f - 1;  // plane restricted in this step
                 T acc0 = T(0), acc1 = T(0);
-                const T* Rp = Rs(fr);
+                const T* Rp = Rbase + (K & 1) * (PW * RH);
 #pragma unroll
                 for (int b3 = 0; b3 < 4; ++b3) {
                     const T* row = Rp + q_off + PW * b3;
@@ -408,15 +425,15 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
                     acc0 += wy[b3] * p0;
                     acc1 += wy[b3] * p1;
                 }
-                st2(Rxq + ring4(fr) * RXY, acc0, acc1);
-                if (fr >= fz0 + 2 && ((fr - fz0) & 1) == 0) {
+                st2(Rxq + ((K + 2) & 3) * RXY, acc0, acc1);
+                if ((K & 1) == 0 && t >= 4) {
                     // coarse plane Z = fr/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = fr-3 .. fr
                     const int Z = (fr - 2) >> 1;
                     const T w3 = (T)restrict_w(3, Z, nc);
                     T z0 = w3 * acc0, z1 = w3 * acc1;
 #pragma unroll
                     for (int c3 = 0; c3 < 3; ++c3) {
-                        const V2<T> v = ld2(Rxq + ring4(fr - 3 + c3) * RXY);
+                        const V2<T> v = ld2(Rxq + ((K + 3 + c3) & 3) * RXY);
                         const T w = (T)restrict_w(c3, Z, nc);
                         z0 += w * v.v[0];
                         z1 += w * v.v[1];
@@ -425,24 +442,36 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 3)
                 }
             }
             __syncthreads();
-            // planes up to f + 2 (tile plane f - fz0 + 4) are consumed: their slots are free
-            if (tid == kProducer) issue_upto(f - fz0 + 4 + kDownStages);
+            // tile planes up to t + 3 are consumed: their slots are free
+            if (tid == kProducer) issue_upto(t + 3 + kRing);
+        };
+        commit(IC<0>{}, fz0 - 2);
+        commit(IC<1>{}, fz0 - 1);
+        commit(IC<2>{}, fz0);
+        __syncthreads();
+        if (tid == kProducer) issue_upto(2 + kRing);  // tile planes 0 .. 2 are consumed
+        const int nsteps = SZ + 3;  // f = fz0 - 1 .. fz0 + SZ + 1
+        for (int t0 = 0; t0 < nsteps; t0 += 4) {
+            step(IC<0>{}, t0);
+            if (t0 + 1 < nsteps) step(IC<1>{}, t0 + 1);
+            if (t0 + 2 < nsteps) step(IC<2>{}, t0 + 2);
+            if (t0 + 3 < nsteps) step(IC<3>{}, t0 + 3);
         }
-        if (tid == kProducer && s_abort) ring.drain(seq, seq + issued);
-        seq += nplanes;
+        if (tid == kProducer && s_abort) ring.drain();
     }
 }
 
 // ---------------------------------------------------------------------------
 // Up sweep at level l: x = omega D^{-1} b + P ec ; y = x + omega D^{-1} (b - A x)
 //     = (1 - omega) x + omega D^{-1} b + omega s c D^{-1} sum_{neighbours} x,
-// optional partial sums of b.y (the MINRES beta^2 contribution).  Step g:
-// warps 0-5 form x(g+1) on the tile + halo 1 from b(g+1) and two coarse planes,
-// warps 4-7 form y(g-1) from x planes g-2 .. g and b(g-1).  The prolongation of
-// a 4-cell segment blends two coarse planes (z), two coarse rows (y) and then
-// the four coarse x values the segment touches.  Coarse planes are stored
-// with clamped x and y indices, which is the wall reflection of P; coarse
-// plane Z lives in slot Z mod 3, x planes in 4 slots.
+// optional partial sums of b.y (the MINRES beta^2 contribution).  Step t
+// (g = fz0 + t): warps 0-5 form x(g+1) on the tile + halo 1 from b(g+1) and two
+// coarse planes, warps 4-7 form y(g-1) from x planes g-2 .. g and b(g-1).  The
+// prolongation of a 4-cell segment blends two coarse planes (z), two coarse
+// rows (y) and then the four coarse x values the segment touches.  Coarse
+// planes are stored with clamped x and y indices, which is the wall reflection
+// of P; coarse plane Z lives in slot Z mod 4, x planes in 4 slots (fixed at
+// compile time in the z-march unrolled by 4).
 // ---------------------------------------------------------------------------
 constexpr int kOutBase = kTileThreads - SX * SY / 4;  // the output threads: the last four warps
 
@@ -454,17 +483,16 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
     __shared__ T s_oi[8], s_ois[8];
-    __shared__ uint64_t s_bar[kUpStages];
+    __shared__ uint64_t s_bar[kRing];
     __shared__ int s_abort;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
     if (*(volatile int*)&g_mg_fault) return;
     const int tid = threadIdx.x + 32 * threadIdx.y;
-    const PlaneRing<T, kUpStages> ring = ring_setup<T, kUpStages>(smem_raw, BH, s_bar, &s_abort, tid);
-    T* const Xbase = ring.slots + kUpStages * ring.slot;  // 4 x plane slots, PW x BH
-    T* const Cbase = Xbase + 4 * PW * BH;                 // 3 coarse plane slots, CW x CH
-    auto Xs = [&](int g) { return Xbase + ((g + 4) & 3) * (PW * BH); };   // g >= -4
-    auto Cs = [&](int Z) { return Cbase + ((Z + 3) % 3) * (CW * CH); };  // Z >= -3
+    PlaneRing<T, kRing> ring = ring_setup<T, kRing>(smem_raw, BH, s_bar, &s_abort, tid);
+    T* const Xbase = ring.slots + kRing * ring.slot;  // 4 x plane slots, PW x BH
+    T* const Cbase = Xbase + 4 * PW * BH;             // 4 coarse plane slots, CW x CH
+    auto Cs = [&](int Z) { return Cbase + ((Z + 4) & 3) * (CW * CH); };  // Z >= -4
 #pragma unroll
     for (int k = 0; k < 7; ++k)
         if (tid == k) {
@@ -480,8 +508,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     const T om1 = T(1) - q.omega;
     const T w0 = T(0.75), w1 = T(0.25);
     const int nplanes = SZ + 2;  // b planes fz0 - 1 .. fz0 + SZ per tile
-    uint32_t seq = 0;
-    T dacc = T(0);  // per-thread partial of b.y in the element type; FP64 across threads
+    T dacc = T(0);  // per-thread partial of b.y in the element type; FP64 across warps
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tX = tile % ntx, tY = (tile / ntx) % nty, tZ = tile / (ntx * nty);
@@ -491,9 +518,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         int issued = 0;
         auto issue_upto = [&](int jmax) {
             for (; issued < nplanes && issued <= jmax; ++issued)
-                ring.issue(seq + issued, &bmap, fx0 - 4, fy0 - 1, fz0 - 1 + issued, col);
+                if (!ring.issue(issued & (kRing - 1), &bmap, fx0 - 4, fy0 - 1, fz0 - 1 + issued, col)) break;
         };
-        if (tid == kProducer) issue_upto(kUpStages - 1);
+        if (tid == kProducer) issue_upto(kRing - 1);
         // --- per-tile slot data
         int c_src = -1;  // coarse plane element of this thread (clamped x, y), or -1
         if (tid < CW * CH) {
@@ -540,10 +567,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         auto fetch_c = [&](int Z) -> T {
             return (c_src >= 0) ? es[c_src + cplane * min(max(Z, 0), nc - 1)] : T(0);
         };
-        // x(g) on the tile + halo 1 from b(g) (tile plane g - fz0 + 1) and the coarse planes Iz = g >> 1
-        // (weight 3/4) and its z neighbour (Iz - 1 for even g, Iz + 1 for odd g)
-        auto make_x = [&](int g) {
-            const T* Bg = ring.take(seq + (g - fz0 + 1));
+        // x(g) on the tile + halo 1 from b(g) = tile plane j = g - fz0 + 1 (ring slot JS = j mod 4,
+        // x slot (j + 3) mod 4) and the coarse planes Iz = g >> 1 (weight 3/4) and its z neighbour
+        // (Iz - 1 for even g, Iz + 1 for odd g)
+        auto make_x = [&](auto js, int g) {
+            constexpr int JS = decltype(js)::value;
+            const T* Bg = ring.take(JS);
             if (!has_x) return;
             V4<T> v = zero4<T>();
             if (x_in && in_range(g, nf)) {
@@ -574,37 +603,31 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                     for (int e = 0; e < 4; ++e) v.v[e] = s_oi[kxy_of(x_k, e) + 1] * bb.v[e] + pe[e];
                 }
             }
-            st4(Xs(g) + x_off, v);
+            st4(Xbase + ((JS + 3) & 3) * (PW * BH) + x_off, v);
         };
-        // prologue: coarse planes cz0-1 .. cz0+1, then x(fz0 - 1) and x(fz0)
-        if (c_src >= 0) {
-            Cs(cz0 - 1)[tid] = fetch_c(cz0 - 1);
-            Cs(cz0)[tid] = fetch_c(cz0);
-            Cs(cz0 + 1)[tid] = fetch_c(cz0 + 1);
-        }
-        T pc = fetch_c(cz0 + 2);  // stored while x(fz0 + 2) is formed, first used by x(fz0 + 3)
-        __syncthreads();
-        make_x(fz0 - 1);
-        make_x(fz0);
-        __syncthreads();
-        if (tid == kProducer) issue_upto(kUpStages);  // plane 0 (b(fz0 - 1)) is consumed
-        for (int g = fz0; g <= fz0 + SZ; ++g) {
+        T pc = T(0);
+        // step t (g = fz0 + t): x(g + 1) from tile plane t + 2, y(g - 1) from tile plane t
+        auto step = [&](auto kc, int t) {
+            constexpr int K = decltype(kc)::value;  // t mod 4
+            const int g = fz0 + t;
             const int gn = g + 1;  // x plane formed in this step
             if (gn <= fz0 + SZ) {
-                if ((gn & 1) == 0) {
-                    // coarse plane gn/2 + 1 (slot of gn/2 - 2, no longer read) for x(gn + 1) onwards
+                if ((K & 1) == 1) {  // gn even
+                    // coarse plane gn/2 + 1 (slot of gn/2 - 3, no longer read) for x(gn + 1) onwards
                     if (c_src >= 0) Cs((gn >> 1) + 1)[tid] = pc;
                     if (gn + 2 <= fz0 + SZ) pc = fetch_c((gn >> 1) + 2);
                 }
-                make_x(gn);
+                make_x(IC<(K + 2) & 3>{}, gn);
             }
-            const int f = g - 1;  // output plane: x planes f-1, f, f+1 and b(f)
-            if (f >= fz0 && has_out) {
+            const int f = g - 1;  // output plane: x planes f-1, f, f+1 and b(f) (tile plane t)
+            if (t >= 1 && has_out) {
                 const bool wall = (f == 0 || f == nf - 1);
-                const T* Xc = Xs(f);
-                const T* Bf = ring.at(seq + (f - fz0 + 1));
+                const T* Xc = Xbase + ((K + 3) & 3) * (PW * BH);
+                const T* Xm = Xbase + ((K + 2) & 3) * (PW * BH);
+                const T* Xp = Xbase + (K & 3) * (PW * BH);
+                const T* Bf = ring.at(K & 3);
                 const V4<T> c = ld4(Xc + o_xi), u = ld4(Xc + o_xi - PW), d = ld4(Xc + o_xi + PW);
-                const V4<T> m = ld4(Xs(f - 1) + o_xi), p = ld4(Xs(f + 1) + o_xi), bb = ld4(Bf + o_xi);
+                const V4<T> m = ld4(Xm + o_xi), p = ld4(Xp + o_xi), bb = ld4(Bf + o_xi);
                 const T xl = Xc[o_xi - 1], xr = Xc[o_xi + 4];
                 T nbs[4];
 #pragma unroll
@@ -629,11 +652,29 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 st4(ys + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f, out);
             }
             __syncthreads();
-            // b planes up to f (tile plane g - fz0) are consumed: their slots are free
-            if (tid == kProducer) issue_upto(g - fz0 + kUpStages);
+            // tile planes up to t are consumed: their slots are free
+            if (tid == kProducer) issue_upto(t + kRing);
+        };
+        // prologue: coarse planes cz0-1 .. cz0+1, then x(fz0 - 1) and x(fz0)
+        if (c_src >= 0) {
+            Cs(cz0 - 1)[tid] = fetch_c(cz0 - 1);
+            Cs(cz0)[tid] = fetch_c(cz0);
+            Cs(cz0 + 1)[tid] = fetch_c(cz0 + 1);
         }
-        if (tid == kProducer && s_abort) ring.drain(seq, seq + issued);
-        seq += nplanes;
+        pc = fetch_c(cz0 + 2);  // stored while x(fz0 + 2) is formed, first used by x(fz0 + 3)
+        __syncthreads();
+        make_x(IC<0>{}, fz0 - 1);
+        make_x(IC<1>{}, fz0);
+        __syncthreads();
+        if (tid == kProducer) issue_upto(kRing);  // tile plane 0 (b(fz0 - 1)) is consumed
+        const int nsteps = SZ + 1;  // g = fz0 .. fz0 + SZ
+        for (int t0 = 0; t0 < nsteps; t0 += 4) {
+            step(IC<0>{}, t0);
+            if (t0 + 1 < nsteps) step(IC<1>{}, t0 + 1);
+            if (t0 + 2 < nsteps) step(IC<2>{}, t0 + 2);
+            if (t0 + 3 < nsteps) step(IC<3>{}, t0 + 3);
+        }
+        if (tid == kProducer && s_abort) ring.drain();
     }
     if (dot_part) {
         const double tsum = block_sum_t<kTileThreads, T>(dacc, red);
