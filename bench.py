@@ -338,6 +338,31 @@ def dct_field(xi, n, h, kappa, sigma):
     return (g * f).reshape(xi.shape)
 
 
+def fp64_peak_tflops():
+    """FP64 roof of this GPU (the peaks file has none): a float64 4096^3 matmul, best of 5."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2.0 * 4096 ** 3 / (best / 1000.0) / 1e12
+
+
+# FP64 arithmetic per cell of the FP64 kernels (own count of the operations each performs)
+FP64_FLOPS_PER_CELL = {
+    "residual64": 10.0,       # cell row: 3 differences, 2 sums, kappa term (fma), F - Au, square-accumulate (fma)
+    "flux_from_theta": 18.0,  # per axis: difference, fma, scale (forward), fma (back substitution)
+}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -527,6 +552,41 @@ def run_ours(args):
         fields_rate = S / (a.elapsed_time(b) / 1000.0)
         fst = smp.stats()
         smp.set_fields(0, None, None)
+        # the crooked-pipe stand-in: quarter cylinder (radius 2, height 7, elements graded toward the
+        # r = 1 layer) in a cubic box of side 8 whose (0,3)^2 x (0,8) corner is the paper's embedding box
+        log("quarter-cylinder workload")
+        from synth import quarter_cylinder_mesh
+        cxyz, ctets = quarter_cylinder_mesh(32, 48, 112)
+        cyl = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local)
+        cyl.add_level(0, n, (0.0, 0.0, 0.0), (8.0, 8.0, 8.0))
+        cyl.attach_mesh(0, cxyz, ctets)
+        cset = cyl.stats()
+        cout = torch.empty((S, len(ctets)), dtype=torch.float32, device="cuda")
+        cyl.sample(0, S, 2.0, 1.0, W["seed"], first_sample(1000, rank, world, S), pkg.SPDE_OUT_LOGNORMAL, cout, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        cyl.sample(0, S, 2.0, 1.0, W["seed"], first_sample(0, rank, world, S), pkg.SPDE_OUT_LOGNORMAL, cout, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cyl_rate = S / (a.elapsed_time(b) / 1000.0)
+        cst = cyl.stats()
+        cyl.close()
+        del cout
+        cylinder = {"value": cyl_rate, "unit": "samples/s", "samples": S, "ntets": int(len(ctets)),
+                    "mesh": "quarter cylinder r = 2, height 7, 32 radial (graded to r = 1) x 48 x 112 cells",
+                    "box": "[0,8]^3, n = %d" % n, "kappa": 2.0, "sigma": 1.0, "clip_ms": cset["setup_ms"],
+                    "nnz": cset["nnz"], "outer_iters": cst["outer_iters"], "inner_iters": cst["inner_iters"],
+                    "paper_box_fraction_of_grid": 3.0 * 3.0 * 8.0 / 8.0 ** 3}
+        # FP64 roof and the FP64 kernels against it
+        log("fp64 roof")
+        fp64_peak = fp64_peak_tflops()
+        fp64 = {"peak_tflops": fp64_peak, "peak_source": "torch float64 matmul 4096^3, best of 5", "kernels": {}}
+        for name, fl in FP64_FLOPS_PER_CELL.items():
+            kk = kernels.get(name)
+            if kk and kk["ms"] > 0:
+                tf = fl * float(n) ** 3 * S * kk["launches"] / (kk["ms"] / 1000.0) / 1e12
+                fp64["kernels"][name] = {"tflops": tf, "frac": tf / fp64_peak, "flops_per_cell": fl,
+                                         "hbm_frac": kk["GBps"] / peak if kk["GBps"] else None}
         # the oracle on the host cores, bounded sample
         log("cpu baseline")
         oc = OracleCost(1000)
@@ -551,6 +611,8 @@ def run_ours(args):
                            "kappa": "20 (1 + 0.5 sin(2 pi x) cos(2 pi z)) per cell", "sigma": "0.75 + 0.5 y per cell",
                            "outer_iters": fst["outer_iters"], "inner_iters": fst["inner_iters"],
                            "max_rel_residual": fst["max_rel_residual"]},
+                "fp64": fp64,
+                "quarter_cylinder": cylinder,
                 "solver": {"outer_iters": iters["outer_iters"], "inner_iters": iters["inner_iters"],
                            "max_rel_residual": iters["max_rel_residual"]},
                 "setup": {"clip_ms": setup["setup_ms"], "nnz": setup["nnz"]},

@@ -6,3 +6,4 @@ numbers it draws (vertex jitter, request parameters) come from NumPy's PCG64,
 not from the Philox generator the method uses for white noise.
 """
 from .mesh import kuhn_mesh, box_mesh, lprism_mesh, MeshSpec  # noqa: F401
+from .cylinder import quarter_cylinder_mesh, polygon_prism_volume, radial_nodes  # noqa: F401
