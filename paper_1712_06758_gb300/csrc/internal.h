@@ -64,6 +64,9 @@ struct MGPlan {
     // each [S][n_l^3]
     void* b[16] = {};
     void* e[16] = {};
+    // per-cell diagonal s (a_c + c k_c) of every level (element type of the plan), for
+    // cell-wise kappa; null: one coefficient for the whole level
+    const void* D[16] = {};
 };
 
 // ---- noise.cu
@@ -83,6 +86,10 @@ cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_
 int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x,
                       float* r32, double* r64, double* part, const int* active, cudaStream_t st,
                       const double* kh2c = nullptr);
+// the multigrid diagonal of a level with cell-wise (kappa h)^2: a_c = mean of the children's a
+// (a_0 = (kappa_c h)^2), D = 2^l (a_c 4^l + c k_c) with k_c the cell's existing neighbours
+cudaError_t launch_restrict_mean(int nf, const double* af, double* ac, cudaStream_t st);
+cudaError_t launch_level_diag(int n, int l, double c, const double* a, double* D64, float* D32, cudaStream_t st);
 // F[s][e] *= c[e] (per-cell noise factor of a level with fields)
 cudaError_t launch_scale_cells(int64_t n3, int S, double* F, int64_t stride, const double* c, cudaStream_t st);
 // (kappa h)^2 (FP64, FP32) and -g h per cell from cell-wise kappa, sigma (device arrays)

@@ -274,10 +274,10 @@ __device__ __forceinline__ PlaneRing<T, NS> ring_setup(unsigned char* raw, int r
 // ---------------------------------------------------------------------------
 constexpr int kRestrictBase = kTileThreads - RXY / 2;  // the restriction threads: the last two warps
 
-template <typename T>
+template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
     k_mg_down(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
-              int64_t bc_stride, const int* __restrict__ active, int act_stride) {
+              int64_t bc_stride, const int* __restrict__ active, int act_stride, const T* __restrict__ Dg) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_oi[8], s_rcD[8];
     __shared__ uint64_t s_bar[kRing];
@@ -316,13 +316,14 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
         // --- per-tile slot data
         // x0 commit: one segment of the x0 plane (tid < kQ * XH); interior-plane factors cached
         const bool has_c = tid < kQ * XH;
-        int c_off = 0, c_k = 0;
+        int c_off = 0, c_k = 0, c_g = -1;  // c_g: plane offset of the segment in the grid, -1 off the box
         T cI[4];
         {
             const int ly = tid / kQ, q4 = tid - ly * kQ;
             const int gy = fy0 - 2 + ly, gx0 = fx0 - 4 + 4 * q4;
             const bool in = has_c && in_range(gy, nf) && in_range(gx0, nf);
             c_off = 4 * q4 + PW * ly;
+            if (in) c_g = gx0 + nf * gy;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
         }
         // residual: one segment of the residual plane (tid < kQ * RH)
         const bool has_r = tid < kQ * RH;
-        int r_off = 0, r_k = 0;
+        int r_off = 0, r_k = 0, r_g = 0;
         bool r_in = false;
         T rI[4];
         {
@@ -340,6 +341,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
             const int gy = fy0 - 1 + ly, gx0 = fx0 - 4 + 4 * q4;
             r_in = has_r && in_range(gy, nf) && in_range(gx0, nf);
             r_off = 4 * q4 + PW * ly;
+            r_g = r_in ? gx0 + nf * gy : 0;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = r_in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
@@ -368,7 +370,14 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
                 const bool wall = (f == 0 || f == nf - 1);  // b = 0 off the box, any factor will do
                 const V4<T> bv = ld4(raw + c_off);
                 V4<T> v;
-                if (!wall) {
+                if constexpr (PC) {  // per-cell diagonal (cell-wise kappa); b = 0 off the box
+                    V4<T> dd;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dd.v[e] = T(1);
+                    if (c_g >= 0 && in_range(f, nf)) dd = ld4(Dg + c_g + (int64_t)nf * nf * f);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v.v[e] = q.omega * bv.v[e] / dd.v[e];
+                } else if (!wall) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * cI[e];
                 } else {
@@ -401,7 +410,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
                         const T right = (e == 3) ? xr : c.v[e + 1];
                         nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
                     }
-                    if (!wall) {
+                    if constexpr (PC) {
+                        const V4<T> dd = ld4(Dg + r_g + (int64_t)nf * nf * f);
+                        const T rc = T(1) / q.omega - T(1);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) r.v[e] = rc * dd.v[e] * c.v[e] + sc * nbs[e];
+                    } else if (!wall) {
 #pragma unroll
                         for (int e = 0; e < 4; ++e) r.v[e] = rI[e] * c.v[e] + sc * nbs[e];
                     } else {
@@ -475,11 +489,11 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
 // ---------------------------------------------------------------------------
 constexpr int kOutBase = kTileThreads - SX * SY / 4;  // the output threads: the last four warps
 
-template <typename T>
+template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     k_mg_up(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
             int64_t ec_stride, T* __restrict__ y, int64_t y_stride, double* __restrict__ dot_part,
-            const int* __restrict__ active, int act_stride) {
+            const int* __restrict__ active, int act_stride, const T* __restrict__ Dg) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
     __shared__ T s_oi[8], s_ois[8];
@@ -530,7 +544,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         }
         // prolongation: one segment of the x plane (tid < kQ * BH)
         const bool has_x = tid < kQ * BH;
-        int x_off = 0, x_k = 0, p_r0 = 0, p_r1 = 0;
+        int x_off = 0, x_k = 0, p_r0 = 0, p_r1 = 0, x_g = 0;
         bool x_in = false;
         T xI[4];
         {
@@ -538,6 +552,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
             const int gy = fy0 - 1 + ly, gx0 = fx0 - 4 + 4 * q4;
             x_in = has_x && in_range(gy, nf) && in_range(gx0, nf);
             x_off = 4 * q4 + PW * ly;
+            x_g = x_in ? gx0 + nf * gy : 0;
             if (x_in) {
                 // coarse rows (gy >> 1) and its other neighbour; coarse x gx0/2 - 1 .. gx0/2 + 2
                 p_r0 = ((gy >> 1) - (cy0 - 1)) * CW + 2 * q4;
@@ -595,7 +610,11 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 const T pe[4] = {w0 * cy[1] + w1 * cy[0], w0 * cy[1] + w1 * cy[2], w0 * cy[2] + w1 * cy[1],
                                  w0 * cy[2] + w1 * cy[3]};
                 const V4<T> bb = ld4(Bg + x_off);
-                if (!wall) {
+                if constexpr (PC) {  // per-cell diagonal (cell-wise kappa)
+                    const V4<T> dd = ld4(Dg + x_g + plane * g);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v.v[e] = q.omega * bb.v[e] / dd.v[e] + pe[e];
+                } else if (!wall) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v.v[e] = xI[e] * bb.v[e] + pe[e];
                 } else {
@@ -637,7 +656,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                     nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
                 }
                 V4<T> out;
-                if (!wall) {
+                if constexpr (PC) {  // y = (1 - omega) x + omega D^{-1} (b + s c sum x)
+                    const V4<T> dd = ld4(Dg + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f);
+                    const T sc = q.s * q.c;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) out.v[e] = om1 * c.v[e] + q.omega * (bb.v[e] + sc * nbs[e]) / dd.v[e];
+                } else if (!wall) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) out.v[e] = om1 * c.v[e] + oI[e] * bb.v[e] + sI[e] * nbs[e];
                 } else {
@@ -690,6 +714,7 @@ struct CoarseDesc {
     int nlev;      // total number of levels (n_{nlev-1} = 1)
     int n0;        // n_lc
     double kh2, c, omega;
+    const void* D[16];  // per-cell diagonals of the levels (cell-wise kappa), or null
 };
 
 template <typename T>
@@ -699,10 +724,27 @@ __device__ __forceinline__ T cz_invD(const CoarseDesc& d, int l, int k) {
     return T(1) / (s * (a + (T)d.c * (T)k));
 }
 
+// 1 / diagonal of cell f (neighbour count kc) on level l
+template <typename T>
+__device__ __forceinline__ T cz_invDf(const CoarseDesc& d, int l, int kc, int f) {
+    if (d.D[l]) return T(1) / static_cast<const T*>(d.D[l])[f];
+    return cz_invD<T>(d, l, kc);
+}
+
 template <typename T>
 __device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, int n, int i, int j, int k) {
     const int f = i + n * (j + n * k);
     const T x0 = x[f];
+    if (d.D[l]) {  // per-cell diagonal: D x0 - s c (sum of existing neighbours)
+        T nb = T(0);
+        if (i > 0) nb += x[f - 1];
+        if (i < n - 1) nb += x[f + 1];
+        if (j > 0) nb += x[f - n];
+        if (j < n - 1) nb += x[f + n];
+        if (k > 0) nb += x[f - n * n];
+        if (k < n - 1) nb += x[f + n * n];
+        return static_cast<const T*>(d.D[l])[f] * x0 - (T)(1 << l) * (T)d.c * nb;
+    }
     T lap = T(0);
     if (i > 0) lap += x0 - x[f - 1];
     if (i < n - 1) lap += x0 - x[f + 1];
@@ -752,7 +794,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
         T* x = sm + offx[l];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % n, j = (f / n) % n, k = f / (n * n);
-            x[f] = om * b[f] * cz_invD<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n));
+            x[f] = om * b[f] * cz_invDf<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n), f);
         }
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
@@ -787,7 +829,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     // bottom: one cell, exact
     {
         const int l = d.nlev - 1;
-        if (threadIdx.x == 0) sm[offx[l]] = sm[offb[l]] * cz_invD<T>(d, l, 0);
+        if (threadIdx.x == 0) sm[offx[l]] = sm[offb[l]] * cz_invDf<T>(d, l, 0, 0);
         __syncthreads();
     }
     // up
@@ -813,7 +855,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % n, j = (f / n) % n, k = f / (n * n);
-            const T iD = cz_invD<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n));
+            const T iD = cz_invDf<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n), f);
             x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, n, i, j, k));
         }
         __syncthreads();
@@ -895,9 +937,13 @@ static cudaError_t mg_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mg_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
+        e = cudaFuncSetAttribute(k_mg_down<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mg_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_smem_bytes<T>());
+        e = cudaFuncSetAttribute(k_mg_down<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mg_up<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_smem_bytes<T>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mg_up<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_smem_bytes<T>());
     return e;
 }
 
@@ -988,6 +1034,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     d.kh2 = plan.kh2;
     d.c = plan.c;
     d.omega = plan.omega;
+    for (int l = 0; l < 16; ++l) d.D[l] = plan.D[l];
     const size_t csm = (size_t)coarse_smem_elems(d.n0, d.lc, d.nlev) * sizeof(T);
     const double w = (double)sizeof(T);
     const double n0c = (double)d.n0 * d.n0 * d.n0;
@@ -1009,8 +1056,13 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         CUtensorMap map;
         if (!plane_map<T>(&map, in, nf, S, in_stride, XH)) return -1;
         prof_begin(PK_MG_DOWN, st);
-        k_mg_down<T><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(map, nf, sz, level_coef<T>(plan, l), out,
-                                                                      (int64_t)nc * nc * nc, active, act_stride);
+        const T* Dl = static_cast<const T*>(plan.D[l]);
+        if (Dl)
+            k_mg_down<T, true><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
+                map, nf, sz, level_coef<T>(plan, l), out, (int64_t)nc * nc * nc, active, act_stride, Dl);
+        else
+            k_mg_down<T, false><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
+                map, nf, sz, level_coef<T>(plan, l), out, (int64_t)nc * nc * nc, active, act_stride, nullptr);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
         in = out;
         in_stride = (int64_t)nc * nc * nc;
@@ -1037,10 +1089,15 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         CUtensorMap map;
         if (!plane_map<T>(&map, bl, nf, S, bls, BH)) return -1;
         prof_begin(PK_MG_UP, st);
-        k_mg_up<T><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(map, nf, sz, level_coef<T>(plan, l),
-                                                                  static_cast<const T*>(plan.e[l + 1]),
-                                                                  (int64_t)nc * nc * nc, yl, yls,
-                                                                  (l == 0) ? dot_part : nullptr, active, act_stride);
+        const T* Dl = static_cast<const T*>(plan.D[l]);
+        if (Dl)
+            k_mg_up<T, true><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
+                map, nf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
+                yls, (l == 0) ? dot_part : nullptr, active, act_stride, Dl);
+        else
+            k_mg_up<T, false><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
+                map, nf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
+                yls, (l == 0) ? dot_part : nullptr, active, act_stride, nullptr);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);
         if (l == 0) nblk0 = nb;
     }

