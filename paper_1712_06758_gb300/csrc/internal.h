@@ -165,8 +165,8 @@ void mg_plan_bind(MGPlan& plan, int S, T* scratch);
 
 // ---- schur.cu (Schur-complement CG on the cell unknowns)
 template <typename T>
-int launch_schur_apply(int n, double kh2, int S, const T* x, T* y, const T* tri, double* dot_part, const CgCol* st,
-                       cudaStream_t stream);
+int launch_schur_apply(int n, double kh2, int S, const T* x, T* y, const T* tri, T* scratch, double* dot_part,
+                       const CgCol* st, cudaStream_t stream);
 template <typename T>
 int launch_cg_xr(int64_t n3, int S, T* x, T* r, const T* p, const T* q, double* part, const CgCol* st, cudaStream_t s);
 template <typename T>

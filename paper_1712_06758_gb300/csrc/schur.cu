@@ -8,57 +8,51 @@
 // matrix-free, one axis at a time: along every grid line the face values
 // g = D1^T x are formed, T u = g is solved exactly by Thomas elimination
 // (T = tridiag(1/6, 2/3, 1/6) on the n-1 interior faces), and the line's
-// divergence D1 u is accumulated into the output.  A CTA takes 32 lines into
-// shared memory (coalesced loads; rows padded against bank conflicts), one
-// thread per line walks it.  The preconditioner is the same V-cycle as the
-// MINRES field block.
+// divergence D1 u is accumulated into the output.  Lines along x are
+// contiguous rows: a CTA stages a tile of rows in shared memory (coalesced)
+// and one warp walks them.  Lines along y and z are walked by one thread each,
+// consecutive threads on consecutive x, so every step is one coalesced row of
+// the grid; the forward elimination keeps its values in a scratch array that
+// the backward substitution reads back (it stays in L2 while the lines are in
+// flight), and the unrolled walks keep several independent loads in flight.
+// The preconditioner is the same V-cycle as the MINRES field block.
 #include "device.cuh"
 #include "internal.h"
 
 namespace spde {
 
-constexpr int kLines = 32;  // lines per CTA, one thread each
+constexpr int kRowThreads = 128;  // x-axis CTA
+constexpr int kRowTileMax = 32;   // rows per x-axis CTA (one warp solves them)
+constexpr int kLineThreads = 256; // y/z-axis CTA: one line per thread
+constexpr size_t kSchurSmemMax = 200 * 1024;
 
-// One axis of y = S x on the cell arrays x, y ([S][n^3]); mode 0: y = (kappa h)^2 x
-// + this axis' term; mode 1: y += term; mode 2: y += term and partial sums of x.y.
-// A CTA (32 threads) takes L lines (L <= 32, a power of two dividing n): for
-// axis 0 the rows (j, k) g L .. g L + L - 1; for axes 1 and 2 the lines at
-// i = i0 .. i0 + L - 1 for one value of the remaining index.  Threads t >= L idle.
 template <typename T>
-__global__ void __launch_bounds__(kLines) k_schur_axis(int n, int L, int axis, int mode, T kh2, const T* __restrict__ x,
-                                                       T* __restrict__ y, const T* __restrict__ tri,
-                                                       double* __restrict__ dot_part,
-                                                       const CgCol* __restrict__ st) {
+static int row_tile(int n) {
+    int R = kRowTileMax;
+    while (R > 1 && ((int64_t)R > (int64_t)n * n || 2 * (size_t)R * (n + 1) * sizeof(T) > kSchurSmemMax)) R >>= 1;
+    return R;
+}
+
+// y = (kappa h)^2 x + the x-axis term, for the R rows (j, k) of one tile
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads) k_schur_x(int n, int R, T kh2, const T* __restrict__ x, T* __restrict__ y,
+                                                         const T* __restrict__ tri, const CgCol* __restrict__ st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[kLines / 32];
-    const int P = n + 1;                     // padded row: no bank conflicts along the line walk
-    T* sx = reinterpret_cast<T*>(smem_raw);  // [L][n + 1]: line values
-    T* su = sx + L * P;                      // [L][n + 1]: face values
     const int s = blockIdx.y;
     if (st && !st[s].active) return;
+    const int P = n + 1;                     // padded row: no bank conflicts along the walk
+    T* sx = reinterpret_cast<T*>(smem_raw);  // [R][n + 1]: x
+    T* su = sx + R * P;                      // [R][n + 1]: face values
     const int64_t n3 = (int64_t)n * n * n;
-    const T* xs = x + (int64_t)s * n3;
-    T* ys = y + (int64_t)s * n3;
+    const int64_t start = (int64_t)s * n3 + (int64_t)blockIdx.x * R * n;  // R contiguous rows
     const int t = threadIdx.x;
-    const int ngi = n / L;
-    const int groups = (n / L) * n;  // n^2 lines per axis, L per group
-    const int64_t sa = (axis == 1) ? n : (int64_t)n * n;           // step along a y / z line
-    const int64_t so = (axis == 1) ? (int64_t)n * n : (int64_t)n;  // step of the remaining index
-    T acc = T(0);
-    for (int g = blockIdx.x; g < groups; g += gridDim.x) {
-    const int i0 = (g % ngi) * L, o = g / ngi;
-    if (axis == 0) {
-        const int64_t start = (int64_t)g * L * n;  // L contiguous rows
-        for (int idx = t; idx < L * n; idx += kLines) {
-            const int l = idx / n, e = idx - l * n;
-            sx[l * P + e] = xs[start + idx];
-        }
-    } else if (t < L) {
-        for (int e = 0; e < n; ++e) sx[t * P + e] = xs[i0 + t + so * o + sa * e];
+    for (int idx = t; idx < R * n; idx += kRowThreads) {
+        const int l = idx / n, e = idx - l * n;
+        sx[l * P + e] = x[start + idx];
     }
     __syncthreads();
-    if (t < L) {
-        // T u = D1^T x along the line, (D1^T x)_f = x_f - x_{f+1}; Thomas elimination
+    if (t < R) {
+        // T u = D1^T x along the row, (D1^T x)_f = x_f - x_{f+1}; Thomas elimination
         const T* xl = sx + t * P;
         T* ul = su + t * P;
         const T* cp = tri;
@@ -70,75 +64,107 @@ __global__ void __launch_bounds__(kLines) k_schur_axis(int n, int L, int axis, i
             ul[f] = dp;
             prev = dp;
         }
-        T xn = prev;  // u_{n-2}
+        T un = prev;  // u_{n-2}
         for (int f = n - 3; f >= 0; --f) {
-            const T xf = ul[f] - cp[f] * xn;
-            ul[f] = xf;
-            xn = xf;
+            const T uf = ul[f] - cp[f] * un;
+            ul[f] = uf;
+            un = uf;
         }
         ul[n - 1] = T(0);  // wall face
     }
     __syncthreads();
-    // divergence: cell f gains u_f - u_{f-1}
-    if (axis == 0) {
-        const int64_t start = (int64_t)g * L * n;
-        for (int idx = t; idx < L * n; idx += kLines) {
-            const int l = idx / n, e = idx - l * n;
-            const T* ul = su + l * P;
-            const T term = ul[e] - (e > 0 ? ul[e - 1] : T(0));
-            const T xv = sx[l * P + e];
-            const T v = (mode == 0) ? kh2 * xv + term : ys[start + idx] + term;
-            ys[start + idx] = v;
-            if (mode == 2) acc += xv * v;
-        }
-    } else if (t < L) {
-        const T* ul = su + t * P;
-        for (int e = 0; e < n; ++e) {
-            const int64_t gi = i0 + t + so * o + sa * e;
-            const T term = ul[e] - (e > 0 ? ul[e - 1] : T(0));
-            const T xv = sx[t * P + e];
-            const T v = (mode == 0) ? kh2 * xv + term : ys[gi] + term;
-            ys[gi] = v;
-            if (mode == 2) acc += xv * v;
-        }
-    }
-    __syncthreads();  // the next group reuses the shared rows
-    }
-    if (mode == 2 && dot_part) {
-        const double tsum = block_sum<kLines>((double)acc, red);
-        if (t == 0) dot_part[(int64_t)s * kMaxPartials + blockIdx.x] = tsum;
+    for (int idx = t; idx < R * n; idx += kRowThreads) {  // cell e gains u_e - u_{e-1}
+        const int l = idx / n, e = idx - l * n;
+        const T* ul = su + l * P;
+        y[start + idx] = kh2 * sx[l * P + e] + (ul[e] - (e > 0 ? ul[e - 1] : T(0)));
     }
 }
 
-constexpr size_t kSchurSmemMax = 200 * 1024;
-
-template <typename T>
-static int schur_lines(int n) {
-    int L = kLines;
-    while (L > 1 && (L > n || 2 * (size_t)L * (n + 1) * sizeof(T) > kSchurSmemMax)) L >>= 1;
-    return L;
+// y += the term of axis AXIS (1: y, 2: z); with DOT, partial sums of x.y (y final)
+template <typename T, int AXIS, bool DOT>
+__global__ void __launch_bounds__(kLineThreads) k_schur_line(int n, int logn, const T* __restrict__ x, T* __restrict__ y,
+                                                             T* __restrict__ scratch, const T* __restrict__ tri,
+                                                             double* __restrict__ dot_part,
+                                                             const CgCol* __restrict__ st) {
+    __shared__ double red[kLineThreads / 32];
+    const int s = blockIdx.y;
+    if (st && !st[s].active) return;
+    const int L = blockIdx.x * kLineThreads + threadIdx.x;  // line: x index i fastest
+    const int nlines = 1 << (2 * logn);
+    T acc = T(0);
+    if (L < nlines) {
+        const int i = L & (n - 1), o = L >> logn;
+        const int64_t base = (AXIS == 1) ? i + ((int64_t)o << (2 * logn)) : i + ((int64_t)o << logn);
+        const int64_t stride = (AXIS == 1) ? n : (int64_t)n * n;
+        const int64_t off = (int64_t)s * ((int64_t)n * n * n) + base;
+        const T* xs = x + off;
+        T* ys = y + off;
+        T* gs = scratch + off;
+        const T* cp = tri;
+        const T* inv = tri + (n - 1);
+        const T a = T(1) / T(6);
+        T prev = T(0), xc = xs[0];
+#pragma unroll 8
+        for (int f = 0; f < n - 1; ++f) {
+            const T xn = xs[(int64_t)(f + 1) * stride];
+            const T dp = ((xc - xn) - a * prev) * inv[f];
+            gs[(int64_t)f * stride] = dp;
+            prev = dp;
+            xc = xn;
+        }
+        // backward substitution; cell c gains u_c - u_{c-1} (u_{-1} = u_{n-1} = 0)
+        T un = prev;  // u_{n-2}
+        {
+            const int64_t gc = (int64_t)(n - 1) * stride;
+            const T v = ys[gc] - un;
+            ys[gc] = v;
+            if (DOT) acc += xs[gc] * v;
+        }
+#pragma unroll 8
+        for (int f = n - 3; f >= 0; --f) {
+            const T uf = gs[(int64_t)f * stride] - cp[f] * un;
+            const int64_t gc = (int64_t)(f + 1) * stride;
+            const T v = ys[gc] + (un - uf);
+            ys[gc] = v;
+            if (DOT) acc += xs[gc] * v;
+            un = uf;
+        }
+        {
+            const T v = ys[0] + un;  // cell 0: u_0
+            ys[0] = v;
+            if (DOT) acc += xs[0] * v;
+        }
+    }
+    if (DOT) {
+        const double tsum = block_sum_t<kLineThreads, T>(acc, red);
+        if (threadIdx.x == 0) dot_part[(int64_t)s * kMaxPartials + blockIdx.x] = tsum;
+    }
 }
 
 template <typename T>
 static cudaError_t schur_attrs() {
     static const cudaError_t e =
-        cudaFuncSetAttribute(k_schur_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSchurSmemMax);
+        cudaFuncSetAttribute(k_schur_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSchurSmemMax);
     return e;
 }
 
-// y = S x for S columns; partial sums of x.y per column into dot_part (nblk returned, or -1)
+// y = S x for S columns (scratch: [S][n^3] of the element type); partial sums of x.y per column
+// into dot_part (blocks per column returned, or -1)
 template <typename T>
-int launch_schur_apply(int n, double kh2, int S, const T* x, T* y, const T* tri, double* dot_part, const CgCol* st,
-                       cudaStream_t stream) {
+int launch_schur_apply(int n, double kh2, int S, const T* x, T* y, const T* tri, T* scratch, double* dot_part,
+                       const CgCol* st, cudaStream_t stream) {
     if (schur_attrs<T>() != cudaSuccess) return -1;
-    const int L = schur_lines<T>(n);
-    const size_t smem = 2 * (size_t)L * (n + 1) * sizeof(T);
-    const int groups = n * n / L;  // n^2 lines per axis
-    const int nb = groups < kMaxPartials ? groups : kMaxPartials;
+    const int logn = 31 - __builtin_clz(n);
+    const int R = row_tile<T>(n);
+    const size_t smem = 2 * (size_t)R * (n + 1) * sizeof(T);
+    k_schur_x<T><<<dim3(n * n / R, S), kRowThreads, smem, stream>>>(n, R, (T)kh2, x, y, tri, st);
+    const int nb = (n * n + kLineThreads - 1) / kLineThreads;
     dim3 grid(nb, S);
-    for (int axis = 0; axis < 3; ++axis)
-        k_schur_axis<T><<<grid, kLines, smem, stream>>>(n, L, axis, axis == 0 ? 0 : (axis == 2 ? 2 : 1), (T)kh2, x,
-                                                         y, tri, dot_part, st);
+    k_schur_line<T, 1, false><<<grid, kLineThreads, 0, stream>>>(n, logn, x, y, scratch, tri, nullptr, st);
+    if (dot_part)
+        k_schur_line<T, 2, true><<<grid, kLineThreads, 0, stream>>>(n, logn, x, y, scratch, tri, dot_part, st);
+    else
+        k_schur_line<T, 2, false><<<grid, kLineThreads, 0, stream>>>(n, logn, x, y, scratch, tri, nullptr, st);
     return nb;
 }
 
@@ -346,7 +372,7 @@ cudaError_t launch_cg_set_active(int S, const int* mask, CgCol* st, cudaStream_t
 }
 
 #define SPDE_SCHUR_INST(T)                                                                                          \
-    template int launch_schur_apply<T>(int, double, int, const T*, T*, const T*, double*, const CgCol*,             \
+    template int launch_schur_apply<T>(int, double, int, const T*, T*, const T*, T*, double*, const CgCol*,             \
                                        cudaStream_t);                                                               \
     template int launch_cg_xr<T>(int64_t, int, T*, T*, const T*, const T*, double*, const CgCol*, cudaStream_t);   \
     template cudaError_t launch_cg_p<T>(int64_t, int, T*, const T*, const CgCol*, cudaStream_t);                   \

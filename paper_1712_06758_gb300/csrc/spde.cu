@@ -439,7 +439,7 @@ spde_status cg_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws
         plan.prof_cols = cols;
         for (int k = 0; k < chunk; ++k) {
             prof_begin(PK_SCHUR_APPLY, st);
-            const int nq = launch_schur_apply<T>(n, kh2, S, p, q, tri, ws.partA, ws.cg, st);
+            const int nq = launch_schur_apply<T>(n, kh2, S, p, q, tri, static_cast<T*>(ws.vec[6]), ws.partA, ws.cg, st);
             prof_end(st, cols * 8.0 * n3d * w);  // axis passes: read p, write q; read p, q, write q (x2)
             if (nq < 0) return fail(SPDE_ECUDA, "Schur operator launch configuration failed");
             prof_begin(PK_ALPHA, st);
@@ -1762,23 +1762,33 @@ spde_status spde_schur_apply(int n, double h, double kappa, int nsamples, int pr
         cprev = tri[f];
     }
     void* dtri = nullptr;
-    const size_t tb = tri.size() * (prec == SPDE_PREC_FP64 ? 8 : 4);
+    void* scratch = nullptr;
+    const size_t esz = prec == SPDE_PREC_FP64 ? 8 : 4;
+    const size_t tb = tri.size() * esz;
     CUDA_TRY(cudaMalloc(&dtri, tb));
+    if (cudaMalloc(&scratch, (size_t)nsamples * n * n * n * esz) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dtri);
+        return fail(SPDE_ENOMEM, "scratch allocation failed");
+    }
     cudaError_t e;
     int nb;
     if (prec == SPDE_PREC_FP64) {
         e = cudaMemcpy(dtri, tri.data(), tb, cudaMemcpyHostToDevice);
         nb = launch_schur_apply<double>(n, kh2, nsamples, static_cast<const double*>(x), static_cast<double*>(y),
-                                        static_cast<const double*>(dtri), nullptr, nullptr, st);
+                                        static_cast<const double*>(dtri), static_cast<double*>(scratch), nullptr,
+                                        nullptr, st);
     } else {
         std::vector<float> t32(tri.begin(), tri.end());
         e = cudaMemcpy(dtri, t32.data(), tb, cudaMemcpyHostToDevice);
         nb = launch_schur_apply<float>(n, kh2, nsamples, static_cast<const float*>(x), static_cast<float*>(y),
-                                       static_cast<const float*>(dtri), nullptr, nullptr, st);
+                                       static_cast<const float*>(dtri), static_cast<float*>(scratch), nullptr,
+                                       nullptr, st);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(dtri);
+    cudaFree(scratch);
     CUDA_TRY(e);
     if (nb < 0) return fail(SPDE_ECUDA, "launch configuration failed");
     return SPDE_OK;
