@@ -577,6 +577,33 @@ def run_ours(args):
                     "box": "[0,8]^3, n = %d" % n, "kappa": 2.0, "sigma": 1.0, "clip_ms": cset["setup_ms"],
                     "nnz": cset["nnz"], "outer_iters": cst["outer_iters"], "inner_iters": cst["inner_iters"],
                     "paper_box_fraction_of_grid": 3.0 * 3.0 * 8.0 / 8.0 ** 3}
+        # the SPE10-sized box (Sec. 7.2): 60 x 220 x 85 hexes of 20 x 10 x 2 ft, six tets each, centred
+        # in the 1600 x 2420 x 240 ft bounding box at the corner of a cubic grid of side 2432 ft
+        log("SPE10-box workload")
+        from synth import spe10_mesh
+        exyz, etets = spe10_mesh()
+        ne, side, es = 256, 2432.0, 32
+        spe = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local)
+        spe.add_level(0, ne, (0.0, 0.0, 0.0), (side, side, side))
+        spe.attach_mesh(0, exyz, etets)
+        eset = spe.stats()
+        eout = torch.empty((es, len(etets)), dtype=torch.float32, device="cuda")
+        spe.sample(0, es, 0.02, 1.0, W["seed"], first_sample(1000, rank, world, es), pkg.SPDE_OUT_LOGNORMAL, eout, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        spe.sample(0, es, 0.02, 1.0, W["seed"], first_sample(0, rank, world, es), pkg.SPDE_OUT_LOGNORMAL, eout, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        spe_rate = es / (a.elapsed_time(b) / 1000.0)
+        est = spe.stats()
+        spe.close()
+        del eout
+        spe10 = {"value": spe_rate, "unit": "samples/s", "samples": es, "ntets": int(len(etets)),
+                 "mesh": "SPE10 box 1200 x 2220 x 170 ft, 60 x 220 x 85 hexes of 20 x 10 x 2 ft, Kuhn-split",
+                 "box": "[0,%g]^3 ft, n = %d (h = %g ft)" % (side, ne, side / ne), "kappa": 0.02,
+                 "correlation_length_ft": 50.0, "sigma": 1.0, "clip_ms": eset["setup_ms"], "nnz": eset["nnz"],
+                 "outer_iters": est["outer_iters"], "inner_iters": est["inner_iters"],
+                 "paper_box_fraction_of_grid": 1600.0 * 2420.0 * 240.0 / side ** 3}
         # FP64 roof and the FP64 kernels against it
         log("fp64 roof")
         fp64_peak = fp64_peak_tflops()
@@ -613,6 +640,7 @@ def run_ours(args):
                            "max_rel_residual": fst["max_rel_residual"]},
                 "fp64": fp64,
                 "quarter_cylinder": cylinder,
+                "spe10_box": spe10,
                 "solver": {"outer_iters": iters["outer_iters"], "inner_iters": iters["inner_iters"],
                            "max_rel_residual": iters["max_rel_residual"]},
                 "setup": {"clip_ms": setup["setup_ms"], "nnz": setup["nnz"]},

@@ -7,3 +7,4 @@ not from the Philox generator the method uses for white noise.
 """
 from .mesh import kuhn_mesh, box_mesh, lprism_mesh, MeshSpec  # noqa: F401
 from .cylinder import quarter_cylinder_mesh, polygon_prism_volume, radial_nodes  # noqa: F401
+from .spe10 import cartesian_kuhn_mesh, spe10_mesh, SPE10_BOUNDING_BOX, SPE10_CELLS, SPE10_DOMAIN  # noqa: F401
