@@ -578,13 +578,14 @@ def run_ours(args):
                     "nnz": cset["nnz"], "outer_iters": cst["outer_iters"], "inner_iters": cst["inner_iters"],
                     "paper_box_fraction_of_grid": 3.0 * 3.0 * 8.0 / 8.0 ** 3}
         # the SPE10-sized box (Sec. 7.2): 60 x 220 x 85 hexes of 20 x 10 x 2 ft, six tets each, centred
-        # in the 1600 x 2420 x 240 ft bounding box at the corner of a cubic grid of side 2432 ft
+        # in the 1600 x 2420 x 240 ft bounding box, on a 256 x 256 x 32 box grid of 9.5 ft cells
+        # (2432 x 2432 x 304 ft) whose corner is the bounding box's
         log("SPE10-box workload")
         from synth import spe10_mesh
         exyz, etets = spe10_mesh()
-        ne, side, es = 256, 2432.0, 32
+        edims, eh, es = (256, 256, 32), 9.5, 64
         spe = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local)
-        spe.add_level(0, ne, (0.0, 0.0, 0.0), (side, side, side))
+        spe.add_level(0, edims, (0.0, 0.0, 0.0), tuple(eh * v for v in edims))
         spe.attach_mesh(0, exyz, etets)
         eset = spe.stats()
         eout = torch.empty((es, len(etets)), dtype=torch.float32, device="cuda")
@@ -600,10 +601,10 @@ def run_ours(args):
         del eout
         spe10 = {"value": spe_rate, "unit": "samples/s", "samples": es, "ntets": int(len(etets)),
                  "mesh": "SPE10 box 1200 x 2220 x 170 ft, 60 x 220 x 85 hexes of 20 x 10 x 2 ft, Kuhn-split",
-                 "box": "[0,%g]^3 ft, n = %d (h = %g ft)" % (side, ne, side / ne), "kappa": 0.02,
+                 "grid": "%d x %d x %d cells of %g ft from the origin" % (edims + (eh,)), "kappa": 0.02,
                  "correlation_length_ft": 50.0, "sigma": 1.0, "clip_ms": eset["setup_ms"], "nnz": eset["nnz"],
                  "outer_iters": est["outer_iters"], "inner_iters": est["inner_iters"],
-                 "paper_box_fraction_of_grid": 1600.0 * 2420.0 * 240.0 / side ** 3}
+                 "paper_box_fraction_of_grid": 1600.0 * 2420.0 * 240.0 / float(np.prod(edims) * eh ** 3)}
         # FP64 roof and the FP64 kernels against it
         log("fp64 roof")
         fp64_peak = fp64_peak_tflops()

@@ -124,6 +124,18 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts);
  * axes (cubic cells).  Replaces an existing level of the same index. */
 spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]);
 
+/* Define embedding grid `level` as a box of n[0] x n[1] x n[2] cubic cells on
+ * [lo, hi] (Sec. 4.1: the embedding domain is a box around the target mesh,
+ * as the 1600 x 2420 x 240 ft box of Sec. 7.2).  Every n[a] is a power of two
+ * in [4, 1024] and (hi - lo)[a] / n[a] is the same spacing h on all axes
+ * (relative difference <= 1e-12).  The multigrid hierarchy halves every
+ * extent above 1; the first level whose extents are not multiples of
+ * 32 x 16 x 8 must have at most 4096 cells (e.g. 256 x 256 x 32 is accepted,
+ * 512 x 512 x 16 is not).  Cell (i, j, k) has index i + n[0] (j + n[1] k).
+ * Otherwise as spde_level_add (SPDE_EINVAL for bad arguments; the Schur-CG
+ * solver option needs cubic grids and returns SPDE_EINVAL on a box). */
+spde_status spde_level_add_box(spde_ctx* ctx, int level, const int n[3], const double lo[3], const double hi[3]);
+
 /* Attach the target tet mesh of `level` and build its L2-projection operator
  * on the device (Sec. 5.1-5.2): G[tau][c] = |tau cap c| by exact FP64
  * clipping, Pi = W_h^{-1} G stored as CSR (rows = tets).
@@ -286,6 +298,13 @@ spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uin
 spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x,
                        void* y, void* stream);
 
+/* spde_apply on a box of n[0] x n[1] x n[2] cells (each a power of two in
+ * [4, 1024]); every block of a vector has n[0] n[1] n[2] entries, cell
+ * (i, j, k) at i + n[0] (j + n[1] k), wall entries at i = n[0]-1 (ux),
+ * j = n[1]-1 (uy), k = n[2]-1 (uz). */
+spde_status spde_apply_box(const int n[3], double h, double kappa, int nsamples, int prec, const void* x,
+                           void* y, void* stream);
+
 /* z = P^{-1} r for the block-diagonal MINRES preconditioner: flux block
  * opts->flux_diag * I, field block one symmetric V-cycle (damped Jacobi,
  * cell-centred linear prolongation, R = P^T, coarse operators
@@ -294,6 +313,13 @@ spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, co
  * (n, nsamples, prec), kept until process exit). */
 spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec,
                          const spde_opts* opts, const void* r, void* z, void* stream);
+
+/* spde_precond on a box grid (layout as spde_apply_box; shape rules as
+ * spde_level_add_box).  The level operators are s_l ((kappa h)^2 4^l I +
+ * c L_l), where s_l multiplies by (children per coarse cell) / 4 at each
+ * coarsening (2^l while all three extents halve). */
+spde_status spde_precond_box(const int n[3], double h, double kappa, int nsamples, int prec,
+                             const spde_opts* opts, const void* r, void* z, void* stream);
 
 /* spde_precond for callers that cannot allocate device memory: the same
  * preconditioner on the same arguments, with the V-cycle's coarse-level

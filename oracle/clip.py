@@ -116,18 +116,19 @@ def tet_box_volume(p, lo, hi, eps=1e-12):
 def coupling_rows(xyz, tets, n, lo=0.0, h=None, rows=None):
     """Rows of G for the listed tets: dict tet -> {cell: volume}.
 
-    The grid has n^3 cells of edge h from lo (cell (i,j,k) has flat index
-    i + n (j + n k)).  Candidate cells are those whose closed box meets the
-    tet's bounding box.
+    The grid has n cells per axis (one number, a cube) or (nx, ny, nz) cells
+    (a box) of edge h from lo; cell (i,j,k) has flat index i + nx (j + ny k).
+    Candidate cells are those whose closed box meets the tet's bounding box.
     """
-    h = (1.0 / n) if h is None else h
+    ext = np.broadcast_to(np.asarray(n, dtype=np.int64), (3,))
+    h = (1.0 / ext[0]) if h is None else h
     lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (3,))
     rows = range(len(tets)) if rows is None else rows
     out = {}
     for t in rows:
         p = xyz[tets[t]]
-        a = np.clip(np.floor((p.min(axis=0) - lo) / h).astype(int), 0, n - 1)
-        b = np.clip(np.floor((p.max(axis=0) - lo) / h).astype(int), 0, n - 1)
+        a = np.clip(np.floor((p.min(axis=0) - lo) / h).astype(int), 0, ext - 1)
+        b = np.clip(np.floor((p.max(axis=0) - lo) / h).astype(int), 0, ext - 1)
         row = {}
         for k in range(a[2], b[2] + 1):
             for j in range(a[1], b[1] + 1):
@@ -135,6 +136,6 @@ def coupling_rows(xyz, tets, n, lo=0.0, h=None, rows=None):
                     blo = lo + h * np.array([i, j, k])
                     v = tet_box_volume(p, blo, blo + h)
                     if v > 0.0:
-                        row[i + n * (j + n * k)] = v
+                        row[int(i + ext[0] * (j + ext[1] * k))] = v
         out[int(t)] = row
     return out

@@ -18,12 +18,13 @@ The normaliser g follows Sec. 4: g = (4 pi)^{d/4} kappa^nu
 sqrt(Gamma(nu + d/2) / Gamma(nu)), times sigma for marginal variance sigma^2;
 at nu = 1/2, d = 3 this is g^2 = 8 pi kappa sigma^2.
 
-Grid: n^3 cubes of edge h on [lo, lo + n h]^3.  Unknown ordering of this
-module (its own; unrelated to any device layout):
-  x-faces (i = 1..n-1, j, k)  id = (i-1) + (n-1) (j + n k)
-  y-faces (i, j = 1..n-1, k)  id = Nx + i + n ((j-1) + (n-1) k)
-  z-faces (i, j, k = 1..n-1)  id = Nx + Ny + i + n (j + n (k-1))
-  cells   (i, j, k)           id = Nu + i + n (j + n k)
+Grid: nx x ny x nz cubes of edge h on the box lo + [0, nx h] x [0, ny h] x
+[0, nz h] (n^3 for a cube; Sec. 7.2 embeds its domain in a non-cubic box).
+Unknown ordering of this module (its own; unrelated to any device layout):
+  x-faces (i = 1..nx-1, j, k)  id = (i-1) + (nx-1) (j + ny k)
+  y-faces (i, j = 1..ny-1, k)  id = Nx + i + nx ((j-1) + (ny-1) k)
+  z-faces (i, j, k = 1..nz-1)  id = Nx + Ny + i + nx (j + ny (k-1))
+  cells   (i, j, k)            id = Nu + i + nx (j + ny k)
 RT0 degree of freedom = the normal component u.e_axis on the face (the
 paper fixes no scaling; theta does not depend on it).  Boundary faces carry
 the essential condition u.n = 0 and are eliminated.
@@ -34,8 +35,8 @@ space; the paper gives no formula).  Reading taken here: kappa and sigma are
 constant per cell of the embedding grid.  Then the reaction block is
 diag(kappa_c^2) W and the noise of cell c carries the normaliser of Sec. 4
 evaluated with that cell's kappa_c, sigma_c.  Every routine below that takes
-`kappa` / `sigma` accepts either a number or an array of the n^3 cell values
-(cell order i + n (j + n k)).
+`kappa` / `sigma` accepts either a number or an array of the cell values
+(cell order i + nx (j + ny k)).
 """
 import math
 
@@ -89,37 +90,49 @@ def _local_matrices():
     return mass, div
 
 
+def _dims(n):
+    """(nx, ny, nz) from one n (a cube) or three extents."""
+    if np.ndim(n) == 0:
+        return (int(n),) * 3
+    return tuple(int(v) for v in n)
+
+
 class MixedSystem:
-    """Assembled [[M, B^T], [B, -kappa^2 W]] on an n^3 grid of spacing h."""
+    """Assembled [[M, B^T], [B, -kappa^2 W]] on a grid of spacing h: n is the
+    number of cells per axis of a cube, or the extents (nx, ny, nz) of a box."""
 
     def __init__(self, n, h=None, lo=0.0):
-        self.n = n = int(n)
-        self.h = h = (1.0 / n) if h is None else float(h)
+        nx, ny, nz = self.dims = _dims(n)
+        self.n = nx if nx == ny == nz else None
+        self.h = h = (1.0 / nx) if h is None else float(h)
         self.lo = lo
-        self.Nx = self.Ny = self.Nz = (n - 1) * n * n
-        self.Nu = 3 * (n - 1) * n * n
-        self.Nt = n ** 3
+        self.Nx = (nx - 1) * ny * nz
+        self.Ny = nx * (ny - 1) * nz
+        self.Nz = nx * ny * (nz - 1)
+        self.Nu = self.Nx + self.Ny + self.Nz
+        self.Nt = nx * ny * nz
         mass_ref, div_ref = _local_matrices()
         # physical cell: phi(x) = phi_ref((x - x0)/h), so
         #   int phi_a.phi_b = h^3 mass_ref,  int div phi_a = h^3 (1/h) div_ref
         mloc = h ** 3 * mass_ref
         bloc = h ** 2 * div_ref
-        i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
         i, j, k = i.ravel(), j.ravel(), k.ravel()
-        cell = i + n * (j + n * k)
+        cell = i + nx * (j + ny * k)
+        ext = (nx, ny, nz)
         gids = np.full((len(cell), 6), -1, dtype=np.int64)
         for a in range(6):
             axis, side = divmod(a, 2)
             fi = [i.copy(), j.copy(), k.copy()]
-            fi[axis] = fi[axis] + side  # face position along axis, 0..n
+            fi[axis] = fi[axis] + side  # face position along axis, 0..n_axis
             pos = fi[axis]
-            inner = (pos >= 1) & (pos <= n - 1)
+            inner = (pos >= 1) & (pos <= ext[axis] - 1)
             if axis == 0:
-                gid = (fi[0] - 1) + (n - 1) * (fi[1] + n * fi[2])
+                gid = (fi[0] - 1) + (nx - 1) * (fi[1] + ny * fi[2])
             elif axis == 1:
-                gid = self.Nx + fi[0] + n * ((fi[1] - 1) + (n - 1) * fi[2])
+                gid = self.Nx + fi[0] + nx * ((fi[1] - 1) + (ny - 1) * fi[2])
             else:
-                gid = self.Nx + self.Ny + fi[0] + n * (fi[1] + n * (fi[2] - 1))
+                gid = self.Nx + self.Ny + fi[0] + nx * (fi[1] + ny * (fi[2] - 1))
             gids[:, a] = np.where(inner, gid, -1)
         rows, cols, vals = [], [], []
         for a in range(6):
@@ -170,27 +183,34 @@ class MixedSystem:
 
 
 # --- closed form on the uniform box --------------------------------------
-# Per axis the divergence maps DST-I face modes to DCT-II cell modes with
-# factor 2 h^2 sin(pi k / 2n), and the 1-D RT0 mass matrix (tridiagonal
-# h^3 (1/6, 2/3, 1/6)) is diagonal on DST-I modes with eigenvalue
-# h^3 (2 + cos(pi k / n)) / 3.  Hence S = kappa^2 W + B M^{-1} B^T is
-# diagonalised by the orthonormal 3-D DCT-II with eigenvalues
-#   Lambda(k) = kappa^2 h^3 + h sum_d 12 sin^2(pi k_d / 2n) / (2 + cos(pi k_d / n)).
+# Per axis (n_d cells along axis d) the divergence maps DST-I face modes to
+# DCT-II cell modes with factor 2 h^2 sin(pi k / 2 n_d), and the 1-D RT0 mass
+# matrix (tridiagonal h^3 (1/6, 2/3, 1/6)) is diagonal on DST-I modes with
+# eigenvalue h^3 (2 + cos(pi k / n_d)) / 3.  Hence S = kappa^2 W + B M^{-1} B^T
+# is diagonalised by the orthonormal 3-D DCT-II with eigenvalues
+#   Lambda(k) = kappa^2 h^3 + h sum_d 12 sin^2(pi k_d / 2 n_d) / (2 + cos(pi k_d / n_d)).
 def schur_eigenvalues(n, h, kappa):
-    k = np.arange(n)
-    lam1 = 12.0 * np.sin(np.pi * k / (2 * n)) ** 2 / (2.0 + np.cos(np.pi * k / n))
-    return kappa ** 2 * h ** 3 + h * (lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :])
+    """Lambda on the [z, y, x] mode grid; n: one extent (a cube) or (nx, ny, nz)."""
+    nx, ny, nz = _dims(n)
+
+    def lam1(m):
+        k = np.arange(m)
+        return 12.0 * np.sin(np.pi * k / (2 * m)) ** 2 / (2.0 + np.cos(np.pi * k / m))
+
+    return kappa ** 2 * h ** 3 + h * (lam1(nz)[:, None, None] + lam1(ny)[None, :, None] + lam1(nx)[None, None, :])
 
 
 def solve_dct(n, kappa, sigma, xi, h=None):
     """theta = g S^{-1} W^{1/2} xi by the DCT-II diagonalisation.
 
-    xi is a flat array of n^3 cell values (x fastest) or [S, n^3].
+    n: cells per axis of a cube, or (nx, ny, nz); xi is a flat array of the
+    cell values (x fastest) or [S, cells].
     """
-    h = (1.0 / n) if h is None else h
-    lam = schur_eigenvalues(n, h, kappa)
+    nx, ny, nz = _dims(n)
+    h = (1.0 / nx) if h is None else h
+    lam = schur_eigenvalues((nx, ny, nz), h, kappa)
     xi = np.asarray(xi, dtype=np.float64)
-    batch = xi.reshape(-1, n, n, n)  # [S, z, y, x]
+    batch = xi.reshape(-1, nz, ny, nx)  # [S, z, y, x]
     f = h ** 1.5 * batch
     th = scipy.fft.idctn(scipy.fft.dctn(f, type=2, norm="ortho", axes=(1, 2, 3), workers=-1) / lam,
                          type=2, norm="ortho", axes=(1, 2, 3), workers=-1)

@@ -50,6 +50,8 @@ _SIGS = {
     "spde_opts_init": [ctypes.POINTER(spde_opts)],
     "spde_grid_create": [ctypes.POINTER(_P), ctypes.POINTER(spde_opts)],
     "spde_level_add": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "spde_level_add_box": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)],
     "spde_mesh_attach": [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int64, _P],
     "spde_sample": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                     ctypes.c_uint64, ctypes.c_int, _P, _P],
@@ -74,8 +76,12 @@ _SIGS = {
     "spde_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "spde_apply": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
+    "spde_apply_box": [ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                       _P, _P, _P],
     "spde_precond": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                      ctypes.POINTER(spde_opts), _P, _P, _P],
+    "spde_precond_box": [ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                         ctypes.POINTER(spde_opts), _P, _P, _P],
     "spde_precond_noalloc": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                              ctypes.POINTER(spde_opts), _P, _P, _P],
     "spde_schur_apply": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
@@ -153,6 +159,14 @@ def spde_level_add(ctx, level, n, lo, hi):
     lo = (ctypes.c_double * 3)(*lo)
     hi = (ctypes.c_double * 3)(*hi)
     _check(lib().spde_level_add(ctx, level, n, lo, hi))
+
+
+def spde_level_add_box(ctx, level, n, lo, hi):
+    """n: cells per axis (three ints)."""
+    n = (ctypes.c_int * 3)(*[int(v) for v in n])
+    lo = (ctypes.c_double * 3)(*lo)
+    hi = (ctypes.c_double * 3)(*hi)
+    _check(lib().spde_level_add_box(ctx, level, n, lo, hi))
 
 
 def spde_mesh_attach(ctx, level, xyz, tets):
@@ -279,6 +293,17 @@ def spde_apply(n, h, kappa, nsamples, prec, x, y, stream=None):
     _check(lib().spde_apply(n, h, kappa, nsamples, prec, _ptr(x), _ptr(y), _stream(stream)))
 
 
+def spde_apply_box(n, h, kappa, nsamples, prec, x, y, stream=None):
+    n = (ctypes.c_int * 3)(*[int(v) for v in n])
+    _check(lib().spde_apply_box(n, h, kappa, nsamples, prec, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def spde_precond_box(n, h, kappa, nsamples, prec, r, z, opts=None, stream=None):
+    n = (ctypes.c_int * 3)(*[int(v) for v in n])
+    _check(lib().spde_precond_box(n, h, kappa, nsamples, prec, ctypes.byref(opts) if opts is not None else None,
+                                  _ptr(r), _ptr(z), _stream(stream)))
+
+
 def spde_precond(n, h, kappa, nsamples, prec, r, z, opts=None, stream=None):
     _check(lib().spde_precond(n, h, kappa, nsamples, prec, ctypes.byref(opts) if opts is not None else None,
                               _ptr(r), _ptr(z), _stream(stream)))
@@ -319,8 +344,14 @@ class Sampler:
         self.levels = {}
 
     def add_level(self, level, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
-        spde_level_add(self.ctx, level, n, lo, hi)
-        self.levels[level] = (n, tuple(lo), tuple(hi))
+        """n: cells per axis, one int (a cube) or three (a box of cubic cells)."""
+        if isinstance(n, (int, np.integer)):
+            spde_level_add(self.ctx, level, int(n), lo, hi)
+            cells = int(n) ** 3
+        else:
+            spde_level_add_box(self.ctx, level, n, lo, hi)
+            cells = int(n[0]) * int(n[1]) * int(n[2])
+        self.levels[level] = (cells, tuple(lo), tuple(hi))
 
     def attach_mesh(self, level, xyz, tets):
         spde_mesh_attach(self.ctx, level, xyz, tets)
@@ -332,8 +363,8 @@ class Sampler:
                stream=None):
         import torch
         if out is None:
-            n = self.levels[level][0]
-            per = n ** 3 if (out_kind & 15) == SPDE_OUT_GRID_GAUSSIAN else self.ntets(level)
+            cells = self.levels[level][0]
+            per = cells if (out_kind & 15) == SPDE_OUT_GRID_GAUSSIAN else self.ntets(level)
             dt = torch.float64 if out_kind & SPDE_OUT_F64 else torch.float32
             out = torch.empty((nsamples, per), dtype=dt, device="cuda")
         spde_sample(self.ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out, stream)
@@ -341,18 +372,18 @@ class Sampler:
 
     def set_fields(self, level, kappa_cells, sigma_cells):
         import numpy as np
-        n = self.levels[level][0]
+        cells = self.levels[level][0]
         for a in (kappa_cells, sigma_cells):
-            if a is not None and np.size(a) != n ** 3:
-                raise ValueError("fields of level %d need %d cell values" % (level, n ** 3))
+            if a is not None and np.size(a) != cells:
+                raise ValueError("fields of level %d need %d cell values" % (level, cells))
         spde_level_set_fields(self.ctx, level, kappa_cells, sigma_cells)
 
     def sample_fields(self, level, nsamples, seed, first_sample=0, out_kind=SPDE_OUT_LOGNORMAL, out=None,
                       stream=None):
         import torch
         if out is None:
-            n = self.levels[level][0]
-            per = n ** 3 if (out_kind & 15) == SPDE_OUT_GRID_GAUSSIAN else self.ntets(level)
+            cells = self.levels[level][0]
+            per = cells if (out_kind & 15) == SPDE_OUT_GRID_GAUSSIAN else self.ntets(level)
             dt = torch.float64 if out_kind & SPDE_OUT_F64 else torch.float32
             out = torch.empty((nsamples, per), dtype=dt, device="cuda")
         spde_sample_fields(self.ctx, level, nsamples, seed, first_sample, out_kind, out, stream)

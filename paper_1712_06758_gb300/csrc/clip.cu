@@ -145,7 +145,7 @@ __device__ double tet_unit_cube_volume(const D3 p[4]) {
 }
 
 struct ClipGrid {
-    int n;
+    int n[3];  // cells per axis
     double h;
     double lo[3];
 };
@@ -201,10 +201,10 @@ __global__ void k_tet_prep(ClipGrid g, int64_t nverts, const double* __restrict_
         }
         const double a = (mn - g.lo[ax]) / g.h, b = (mx - g.lo[ax]) / g.h;
         const double tol = 1e-9;
-        if (a < -tol || b > g.n + tol) outside = true;
+        if (a < -tol || b > g.n[ax] + tol) outside = true;
         int ia = (int)floor(a), ib = (int)floor(b);
-        ia = min(max(ia, 0), g.n - 1);
-        ib = min(max(ib, 0), g.n - 1);
+        ia = min(max(ia, 0), g.n[ax] - 1);
+        ib = min(max(ib, 0), g.n[ax] - 1);
         lo_i[ax] = ia;
         hi_i[ax] = ib;
     }
@@ -254,7 +254,7 @@ __global__ void k_tet_clip(ClipGrid g, const double* __restrict__ xyz, int64_t n
                 if (!(v > 1e-14)) v = 0.0;
                 else ++cnt;
                 cvol[o] = v * g.h * g.h * g.h;
-                ccell[o] = (int32_t)(i + (int64_t)g.n * (j + (int64_t)g.n * k));
+                ccell[o] = (int32_t)(i + (int64_t)g.n[0] * (j + (int64_t)g.n[1] * k));
                 ++o;
             }
     nz[t] = cnt;
@@ -356,11 +356,11 @@ static cudaError_t exclusive_scan(int64_t n, const int64_t* in, int64_t* out, in
         }                                        \
     } while (0)
 
-cudaError_t build_coupling(int n, double h, const double lo[3], int64_t nverts, const double* d_xyz, int64_t ntets,
+cudaError_t build_coupling(const int n[3], double h, const double lo[3], int64_t nverts, const double* d_xyz, int64_t ntets,
                            const int32_t* d_tets_in, double* d_vol, int64_t** d_rowptr, int32_t** d_col, double** d_g,
                            float** d_pi, ClipResult* res, cudaStream_t st) {
     cudaError_t err = cudaSuccess;
-    ClipGrid g{n, h, {lo[0], lo[1], lo[2]}};
+    ClipGrid g{{n[0], n[1], n[2]}, h, {lo[0], lo[1], lo[2]}};
     int32_t* tets = const_cast<int32_t*>(d_tets_in);
     int64_t *cand = nullptr, *cand_off = nullptr, *nz = nullptr, *tmp = nullptr, *rowptr = nullptr;
     int* range = nullptr;

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "internal.h"
+
 namespace spde {
 
 // ---------------------------------------------------------------------------
@@ -81,48 +83,13 @@ __device__ __forceinline__ double block_sum_t(T v, double* smem /* >= BLOCK/32 *
 __device__ __forceinline__ int nb_count1(int i, int n) { return (i > 0) + (i < n - 1); }
 
 // ---------------------------------------------------------------------------
-// The scaled mixed operator at one cell (Eq. linsys_blocks after the symmetric
-// scaling by h^{-3/2} on fluxes and h^{-1/2} on cells).  xs points at the
-// sample's ux block; the four blocks are n^3 apart.  Wall fluxes (i = n-1
-// for ux, ...) are essential zeros and are never read.
-// ---------------------------------------------------------------------------
-template <typename S>
-struct Cell4 {
-    S ux, uy, uz, th;
-};
-
-template <typename T, typename S>
-__device__ __forceinline__ Cell4<S> apply_cell(const T* __restrict__ xs, int64_t n3, int n, int i, int j, int k,
-                                               int64_t c, S kh2) {
-    const T* ux = xs;
-    const T* uy = xs + n3;
-    const T* uz = xs + 2 * n3;
-    const T* th = xs + 3 * n3;
-    const int64_t sy = n, sz = (int64_t)n * n;
-    const S zero = S(0);
-    const S t0 = (S)th[c];
-    const S ux0 = (i < n - 1) ? (S)ux[c] : zero;
-    const S uy0 = (j < n - 1) ? (S)uy[c] : zero;
-    const S uz0 = (k < n - 1) ? (S)uz[c] : zero;
-    const S uxm = (i > 0) ? (S)ux[c - 1] : zero;
-    const S uym = (j > 0) ? (S)uy[c - sy] : zero;
-    const S uzm = (k > 0) ? (S)uz[c - sz] : zero;
-    const S a6 = S(1) / S(6), a23 = S(2) / S(3);
-    Cell4<S> y;
-    y.ux = (i < n - 1) ? a23 * ux0 + a6 * (uxm + ((i + 1 < n - 1) ? (S)ux[c + 1] : zero)) + (t0 - (S)th[c + 1]) : zero;
-    y.uy = (j < n - 1) ? a23 * uy0 + a6 * (uym + ((j + 1 < n - 1) ? (S)uy[c + sy] : zero)) + (t0 - (S)th[c + sy])
-                       : zero;
-    y.uz = (k < n - 1) ? a23 * uz0 + a6 * (uzm + ((k + 1 < n - 1) ? (S)uz[c + sz] : zero)) + (t0 - (S)th[c + sz])
-                       : zero;
-    y.th = (ux0 - uxm) + (uy0 - uym) + (uz0 - uzm) - kh2 * t0;
-    return y;
-}
-
-// ---------------------------------------------------------------------------
 // Four consecutive cells along x (i0 .. i0+3, i0 a multiple of 4) of the
-// scaled mixed operator, with 32-bit indices (n a power of two <= 1024, so
-// c < 2^30).  Center values come in as 16-byte vector loads; the x-neighbours
-// outside the quad as two scalars.  Wall fluxes are masked by index.
+// scaled mixed operator (Eq. linsys_blocks after the symmetric scaling by
+// h^{-3/2} on fluxes and h^{-1/2} on cells), with 32-bit indices (extents are
+// powers of two and a grid has at most 2^30 cells).  Center values come in as
+// 16-byte vector loads; the x-neighbours outside the quad as two scalars.
+// Wall fluxes (i = nx-1 for ux, j = ny-1 for uy, k = nz-1 for uz) are
+// essential zeros, masked by index and never read.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct V4 {
@@ -167,34 +134,35 @@ __device__ __forceinline__ V4<T> zero4() {
     return r;
 }
 
-// quad index q of an n^3 grid -> (i0, j, k), c = i0 + n (j + n k)
+// quad index q of a grid (nx >= 4) -> (i0, j, k), c = i0 + nx (j + ny k)
 struct QuadPos {
     int i0, j, k, c;
 };
-__device__ __forceinline__ QuadPos quad_pos(int q, int logn) {
-    const int lq = logn - 2;  // quads per row = n / 4
+__device__ __forceinline__ QuadPos quad_pos(int q, const Grid3& g) {
+    const int lq = g.lx - 2;  // quads per row = nx / 4
     QuadPos p;
     p.i0 = (q & ((1 << lq) - 1)) << 2;
-    p.j = (q >> lq) & ((1 << logn) - 1);
-    p.k = q >> (lq + logn);
-    p.c = p.i0 + ((p.j + (p.k << logn)) << logn);
+    p.j = (q >> lq) & (g.ny - 1);
+    p.k = q >> (lq + g.ly);
+    p.c = p.i0 + ((p.j + (p.k << g.ly)) << g.lx);
     return p;
 }
 
-// y = A x on the quad; xs points at the sample's ux block (blocks n^3 apart)
+// y = A x on the quad; xs points at the sample's ux block (blocks nx ny nz apart)
 template <typename T, typename S>
-__device__ __forceinline__ void apply_quad(const T* __restrict__ xs, int n, int logn, const QuadPos& p, S kh2,
+__device__ __forceinline__ void apply_quad(const T* __restrict__ xs, const Grid3& g, const QuadPos& p, S kh2,
                                            S yu[4], S yv[4], S yw[4], S yt[4]) {
-    const int n3 = 1 << (3 * logn);
-    const int sy = n, sz = n << logn;
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
+    const int n = g.nx;
+    const int sy = g.nx, sz = g.nx << g.ly;
     const T* ux = xs;
     const T* uy = xs + n3;
     const T* uz = xs + 2 * n3;
     const T* th = xs + 3 * n3;
     const int c = p.c;
     const V4<T> ux4 = ld4(ux + c), uy4 = ld4(uy + c), uz4 = ld4(uz + c), th4 = ld4(th + c);
-    const bool jl = p.j > 0, jh = p.j < n - 1, jhh = p.j + 1 < n - 1;
-    const bool kl = p.k > 0, kh = p.k < n - 1, khh = p.k + 1 < n - 1;
+    const bool jl = p.j > 0, jh = p.j < g.ny - 1, jhh = p.j + 1 < g.ny - 1;
+    const bool kl = p.k > 0, kh = p.k < g.nz - 1, khh = p.k + 1 < g.nz - 1;
     const V4<T> uyM = jl ? ld4(uy + c - sy) : zero4<T>();
     const V4<T> uyP = jhh ? ld4(uy + c + sy) : zero4<T>();
     const V4<T> uzM = kl ? ld4(uz + c - sz) : zero4<T>();

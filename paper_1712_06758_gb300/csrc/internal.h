@@ -8,6 +8,47 @@ namespace spde {
 constexpr int kReduceBlock = 256;
 constexpr int kMaxPartials = 4096;   // per column, per partial-sum array
 
+// Cells per axis of a uniform embedding grid (equal spacing h on all axes),
+// each a power of two; cell (i, j, k) has flat index c = i + nx (j + ny k).
+struct Grid3 {
+    int nx = 0, ny = 0, nz = 0;
+    int lx = 0, ly = 0, lz = 0;  // log2 of each extent
+    __host__ __device__ int64_t cells() const { return (int64_t)nx * ny * nz; }
+    __host__ __device__ int ext(int axis) const { return axis == 0 ? nx : (axis == 1 ? ny : nz); }
+    __host__ __device__ int maxn() const { return nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz); }
+    __host__ __device__ bool cube() const { return nx == ny && ny == nz; }
+    // the next coarser grid of the multigrid hierarchy: every extent above 1 halves
+    __host__ __device__ Grid3 coarser() const {
+        Grid3 c;
+        c.nx = nx > 1 ? nx >> 1 : 1;
+        c.ny = ny > 1 ? ny >> 1 : 1;
+        c.nz = nz > 1 ? nz >> 1 : 1;
+        c.lx = lx > 0 ? lx - 1 : 0;
+        c.ly = ly > 0 ? ly - 1 : 0;
+        c.lz = lz > 0 ? lz - 1 : 0;
+        return c;
+    }
+    __host__ __device__ bool operator==(const Grid3& o) const { return nx == o.nx && ny == o.ny && nz == o.nz; }
+};
+
+inline int log2_exact(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+inline Grid3 make_grid(int nx, int ny, int nz) {
+    Grid3 g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.lx = log2_exact(nx);
+    g.ly = log2_exact(ny);
+    g.lz = log2_exact(nz);
+    return g;
+}
+inline Grid3 make_grid(int n) { return make_grid(n, n, n); }
+
 // Per-column MINRES state (Paige-Saunders recurrences), kept in FP64.
 struct MinresCol {
     double beta, oldb, alpha, dbar, epsln, oldeps, phibar, cs, sn, gamma, delta, phi, beta1;
@@ -53,15 +94,17 @@ struct CgCol {
 
 // Multigrid plan of one grid size for a batch of S columns.
 struct MGPlan {
-    int n = 0;          // fine cells per axis (power of two)
-    int nlev = 0;       // levels 0..nlev-1, n_l = n >> l, n_{nlev-1} = 1
-    int lc = 0;         // first level handled by the one-CTA coarse kernel (n_lc <= 16)
+    Grid3 g[16];        // grids of the levels: g[l + 1] = g[l].coarser(), g[nlev - 1] has one cell
+    double ls[16] = {}; // level factors: A_l = ls (kh2 lq I + c L_l); 2^l and 4^l while all axes halve
+    double lq[16] = {};
+    int nlev = 0;       // levels 0..nlev-1
+    int lc = 0;         // first level handled by the one-CTA coarse kernel (<= 4096 cells)
     double kh2 = 0.0;   // (kappa h)^2 on level 0
     double c = 1.0;     // Schur weight
     double omega = 0.8; // Jacobi weight
     double prof_cols = 0.0; // columns assumed active, for the profiler's byte counts (0: all)
     // scratch (element type of the plan) for levels 1..lc: rhs b_l and result e_l,
-    // each [S][n_l^3]
+    // each [S][cells of level l]
     void* b[16] = {};
     void* e[16] = {};
     // per-cell diagonal s (a_c + c k_c) of every level (element type of the plan), for
@@ -80,16 +123,18 @@ cudaError_t launch_noise_cols(int64_t ncells, int S, const uint64_t* seed, const
 
 // ---- stencil.cu (element type T = float or double)
 template <typename T>
-cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_t st);
+cudaError_t launch_apply(const Grid3& g, double kh2, int S, const T* x, T* y, cudaStream_t st);
 // r = [0; F] - A x (FP64), written to r32 (float, may be null) and r64 (double, may be
 // null); partial sums of r.r per column into part [S][nblk]; returns nblk
-int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x,
+int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
                       float* r32, double* r64, double* part, const int* active, cudaStream_t st,
                       const double* kh2c = nullptr);
 // the multigrid diagonal of a level with cell-wise (kappa h)^2: a_c = mean of the children's a
-// (a_0 = (kappa_c h)^2), D = 2^l (a_c 4^l + c k_c) with k_c the cell's existing neighbours
-cudaError_t launch_restrict_mean(int nf, const double* af, double* ac, cudaStream_t st);
-cudaError_t launch_level_diag(int n, int l, double c, const double* a, double* D64, float* D32, cudaStream_t st);
+// (a_0 = (kappa_c h)^2; gf is the finer grid), D = s (a_c q + c k_c) with k_c the cell's
+// existing neighbours and s, q the level's factors (2^l, 4^l on a cube)
+cudaError_t launch_restrict_mean(const Grid3& gf, const double* af, double* ac, cudaStream_t st);
+cudaError_t launch_level_diag(const Grid3& g, double s, double q, double c, const double* a, double* D64, float* D32,
+                              cudaStream_t st);
 // F[s][e] *= c[e] (per-cell noise factor of a level with fields)
 cudaError_t launch_scale_cells(int64_t n3, int S, double* F, int64_t stride, const double* c, cudaStream_t st);
 // (kappa h)^2 (FP64, FP32) and -g h per cell from cell-wise kappa, sigma (device arrays)
@@ -98,17 +143,19 @@ cudaError_t launch_field_coefs(int64_t n3, double h, const double* kappa, const 
 // x += d (double += float) on active columns
 cudaError_t launch_add_correction(int64_t nelem, int S, double* x, const float* d, const int* active,
                                   cudaStream_t st);
-// u = -T^{-1} D1^T theta into the flux blocks of x ([S][4 n^3], FP64), line by line;
-// tri: Thomas factors (2n - 2 doubles, see k_flux_lines)
-cudaError_t launch_flux_from_theta(int n, int S, double* x, int64_t col_stride, const double* tri, cudaStream_t st);
+// u = -T^{-1} D1^T theta into the flux blocks of x ([S][4 cells], FP64), line by line;
+// tri: Thomas factors of the longest extent tn (2 tn - 2 doubles, see k_flux_lines)
+cudaError_t launch_flux_from_theta(const Grid3& g, int S, double* x, int64_t col_stride, const double* tri,
+                                   cudaStream_t st);
 // x cell block += d ([S][n^3]) for columns whose inner solve ran
 template <typename T>
 cudaError_t launch_add_theta(int64_t n3, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st);
 // two-level coupling: F_c = (1/sqrt 2) sum over children of F_f; theta~_f = theta~_c(parent) / sqrt 2
-cudaError_t launch_restrict_rhs(int nc, int S, const double* Ff, int64_t f_stride, double* Fc, int64_t c_stride,
-                                cudaStream_t st);
-cudaError_t launch_inject_theta(int nc, int S, const double* xc, int64_t c_stride, double* xf, int64_t f_stride,
-                                cudaStream_t st);
+// (gc: the coarse grid; the fine grid is twice it along every axis)
+cudaError_t launch_restrict_rhs(const Grid3& gc, int S, const double* Ff, int64_t f_stride, double* Fc,
+                                int64_t c_stride, cudaStream_t st);
+cudaError_t launch_inject_theta(const Grid3& gc, int S, const double* xc, int64_t c_stride, double* xf,
+                                int64_t f_stride, cudaStream_t st);
 // partial sums of a.a over columns of a strided array; returns nblk
 int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* part, cudaStream_t st);
 // out[s] = sum_b part[s][b] (fixed order)
@@ -118,7 +165,7 @@ cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cuda
 // A(k+1) fused with the pending D(k) when yprev != null (see krylov.cu).  The
 // preconditioned Lanczos vector is fd * u on the flux blocks and y's cell block.
 template <typename T>
-int launch_minres_A(int n, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
+int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
                     MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st,
                     const T* kh2c = nullptr);
 // r1 -= (alpha / beta) r2 and the flux part of the next beta^2 (the flux block of
@@ -159,7 +206,13 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
                   double* dot_part, const int* active, int act_stride, cudaStream_t st);
 template <typename T>
 size_t mg_scratch_elems(int n, int S);
+template <typename T>
+size_t mg_scratch_elems(const Grid3& g, int S);
+// false when the hierarchy does not fit the kernels (more than 4096 cells on the
+// first level whose extents are not multiples of the 32 x 16 x 8 tile)
+bool mg_plan_init(MGPlan& plan, const Grid3& g, double kh2, double c, double omega);
 void mg_plan_init(MGPlan& plan, int n, double kh2, double c, double omega);
+bool mg_grid_supported(const Grid3& g);
 template <typename T>
 void mg_plan_bind(MGPlan& plan, int S, T* scratch);
 
@@ -190,7 +243,7 @@ struct ClipResult {
 };
 // Build CSR (row_ptr, col, G, Pi) for a mesh already on the device.  Allocates the CSR
 // arrays with cudaMalloc (ownership passes to the caller).  Synchronises st.
-cudaError_t build_coupling(int n, double h, const double lo[3], int64_t nverts, const double* d_xyz,
+cudaError_t build_coupling(const int n[3], double h, const double lo[3], int64_t nverts, const double* d_xyz,
                            int64_t ntets, const int32_t* d_tets, double* d_vol, int64_t** d_rowptr,
                            int32_t** d_col, double** d_g, float** d_pi, ClipResult* res,
                            cudaStream_t st);

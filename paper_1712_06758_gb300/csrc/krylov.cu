@@ -47,18 +47,19 @@ __device__ __forceinline__ void set_coef(MinresCol& c, int k, double v) {
 // caller scales the flux part of its inner product by fd); wall fluxes are
 // masked by index.
 template <typename T>
-__device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T* __restrict__ th, T fd, int n,
-                                              int logn, const QuadPos& p, const V4<T>& kh2, T yu[4], T yv[4],
+__device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T* __restrict__ th, T fd,
+                                              const Grid3& g, const QuadPos& p, const V4<T>& kh2, T yu[4], T yv[4],
                                               T yw[4], T yt[4], V4<T> vc[4]) {
-    const int n3 = 1 << (3 * logn);
-    const int sy = n, sz = n << logn;
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
+    const int n = g.nx;
+    const int sy = g.nx, sz = g.nx << g.ly;
     const T* ux = us;
     const T* uy = us + n3;
     const T* uz = us + 2 * n3;
     const int c = p.c;
     const V4<T> ux4 = ld4(ux + c), uy4 = ld4(uy + c), uz4 = ld4(uz + c), th4 = ld4(th + c);
-    const bool jl = p.j > 0, jh = p.j < n - 1, jhh = p.j + 1 < n - 1;
-    const bool kl = p.k > 0, kh = p.k < n - 1, khh = p.k + 1 < n - 1;
+    const bool jl = p.j > 0, jh = p.j < g.ny - 1, jhh = p.j + 1 < g.ny - 1;
+    const bool kl = p.k > 0, kh = p.k < g.nz - 1, khh = p.k + 1 < g.nz - 1;
     const V4<T> uyM = jl ? ld4(uy + c - sy) : zero4<T>();
     const V4<T> uyP = jhh ? ld4(uy + c + sy) : zero4<T>();
     const V4<T> uzM = kl ? ld4(uz + c - sz) : zero4<T>();
@@ -91,8 +92,10 @@ __device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T*
     vc[3] = th4;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n, T kh2, const T* __restrict__ y, const T* __restrict__ u, T fd, T* __restrict__ r1,
+// CUBE: the grid is a cube (all extents and logs taken from x, which keeps the
+// index arithmetic and register use of the cubic case minimal)
+template <typename T, bool CUBE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 gin, T kh2, const T* __restrict__ y, const T* __restrict__ u, T fd, T* __restrict__ r1,
                                                      double* __restrict__ partA, const MinresCol* __restrict__ st,
                                                      const T* __restrict__ yprev, T* __restrict__ w1,
                                                      const T* __restrict__ w2, T* __restrict__ xd,
@@ -103,8 +106,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
     const bool doA = cs.active != 0;
     const bool doD = yprev != nullptr && cs.upd != 0;
     if (!doA && !doD) return;
-    const int logn = ilog2(n);
-    const int n3 = 1 << (3 * logn);
+    Grid3 g = gin;
+    if constexpr (CUBE) {
+        g.ny = g.nz = gin.nx;
+        g.lx = g.ly = g.lz = ilog2(gin.nx);
+    }
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int nq = n3 >> 2;
     const int64_t off = (int64_t)s * 4 * n3;
     const T* ys = y + off;   // only its cell block is read
@@ -117,7 +124,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
         // r1 holds no data before the second iteration (coef == 0): do not read it
         const bool use_r1 = coef != T(0);
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-            const QuadPos p = quad_pos(q, logn);
+            const QuadPos p = quad_pos(q, g);
             T yu[4], yv[4], yw[4], yt[4];
             V4<T> vc[4];
             V4<T> k4;  // (kappa h)^2 per cell: one value, or the level's field
@@ -125,7 +132,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
             else
 #pragma unroll
                 for (int e = 0; e < 4; ++e) k4.v[e] = kh2;
-            apply_quad_fd<T>(us, ys + 3 * n3, fd, n, logn, p, k4, yu, yv, yw, yt, vc);
+            apply_quad_fd<T>(us, ys + 3 * n3, fd, g, p, k4, yu, yv, yw, yt, vc);
             const V4<T> v0 = vc[0], v1 = vc[1], v2 = vc[2], v3 = vc[3];
             V4<T> z0, z1, z2, z3;
             if (use_r1) {
@@ -179,12 +186,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(int n,
 }
 
 template <typename T>
-int launch_minres_A(int n, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
+int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
                     MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st, const T* kh2c) {
-    const int64_t n3 = (int64_t)n * n * n;
-    const int nb = cell_blocks(n3 / 16);  // four quads per thread: one reduction per 1024 quads
+    const int nb = cell_blocks(g.cells() / 16);  // four quads per thread: one reduction per 1024 quads
     dim3 grid(nb, S);
-    k_minres_A<T><<<grid, 256, 0, st>>>(n, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c);
+    if (g.cube())
+        k_minres_A<T, true><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c);
+    else
+        k_minres_A<T, false><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c);
     return nb;
 }
 
@@ -423,7 +432,7 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 }
 
 #define SPDE_KRYLOV_INST(T)                                                                                        \
-    template int launch_minres_A<T>(int, double, int, const T*, const T*, double, T*, double*, MinresCol*,        \
+    template int launch_minres_A<T>(const Grid3&, double, int, const T*, const T*, double, T*, double*, MinresCol*,        \
                                     const T*, T*, const T*, T*, cudaStream_t, const T*);                           \
     template int launch_minres_B<T>(int64_t, int, int, T*, const T*, double, double*, MinresCol*, cudaStream_t);   \
     template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \

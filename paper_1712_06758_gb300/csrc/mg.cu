@@ -3,21 +3,27 @@
 //     A_0 = (kappa h)^2 I + c L          (L: Neumann graph Laplacian)
 // on the nested embedding grids of Sec. 6.1.
 //
-// Level l has n_l = n >> l cells per axis and operator
-//     A_l = 2^l ((kappa h)^2 4^l I + c L_l),   D_l = diag(A_l),
-// transfers P = tensor product of the 1-D cell-centred linear prolongation
+// Level l + 1 halves every extent of level l that is above 1 (on a cube of n
+// cells per axis: n_l = n >> l).  Level operator
+//     A_l = s_l ((kappa h)^2 q_l I + c L_l),   D_l = diag(A_l),
+// with q_l = 4^l and s_l the product over the coarsenings above it of
+// (children per coarse cell) / 4, i.e. s_l = 2^l while all three axes halve
+// (the rediscretised operator); an axis of extent 1 has no neighbours, so one
+// weight serves every axis.  Transfers P = tensor product of the 1-D
+// cell-centred linear prolongation
 //     fine 2I <- 3/4 e_I + 1/4 e_{I-1},  fine 2I+1 <- 3/4 e_I + 1/4 e_{I+1}
-// (indices clamped at the walls: reflection for the no-flux boundary) and
-// R = P^T.  Each level: x = omega D^{-1} b (one Jacobi sweep from zero),
-// coarse correction with r = b - A x, then one more Jacobi sweep; the
-// one-cell level is solved exactly.  Same sweep before and after makes the
-// operator symmetric; with 0 < omega < 1 it is positive definite, as MINRES
-// needs.
+// (indices clamped at the walls: reflection for the no-flux boundary; the
+// identity along an axis that is not coarsened) and R = P^T.  Each level:
+// x = omega D^{-1} b (one Jacobi sweep from zero), coarse correction with
+// r = b - A x, then one more Jacobi sweep; the one-cell level is solved
+// exactly.  Same sweep before and after makes the operator symmetric; with
+// 0 < omega < 1 it is positive definite, as MINRES needs.
 //
-// Kernels: levels with n_l >= 32 use shared-memory tiles (a down sweep that
-// smooths, forms the residual and restricts in one pass; an up sweep that
-// prolongs, corrects and post-smooths in one pass).  All levels with
-// n_l <= 16 run inside one CTA per sample in shared memory.
+// Kernels: levels whose extents are multiples of the tile (32 x 16 x 8) use
+// shared-memory tiles (a down sweep that smooths, forms the residual and
+// restricts in one pass; an up sweep that prolongs, corrects and post-smooths
+// in one pass).  The remaining levels (at most 4096 cells) run inside one CTA
+// per sample in shared memory.
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 
 #include <type_traits>
@@ -45,8 +51,8 @@ struct LevelCoef {
 template <typename T>
 static LevelCoef<T> level_coef(const MGPlan& p, int l) {
     LevelCoef<T> q;
-    const double s = (double)(1 << l);
-    const double a = p.kh2 * (double)(1ll << (2 * l));
+    const double s = p.ls[l];
+    const double a = p.kh2 * p.lq[l];
     q.s = (T)s;
     q.c = (T)p.c;
     q.omega = (T)p.omega;
@@ -276,7 +282,7 @@ constexpr int kRestrictBase = kTileThreads - RXY / 2;  // the restriction thread
 
 template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
-    k_mg_down(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
+    k_mg_down(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
               int64_t bc_stride, const int* __restrict__ active, int act_stride, const T* __restrict__ Dg) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_oi[8], s_rcD[8];
@@ -296,8 +302,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
             s_oi[k] = q.oi[k];
             s_rcD[k] = q.rcD[k];
         }
-    const int nc = nf >> 1;
-    const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
+    const int nfx = gf.nx, nfy = gf.ny, nfz = gf.nz;  // all three halve (tiled levels)
+    const int ncx = nfx >> 1, ncy = nfy >> 1, ncz = nfz >> 1;
+    const int64_t fplane = (int64_t)nfx * nfy;
+    const int ntx = nfx / SX, nty = nfy / SY, ntz = nfz / SZ;
     const int ntiles = ntx * nty * ntz;
     T* bcs = bc + (int64_t)col * bc_stride;
     const T sc = q.s * q.c;
@@ -321,12 +329,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
         {
             const int ly = tid / kQ, q4 = tid - ly * kQ;
             const int gy = fy0 - 2 + ly, gx0 = fx0 - 4 + 4 * q4;
-            const bool in = has_c && in_range(gy, nf) && in_range(gx0, nf);
+            const bool in = has_c && in_range(gy, nfy) && in_range(gx0, nfx);
             c_off = 4 * q4 + PW * ly;
-            if (in) c_g = gx0 + nf * gy;
+            if (in) c_g = gx0 + nfx * gy;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int k = in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
+                const int k = in ? nb_count1(gy, nfy) + nb_count1(gx0 + e, nfx) : 0;
                 c_k |= k << (3 * e);
                 cI[e] = s_oi[k + 2];
             }
@@ -339,12 +347,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
         {
             const int ly = tid / kQ, q4 = tid - ly * kQ;
             const int gy = fy0 - 1 + ly, gx0 = fx0 - 4 + 4 * q4;
-            r_in = has_r && in_range(gy, nf) && in_range(gx0, nf);
+            r_in = has_r && in_range(gy, nfy) && in_range(gx0, nfx);
             r_off = 4 * q4 + PW * ly;
-            r_g = r_in ? gx0 + nf * gy : 0;
+            r_g = r_in ? gx0 + nfx * gy : 0;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int k = r_in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
+                const int k = r_in ? nb_count1(gy, nfy) + nb_count1(gx0 + e, nfx) : 0;
                 r_k |= k << (3 * e);
                 rI[e] = s_rcD[k + 2];
             }
@@ -356,9 +364,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
         T wa[4], wb[4], wy[4];
 #pragma unroll
         for (int a3 = 0; a3 < 4; ++a3) {
-            wa[a3] = (T)restrict_w(a3, cx0 + 2 * qm, nc);
-            wb[a3] = (T)restrict_w(a3, cx0 + 2 * qm + 1, nc);
-            wy[a3] = (T)restrict_w(a3, cy0 + qj, nc);
+            wa[a3] = (T)restrict_w(a3, cx0 + 2 * qm, ncx);
+            wb[a3] = (T)restrict_w(a3, cx0 + 2 * qm + 1, ncx);
+            wy[a3] = (T)restrict_w(a3, cy0 + qj, ncy);
         }
         const int q_off = 4 * qm + 3 + PW * (2 * qj);  // residual of fine (2I - 1, 2J - 1), I = cx0 + 2 qm
         T* const Rxq = Rxy + 2 * (qt & (RXY / 2 - 1));
@@ -367,14 +375,14 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
             constexpr int JS = decltype(js)::value;
             const T* raw = ring.take(JS);
             if (has_c) {
-                const bool wall = (f == 0 || f == nf - 1);  // b = 0 off the box, any factor will do
+                const bool wall = (f == 0 || f == nfz - 1);  // b = 0 off the box, any factor will do
                 const V4<T> bv = ld4(raw + c_off);
                 V4<T> v;
                 if constexpr (PC) {  // per-cell diagonal (cell-wise kappa); b = 0 off the box
                     V4<T> dd;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) dd.v[e] = T(1);
-                    if (c_g >= 0 && in_range(f, nf)) dd = ld4(Dg + c_g + (int64_t)nf * nf * f);
+                    if (c_g >= 0 && in_range(f, nfz)) dd = ld4(Dg + c_g + fplane * f);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v.v[e] = q.omega * bv.v[e] / dd.v[e];
                 } else if (!wall) {
@@ -394,8 +402,8 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
             if (t <= SZ) commit(IC<(K + 3) & 3>{}, f + 2);
             if (has_r && t <= SZ + 1) {
                 V4<T> r = zero4<T>();
-                if (r_in && in_range(f, nf)) {
-                    const bool wall = (f == 0 || f == nf - 1);
+                if (r_in && in_range(f, nfz)) {
+                    const bool wall = (f == 0 || f == nfz - 1);
                     const int xo = r_off + PW;  // x0 rows start one row above the residual rows
                     const T* Xc = Xbase + ((K + 3) & 3) * (PW * XH);
                     const T* Xm = Xbase + ((K + 2) & 3) * (PW * XH);
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
                         nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
                     }
                     if constexpr (PC) {
-                        const V4<T> dd = ld4(Dg + r_g + (int64_t)nf * nf * f);
+                        const V4<T> dd = ld4(Dg + r_g + fplane * f);
                         const T rc = T(1) / q.omega - T(1);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) r.v[e] = rc * dd.v[e] * c.v[e] + sc * nbs[e];
@@ -443,16 +451,16 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
                 if ((K & 1) == 0 && t >= 4) {
                     // coarse plane Z = fr/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = fr-3 .. fr
                     const int Z = (fr - 2) >> 1;
-                    const T w3 = (T)restrict_w(3, Z, nc);
+                    const T w3 = (T)restrict_w(3, Z, ncz);
                     T z0 = w3 * acc0, z1 = w3 * acc1;
 #pragma unroll
                     for (int c3 = 0; c3 < 3; ++c3) {
                         const V2<T> v = ld2(Rxq + ((K + 3 + c3) & 3) * RXY);
-                        const T w = (T)restrict_w(c3, Z, nc);
+                        const T w = (T)restrict_w(c3, Z, ncz);
                         z0 += w * v.v[0];
                         z1 += w * v.v[1];
                     }
-                    st2(bcs + (cx0 + 2 * qm) + (int64_t)nc * ((cy0 + qj) + (int64_t)nc * Z), z0, z1);
+                    st2(bcs + (cx0 + 2 * qm) + (int64_t)ncx * ((cy0 + qj) + (int64_t)ncy * Z), z0, z1);
                 }
             }
             __syncthreads();
@@ -491,7 +499,7 @@ constexpr int kOutBase = kTileThreads - SX * SY / 4;  // the output threads: the
 
 template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
-    k_mg_up(const __grid_constant__ CUtensorMap bmap, int nf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
+    k_mg_up(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
             int64_t ec_stride, T* __restrict__ y, int64_t y_stride, double* __restrict__ dot_part,
             const int* __restrict__ active, int act_stride, const T* __restrict__ Dg) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -513,10 +521,11 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
             s_oi[k] = q.oi[k];
             s_ois[k] = q.ois[k];
         }
-    const int nc = nf >> 1;
-    const int ntx = nf / SX, nty = nf / SY, ntz = nf / SZ;
+    const int nfx = gf.nx, nfy = gf.ny, nfz = gf.nz;  // all three halve (tiled levels)
+    const int ncx = nfx >> 1, ncy = nfy >> 1, ncz = nfz >> 1;
+    const int ntx = nfx / SX, nty = nfy / SY, ntz = nfz / SZ;
     const int ntiles = ntx * nty * ntz;
-    const int64_t plane = (int64_t)nf * nf, cplane = (int64_t)nc * nc;
+    const int64_t plane = (int64_t)nfx * nfy, cplane = (int64_t)ncx * ncy;
     const T* es = ec + (int64_t)col * ec_stride;
     T* ys = y + (int64_t)col * y_stride;
     const T om1 = T(1) - q.omega;
@@ -539,8 +548,8 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         int c_src = -1;  // coarse plane element of this thread (clamped x, y), or -1
         if (tid < CW * CH) {
             const int ly = tid / CW, lx = tid - ly * CW;
-            const int gx = min(max(cx0 - 3 + lx, 0), nc - 1), gy = min(max(cy0 - 1 + ly, 0), nc - 1);
-            c_src = gx + nc * gy;
+            const int gx = min(max(cx0 - 3 + lx, 0), ncx - 1), gy = min(max(cy0 - 1 + ly, 0), ncy - 1);
+            c_src = gx + ncx * gy;
         }
         // prolongation: one segment of the x plane (tid < kQ * BH)
         const bool has_x = tid < kQ * BH;
@@ -550,9 +559,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         {
             const int ly = tid / kQ, q4 = tid - ly * kQ;
             const int gy = fy0 - 1 + ly, gx0 = fx0 - 4 + 4 * q4;
-            x_in = has_x && in_range(gy, nf) && in_range(gx0, nf);
+            x_in = has_x && in_range(gy, nfy) && in_range(gx0, nfx);
             x_off = 4 * q4 + PW * ly;
-            x_g = x_in ? gx0 + nf * gy : 0;
+            x_g = x_in ? gx0 + nfx * gy : 0;
             if (x_in) {
                 // coarse rows (gy >> 1) and its other neighbour; coarse x gx0/2 - 1 .. gx0/2 + 2
                 p_r0 = ((gy >> 1) - (cy0 - 1)) * CW + 2 * q4;
@@ -560,7 +569,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int k = x_in ? nb_count1(gy, nf) + nb_count1(gx0 + e, nf) : 0;
+                const int k = x_in ? nb_count1(gy, nfy) + nb_count1(gx0 + e, nfx) : 0;
                 x_k |= k << (3 * e);
                 xI[e] = s_oi[k + 2];
             }
@@ -574,13 +583,13 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
         T oI[4], sI[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int k = has_out ? nb_count1(fy0 + oy, nf) + nb_count1(fx0 + ox0 + e, nf) : 0;
+            const int k = has_out ? nb_count1(fy0 + oy, nfy) + nb_count1(fx0 + ox0 + e, nfx) : 0;
             o_k |= k << (3 * e);
             oI[e] = s_oi[k + 2];
             sI[e] = s_ois[k + 2];
         }
         auto fetch_c = [&](int Z) -> T {
-            return (c_src >= 0) ? es[c_src + cplane * min(max(Z, 0), nc - 1)] : T(0);
+            return (c_src >= 0) ? es[c_src + cplane * min(max(Z, 0), ncz - 1)] : T(0);
         };
         // x(g) on the tile + halo 1 from b(g) = tile plane j = g - fz0 + 1 (ring slot JS = j mod 4,
         // x slot (j + 3) mod 4) and the coarse planes Iz = g >> 1 (weight 3/4) and its z neighbour
@@ -590,8 +599,8 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
             const T* Bg = ring.take(JS);
             if (!has_x) return;
             V4<T> v = zero4<T>();
-            if (x_in && in_range(g, nf)) {
-                const bool wall = (g == 0 || g == nf - 1);
+            if (x_in && in_range(g, nfz)) {
+                const bool wall = (g == 0 || g == nfz - 1);
                 const int Iz = g >> 1;
                 const T* C0 = Cs(Iz);
                 const T* C1 = Cs((g & 1) ? Iz + 1 : Iz - 1);
@@ -640,7 +649,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
             }
             const int f = g - 1;  // output plane: x planes f-1, f, f+1 and b(f) (tile plane t)
             if (t >= 1 && has_out) {
-                const bool wall = (f == 0 || f == nf - 1);
+                const bool wall = (f == 0 || f == nfz - 1);
                 const T* Xc = Xbase + ((K + 3) & 3) * (PW * BH);
                 const T* Xm = Xbase + ((K + 2) & 3) * (PW * BH);
                 const T* Xp = Xbase + (K & 3) * (PW * BH);
@@ -657,7 +666,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 }
                 V4<T> out;
                 if constexpr (PC) {  // y = (1 - omega) x + omega D^{-1} (b + s c sum x)
-                    const V4<T> dd = ld4(Dg + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f);
+                    const V4<T> dd = ld4(Dg + (fx0 + ox0) + (int64_t)nfx * (fy0 + oy) + plane * f);
                     const T sc = q.s * q.c;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) out.v[e] = om1 * c.v[e] + q.omega * (bb.v[e] + sc * nbs[e]) / dd.v[e];
@@ -673,7 +682,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) dacc += bb.v[e] * out.v[e];
-                st4(ys + (fx0 + ox0) + (int64_t)nf * (fy0 + oy) + plane * f, out);
+                st4(ys + (fx0 + ox0) + (int64_t)nfx * (fy0 + oy) + plane * f, out);
             }
             __syncthreads();
             // tile planes up to t are consumed: their slots are free
@@ -707,20 +716,23 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
 }
 
 // ---------------------------------------------------------------------------
-// All levels n_l <= 16 in one CTA per sample (shared memory).
+// The levels from lc down (at most 4096 cells on level lc) in one CTA per
+// sample (shared memory).  Extents may differ per axis; an axis that has
+// reached extent 1 is no longer coarsened (its transfers are the identity).
 // ---------------------------------------------------------------------------
 struct CoarseDesc {
     int lc;        // first (absolute) level handled here
-    int nlev;      // total number of levels (n_{nlev-1} = 1)
-    int n0;        // n_lc
+    int nlev;      // total number of levels (the last one has one cell)
+    Grid3 g[16];   // grids of the levels (absolute index)
     double kh2, c, omega;
+    double ls[16], lq[16];  // level factors s_l, q_l
     const void* D[16];  // per-cell diagonals of the levels (cell-wise kappa), or null
 };
 
 template <typename T>
 __device__ __forceinline__ T cz_invD(const CoarseDesc& d, int l, int k) {
-    const T s = (T)(1 << l);
-    const T a = (T)(d.kh2 * (double)(1ll << (2 * l)));
+    const T s = (T)d.ls[l];
+    const T a = (T)(d.kh2 * d.lq[l]);
     return T(1) / (s * (a + (T)d.c * (T)k));
 }
 
@@ -732,29 +744,59 @@ __device__ __forceinline__ T cz_invDf(const CoarseDesc& d, int l, int kc, int f)
 }
 
 template <typename T>
-__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, int n, int i, int j, int k) {
-    const int f = i + n * (j + n * k);
+__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, const Grid3& g, int i, int j, int k) {
+    const int sy = g.nx, sz = g.nx * g.ny;
+    const int f = i + g.nx * (j + g.ny * k);
     const T x0 = x[f];
     if (d.D[l]) {  // per-cell diagonal: D x0 - s c (sum of existing neighbours)
         T nb = T(0);
         if (i > 0) nb += x[f - 1];
-        if (i < n - 1) nb += x[f + 1];
-        if (j > 0) nb += x[f - n];
-        if (j < n - 1) nb += x[f + n];
-        if (k > 0) nb += x[f - n * n];
-        if (k < n - 1) nb += x[f + n * n];
-        return static_cast<const T*>(d.D[l])[f] * x0 - (T)(1 << l) * (T)d.c * nb;
+        if (i < g.nx - 1) nb += x[f + 1];
+        if (j > 0) nb += x[f - sy];
+        if (j < g.ny - 1) nb += x[f + sy];
+        if (k > 0) nb += x[f - sz];
+        if (k < g.nz - 1) nb += x[f + sz];
+        return static_cast<const T*>(d.D[l])[f] * x0 - (T)d.ls[l] * (T)d.c * nb;
     }
     T lap = T(0);
     if (i > 0) lap += x0 - x[f - 1];
-    if (i < n - 1) lap += x0 - x[f + 1];
-    if (j > 0) lap += x0 - x[f - n];
-    if (j < n - 1) lap += x0 - x[f + n];
-    if (k > 0) lap += x0 - x[f - n * n];
-    if (k < n - 1) lap += x0 - x[f + n * n];
-    const T s = (T)(1 << l);
-    const T a = (T)(d.kh2 * (double)(1ll << (2 * l)));
+    if (i < g.nx - 1) lap += x0 - x[f + 1];
+    if (j > 0) lap += x0 - x[f - sy];
+    if (j < g.ny - 1) lap += x0 - x[f + sy];
+    if (k > 0) lap += x0 - x[f - sz];
+    if (k < g.nz - 1) lap += x0 - x[f + sz];
+    const T s = (T)d.ls[l];
+    const T a = (T)(d.kh2 * d.lq[l]);
     return s * (a * x0 + (T)d.c * lap);
+}
+
+// the taps of the 1-D restriction onto coarse index I along one axis: fine
+// indices f0 .. f0 + nt - 1 with weights w (zero outside the grid)
+__device__ __forceinline__ int restrict_taps(bool coarsened, int I, int nc, int& f0, float w[4]) {
+    if (!coarsened) {
+        f0 = I;
+        w[0] = 1.0f;
+        return 1;
+    }
+    f0 = 2 * I - 1;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) w[a] = restrict_w(a, I, nc);
+    return 4;
+}
+
+// the two taps of the 1-D prolongation onto fine index i along one axis
+__device__ __forceinline__ void prolong_taps(bool coarsened, int i, int nc, int p[2], float w[2]) {
+    if (!coarsened) {
+        p[0] = p[1] = i;
+        w[0] = 1.0f;
+        w[1] = 0.0f;
+        return;
+    }
+    const int I = i >> 1;
+    p[0] = I;
+    p[1] = min(max((i & 1) ? I + 1 : I - 1, 0), nc - 1);
+    w[0] = 0.75f;
+    w[1] = 0.25f;
 }
 
 template <typename T>
@@ -767,58 +809,64 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int col = blockIdx.x;
     if (active && !active[(int64_t)col * act_stride]) return;
-    // layout: b_l and x_l for l = lc .. nlev-1, then a temp of n0^3
-    int offb[16], offx[16], nn[16];
+    // layout: b_l and x_l for l = lc .. nlev-1, then a temp of level lc's size
+    int offb[16], offx[16];
     int o = 0;
     for (int l = d.lc; l < d.nlev; ++l) {
-        const int n = d.n0 >> (l - d.lc);
-        nn[l] = n;
+        const int nl = (int)d.g[l].cells();
         offb[l] = o;
-        o += n * n * n;
+        o += nl;
         offx[l] = o;
-        o += n * n * n;
+        o += nl;
     }
     T* tmp = sm + o;
     const T* bs = bin + (int64_t)col * b_stride;
     T* es = eout + (int64_t)col * e_stride;
     {
-        const int n = d.n0, n3 = n * n * n;
+        const int n3 = (int)d.g[d.lc].cells();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) sm[offb[d.lc] + f] = bs[f];
     }
     __syncthreads();
     const T om = (T)d.omega;
     // down
     for (int l = d.lc; l < d.nlev - 1; ++l) {
-        const int n = nn[l], n3 = n * n * n, nc = n >> 1;
+        const Grid3 g = d.g[l], gc = d.g[l + 1];
+        const int n3 = (int)g.cells();
         T* b = sm + offb[l];
         T* x = sm + offx[l];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
-            const int i = f % n, j = (f / n) % n, k = f / (n * n);
-            x[f] = om * b[f] * cz_invDf<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n), f);
+            const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
+            x[f] = om * b[f] * cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f);
         }
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
-            const int i = f % n, j = (f / n) % n, k = f / (n * n);
-            tmp[f] = b[f] - cz_Ax<T>(d, l, x, n, i, j, k);
+            const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
+            tmp[f] = b[f] - cz_Ax<T>(d, l, x, g, i, j, k);
         }
         __syncthreads();
         T* bc = sm + offb[l + 1];
-        for (int C = threadIdx.x; C < nc * nc * nc; C += blockDim.x) {
-            const int I = C % nc, J = (C / nc) % nc, K = C / (nc * nc);
+        const int nc3 = (int)gc.cells();
+        for (int C = threadIdx.x; C < nc3; C += blockDim.x) {
+            const int I = C % gc.nx, J = (C / gc.nx) % gc.ny, K = C / (gc.nx * gc.ny);
+            int fi0, fj0, fk0;
+            float wxs[4], wys[4], wzs[4];
+            const int ni = restrict_taps(g.nx > 1, I, gc.nx, fi0, wxs);
+            const int nj = restrict_taps(g.ny > 1, J, gc.ny, fj0, wys);
+            const int nk = restrict_taps(g.nz > 1, K, gc.nz, fk0, wzs);
             T acc = T(0);
-            for (int c3 = 0; c3 < 4; ++c3) {
-                const int fk = 2 * K - 1 + c3;
-                const T wz = (T)restrict_w(c3, K, nc);
+            for (int c3 = 0; c3 < nk; ++c3) {
+                const int fk = fk0 + c3;
+                const T wz = (T)wzs[c3];
                 if (wz == T(0)) continue;
-                for (int b3 = 0; b3 < 4; ++b3) {
-                    const int fj = 2 * J - 1 + b3;
-                    const T wy = (T)restrict_w(b3, J, nc) * wz;
+                for (int b3 = 0; b3 < nj; ++b3) {
+                    const int fj = fj0 + b3;
+                    const T wy = (T)wys[b3] * wz;
                     if (wy == T(0)) continue;
-                    for (int a3 = 0; a3 < 4; ++a3) {
-                        const int fi = 2 * I - 1 + a3;
-                        const T w = (T)restrict_w(a3, I, nc) * wy;
+                    for (int a3 = 0; a3 < ni; ++a3) {
+                        const int fi = fi0 + a3;
+                        const T w = (T)wxs[a3] * wy;
                         if (w == T(0)) continue;
-                        acc += w * tmp[fi + n * (fj + n * fk)];
+                        acc += w * tmp[fi + g.nx * (fj + g.ny * fk)];
                     }
                 }
             }
@@ -834,36 +882,37 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     }
     // up
     for (int l = d.nlev - 2; l >= d.lc; --l) {
-        const int n = nn[l], n3 = n * n * n, nc = n >> 1;
+        const Grid3 g = d.g[l], gc = d.g[l + 1];
+        const int n3 = (int)g.cells();
         const T* b = sm + offb[l];
         T* x = sm + offx[l];
         const T* e = sm + offx[l + 1];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
-            const int i = f % n, j = (f / n) % n, k = f / (n * n);
-            const int Ix = i >> 1, Iy = j >> 1, Iz = k >> 1;
-            const int Ox = min(max((i & 1) ? Ix + 1 : Ix - 1, 0), nc - 1);
-            const int Oy = min(max((j & 1) ? Iy + 1 : Iy - 1, 0), nc - 1);
-            const int Oz = min(max((k & 1) ? Iz + 1 : Iz - 1, 0), nc - 1);
-            const int px[2] = {Ix, Ox}, py[2] = {Iy, Oy}, pz[2] = {Iz, Oz};
-            const T w[2] = {T(0.75), T(0.25)};
+            const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
+            int px[2], py[2], pz[2];
+            float wx[2], wy[2], wz[2];
+            prolong_taps(g.nx > 1, i, gc.nx, px, wx);
+            prolong_taps(g.ny > 1, j, gc.ny, py, wy);
+            prolong_taps(g.nz > 1, k, gc.nz, pz, wz);
             T pe = T(0);
             for (int c3 = 0; c3 < 2; ++c3)
                 for (int b3 = 0; b3 < 2; ++b3)
-                    for (int a3 = 0; a3 < 2; ++a3) pe += w[a3] * w[b3] * w[c3] * e[px[a3] + nc * (py[b3] + nc * pz[c3])];
+                    for (int a3 = 0; a3 < 2; ++a3)
+                        pe += (T)wx[a3] * (T)wy[b3] * (T)wz[c3] * e[px[a3] + gc.nx * (py[b3] + gc.ny * pz[c3])];
             tmp[f] = x[f] + pe;
         }
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
-            const int i = f % n, j = (f / n) % n, k = f / (n * n);
-            const T iD = cz_invDf<T>(d, l, nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n), f);
-            x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, n, i, j, k));
+            const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
+            const T iD = cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f);
+            x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, g, i, j, k));
         }
         __syncthreads();
     }
     // write out (and b.e partial when this is the whole V-cycle)
     double dacc = 0.0;
     {
-        const int n = d.n0, n3 = n * n * n;
+        const int n3 = (int)d.g[d.lc].cells();
         const T* x = sm + offx[d.lc];
         const T* b = sm + offb[d.lc];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
@@ -877,65 +926,90 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     }
 }
 
-static int coarse_smem_elems(int n0, int lc, int nlev) {
-    int o = 0;
-    for (int l = lc; l < nlev; ++l) {
-        const int n = n0 >> (l - lc);
-        o += 2 * n * n * n;
-    }
-    return o + n0 * n0 * n0;
-}
+constexpr int kCoarseMaxCells = 4096;  // cells of the finest level the one-CTA kernel takes
 
-void mg_plan_init(MGPlan& plan, int n, double kh2, double c, double omega) {
-    plan.n = n;
+static int coarse_smem_elems(const MGPlan& p) {
+    int o = 0;
+    for (int l = p.lc; l < p.nlev; ++l) o += 2 * (int)p.g[l].cells();
+    return o + (int)p.g[p.lc].cells();
+}
+// bound over every plan: the levels below one of <= 4096 cells hold at most
+// as many cells again in total (each has at most half the cells of the one above)
+constexpr int kCoarseSmemElemsMax = 2 * (2 * kCoarseMaxCells) + kCoarseMaxCells;
+
+static bool tiled_level(const Grid3& g) { return g.nx % SX == 0 && g.ny % SY == 0 && g.nz % 8 == 0; }
+
+bool mg_plan_init(MGPlan& plan, const Grid3& g, double kh2, double c, double omega) {
     plan.kh2 = kh2;
     plan.c = c;
     plan.omega = omega;
+    plan.g[0] = g;
+    plan.ls[0] = 1.0;
+    plan.lq[0] = 1.0;
     int nlev = 1;
-    while ((n >> (nlev - 1)) > 1) ++nlev;
+    while (plan.g[nlev - 1].cells() > 1 && nlev < 16) {
+        const Grid3& f = plan.g[nlev - 1];
+        const int children = (f.nx > 1 ? 2 : 1) * (f.ny > 1 ? 2 : 1) * (f.nz > 1 ? 2 : 1);
+        plan.g[nlev] = f.coarser();
+        plan.ls[nlev] = plan.ls[nlev - 1] * children / 4.0;
+        plan.lq[nlev] = plan.lq[nlev - 1] * 4.0;
+        ++nlev;
+    }
     plan.nlev = nlev;
     int lc = 0;
-    while ((n >> lc) > 16) ++lc;
+    while (lc < nlev - 1 && tiled_level(plan.g[lc])) ++lc;
     plan.lc = lc;
+    return plan.g[nlev - 1].cells() == 1 && plan.g[lc].cells() <= kCoarseMaxCells;
+}
+
+bool mg_grid_supported(const Grid3& g) {
+    MGPlan p;
+    return mg_plan_init(p, g, 0.0, 1.0, 0.8);
+}
+
+void mg_plan_init(MGPlan& plan, int n, double kh2, double c, double omega) {
+    mg_plan_init(plan, make_grid(n), kh2, c, omega);
+}
+
+template <typename T>
+size_t mg_scratch_elems(const Grid3& g, int S) {
+    MGPlan p;
+    mg_plan_init(p, g, 0.0, 1.0, 0.8);
+    size_t tot = 0;
+    for (int l = 1; l <= p.lc; ++l) tot += 2 * (size_t)p.g[l].cells();
+    return tot * (size_t)S;
 }
 
 template <typename T>
 size_t mg_scratch_elems(int n, int S) {
-    MGPlan p;
-    mg_plan_init(p, n, 0.0, 1.0, 0.8);
-    size_t tot = 0;
-    for (int l = 1; l <= p.lc; ++l) {
-        const size_t nl = (size_t)(n >> l);
-        tot += 2 * nl * nl * nl;
-    }
-    return tot * (size_t)S;
+    return mg_scratch_elems<T>(make_grid(n), S);
 }
 
 template <typename T>
 void mg_plan_bind(MGPlan& plan, int S, T* scratch) {
     size_t o = 0;
     for (int l = 1; l <= plan.lc; ++l) {
-        const size_t nl = (size_t)(plan.n >> l);
+        const size_t nl = (size_t)plan.g[l].cells();
         plan.b[l] = scratch + o;
-        o += nl * nl * nl * (size_t)S;
+        o += nl * (size_t)S;
         plan.e[l] = scratch + o;
-        o += nl * nl * nl * (size_t)S;
+        o += nl * (size_t)S;
     }
 }
 
 // z planes per CTA for the level sweeps: the longest march (fewest halo planes)
 // that still gives at least four CTAs per SM of a 152-SM GPU
-static int pick_sz(int nf, int S) {
-    const int base = (nf / SX) * (nf / SY);
+static int pick_sz(const Grid3& g, int S) {
+    const int base = (g.nx / SX) * (g.ny / SY);
     for (int sz = 32; sz > 8; sz >>= 1)
-        if (nf % sz == 0 && (int64_t)base * (nf / sz) * S >= 4 * 152) return sz;
+        if (g.nz % sz == 0 && (int64_t)base * (g.nz / sz) * S >= 4 * 152) return sz;
     return 8;
 }
 
 template <typename T>
 static cudaError_t mg_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         coarse_smem_elems(16, 0, 5) * (int)sizeof(T));
+                                         kCoarseSmemElemsMax * (int)sizeof(T));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_down<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
     if (e == cudaSuccess)
@@ -967,14 +1041,15 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// tensor map of S stacked n^3 grids (column stride col_stride elements), box PW x rows x 1 x 1
+// tensor map of S stacked grids (column stride col_stride elements), box PW x rows x 1 x 1
 template <typename T>
-static bool plane_map(CUtensorMap* m, const T* base, int n, int S, int64_t col_stride, int rows) {
+static bool plane_map(CUtensorMap* m, const T* base, const Grid3& g, int S, int64_t col_stride, int rows) {
     const EncodeTiledFn fn = encode_tiled();
     const size_t es = sizeof(T);
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || ((col_stride * es) & 15) || ((n * es) & 15)) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)S};
-    const cuuint64_t strides[3] = {(cuuint64_t)n * es, (cuuint64_t)n * n * es, (cuuint64_t)col_stride * es};
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || ((col_stride * es) & 15) || ((g.nx * es) & 15))
+        return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)S};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)col_stride * es};
     const cuuint32_t box[4] = {(cuuint32_t)PW, (cuuint32_t)rows, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
@@ -1026,79 +1101,83 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
                   const int* active, int act_stride, cudaStream_t st) {
     const double prof_cols = plan.prof_cols > 0 ? plan.prof_cols : (double)S;
     if (mg_attrs<T>() != cudaSuccess) return -1;
-    const int n = plan.n;
     CoarseDesc d;
     d.lc = plan.lc;
     d.nlev = plan.nlev;
-    d.n0 = n >> plan.lc;
     d.kh2 = plan.kh2;
     d.c = plan.c;
     d.omega = plan.omega;
-    for (int l = 0; l < 16; ++l) d.D[l] = plan.D[l];
-    const size_t csm = (size_t)coarse_smem_elems(d.n0, d.lc, d.nlev) * sizeof(T);
+    for (int l = 0; l < 16; ++l) {
+        d.g[l] = plan.g[l];
+        d.ls[l] = plan.ls[l];
+        d.lq[l] = plan.lq[l];
+        d.D[l] = plan.D[l];
+    }
+    const size_t csm = (size_t)coarse_smem_elems(plan) * sizeof(T);
     const double w = (double)sizeof(T);
-    const double n0c = (double)d.n0 * d.n0 * d.n0;
+    const int64_t s3 = plan.g[plan.lc].cells();
     if (plan.lc == 0) {
         prof_begin(PK_MG_COARSE, st);
         k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, b, b_stride, y, y_stride, dot_part, active, act_stride);
-        prof_end(st, prof_cols * 2.0 * n0c * w);
+        prof_end(st, prof_cols * 2.0 * (double)s3 * w);
         return 1;
     }
     // down sweeps
     const T* in = b;
     int64_t in_stride = b_stride;
     for (int l = 0; l < plan.lc; ++l) {
-        const int nf = n >> l, nc = nf >> 1;
-        const int sz = pick_sz(nf, S);
-        const int ntiles = (nf / SX) * (nf / SY) * (nf / sz);
+        const Grid3& gf = plan.g[l];
+        const int64_t nc3 = plan.g[l + 1].cells();
+        const int sz = pick_sz(gf, S);
+        const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
         CUtensorMap map;
-        if (!plane_map<T>(&map, in, nf, S, in_stride, XH)) return -1;
+        if (!plane_map<T>(&map, in, gf, S, in_stride, XH)) return -1;
         prof_begin(PK_MG_DOWN, st);
         const T* Dl = static_cast<const T*>(plan.D[l]);
         if (Dl)
             k_mg_down<T, true><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
-                map, nf, sz, level_coef<T>(plan, l), out, (int64_t)nc * nc * nc, active, act_stride, Dl);
+                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, Dl);
         else
             k_mg_down<T, false><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
-                map, nf, sz, level_coef<T>(plan, l), out, (int64_t)nc * nc * nc, active, act_stride, nullptr);
-        prof_end(st, prof_cols * (1.0 + 0.125) * (double)nf * nf * nf * w);
+                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, nullptr);
+        prof_end(st, prof_cols * (1.0 + 0.125) * (double)gf.cells() * w);
         in = out;
-        in_stride = (int64_t)nc * nc * nc;
+        in_stride = nc3;
     }
     {
-        const int64_t s3 = (int64_t)d.n0 * d.n0 * d.n0;
         prof_begin(PK_MG_COARSE, st);
         k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, static_cast<const T*>(plan.b[plan.lc]), s3,
                                                        static_cast<T*>(plan.e[plan.lc]), s3, nullptr, active,
                                                        act_stride);
-        prof_end(st, prof_cols * 2.0 * n0c * w);
+        prof_end(st, prof_cols * 2.0 * (double)s3 * w);
     }
     int nblk0 = 1;
     for (int l = plan.lc - 1; l >= 0; --l) {
-        const int nf = n >> l, nc = nf >> 1;
-        const int sz = pick_sz(nf, S);
-        const int ntiles = (nf / SX) * (nf / SY) * (nf / sz);
+        const Grid3& gf = plan.g[l];
+        const int64_t nf3 = gf.cells(), nc3 = plan.g[l + 1].cells();
+        const int sz = pick_sz(gf, S);
+        const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
         dim3 grid(nb, S);
         const T* bl = (l == 0) ? b : static_cast<const T*>(plan.b[l]);
-        const int64_t bls = (l == 0) ? b_stride : (int64_t)nf * nf * nf;
+        const int64_t bls = (l == 0) ? b_stride : nf3;
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
-        const int64_t yls = (l == 0) ? y_stride : (int64_t)nf * nf * nf;
+        const int64_t yls = (l == 0) ? y_stride : nf3;
         CUtensorMap map;
-        if (!plane_map<T>(&map, bl, nf, S, bls, BH)) return -1;
+        if (!plane_map<T>(&map, bl, gf, S, bls, BH)) return -1;
         prof_begin(PK_MG_UP, st);
         const T* Dl = static_cast<const T*>(plan.D[l]);
         if (Dl)
             k_mg_up<T, true><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
-                map, nf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
-                yls, (l == 0) ? dot_part : nullptr, active, act_stride, Dl);
+                map, gf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
+                (l == 0) ? dot_part : nullptr, active, act_stride, Dl);
         else
             k_mg_up<T, false><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
-                map, nf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), (int64_t)nc * nc * nc, yl,
-                yls, (l == 0) ? dot_part : nullptr, active, act_stride, nullptr);
-        prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf * nf * nf * w);
+                map, gf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
+                (l == 0) ? dot_part : nullptr, active, act_stride, nullptr);
+        prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf3 * w);
         if (l == 0) nblk0 = nb;
     }
     return nblk0;
@@ -1108,6 +1187,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     template int launch_vcycle<T>(const MGPlan&, int, const T*, int64_t, T*, int64_t, double*, const int*, int,   \
                                   cudaStream_t);                                                                   \
     template size_t mg_scratch_elems<T>(int, int);                                                                 \
+    template size_t mg_scratch_elems<T>(const Grid3&, int);                                                        \
     template void mg_plan_bind<T>(MGPlan&, int, T*);
 SPDE_MG_INST(float)
 SPDE_MG_INST(double)

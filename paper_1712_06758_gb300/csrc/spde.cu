@@ -92,7 +92,8 @@ void dev_free(T*& p) {
 
 // Solver workspace for S columns of one grid size and inner precision.
 struct Workspace {
-    int n = 0, S = 0, inner64 = -1;
+    Grid3 g;
+    int S = 0, inner64 = -1;
     double* x64 = nullptr;   // [S][4n^3] refinement iterate (scaled unknowns)
     double* F = nullptr;     // [S][n^3] cell block of the scaled RHS
     void* vec[7] = {};       // inner vectors: d, wA, wB ([S][n^3], cell block only), r1, r2, yA, yB
@@ -138,16 +139,17 @@ struct Workspace {
         h_nact = nullptr;
         h_col = nullptr;
         h_st = nullptr;
-        n = S = 0;
+        g = Grid3();
+        S = 0;
         inner64 = -1;
     }
 };
 
-int64_t workspace_bytes(int n, int S, bool inner64) {
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+int64_t workspace_bytes(const Grid3& g, int S, bool inner64) {
+    const int64_t n3 = g.cells(), N4 = 4 * n3;
     const int64_t w = inner64 ? 8 : 4;
     int64_t b = (int64_t)S * (8 * N4 + 8 * n3 + 4 * w * N4 + 3 * w * n3 + 4 * n3);
-    b += (int64_t)(inner64 ? mg_scratch_elems<double>(n, S) * 8 : mg_scratch_elems<float>(n, S) * 4);
+    b += (int64_t)(inner64 ? mg_scratch_elems<double>(g, S) * 8 : mg_scratch_elems<float>(g, S) * 4);
     b += 4LL * S * kMaxPartials * 8 + 2LL * S * 8 + (int64_t)S * sizeof(MinresCol);
     return b;
 }
@@ -200,7 +202,7 @@ struct Fields {
 
 struct Level {
     bool defined = false;
-    int n = 0;
+    Grid3 g;
     double h = 0.0;
     double lo[3] = {0, 0, 0};
     Mesh mesh;
@@ -227,10 +229,10 @@ struct spde_ctx {
 
 namespace {
 
-spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
-    if (ws.n == n && ws.S >= S && ws.inner64 == (int)inner64) return SPDE_OK;
+spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64) {
+    if (ws.g == g && ws.S >= S && ws.inner64 == (int)inner64) return SPDE_OK;
     ws.release();
-    const size_t n3 = (size_t)n * n * n, N4 = 4 * n3;
+    const size_t n3 = (size_t)g.cells(), N4 = 4 * n3;
     const size_t w = inner64 ? 8 : 4;
     STATUS_TRY(dev_alloc(&ws.x64, (size_t)S * N4));
     STATUS_TRY(dev_alloc(&ws.F, (size_t)S * n3));
@@ -241,10 +243,10 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
             v = nullptr;
             cudaGetLastError();
             ws.release();
-            return fail(SPDE_ENOMEM, "workspace allocation failed (%d columns of %d^3)", S, n);
+            return fail(SPDE_ENOMEM, "workspace allocation failed (%d columns of %d x %d x %d)", S, g.nx, g.ny, g.nz);
         }
     }
-    const size_t mgb = inner64 ? mg_scratch_elems<double>(n, S) * 8 : mg_scratch_elems<float>(n, S) * 4;
+    const size_t mgb = inner64 ? mg_scratch_elems<double>(g, S) * 8 : mg_scratch_elems<float>(g, S) * 4;
     if (mgb) {
         cudaError_t e = cudaMalloc(&ws.mg, mgb);
         if (e != cudaSuccess) {
@@ -265,7 +267,9 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
     STATUS_TRY(dev_alloc(&ws.nact, 2 * kMaxChunk));
     STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
     {
-        // Thomas factors of tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of a line
+        // Thomas factors of tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of a line of the
+        // longest extent n (the factors of a shorter line are the first ones of the same table)
+        const int n = g.maxn();
         std::vector<double> tri(2 * (size_t)n - 2);
         double cprev = 0.0;
         for (int f = 0; f < n - 1; ++f) {
@@ -291,7 +295,7 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
         ws.release();
         return fail(SPDE_ENOMEM, "pinned host allocation failed");
     }
-    ws.n = n;
+    ws.g = g;
     ws.S = S;
     ws.inner64 = inner64 ? 1 : 0;
     return SPDE_OK;
@@ -300,9 +304,9 @@ spde_status ensure_workspace(Workspace& ws, int n, int S, bool inner64) {
 // Batched MINRES on the scaled mixed system for the columns flagged in
 // st[].active; right-hand sides in r2 (inner type T), solution in d.
 template <typename T>
-spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws, double inner_tol,
+spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Workspace& ws, double inner_tol,
                          int* iters_out, cudaStream_t st, const T* kh2c = nullptr, T* const* Dlev = nullptr) {
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const int64_t n3 = g.cells(), N4 = 4 * n3;
     T* d = static_cast<T*>(ws.vec[0]);
     T* w1 = static_cast<T*>(ws.vec[1]);
     T* w2 = static_cast<T*>(ws.vec[2]);
@@ -311,7 +315,7 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
     T* ycur = static_cast<T*>(ws.vec[5]);
     T* ynext = static_cast<T*>(ws.vec[6]);
     MGPlan plan;
-    mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
+    if (!mg_plan_init(plan, g, kh2, o.schur_c, o.omega)) return fail(SPDE_EINVAL, "grid shape not supported by the V-cycle");
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
@@ -351,7 +355,7 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
             rec[q] = t_prof ? t_prof->mark() : 0;
             // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
-            const int nA = launch_minres_A<T>(n, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
+            const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
                                               pending ? yprev : nullptr, w1, w2, d, st, kh2c);
             a_bytes[q] = ((itn >= 2 ? 12.0 : 8.0) + (kh2c ? 1.0 : 0.0)) * n3d * w;
             d_bytes[q] = pending ? (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0;
@@ -404,9 +408,11 @@ spde_status minres_batch(const spde_opts& o, int n, double kh2, int S, Workspace
 // r_theta the cell block of the mixed residual in ws.vec[4] (inner type T);
 // d in ws.vec[0] ([S][n^3]).
 template <typename T>
-spde_status cg_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws, double inner_tol, int* iters_out,
-                     cudaStream_t st) {
-    const int64_t n3 = (int64_t)n * n * n;
+spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Workspace& ws, double inner_tol,
+                     int* iters_out, cudaStream_t st) {
+    if (!g.cube()) return fail(SPDE_EINVAL, "the Schur-complement CG solver needs a cubic grid");
+    const int n = g.nx;
+    const int64_t n3 = g.cells();
     T* x = static_cast<T*>(ws.vec[0]);
     T* r = static_cast<T*>(ws.vec[1]);
     T* p = static_cast<T*>(ws.vec[2]);
@@ -415,7 +421,7 @@ spde_status cg_batch(const spde_opts& o, int n, double kh2, int S, Workspace& ws
     const T* mixed_r = static_cast<const T*>(ws.vec[4]);
     const T* tri = std::is_same<T, float>::value ? reinterpret_cast<const T*>(ws.tri32) : reinterpret_cast<const T*>(ws.tri);
     MGPlan plan;
-    mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
+    mg_plan_init(plan, g, kh2, o.schur_c, o.omega);
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.prof_cols = (double)S;
     const int act_stride = (int)(sizeof(CgCol) / sizeof(int));
@@ -480,10 +486,11 @@ static spde_status fault_status(int fault, cudaStream_t st) {
 // inner MINRES of element type T.  F, x64 in ws; returns the max relative
 // residual in *maxrel.
 template <typename T>
-spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws, double* maxrel, int* outer_out,
-                         int* inner_out, cudaStream_t st, bool warm = false, const Fields* fl = nullptr) {
+spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Workspace& ws, double* maxrel,
+                         int* outer_out, int* inner_out, cudaStream_t st, bool warm = false,
+                         const Fields* fl = nullptr) {
     const spde_opts& o = ctx->opts;
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const int64_t n3 = g.cells(), N4 = 4 * n3;
     // ||F||^2 per column
     prof_begin(PK_SUMSQ, st);
     int nb = launch_sumsq(n3, S, ws.F, n3, ws.partR, st);
@@ -505,11 +512,11 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         if (outer > 0 || warm) {
             // flux rows exact for the current cell field: u = -T^{-1} D1^T theta
             prof_begin(PK_FLUX, st);
-            CUDA_TRY(launch_flux_from_theta(n, S, ws.x64, N4, ws.tri, st));
+            CUDA_TRY(launch_flux_from_theta(g, S, ws.x64, N4, ws.tri, st));
             prof_end(st, (double)S * 96.0 * (double)n3);
         }
         prof_begin(PK_RESIDUAL, st);
-        nb = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st, fl ? fl->kh2_64 : nullptr);
+        nb = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st, fl ? fl->kh2_64 : nullptr);
         prof_end(st, (double)S * (40.0 + 4.0 * sizeof(T) + (fl ? 8.0 : 0.0)) * (double)n3);
         CUDA_TRY(cudaGetLastError());
         prof_begin(PK_OTHER, st);
@@ -540,7 +547,7 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
         double itol = o.inner_tol;
         if (std::is_same<T, double>::value) itol = std::max(0.1 * o.tol / std::max(worst, 1e-300), 1e-15);
         int its = 0;
-        if (o.solver == SPDE_SOLVER_SCHUR_CG) STATUS_TRY(cg_batch<T>(o, n, kh2, S, ws, itol, &its, st));
+        if (o.solver == SPDE_SOLVER_SCHUR_CG) STATUS_TRY(cg_batch<T>(o, g, kh2, S, ws, itol, &its, st));
         else {
             const T* kh2c = nullptr;
             T* const* Dlev = nullptr;
@@ -553,7 +560,7 @@ spde_status refine_solve(spde_ctx* ctx, int n, double kh2, int S, Workspace& ws,
                     Dlev = fl->D64;
                 }
             }
-            STATUS_TRY(minres_batch<T>(o, n, kh2, S, ws, itol, &its, st, kh2c, Dlev));
+            STATUS_TRY(minres_batch<T>(o, g, kh2, S, ws, itol, &its, st, kh2c, Dlev));
         }
         inner_total += its;
         prof_begin(PK_ADD_CORR, st);
@@ -584,14 +591,14 @@ spde_status check_params(double kappa, double sigma) {
 }
 
 // columns per batch that fit in free memory (mixed path)
-int batch_capacity(int n, int S, bool inner64) {
+int batch_capacity(const Grid3& g, int S, bool inner64) {
     size_t freeb = 0, totb = 0;
     if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
         cudaGetLastError();
         return S;
     }
     int cap = S;
-    while (cap > 1 && workspace_bytes(n, cap, inner64) > (int64_t)(0.85 * (double)freeb)) cap = (cap + 1) / 2;
+    while (cap > 1 && workspace_bytes(g, cap, inner64) > (int64_t)(0.85 * (double)freeb)) cap = (cap + 1) / 2;
     return cap;
 }
 
@@ -600,8 +607,7 @@ int batch_capacity(int n, int S, bool inner64) {
 // is -g_c h xi_c cell by cell and the operator takes (kappa_c h)^2 per cell.
 spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double sigma, uint64_t seed, uint64_t first,
                           cudaStream_t st, const Fields* fl = nullptr) {
-    const int n = L.n;
-    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t n3 = L.g.cells();
     const double kh2 = fl ? fl->kh2_mean : (kappa * L.h) * (kappa * L.h);
     // scaled RHS cell block: h^{-1/2} (-g h^{3/2} xi) = -g h xi
     prof_begin(PK_NOISE, st);
@@ -611,8 +617,8 @@ spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double s
     double rel = 0.0;
     int outer = 0, inner = 0;
     spde_status s;
-    if (L.ws.inner64 == 1) s = refine_solve<double>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st, false, fl);
-    else s = refine_solve<float>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st, false, fl);
+    if (L.ws.inner64 == 1) s = refine_solve<double>(ctx, L.g, kh2, S, L.ws, &rel, &outer, &inner, st, false, fl);
+    else s = refine_solve<float>(ctx, L.g, kh2, S, L.ws, &rel, &outer, &inner, st, false, fl);
     ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
     ctx->stats.inner_iters = std::max(ctx->stats.inner_iters, inner);
     ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
@@ -620,8 +626,7 @@ spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double s
 }
 
 spde_status write_output(Level& L, int S, int out_kind, void* out_dev, cudaStream_t st) {
-    const int n = L.n;
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const int64_t n3 = L.g.cells(), N4 = 4 * n3;
     const int kind = out_kind & 15;
     const int out64 = (out_kind & SPDE_OUT_F64) ? 1 : 0;
     const double unscale = 1.0 / std::sqrt(L.h);  // theta = h^{-1/2} scaled theta
@@ -644,7 +649,7 @@ spde_status write_output(Level& L, int S, int out_kind, void* out_dev, cudaStrea
 
 size_t out_elem_count(const Level& L, int S, int out_kind) {
     const int kind = out_kind & 15;
-    const size_t per = kind == SPDE_OUT_GRID_GAUSSIAN ? (size_t)L.n * L.n * L.n : (size_t)L.mesh.ntets;
+    const size_t per = kind == SPDE_OUT_GRID_GAUSSIAN ? (size_t)L.g.cells() : (size_t)L.mesh.ntets;
     return per * (size_t)S;
 }
 
@@ -765,13 +770,13 @@ void lane_free(Lane* L) {
     cudaGetLastError();
 }
 
-spde_status lane_alloc(Lane* L, int n) {
+spde_status lane_alloc(Lane* L, const Grid3& g) {
     const int cap = L->cap;
     if (cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         return fail(SPDE_ECUDA, "stream creation failed");
     }
-    STATUS_TRY(ensure_workspace(L->ws, n, cap, false));
+    STATUS_TRY(ensure_workspace(L->ws, g, cap, false));
     STATUS_TRY(dev_alloc(&L->d_seed, cap));
     STATUS_TRY(dev_alloc(&L->d_sample, cap));
     STATUS_TRY(dev_alloc(&L->d_scale, cap));
@@ -798,8 +803,9 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
     spde_ctx* ctx = L->srv->ctx;
     const spde_opts& o = ctx->opts;
     Level& LV = ctx->lev[L->level];
-    const int n = LV.n, S = L->cap;
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const Grid3 g = LV.g;
+    const int S = L->cap;
+    const int64_t n3 = g.cells(), N4 = 4 * n3;
     const double kh2 = (L->kappa * LV.h) * (L->kappa * LV.h);
     Workspace& ws = L->ws;
     cudaStream_t st = L->st;
@@ -835,8 +841,8 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
     // residual of every occupied column (flux rows exact from theta first)
     for (int c = 0; c < S; ++c) L->h_mask[c] = L->slots[c].used ? 1 : 0;
     CUDA_TRY(cudaMemcpyAsync(L->d_mask, L->h_mask, S * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (any_old) CUDA_TRY(launch_flux_from_theta(n, S, ws.x64, N4, ws.tri, st));
-    const int nbr = launch_residual64(n, kh2, S, ws.F, n3, ws.x64, static_cast<float*>(ws.vec[4]), nullptr, ws.partR,
+    if (any_old) CUDA_TRY(launch_flux_from_theta(g, S, ws.x64, N4, ws.tri, st));
+    const int nbr = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, static_cast<float*>(ws.vec[4]), nullptr, ws.partR,
                                       L->d_mask, st);
     CUDA_TRY(launch_reduce(S, ws.partR, nbr, ws.colv, st));
     CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -906,7 +912,7 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
         CUDA_TRY(cudaMemcpyAsync(L->d_mask, L->h_mask, S * sizeof(int), cudaMemcpyHostToDevice, st));
         CUDA_TRY(launch_set_active(S, L->d_mask, ws.st, st));
         int its = 0;
-        STATUS_TRY(minres_batch<float>(o, n, kh2, S, ws, o.inner_tol, &its, st));
+        STATUS_TRY(minres_batch<float>(o, g, kh2, S, ws, o.inner_tol, &its, st));
         CUDA_TRY(launch_add_theta<float>(n3, S, ws.x64, static_cast<const float*>(ws.vec[0]), ws.st, st));
         for (int c : going) L->slots[c].outer += 1;
     }
@@ -1039,12 +1045,12 @@ void server_dispatch(Server* srv) {
             srv->graveyard.push_back(std::move(it->second));
             srv->lanes.erase(it);
         }
-        const int n = ctx->lev[r->level].n;
-        const int64_t per_col = workspace_bytes(n, 1, false);
+        const Grid3 g = ctx->lev[r->level].g;
+        const int64_t per_col = workspace_bytes(g, 1, false);
         int cap = std::max(1, std::min(o.serve_max_batch, (int)(o.serve_budget_bytes / 4 / std::max<int64_t>(per_col, 1))));
-        while (cap > 1 && srv->used_bytes + workspace_bytes(n, cap, false) + lane_param_bytes(cap) > o.serve_budget_bytes)
+        while (cap > 1 && srv->used_bytes + workspace_bytes(g, cap, false) + lane_param_bytes(cap) > o.serve_budget_bytes)
             cap /= 2;
-        const int64_t need = workspace_bytes(n, cap, false) + lane_param_bytes(cap);
+        const int64_t need = workspace_bytes(g, cap, false) + lane_param_bytes(cap);
         if (srv->used_bytes + need > o.serve_budget_bytes) {
             still.push_back(r);  // wait for a lane to free memory
             continue;
@@ -1056,7 +1062,7 @@ void server_dispatch(Server* srv) {
         L->cap = cap;
         L->bytes = need;
         cudaSetDevice(ctx->opts.device);
-        const spde_status s = lane_alloc(L.get(), n);
+        const spde_status s = lane_alloc(L.get(), g);
         if (s != SPDE_OK) {
             lane_free(L.get());
             still.push_back(r);
@@ -1172,16 +1178,26 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
     return SPDE_OK;
 }
 
-spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]) {
+namespace {
+// a level of nx x ny x nz cells on the box lo .. hi (equal spacing on every axis)
+spde_status level_add_impl(spde_ctx* ctx, int level, const int n[3], const double lo[3], const double hi[3]) {
     if (!ctx || !lo || !hi) return fail(SPDE_EINVAL, "null argument");
     if (level < 0 || level >= 16) return fail(SPDE_EINVAL, "level must lie in [0, 16)");
-    if (!is_pow2(n) || n < 4 || n > 1024) return fail(SPDE_EINVAL, "n must be a power of two in [4, 1024]");
-    const double ext = hi[0] - lo[0];
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a)
+        if (!is_pow2(n[a]) || n[a] < 4 || n[a] > 1024)
+            return fail(SPDE_EINVAL, "cells per axis must be powers of two in [4, 1024]");
+    for (int a = 0; a < 3; ++a)
         if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a]))
             return fail(SPDE_EINVAL, "box must have hi > lo on every axis");
-        if (std::fabs((hi[a] - lo[a]) - ext) > 1e-12 * ext) return fail(SPDE_EINVAL, "cells must be cubes");
-    }
+    const double h = (hi[0] - lo[0]) / n[0];
+    for (int a = 1; a < 3; ++a)
+        if (std::fabs((hi[a] - lo[a]) / n[a] - h) > 1e-12 * h) return fail(SPDE_EINVAL, "cells must be cubes");
+    const Grid3 gr = make_grid(n[0], n[1], n[2]);
+    if (!mg_grid_supported(gr))
+        return fail(SPDE_EINVAL,
+                    "grid %d x %d x %d not supported: the first level whose extents are not multiples of 32 x 16 x 8 "
+                    "must have at most 4096 cells",
+                    n[0], n[1], n[2]);
     std::lock_guard<std::mutex> g(ctx->mu);
     if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; grids cannot change");
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
@@ -1190,10 +1206,29 @@ spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], 
     L.ws.release();
     L.fields.release();
     L.defined = true;
-    L.n = n;
-    L.h = ext / n;
+    L.g = gr;
+    L.h = h;
     for (int a = 0; a < 3; ++a) L.lo[a] = lo[a];
     return SPDE_OK;
+}
+}  // namespace
+
+spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]) {
+    if (!is_pow2(n) || n < 4 || n > 1024) return fail(SPDE_EINVAL, "n must be a power of two in [4, 1024]");
+    if (lo && hi) {
+        const double ext = hi[0] - lo[0];
+        for (int a = 0; a < 3; ++a)
+            if (std::isfinite(lo[a]) && std::isfinite(hi[a]) && hi[a] > lo[a] &&
+                std::fabs((hi[a] - lo[a]) - ext) > 1e-12 * ext)
+                return fail(SPDE_EINVAL, "cells must be cubes (spde_level_add_box takes a box of n[0] x n[1] x n[2] cells)");
+    }
+    const int nn[3] = {n, n, n};
+    return level_add_impl(ctx, level, nn, lo, hi);
+}
+
+spde_status spde_level_add_box(spde_ctx* ctx, int level, const int n[3], const double lo[3], const double hi[3]) {
+    if (!n) return fail(SPDE_EINVAL, "null argument");
+    return level_add_impl(ctx, level, n, lo, hi);
 }
 
 spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const double* xyz, int64_t ntets,
@@ -1218,7 +1253,8 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
     CUDA_TRY(cudaMemcpy(m.tets, tets, (size_t)ntets * 4 * sizeof(int32_t), cudaMemcpyHostToDevice));
     ClipResult res;
     CUDA_TRY(cudaEventRecord(e0, st));
-    cudaError_t e = build_coupling(L.n, L.h, L.lo, nverts, m.xyz, ntets, m.tets, m.vol, &m.rowptr, &m.col, &m.g,
+    const int gn[3] = {L.g.nx, L.g.ny, L.g.nz};
+    cudaError_t e = build_coupling(gn, L.h, L.lo, nverts, m.xyz, ntets, m.tets, m.vol, &m.rowptr, &m.col, &m.g,
                                    &m.pi, &res, st);
     CUDA_TRY(cudaEventRecord(e1, st));
     CUDA_TRY(cudaEventSynchronize(e1));
@@ -1243,7 +1279,7 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
     m.nnz = res.nnz;
     {
         int64_t used = 0;
-        CUDA_TRY(count_used_columns(res.nnz, m.col, (int64_t)L.n * L.n * L.n, &used, st));
+        CUDA_TRY(count_used_columns(res.nnz, m.col, L.g.cells(), &used, st));
         m.ncols_used = used;
     }
     ctx->stats.setup_ms = ms;
@@ -1273,7 +1309,7 @@ spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_
     Level& L = ctx->lev[level];
     L.fields.release();
     if (!kappa_cells) return SPDE_OK;
-    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    const int64_t n3 = L.g.cells();
     double sum = 0.0;
     for (int64_t e = 0; e < n3; ++e) {
         const double k = kappa_cells[e], sg = sigma_cells[e];
@@ -1297,17 +1333,20 @@ spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_
     // multigrid diagonals, level by level: a_0 = (kappa_c h)^2, a_l = mean of the children
     double* a_prev = f.kh2_64;
     double* a_tmp[2] = {dk, ds};  // the device copies of kappa and sigma are free now: reuse them
-    for (int l = 0, nl = L.n; nl >= 1 && l < 16 && st == SPDE_OK && e == cudaSuccess; ++l, nl >>= 1) {
-        const size_t m = (size_t)nl * nl * nl;
+    MGPlan hier;
+    mg_plan_init(hier, L.g, 0.0, ctx->opts.schur_c, ctx->opts.omega);
+    for (int l = 0; l < hier.nlev && st == SPDE_OK && e == cudaSuccess; ++l) {
+        const size_t m = (size_t)hier.g[l].cells();
         st = dev_alloc(&f.D64[l], m);
         if (st == SPDE_OK) st = dev_alloc(&f.D32[l], m);
         if (st != SPDE_OK) break;
         double* a_l = a_prev;
         if (l > 0) {
             a_l = a_tmp[l & 1];
-            e = launch_restrict_mean(2 * nl, a_prev, a_l, 0);
+            e = launch_restrict_mean(hier.g[l - 1], a_prev, a_l, 0);
         }
-        if (e == cudaSuccess) e = launch_level_diag(nl, l, ctx->opts.schur_c, a_l, f.D64[l], f.D32[l], 0);
+        if (e == cudaSuccess)
+            e = launch_level_diag(hier.g[l], hier.ls[l], hier.lq[l], ctx->opts.schur_c, a_l, f.D64[l], f.D32[l], 0);
         a_prev = a_l;
         if (e == cudaSuccess) e = cudaDeviceSynchronize();  // a_tmp alternates: finish before reuse
     }
@@ -1355,16 +1394,16 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
     // plain path: one sample per solve; mixed path: batches that fit in memory
     int cap = 1;
     if (!plain) {
-        if (L.ws.n == L.n && L.ws.S >= nsamples && L.ws.inner64 == 0) cap = nsamples;
+        if (L.ws.g == L.g && L.ws.S >= nsamples && L.ws.inner64 == 0) cap = nsamples;
         else {
             L.ws.release();
-            cap = batch_capacity(L.n, nsamples, false);
+            cap = batch_capacity(L.g, nsamples, false);
         }
     }
     spde_status worst = SPDE_OK;
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
-        STATUS_TRY(ensure_workspace(L.ws, L.n, plain ? 1 : std::min(cap, nsamples), plain));
+        STATUS_TRY(ensure_workspace(L.ws, L.g, plain ? 1 : std::min(cap, nsamples), plain));
         spde_status s = solve_samples(ctx, L, S, kappa, sigma, seed, first_sample + (uint64_t)s0, st,
                                       use_fields ? &L.fields : nullptr);
         if (s != SPDE_OK && s != SPDE_ENOCONV) return s;
@@ -1482,8 +1521,8 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& F = ctx->lev[fine_level];
     Level& C = ctx->lev[coarse_level];
-    if (F.n != 2 * C.n || std::fabs(F.h * 2 - C.h) > 1e-12 * C.h)
-        return fail(SPDE_EINVAL, "coarse grid must be the fine grid coarsened once (n_c = n_f / 2, same box)");
+    if (F.g.nx != 2 * C.g.nx || F.g.ny != 2 * C.g.ny || F.g.nz != 2 * C.g.nz || std::fabs(F.h * 2 - C.h) > 1e-12 * C.h)
+        return fail(SPDE_EINVAL, "coarse grid must be the fine grid coarsened once (half the cells per axis, same box)");
     for (int a = 0; a < 3; ++a)
         if (std::fabs(F.lo[a] - C.lo[a]) > 1e-12 * C.h) return fail(SPDE_EINVAL, "levels must share the box");
     if (kind != SPDE_OUT_GRID_GAUSSIAN && (!F.mesh.rowptr || !C.mesh.rowptr))
@@ -1497,9 +1536,9 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
     ctx->stats.max_rel_residual = 0.0;
     int cap = 1;
     if (!plain) {
-        const int64_t per = workspace_bytes(F.n, 1, false) + workspace_bytes(C.n, 1, false);
+        const int64_t per = workspace_bytes(F.g, 1, false) + workspace_bytes(C.g, 1, false);
         size_t freeb = 0, totb = 0;
-        if (F.ws.n != F.n || F.ws.S < nsamples || C.ws.n != C.n || C.ws.S < nsamples || F.ws.inner64 != 0 ||
+        if (!(F.ws.g == F.g) || F.ws.S < nsamples || !(C.ws.g == C.g) || C.ws.S < nsamples || F.ws.inner64 != 0 ||
             C.ws.inner64 != 0) {
             F.ws.release();
             C.ws.release();
@@ -1509,27 +1548,27 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
             cap = nsamples;
         }
     }
-    const int64_t nf3 = (int64_t)F.n * F.n * F.n, nc3 = (int64_t)C.n * C.n * C.n;
+    const int64_t nf3 = F.g.cells(), nc3 = C.g.cells();
     spde_status worst = SPDE_OK;
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
-        STATUS_TRY(ensure_workspace(F.ws, F.n, plain ? 1 : std::min(cap, nsamples), plain));
-        STATUS_TRY(ensure_workspace(C.ws, C.n, plain ? 1 : std::min(cap, nsamples), plain));
+        STATUS_TRY(ensure_workspace(F.ws, F.g, plain ? 1 : std::min(cap, nsamples), plain));
+        STATUS_TRY(ensure_workspace(C.ws, C.g, plain ? 1 : std::min(cap, nsamples), plain));
         // fine noise, then its restriction (Sec. 6.2: the same xi drives both levels)
         CUDA_TRY(launch_noise(nf3, S, seed, first_sample + (uint64_t)s0, -g_half(kappa, sigma) * F.h, F.ws.F, nf3, st));
-        CUDA_TRY(launch_restrict_rhs(C.n, S, F.ws.F, nf3, C.ws.F, nc3, st));
+        CUDA_TRY(launch_restrict_rhs(C.g, S, F.ws.F, nf3, C.ws.F, nc3, st));
         double rel = 0.0;
         int outer = 0, inner = 0;
         const double khc = (kappa * C.h) * (kappa * C.h), khf = (kappa * F.h) * (kappa * F.h);
-        spde_status sc = plain ? refine_solve<double>(ctx, C.n, khc, S, C.ws, &rel, &outer, &inner, st)
-                               : refine_solve<float>(ctx, C.n, khc, S, C.ws, &rel, &outer, &inner, st);
+        spde_status sc = plain ? refine_solve<double>(ctx, C.g, khc, S, C.ws, &rel, &outer, &inner, st)
+                               : refine_solve<float>(ctx, C.g, khc, S, C.ws, &rel, &outer, &inner, st);
         if (sc != SPDE_OK && sc != SPDE_ENOCONV) return sc;
         if (sc == SPDE_ENOCONV) worst = sc;
         ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, rel);
         // fine solve started from the coarse field (Sec. 6.2, coarse solution as initial guess)
-        CUDA_TRY(launch_inject_theta(C.n, S, C.ws.x64, 4 * nc3, F.ws.x64, 4 * nf3, st));
-        spde_status sf = plain ? refine_solve<double>(ctx, F.n, khf, S, F.ws, &rel, &outer, &inner, st, true)
-                               : refine_solve<float>(ctx, F.n, khf, S, F.ws, &rel, &outer, &inner, st, true);
+        CUDA_TRY(launch_inject_theta(C.g, S, C.ws.x64, 4 * nc3, F.ws.x64, 4 * nf3, st));
+        spde_status sf = plain ? refine_solve<double>(ctx, F.g, khf, S, F.ws, &rel, &outer, &inner, st, true)
+                               : refine_solve<float>(ctx, F.g, khf, S, F.ws, &rel, &outer, &inner, st, true);
         if (sf != SPDE_OK && sf != SPDE_ENOCONV) return sf;
         if (sf == SPDE_ENOCONV) worst = sf;
         ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
@@ -1550,7 +1589,7 @@ spde_status spde_query_footprint(spde_ctx* ctx, int level, int nsamples, int64_t
     if (!bytes || nsamples < 0) return fail(SPDE_EINVAL, "bad argument");
     const Level& L = ctx->lev[level];
     const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
-    *bytes = workspace_bytes(L.n, plain ? 1 : nsamples, plain);
+    *bytes = workspace_bytes(L.g, plain ? 1 : nsamples, plain);
     return SPDE_OK;
 }
 
@@ -1645,18 +1684,34 @@ spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uin
     return SPDE_OK;
 }
 
+namespace {
+bool grid_dims_ok(const int n[3]) {
+    if (!n) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!is_pow2(n[a]) || n[a] < 4 || n[a] > 1024) return false;
+    return true;
+}
+}  // namespace
+
 spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x, void* y, void* stream) {
-    if (!is_pow2(n) || n < 4 || n > 1024 || nsamples < 0 || !(h > 0.0) || !std::isfinite(kappa) || kappa < 0.0)
+    const int nn[3] = {n, n, n};
+    return spde_apply_box(nn, h, kappa, nsamples, prec, x, y, stream);
+}
+
+spde_status spde_apply_box(const int n[3], double h, double kappa, int nsamples, int prec, const void* x, void* y,
+                           void* stream) {
+    if (!grid_dims_ok(n) || nsamples < 0 || !(h > 0.0) || !std::isfinite(kappa) || kappa < 0.0)
         return fail(SPDE_EINVAL, "bad size or parameters");
+    const Grid3 gr = make_grid(n[0], n[1], n[2]);
     if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
     if (nsamples == 0) return SPDE_OK;
     if (!x || !y) return fail(SPDE_EINVAL, "null buffer");
     const double kh2 = (kappa * h) * (kappa * h);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (prec == SPDE_PREC_FP64)
-        CUDA_TRY(launch_apply<double>(n, kh2, nsamples, static_cast<const double*>(x), static_cast<double*>(y), st));
+        CUDA_TRY(launch_apply<double>(gr, kh2, nsamples, static_cast<const double*>(x), static_cast<double*>(y), st));
     else if (prec == SPDE_PREC_MIXED)
-        CUDA_TRY(launch_apply<float>(n, kh2, nsamples, static_cast<const float*>(x), static_cast<float*>(y), st));
+        CUDA_TRY(launch_apply<float>(gr, kh2, nsamples, static_cast<const float*>(x), static_cast<float*>(y), st));
     else
         return fail(SPDE_EINVAL, "bad precision");
     return SPDE_OK;
@@ -1664,7 +1719,8 @@ spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, co
 
 namespace {
 struct PrecondScratch {
-    int n = 0, S = 0, prec = -1;
+    Grid3 g;
+    int S = 0, prec = -1;
     void* mg = nullptr;
     double* part = nullptr;
 };
@@ -1674,8 +1730,16 @@ PrecondScratch g_pc;
 
 spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, const spde_opts* opts, const void* r,
                          void* z, void* stream) {
-    if (!is_pow2(n) || n < 4 || n > 1024 || nsamples < 0 || !(h > 0.0) || !(kappa > 0.0) || !std::isfinite(kappa))
+    const int nn[3] = {n, n, n};
+    return spde_precond_box(nn, h, kappa, nsamples, prec, opts, r, z, stream);
+}
+
+spde_status spde_precond_box(const int n[3], double h, double kappa, int nsamples, int prec, const spde_opts* opts,
+                             const void* r, void* z, void* stream) {
+    if (!grid_dims_ok(n) || nsamples < 0 || !(h > 0.0) || !(kappa > 0.0) || !std::isfinite(kappa))
         return fail(SPDE_EINVAL, "bad size or parameters");
+    const Grid3 gr = make_grid(n[0], n[1], n[2]);
+    if (!mg_grid_supported(gr)) return fail(SPDE_EINVAL, "grid shape not supported by the V-cycle");
     if (nsamples > 65535) return fail(SPDE_EINVAL, "at most 65535 samples per call");
     if (prec != SPDE_PREC_FP64 && prec != SPDE_PREC_MIXED) return fail(SPDE_EINVAL, "bad precision");
     if (nsamples == 0) return SPDE_OK;
@@ -1684,23 +1748,23 @@ spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, 
     spde_opts_init(&o);
     if (opts) o = *opts;
     std::lock_guard<std::mutex> g(g_pc_mu);
-    if (g_pc.n != n || g_pc.S < nsamples || g_pc.prec != prec) {
+    if (!(g_pc.g == gr) || g_pc.S < nsamples || g_pc.prec != prec) {
         if (g_pc.mg) cudaFree(g_pc.mg);
         dev_free(g_pc.part);
         g_pc = PrecondScratch();
-        const size_t b = prec == SPDE_PREC_FP64 ? mg_scratch_elems<double>(n, nsamples) * 8
-                                                 : mg_scratch_elems<float>(n, nsamples) * 4;
+        const size_t b = prec == SPDE_PREC_FP64 ? mg_scratch_elems<double>(gr, nsamples) * 8
+                                                 : mg_scratch_elems<float>(gr, nsamples) * 4;
         if (b) CUDA_TRY(cudaMalloc(&g_pc.mg, b));
         STATUS_TRY(dev_alloc(&g_pc.part, (size_t)nsamples * kMaxPartials));
-        g_pc.n = n;
+        g_pc.g = gr;
         g_pc.S = nsamples;
         g_pc.prec = prec;
     }
     const double kh2 = (kappa * h) * (kappa * h);
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const int64_t n3 = gr.cells(), N4 = 4 * n3;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MGPlan plan;
-    mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
+    mg_plan_init(plan, gr, kh2, o.schur_c, o.omega);
     if (prec == SPDE_PREC_FP64) {
         mg_plan_bind<double>(plan, nsamples, static_cast<double*>(g_pc.mg));
         const double* rr = static_cast<const double*>(r);
@@ -1806,15 +1870,15 @@ spde_status spde_solve(spde_ctx* ctx, int level, int nsamples, double kappa, con
     Level& L = ctx->lev[level];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
-    const int n = L.n;
-    const int64_t n3 = (int64_t)n * n * n, N4 = 4 * n3;
+    const Grid3 gr = L.g;
+    const int64_t n3 = gr.cells(), N4 = 4 * n3;
     const double kh2 = (kappa * L.h) * (kappa * L.h);
     int cap = 1;
     if (!plain) {
-        if (L.ws.n == n && L.ws.S >= nsamples && L.ws.inner64 == 0) cap = nsamples;
+        if (L.ws.g == gr && L.ws.S >= nsamples && L.ws.inner64 == 0) cap = nsamples;
         else {
             L.ws.release();
-            cap = batch_capacity(n, nsamples, false);
+            cap = batch_capacity(gr, nsamples, false);
         }
     }
     ctx->stats.outer_iters = 0;
@@ -1823,13 +1887,13 @@ spde_status spde_solve(spde_ctx* ctx, int level, int nsamples, double kappa, con
     spde_status worst = SPDE_OK;
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
-        STATUS_TRY(ensure_workspace(L.ws, n, plain ? 1 : std::min(cap, nsamples), plain));
+        STATUS_TRY(ensure_workspace(L.ws, gr, plain ? 1 : std::min(cap, nsamples), plain));
         CUDA_TRY(cudaMemcpyAsync(L.ws.F, rhs + (size_t)s0 * n3, (size_t)S * n3 * sizeof(double),
                                  cudaMemcpyDeviceToDevice, st));
         double rel = 0.0;
         int outer = 0, inner = 0;
-        spde_status s = plain ? refine_solve<double>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st)
-                              : refine_solve<float>(ctx, n, kh2, S, L.ws, &rel, &outer, &inner, st);
+        spde_status s = plain ? refine_solve<double>(ctx, gr, kh2, S, L.ws, &rel, &outer, &inner, st)
+                              : refine_solve<float>(ctx, gr, kh2, S, L.ws, &rel, &outer, &inner, st);
         if (s != SPDE_OK && s != SPDE_ENOCONV) return s;
         if (s == SPDE_ENOCONV) worst = s;
         ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, outer);
@@ -1856,7 +1920,7 @@ spde_status spde_project(spde_ctx* ctx, int level, int nsamples, const double* t
     Level& L = ctx->lev[level];
     if (!L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    const int64_t n3 = L.g.cells();
     float* tT = nullptr;
     STATUS_TRY(dev_alloc(&tT, (size_t)nsamples * n3));
     cudaError_t e = launch_transpose_theta(n3, nsamples, theta, n3, 1.0, tT, st);

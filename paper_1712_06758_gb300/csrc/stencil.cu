@@ -1,9 +1,10 @@
 // K2 / K5: the scaled mixed operator (Eq. linsys_blocks) and the FP64
 // refinement residual.
 //
-// Layout of one sample: [ux | uy | uz | theta], each n^3, c = i + n (j + n k).
-// ux[c] is the flux through the +x face of cell c; entries on the wall
-// (i = n-1 for ux, j = n-1 for uy, k = n-1 for uz) are the essential zeros
+// Layout of one sample: [ux | uy | uz | theta], each nx ny nz long,
+// c = i + nx (j + ny k).  ux[c] is the flux through the +x face of cell c;
+// entries on the wall (i = nx-1 for ux, j = ny-1 for uy, k = nz-1 for uz) are
+// the essential zeros
 // u.n = 0 and are never read as unknowns.  Scaled operator:
 //   y_ux = 1/6 ux[i-1] + 2/3 ux[i] + 1/6 ux[i+1] + th[i] - th[i+1]
 //   y_th = sum_axes (u[c] - u[c - e]) - (kappa h)^2 th[c]
@@ -19,16 +20,15 @@ static inline int stencil_blocks(int64_t n3) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply(int n, T kh2, const T* __restrict__ x, T* __restrict__ y) {
-    const int logn = ilog2(n);
-    const int n3 = 1 << (3 * logn);
+__global__ void __launch_bounds__(256) k_apply(Grid3 g, T kh2, const T* __restrict__ x, T* __restrict__ y) {
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int64_t off = (int64_t)blockIdx.y * 4 * n3;
     const T* xs = x + off;
     T* ys = y + off;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (n3 >> 2); q += gridDim.x * blockDim.x) {
-        const QuadPos p = quad_pos(q, logn);
+        const QuadPos p = quad_pos(q, g);
         V4<T> a, b, c, d;
-        apply_quad<T, T>(xs, n, logn, p, kh2, a.v, b.v, c.v, d.v);
+        apply_quad<T, T>(xs, g, p, kh2, a.v, b.v, c.v, d.v);
         st4(ys + p.c, a);
         st4(ys + n3 + p.c, b);
         st4(ys + 2 * n3 + p.c, c);
@@ -37,14 +37,13 @@ __global__ void __launch_bounds__(256) k_apply(int n, T kh2, const T* __restrict
 }
 
 template <typename T>
-cudaError_t launch_apply(int n, double kh2, int S, const T* x, T* y, cudaStream_t st) {
-    const int64_t n3 = (int64_t)n * n * n;
-    dim3 grid(stencil_blocks(n3 / 4), S);
-    k_apply<T><<<grid, 256, 0, st>>>(n, (T)kh2, x, y);
+cudaError_t launch_apply(const Grid3& g, double kh2, int S, const T* x, T* y, cudaStream_t st) {
+    dim3 grid(stencil_blocks(g.cells() / 4), S);
+    k_apply<T><<<grid, 256, 0, st>>>(g, (T)kh2, x, y);
     return cudaGetLastError();
 }
-template cudaError_t launch_apply<float>(int, double, int, const float*, float*, cudaStream_t);
-template cudaError_t launch_apply<double>(int, double, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_apply<float>(const Grid3&, double, int, const float*, float*, cudaStream_t);
+template cudaError_t launch_apply<double>(const Grid3&, double, int, const double*, double*, cudaStream_t);
 
 // r = [0; F] - A x in FP64; optional float and double copies; partial r.r.
 // Every caller forms the flux of x exactly from its cell field first
@@ -52,15 +51,14 @@ template cudaError_t launch_apply<double>(int, double, int, const double*, doubl
 // r vanish up to the rounding of those solves: they are written as zeros and
 // only the cell row  F - (D1 u - (kappa h)^2 theta)  is formed (the FP64
 // arithmetic, the rate-limiting unit here, drops to a third).
-__global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const double* __restrict__ F, int64_t F_stride,
+__global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const double* __restrict__ F, int64_t F_stride,
                                                     const double* __restrict__ x, float* __restrict__ r32,
                                                     double* __restrict__ r64, double* __restrict__ part,
                                                     const int* __restrict__ active, const double* __restrict__ kh2c) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     if (active && !active[s]) return;
-    const int logn = ilog2(n);
-    const int n3 = 1 << (3 * logn);
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int64_t off = (int64_t)s * 4 * n3;
     const double* xs = x + off;
     const double* ux = xs;
@@ -68,13 +66,13 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
     const double* uz = xs + 2 * n3;
     const double* th = xs + 3 * n3;
     const double* Fs = F + (int64_t)s * F_stride;
-    const int sy = n, sz = n << logn;
+    const int sy = g.nx, sz = g.nx << g.ly;
     double acc = 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (n3 >> 2); q += gridDim.x * blockDim.x) {
-        const QuadPos p = quad_pos(q, logn);
+        const QuadPos p = quad_pos(q, g);
         const int c = p.c;
-        const bool jl = p.j > 0, jh = p.j < n - 1;
-        const bool kl = p.k > 0, kh = p.k < n - 1;
+        const bool jl = p.j > 0, jh = p.j < g.ny - 1;
+        const bool kl = p.k > 0, kh = p.k < g.nz - 1;
         const V4<double> ux4 = ld4(ux + c), uy4 = ld4(uy + c), uz4 = ld4(uz + c), th4 = ld4(th + c);
         const V4<double> uyM = jl ? ld4(uy + c - sy) : zero4<double>();
         const V4<double> uzM = kl ? ld4(uz + c - sz) : zero4<double>();
@@ -89,7 +87,7 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int i = p.i0 + e;
-            const double ux0 = (i < n - 1) ? ux4.v[e] : 0.0;
+            const double ux0 = (i < g.nx - 1) ? ux4.v[e] : 0.0;
             const double uxm = (e > 0) ? ux4.v[e - 1] : uxL;
             const double uy0 = jh ? uy4.v[e] : 0.0;
             const double uz0 = kh ? uz4.v[e] : 0.0;
@@ -121,57 +119,61 @@ __global__ void __launch_bounds__(256) k_residual64(int n, double kh2, const dou
     if (threadIdx.x == 0) part[(int64_t)s * kMaxPartials + blockIdx.x] = t;
 }
 
-int launch_residual64(int n, double kh2, int S, const double* F, int64_t F_stride, const double* x, float* r32,
-                      double* r64, double* part, const int* active, cudaStream_t st, const double* kh2c) {
-    const int64_t n3 = (int64_t)n * n * n;
-    const int nb = stencil_blocks(n3 / 4);
+int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
+                      float* r32, double* r64, double* part, const int* active, cudaStream_t st, const double* kh2c) {
+    const int nb = stencil_blocks(g.cells() / 4);
     dim3 grid(nb, S);
-    k_residual64<<<grid, 256, 0, st>>>(n, kh2, F, F_stride, x, r32, r64, part, active, kh2c);
+    k_residual64<<<grid, 256, 0, st>>>(g, kh2, F, F_stride, x, r32, r64, part, active, kh2c);
     return nb;
 }
 
-// a_c = mean of the 8 children of coarse cell c (fine grid nf, coarse nf / 2)
-__global__ void __launch_bounds__(256) k_restrict_mean(int nf, const double* __restrict__ af, double* __restrict__ ac) {
-    const int nc = nf >> 1;
-    const int64_t n3 = (int64_t)nc * nc * nc;
+// a_c = mean of the children of coarse cell c: the fine grid gf, the coarse grid
+// gf.coarser() (2 children along every axis that is coarsened, 1 along an axis
+// of extent 1)
+__global__ void __launch_bounds__(256) k_restrict_mean(Grid3 gf, const double* __restrict__ af, double* __restrict__ ac) {
+    const Grid3 gc = gf.coarser();
+    const int64_t n3 = gc.cells();
+    const int dx = gf.nx > 1 ? 2 : 1, dy = gf.ny > 1 ? 2 : 1, dz = gf.nz > 1 ? 2 : 1;
+    const double inv = 1.0 / (double)(dx * dy * dz);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
-        const int I = (int)(e % nc), J = (int)((e / nc) % nc), K = (int)(e / ((int64_t)nc * nc));
+        const int I = (int)(e & (gc.nx - 1)), J = (int)((e >> gc.lx) & (gc.ny - 1)), K = (int)(e >> (gc.lx + gc.ly));
         double sum = 0.0;
-        for (int dk = 0; dk < 2; ++dk)
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di)
-                    sum += af[(2 * I + di) + (int64_t)nf * ((2 * J + dj) + (int64_t)nf * (2 * K + dk))];
-        ac[e] = 0.125 * sum;
+        for (int dk = 0; dk < dz; ++dk)
+            for (int dj = 0; dj < dy; ++dj)
+                for (int di = 0; di < dx; ++di)
+                    sum += af[(dx * I + di) + (int64_t)gf.nx * ((dy * J + dj) + (int64_t)gf.ny * (dz * K + dk))];
+        ac[e] = inv * sum;
     }
 }
 
-cudaError_t launch_restrict_mean(int nf, const double* af, double* ac, cudaStream_t st) {
-    const int64_t nc3 = (int64_t)(nf / 2) * (nf / 2) * (nf / 2);
+cudaError_t launch_restrict_mean(const Grid3& gf, const double* af, double* ac, cudaStream_t st) {
+    const int64_t nc3 = gf.coarser().cells();
     int64_t b = (nc3 + 255) / 256;
     if (b > 4096) b = 4096;
-    k_restrict_mean<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(nf, af, ac);
+    k_restrict_mean<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(gf, af, ac);
     return cudaGetLastError();
 }
 
-// D = 2^l (a 4^l + c k) per cell of level l (n cells per axis), FP64 and FP32
-__global__ void __launch_bounds__(256) k_level_diag(int n, int l, double c, const double* __restrict__ a,
+// D = s (a q + c k) per cell of a level (s, q: the level's Laplacian weight and
+// mass-to-Laplacian factor, 2^l and 4^l on a cube), FP64 and FP32
+__global__ void __launch_bounds__(256) k_level_diag(Grid3 g, double s, double q, double c, const double* __restrict__ a,
                                                     double* __restrict__ D64, float* __restrict__ D32) {
-    const int64_t n3 = (int64_t)n * n * n;
-    const double s = (double)(1 << l), q = (double)(1ll << (2 * l));
+    const int64_t n3 = g.cells();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % n), j = (int)((e / n) % n), k = (int)(e / ((int64_t)n * n));
-        const int kc = nb_count1(i, n) + nb_count1(j, n) + nb_count1(k, n);
+        const int i = (int)(e & (g.nx - 1)), j = (int)((e >> g.lx) & (g.ny - 1)), k = (int)(e >> (g.lx + g.ly));
+        const int kc = nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz);
         const double d = s * (a[e] * q + c * kc);
         D64[e] = d;
         D32[e] = (float)d;
     }
 }
 
-cudaError_t launch_level_diag(int n, int l, double c, const double* a, double* D64, float* D32, cudaStream_t st) {
-    const int64_t n3 = (int64_t)n * n * n;
+cudaError_t launch_level_diag(const Grid3& g, double s, double q, double c, const double* a, double* D64, float* D32,
+                              cudaStream_t st) {
+    const int64_t n3 = g.cells();
     int64_t b = (n3 + 255) / 256;
     if (b > 4096) b = 4096;
-    k_level_diag<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(n, l, c, a, D64, D32);
+    k_level_diag<<<(unsigned)(b < 1 ? 1 : b), 256, 0, st>>>(g, s, q, c, a, D64, D32);
     return cudaGetLastError();
 }
 
@@ -268,69 +270,75 @@ cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cuda
 // ---------------------------------------------------------------------------
 // Exact flux of a cell field: u = -T^{-1} D1^T theta, i.e. the first block row
 // of the scaled system (T u + D1^T theta = 0) solved line by line.  T is
-// tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of every line; the wall
-// face (index n-1 in the line) stays 0.  Thomas elimination with the
-// line-independent factors tri[0..n-2] = c'_f (super-diagonal after
-// elimination) and tri[n-1 .. 2n-3] = 1 / pivot_f, computed on the host.
-// One thread per line; consecutive threads take neighbouring lines.
+// tridiag(1/6, 2/3, 1/6) on the m-1 interior faces of a line of m cells; the
+// wall face (index m-1 in the line) stays 0.  Thomas elimination with the
+// factors c'_f (super-diagonal after elimination) and 1 / pivot_f, which
+// depend only on f, not on the line's length: tri[0 .. tn-2] = c'_f and
+// tri[tn-1 .. 2tn-3] = 1 / pivot_f for the longest extent tn, computed on the
+// host, serve every axis.  One thread per line; consecutive threads take
+// neighbouring lines.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_flux_lines(int n, int logn, int axis, const double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_flux_lines(Grid3 g, int tn, int axis, const double* __restrict__ x,
                                                     double* __restrict__ xu, int64_t col_stride,
                                                     const double* __restrict__ tri) {
     const int L = blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= (1 << (2 * logn))) return;
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
+    const int m = g.ext(axis);
+    if (L >= (n3 >> (axis == 0 ? g.lx : (axis == 1 ? g.ly : g.lz)))) return;
     const int64_t off = (int64_t)blockIdx.y * col_stride;
-    const int n3 = 1 << (3 * logn);
     const double* th = x + off + 3 * (int64_t)n3;
     double* u = xu + off + (int64_t)axis * n3;
     int base, stride;
     if (axis == 0) {  // lines along x, indexed by (j, k)
-        base = L << logn;
+        base = L << g.lx;
         stride = 1;
     } else if (axis == 1) {  // along y, indexed by (i, k)
-        base = (L & (n - 1)) + ((L >> logn) << (2 * logn));
-        stride = n;
+        base = (L & (g.nx - 1)) + ((L >> g.lx) << (g.lx + g.ly));
+        stride = g.nx;
     } else {  // along z, indexed by (i, j)
         base = L;
-        stride = n << logn;
+        stride = g.nx << g.ly;
     }
     const double* cp = tri;
-    const double* inv = tri + (n - 1);
+    const double* inv = tri + (tn - 1);
     const double a = 1.0 / 6.0;
     // forward elimination of T u = -(theta_f - theta_{f+1}) = theta_{f+1} - theta_f
     double prev = 0.0, tcur = th[base];
-    for (int f = 0; f < n - 1; ++f) {
+    for (int f = 0; f < m - 1; ++f) {
         const double tnext = th[base + (f + 1) * stride];
         const double dp = ((tnext - tcur) - a * prev) * inv[f];
         u[base + f * stride] = dp;
         prev = dp;
         tcur = tnext;
     }
-    u[base + (n - 1) * stride] = 0.0;
+    u[base + (m - 1) * stride] = 0.0;
     // back substitution
     double xn = prev;
-    for (int f = n - 3; f >= 0; --f) {
+    for (int f = m - 3; f >= 0; --f) {
         const double xf = u[base + f * stride] - cp[f] * xn;
         u[base + f * stride] = xf;
         xn = xf;
     }
 }
 
-// Lines along x are contiguous rows: a CTA stages kRowLines(n) consecutive rows
+// Lines along x are contiguous rows: a CTA stages row_lines consecutive rows
 // of theta in shared memory (coalesced), each thread solves one row in place
 // there, and the tile goes back to the ux block coalesced.
 constexpr int kRowTileElems = 8192;  // doubles of one staged tile (64 KB)
-static inline int row_lines(int n) {
+static inline int row_lines(const Grid3& g) {
+    const int n = g.nx;
+    const int rows = 1 << (g.ly + g.lz);
     const int lr = n >= kRowTileElems / 32 ? kRowTileElems / n : 32;
-    return lr < n * n ? lr : n * n;  // n = 4 has only 16 rows
+    return lr < rows ? lr : rows;  // a 4 x 4 x 4 grid has only 16 rows
 }
 
-__global__ void __launch_bounds__(128) k_flux_rows(int n, int logn, int lines_per_cta, const double* __restrict__ x,
+__global__ void __launch_bounds__(128) k_flux_rows(Grid3 g, int tn, int lines_per_cta, const double* __restrict__ x,
                                                    double* __restrict__ xu, int64_t col_stride,
                                                    const double* __restrict__ tri) {
-    extern __shared__ double srow[];  // lines_per_cta rows of n + 1 (padded against bank conflicts)
+    extern __shared__ double srow[];  // lines_per_cta rows of nx + 1 (padded against bank conflicts)
+    const int n = g.nx, logn = g.lx;
     const int64_t off = (int64_t)blockIdx.y * col_stride;
-    const int n3 = 1 << (3 * logn);
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int64_t row0 = (int64_t)blockIdx.x * lines_per_cta;  // first (j, k) row of the tile
     const double* th = x + off + 3 * (int64_t)n3 + (row0 << logn);
     double* u = xu + off + (row0 << logn);
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(128) k_flux_rows(int n, int logn, int lines_pe
     for (int e = threadIdx.x; e < tile; e += blockDim.x) srow[(e >> logn) * (n + 1) + (e & (n - 1))] = th[e];
     __syncthreads();
     const double* cp = tri;
-    const double* inv = tri + (n - 1);
+    const double* inv = tri + (tn - 1);
     const double a = 1.0 / 6.0;
     for (int L = threadIdx.x; L < lines_per_cta; L += blockDim.x) {
         double* r = srow + L * (n + 1);
@@ -369,16 +377,20 @@ static cudaError_t flux_rows_attr() {
     return e;
 }
 
-cudaError_t launch_flux_from_theta(int n, int S, double* x, int64_t col_stride, const double* tri, cudaStream_t st) {
-    const int logn = 31 - __builtin_clz(n);
-    const int lines = n * n;
-    const int lr = row_lines(n);
+cudaError_t launch_flux_from_theta(const Grid3& g, int S, double* x, int64_t col_stride, const double* tri,
+                                   cudaStream_t st) {
+    const int tn = g.maxn();
+    const int rows = 1 << (g.ly + g.lz);
+    const int lr = row_lines(g);
     const cudaError_t ea = flux_rows_attr();
     if (ea != cudaSuccess) return ea;
-    dim3 grow(lines / lr, S);
-    k_flux_rows<<<grow, 128, (size_t)lr * (n + 1) * sizeof(double), st>>>(n, logn, lr, x, x, col_stride, tri);
-    dim3 grid((lines + 255) / 256, S);
-    for (int axis = 1; axis < 3; ++axis) k_flux_lines<<<grid, 256, 0, st>>>(n, logn, axis, x, x, col_stride, tri);
+    dim3 grow(rows / lr, S);
+    k_flux_rows<<<grow, 128, (size_t)lr * (g.nx + 1) * sizeof(double), st>>>(g, tn, lr, x, x, col_stride, tri);
+    for (int axis = 1; axis < 3; ++axis) {
+        const int lines = (int)(g.cells() / g.ext(axis));
+        dim3 grid((lines + 255) / 256, S);
+        k_flux_lines<<<grid, 256, 0, st>>>(g, tn, axis, x, x, col_stride, tri);
+    }
     return cudaGetLastError();
 }
 
@@ -411,60 +423,60 @@ template cudaError_t launch_add_theta<double>(int64_t, int, double*, const doubl
 // f = W^{1/2} xi this has exactly the coarse covariance W_c).  In the scaled
 // system (cell rows scaled by h^{-1/2}) that is F_c = (1/sqrt 2) sum F_f.
 // ---------------------------------------------------------------------------
-__global__ void k_restrict_rhs(int nc, const double* __restrict__ Ff, int64_t f_stride, double* __restrict__ Fc,
+__global__ void k_restrict_rhs(Grid3 gc, const double* __restrict__ Ff, int64_t f_stride, double* __restrict__ Fc,
                                int64_t c_stride) {
     const int s = blockIdx.y;
-    const int nf = 2 * nc;
-    const int64_t nc3 = (int64_t)nc * nc * nc;
+    const int nfx = 2 * gc.nx, nfy = 2 * gc.ny;  // the fine grid is twice the coarse one along every axis
+    const int64_t nc3 = gc.cells();
     const double* fs = Ff + (int64_t)s * f_stride;
     double* cs = Fc + (int64_t)s * c_stride;
     const double w = 0.70710678118654752440;  // 1 / sqrt(2)
     for (int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; C < nc3; C += (int64_t)gridDim.x * blockDim.x) {
-        const int I = (int)(C % nc), J = (int)((C / nc) % nc), K = (int)(C / ((int64_t)nc * nc));
+        const int I = (int)(C & (gc.nx - 1)), J = (int)((C >> gc.lx) & (gc.ny - 1)), K = (int)(C >> (gc.lx + gc.ly));
         double acc = 0.0;
         for (int dk = 0; dk < 2; ++dk)
             for (int dj = 0; dj < 2; ++dj)
                 for (int di = 0; di < 2; ++di)
-                    acc += fs[(2 * I + di) + (int64_t)nf * ((2 * J + dj) + (int64_t)nf * (2 * K + dk))];
+                    acc += fs[(2 * I + di) + (int64_t)nfx * ((2 * J + dj) + (int64_t)nfy * (2 * K + dk))];
         cs[C] = w * acc;
     }
 }
 
-cudaError_t launch_restrict_rhs(int nc, int S, const double* Ff, int64_t f_stride, double* Fc, int64_t c_stride,
-                                cudaStream_t st) {
-    const int64_t nc3 = (int64_t)nc * nc * nc;
+cudaError_t launch_restrict_rhs(const Grid3& gc, int S, const double* Ff, int64_t f_stride, double* Fc,
+                                int64_t c_stride, cudaStream_t st) {
+    const int64_t nc3 = gc.cells();
     int64_t b = (nc3 + 255) / 256;
     if (b > 4096) b = 4096;
     dim3 grid((unsigned)(b < 1 ? 1 : b), S);
-    k_restrict_rhs<<<grid, 256, 0, st>>>(nc, Ff, f_stride, Fc, c_stride);
+    k_restrict_rhs<<<grid, 256, 0, st>>>(gc, Ff, f_stride, Fc, c_stride);
     return cudaGetLastError();
 }
 
 // Fine initial cell field = coarse field injected (piecewise-constant P of
 // Sec. 6.1): physical theta_f = theta_c(parent), i.e. scaled
 // theta~_f = theta~_c / sqrt 2 (cell scaling h^{1/2}, H = 2h).  Writes the
-// cell block of xf (stride 4 nf^3); the flux blocks are recomputed later.
-__global__ void k_inject_theta(int nc, const double* __restrict__ xc, int64_t c_stride, double* __restrict__ xf,
+// cell block of xf (stride 4 x the fine cells); the flux blocks are recomputed later.
+__global__ void k_inject_theta(Grid3 gc, const double* __restrict__ xc, int64_t c_stride, double* __restrict__ xf,
                                int64_t f_stride) {
     const int s = blockIdx.y;
-    const int nf = 2 * nc;
-    const int64_t nf3 = (int64_t)nf * nf * nf, nc3 = (int64_t)nc * nc * nc;
+    const int64_t nc3 = gc.cells(), nf3 = 8 * nc3;
+    const int lfx = gc.lx + 1, lfy = gc.ly + 1;
     const double* tc = xc + (int64_t)s * c_stride + 3 * nc3;
     double* tf = xf + (int64_t)s * f_stride + 3 * nf3;
     const double w = 0.70710678118654752440;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nf3; c += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nf), j = (int)((c / nf) % nf), k = (int)(c / ((int64_t)nf * nf));
-        tf[c] = w * tc[(i >> 1) + (int64_t)nc * ((j >> 1) + (int64_t)nc * (k >> 1))];
+        const int i = (int)(c & ((1 << lfx) - 1)), j = (int)((c >> lfx) & ((1 << lfy) - 1)), k = (int)(c >> (lfx + lfy));
+        tf[c] = w * tc[(i >> 1) + (int64_t)gc.nx * ((j >> 1) + (int64_t)gc.ny * (k >> 1))];
     }
 }
 
-cudaError_t launch_inject_theta(int nc, int S, const double* xc, int64_t c_stride, double* xf, int64_t f_stride,
-                                cudaStream_t st) {
-    const int64_t nf3 = 8LL * nc * nc * nc;
+cudaError_t launch_inject_theta(const Grid3& gc, int S, const double* xc, int64_t c_stride, double* xf,
+                                int64_t f_stride, cudaStream_t st) {
+    const int64_t nf3 = 8 * gc.cells();
     int64_t b = (nf3 + 255) / 256;
     if (b > 4096) b = 4096;
     dim3 grid((unsigned)b, S);
-    k_inject_theta<<<grid, 256, 0, st>>>(nc, xc, c_stride, xf, f_stride);
+    k_inject_theta<<<grid, 256, 0, st>>>(gc, xc, c_stride, xf, f_stride);
     return cudaGetLastError();
 }
 
