@@ -22,13 +22,15 @@
  *     convergence synchronise it before returning (stated per function).
  *   - A context serialises calls on itself with an internal mutex.
  *
- * Discrete system (scaled form).  Grid: n^3 cubes of edge h.  The mixed
- * unknowns of one sample are stored as four contiguous n^3 arrays
- * [ux | uy | uz | theta], each indexed c = i + n (j + n k) (x fastest).
+ * Discrete system (scaled form).  Grid: N = nx ny nz cubes of edge h (a cube
+ * n^3 from spde_level_add, a box from spde_level_add_box; "n^3" below means N
+ * and "i + n (j + n k)" means i + nx (j + ny k) on a box).  The mixed
+ * unknowns of one sample are stored as four contiguous N-entry arrays
+ * [ux | uy | uz | theta], each indexed c = i + nx (j + ny k) (x fastest).
  * ux[c] is the normal flux through the +x face of cell c (the face between
- * cells i and i+1); the entry with i = n-1 lies on the box wall and is held
- * at 0 (essential condition u.n = 0, Sec. 4.2); likewise uy (j = n-1) and
- * uz (k = n-1).  With D = diag(h^{-3/2} on fluxes, h^{-1/2} on cells) the
+ * cells i and i+1); the entry with i = nx-1 lies on the box wall and is held
+ * at 0 (essential condition u.n = 0, Sec. 4.2); likewise uy (j = ny-1) and
+ * uz (k = nz-1).  With D = diag(h^{-3/2} on fluxes, h^{-1/2} on cells) the
  * library solves the symmetrically scaled system  (D A D) (D^{-1} U) = D F,
  * where A = [[M, B^T], [B, -kappa^2 W]] (Eq. linsys_blocks):
  *     y_u   = T u + D1^T theta,   T = tridiag(1/6, 2/3, 1/6) along each
