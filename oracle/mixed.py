@@ -285,11 +285,11 @@ def restrict_noise(xi_f, n_f):
     cell's value copied to its 8 children).  Written as f_c = W_c^{1/2} xi_c,
     xi_c = W_c^{-1/2} P^T W_f^{1/2} xi_f.  Input/output flat, x fastest.
     """
-    n_c = n_f // 2
-    h_f = 1.0 / n_f
-    h_c = 1.0 / n_c
-    f = (h_f ** 1.5) * np.asarray(xi_f, dtype=np.float64).reshape(n_f, n_f, n_f)
-    fc = f.reshape(n_c, 2, n_c, 2, n_c, 2).sum(axis=(1, 3, 5))
+    nx, ny, nz = _dims(n_f)  # one extent (a cube) or the fine box's (nx, ny, nz), all even
+    h_f = 1.0
+    h_c = 2.0 * h_f
+    f = (h_f ** 1.5) * np.asarray(xi_f, dtype=np.float64).reshape(nz, ny, nx)
+    fc = f.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).sum(axis=(1, 3, 5))
     return (fc / h_c ** 1.5).ravel()
 
 

@@ -152,3 +152,53 @@ def test_box_argument_errors():
     with pytest.raises(pkg.SpdeError):  # the Schur-CG option needs a cube
         sch.sample(0, 1, 20.0, 1.0, 1, 0, pkg.SPDE_OUT_GRID_GAUSSIAN)
     sch.close()
+
+
+def test_box_coupled_two_level_sample():
+    """Sec. 6.2's coupled pair on box grids: the coarse level halves every extent."""
+    fdims, cdims = (64, 32, 16), (32, 16, 8)
+    h, kappa, sigma, ns, seed = 1.0 / 32, 20.0, 1.0, 2, 9
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED)
+    hi = (fdims[0] * h, fdims[1] * h, fdims[2] * h)
+    smp.add_level(0, fdims, (0.0, 0.0, 0.0), hi)
+    smp.add_level(1, cdims, (0.0, 0.0, 0.0), hi)
+    kind = pkg.SPDE_OUT_GRID_GAUSSIAN | pkg.SPDE_OUT_F64
+    nf, nc = int(np.prod(fdims)), int(np.prod(cdims))
+    fine = torch.zeros((ns, nf), dtype=torch.float64, device=DEV)
+    coarse = torch.zeros((ns, nc), dtype=torch.float64, device=DEV)
+    pkg.spde_sample_coupled(smp.ctx, 0, 1, ns, kappa, sigma, seed, 0, kind, fine, coarse)
+    xi = philox.normals_batch(nf, seed, 0, ns)
+    ref_f = mixed.solve_dct(fdims, kappa, sigma, xi, h=h)
+    ref_c = mixed.solve_dct(cdims, kappa, sigma, np.stack([mixed.restrict_noise(x, fdims) for x in xi]), h=2 * h)
+    assert rel(fine.cpu().numpy(), ref_f) <= 1e-8
+    assert rel(coarse.cpu().numpy(), ref_c) <= 1e-8
+    smp.close()
+
+
+def test_box_serving_matches_sample():
+    """Requests on a box level through the serving engine equal spde_sample bit for bit."""
+    dims, h = (64, 32, 16), 1.0 / 32
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, serve_max_batch=4)
+    smp.add_level(0, dims, (0.0, 0.0, 0.0), tuple(h * v for v in dims))
+    kind = pkg.SPDE_OUT_GRID_GAUSSIAN
+    outs = []
+    for k, ns in enumerate((3, 5, 1)):
+        out = torch.full((ns, int(np.prod(dims))), float("nan"), dtype=torch.float32, device=DEV)
+        rid = pkg.spde_submit(smp.ctx, 0, ns, 20.0, 1.0 + 0.25 * k, 40 + k, 3 * k, kind, out)
+        outs.append((rid, ns, k, out))
+    import time
+    pending = {o[0] for o in outs}
+    t0 = time.time()
+    while pending and time.time() - t0 < 120:
+        for rid in list(pending):
+            done, _, st = pkg.spde_poll(smp.ctx, rid)
+            if done:
+                assert st == pkg.SPDE_OK
+                pending.discard(rid)
+        time.sleep(0.002)
+    assert not pending
+    for rid, ns, k, out in outs:
+        alone = torch.full_like(out, float("nan"))
+        pkg.spde_sample(smp.ctx, 0, ns, 20.0, 1.0 + 0.25 * k, 40 + k, 3 * k, kind, alone)
+        assert torch.equal(out, alone)
+    smp.close()

@@ -113,3 +113,17 @@ def test_coupling_rows_on_a_box_grid():
         hexid = t // 6  # six tets per hex, hexes x fastest
         assert list(row) == [hexid]
         assert abs(row[hexid] - h ** 3 / 6.0) <= 1e-15
+
+
+def test_restrict_noise_on_a_box():
+    """Coupled sampling's coarse normals on a box: each coarse cell sums its 8 children,
+    times (h_f / h_c)^{3/2} = 2^{-3/2}; checked by an explicit loop."""
+    nx, ny, nz = 4, 2, 6
+    xi = np.random.default_rng(3).standard_normal(nx * ny * nz)
+    got = mixed.restrict_noise(xi, (nx, ny, nz))
+    ref = np.zeros((nx // 2) * (ny // 2) * (nz // 2))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                ref[(i // 2) + (nx // 2) * ((j // 2) + (ny // 2) * (k // 2))] += xi[i + nx * (j + ny * k)]
+    assert np.allclose(got, ref * 2.0 ** -1.5, rtol=1e-14, atol=0)
