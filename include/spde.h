@@ -88,8 +88,11 @@ enum {
 typedef struct {
     int precision;      /* SPDE_PREC_MIXED (default) or SPDE_PREC_FP64 */
     double tol;         /* stop when ||F - A x||_2 / ||F||_2 <= tol (scaled system, FP64); 1e-10 */
-    double inner_tol;   /* FP32 inner MINRES: stop when its preconditioned residual
-                           estimate drops by this factor; 1e-5 */
+    double inner_tol;   /* FP32 inner MINRES: stop when a column's preconditioned
+                           residual estimate drops by this factor, or by
+                           0.1 tol / (the column's current relative residual)
+                           when that is larger (a last step that needs less does
+                           not over-solve); 1e-5 */
     int max_outer;      /* refinement steps (mixed path); 8 */
     int max_iter;       /* MINRES iterations per solve; 400 */
     double omega;       /* damped-Jacobi weight of the V-cycle smoother; 0.8 */

@@ -181,8 +181,10 @@ cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cud
 // [1] += columns whose w/x update this step left pending
 cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC,
                           MinresCol* st_, int* nactive, cudaStream_t st);
+// col_tol (device [S], optional): each column's own stopping tolerance instead of tol
 cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC,
-                               double tol, MinresCol* st_, int* nactive, cudaStream_t st);
+                               double tol, MinresCol* st_, int* nactive, cudaStream_t st,
+                               const double* col_tol = nullptr);
 // cell-block update: w1, w2, x are [S][n^3]; ycur is [S][4 n^3]
 template <typename T>
 cudaError_t launch_minres_D(int64_t n3, int S, const T* ycur, T* w1, const T* w2, T* x,

@@ -339,7 +339,8 @@ cudaError_t launch_givens(int S, const double* partB, int nB, const double* part
 
 __global__ void __launch_bounds__(256) k_minres_init(const double* __restrict__ partB, int nB,
                                                      const double* __restrict__ partC, int nC, double tol,
-                                                     MinresCol* __restrict__ st, int* __restrict__ nactive) {
+                                                     MinresCol* __restrict__ st, int* __restrict__ nactive,
+                                                     const double* __restrict__ col_tol) {
     __shared__ double red[8];
     const int s = blockIdx.x;
     MinresCol& c = st[s];
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(256) k_minres_init(const double* __restrict__ 
     c.delta = 0.0;
     c.phi = 0.0;
     c.beta1 = beta1;
-    c.tol = tol;
+    c.tol = col_tol ? col_tol[s] : tol;
     c.upd = 0;
     c.iters = 0;
     set_coef(c, KC_IB, 1.0 / beta1);
@@ -375,8 +376,8 @@ __global__ void __launch_bounds__(256) k_minres_init(const double* __restrict__ 
 }
 
 cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC, double tol,
-                               MinresCol* st_, int* nactive, cudaStream_t st) {
-    k_minres_init<<<S, 256, 0, st>>>(partB, nB, partC, nC, tol, st_, nactive);
+                               MinresCol* st_, int* nactive, cudaStream_t st, const double* col_tol) {
+    k_minres_init<<<S, 256, 0, st>>>(partB, nB, partC, nC, tol, st_, nactive, col_tol);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,15 @@ spde_status fail(spde_status s, const char* fmt, ...) {
 // (4 pi)^{3/4} kappa^{1/2} sqrt(Gamma(2) / Gamma(1/2)) sigma = sqrt(8 pi kappa) sigma
 double g_half(double kappa, double sigma) { return sigma * std::sqrt(8.0 * M_PI * kappa); }
 
+// Reduction the FP32 inner solve of a column aims for in one refinement step:
+// opts.inner_tol (its precision floor), loosened to what the column still needs,
+// 0.1 tol / rel, when that is larger (the last step of a solve to 1e-8 need not
+// reach 1e-5).  A function of the column's own residual only, so a column's
+// iterates do not depend on the other columns of its batch.
+double inner_tol_for(const spde_opts& o, double rel) {
+    return std::max(o.inner_tol, 0.1 * o.tol / std::max(rel, 1e-300));
+}
+
 // MINRES iterations between two host checks of the active columns at most
 constexpr int kMaxChunk = 64;
 
@@ -106,6 +115,8 @@ struct Workspace {
     double* partC = nullptr;
     double* partR = nullptr;
     double* colv = nullptr;  // [2S] per-column reductions
+    double* coltol = nullptr;  // [S] per-column tolerance of the FP32 inner solve
+    double* h_tol = nullptr;   // pinned [S]
     MinresCol* st = nullptr;
     int* nact = nullptr;
     int* h_nact = nullptr;   // pinned
@@ -127,6 +138,7 @@ struct Workspace {
         dev_free(partC);
         dev_free(partR);
         dev_free(colv);
+        dev_free(coltol);
         dev_free(st);
         dev_free(nact);
         dev_free(thetaT);
@@ -136,6 +148,8 @@ struct Workspace {
         if (h_nact) cudaFreeHost(h_nact);
         if (h_col) cudaFreeHost(h_col);
         if (h_st) cudaFreeHost(h_st);
+        if (h_tol) cudaFreeHost(h_tol);
+        h_tol = nullptr;
         h_nact = nullptr;
         h_col = nullptr;
         h_st = nullptr;
@@ -261,6 +275,7 @@ spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64)
     STATUS_TRY(dev_alloc(&ws.partC, (size_t)S * kMaxPartials));
     STATUS_TRY(dev_alloc(&ws.partR, (size_t)S * kMaxPartials));
     STATUS_TRY(dev_alloc(&ws.colv, (size_t)2 * S));
+    STATUS_TRY(dev_alloc(&ws.coltol, (size_t)S));
     STATUS_TRY(dev_alloc(&ws.st, (size_t)S));
     STATUS_TRY(dev_alloc(&ws.cg, (size_t)S));
     // per MINRES iteration of a chunk: [2q] columns still active after it, [2q+1] columns it left an update pending
@@ -290,7 +305,8 @@ spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64)
     }
     if (cudaMallocHost(&ws.h_nact, 2 * kMaxChunk * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ws.h_col, 2 * S * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&ws.h_st, S * sizeof(MinresCol)) != cudaSuccess) {
+        cudaMallocHost(&ws.h_st, S * sizeof(MinresCol)) != cudaSuccess ||
+        cudaMallocHost(&ws.h_tol, S * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         ws.release();
         return fail(SPDE_ENOMEM, "pinned host allocation failed");
@@ -305,7 +321,8 @@ spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64)
 // st[].active; right-hand sides in r2 (inner type T), solution in d.
 template <typename T>
 spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Workspace& ws, double inner_tol,
-                         int* iters_out, cudaStream_t st, const T* kh2c = nullptr, T* const* Dlev = nullptr) {
+                         int* iters_out, cudaStream_t st, const T* kh2c = nullptr, T* const* Dlev = nullptr,
+                         const double* col_tol = nullptr) {
     const int64_t n3 = g.cells(), N4 = 4 * n3;
     T* d = static_cast<T*>(ws.vec[0]);
     T* w1 = static_cast<T*>(ws.vec[1]);
@@ -332,7 +349,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
     if (nC0 < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
     CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
     prof_begin(PK_OTHER, st);
-    CUDA_TRY(launch_minres_init(S, ws.partB, nB0, ws.partC, nC0, inner_tol, ws.st, ws.nact, st));
+    CUDA_TRY(launch_minres_init(S, ws.partB, nB0, ws.partC, nC0, inner_tol, ws.st, ws.nact, st, col_tol));
     prof_end(st, (double)S * (nB0 + nC0) * 8.0);
     CUDA_TRY(cudaMemcpyAsync(ws.h_nact, ws.nact, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -535,6 +552,7 @@ spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Works
             worst = std::max(worst, rel);
             mask[s] = (rel > o.tol) ? 1 : 0;
             nact += mask[s];
+            ws.h_tol[s] = inner_tol_for(o, rel);
         }
         if (nact == 0 || outer >= o.max_outer) break;
         CUDA_TRY(cudaMemcpyAsync(d_mask, mask.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -560,7 +578,12 @@ spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Works
                     Dlev = fl->D64;
                 }
             }
-            STATUS_TRY(minres_batch<T>(o, g, kh2, S, ws, itol, &its, st, kh2c, Dlev));
+            const double* col_tol = nullptr;
+            if (std::is_same<T, float>::value) {  // FP32 inner: each column's own reduction
+                CUDA_TRY(cudaMemcpyAsync(ws.coltol, ws.h_tol, S * sizeof(double), cudaMemcpyHostToDevice, st));
+                col_tol = ws.coltol;
+            }
+            STATUS_TRY(minres_batch<T>(o, g, kh2, S, ws, itol, &its, st, kh2c, Dlev, col_tol));
         }
         inner_total += its;
         prof_begin(PK_ADD_CORR, st);
@@ -857,6 +880,7 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
         if (sl.fresh) sl.fnorm2 = ws.h_col[S + c];
         sl.fresh = false;
         const double rel = sl.fnorm2 > 0.0 ? std::sqrt(ws.h_col[c] / sl.fnorm2) : 0.0;
+        ws.h_tol[c] = inner_tol_for(o, rel);
         if (rel <= o.tol || sl.outer >= o.max_outer || sl.req->cancelled) {
             if (rel > o.tol && !sl.req->cancelled) sl.req->status = SPDE_ENOCONV;
             finished.push_back(c);
@@ -912,7 +936,8 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
         CUDA_TRY(cudaMemcpyAsync(L->d_mask, L->h_mask, S * sizeof(int), cudaMemcpyHostToDevice, st));
         CUDA_TRY(launch_set_active(S, L->d_mask, ws.st, st));
         int its = 0;
-        STATUS_TRY(minres_batch<float>(o, g, kh2, S, ws, o.inner_tol, &its, st));
+        CUDA_TRY(cudaMemcpyAsync(ws.coltol, ws.h_tol, S * sizeof(double), cudaMemcpyHostToDevice, st));
+        STATUS_TRY(minres_batch<float>(o, g, kh2, S, ws, o.inner_tol, &its, st, nullptr, nullptr, ws.coltol));
         CUDA_TRY(launch_add_theta<float>(n3, S, ws.x64, static_cast<const float*>(ws.vec[0]), ws.st, st));
         for (int c : going) L->slots[c].outer += 1;
     }
