@@ -125,14 +125,15 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts);
 
 /* Define embedding grid `level` (0 <= level < 16): n^3 cubic cells on the
  * box [lo, hi] (Sec. 4.1, domain embedding; Sec. 6.1, nested grids).
- * n must be a power of two, 4 <= n <= 1024, and hi - lo equal on all three
- * axes (cubic cells).  Replaces an existing level of the same index. */
+ * n must be a power of two, 4 <= n <= 512 (a grid holds at most 2^29 cells),
+ * and hi - lo equal on all three axes (cubic cells).  Replaces an existing
+ * level of the same index. */
 spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]);
 
 /* Define embedding grid `level` as a box of n[0] x n[1] x n[2] cubic cells on
  * [lo, hi] (Sec. 4.1: the embedding domain is a box around the target mesh,
  * as the 1600 x 2420 x 240 ft box of Sec. 7.2).  Every n[a] is a power of two
- * in [4, 1024] and (hi - lo)[a] / n[a] is the same spacing h on all axes
+ * in [4, 1024], n[0] n[1] n[2] <= 2^29, and (hi - lo)[a] / n[a] is the same spacing h on all axes
  * (relative difference <= 1e-12).  The multigrid hierarchy halves every
  * extent above 1; the first level whose extents are not multiples of
  * 32 x 16 x 8 must have at most 4096 cells (e.g. 256 x 256 x 32 is accepted,
@@ -298,13 +299,13 @@ spde_status spde_noise_words(int64_t npairs, uint64_t seed, uint64_t sample, uin
 /* y = (D A D) x, the scaled mixed operator (Eq. linsys_blocks) on an n^3 grid
  * of spacing h, for nsamples stacked vectors of 4 n^3 entries (layout above).
  * prec SPDE_PREC_FP64: x, y are double; SPDE_PREC_MIXED: float.  n is a
- * power of two in [4, 1024]; x and y are 16-byte aligned.
+ * power of two in [4, 512]; x and y are 16-byte aligned.
  * Wall entries of y are written as 0. */
 spde_status spde_apply(int n, double h, double kappa, int nsamples, int prec, const void* x,
                        void* y, void* stream);
 
 /* spde_apply on a box of n[0] x n[1] x n[2] cells (each a power of two in
- * [4, 1024]); every block of a vector has n[0] n[1] n[2] entries, cell
+ * [4, 1024], at most 2^29 cells); every block of a vector has n[0] n[1] n[2] entries, cell
  * (i, j, k) at i + n[0] (j + n[1] k), wall entries at i = n[0]-1 (ux),
  * j = n[1]-1 (uy), k = n[2]-1 (uz). */
 spde_status spde_apply_box(const int n[3], double h, double kappa, int nsamples, int prec, const void* x,

@@ -80,6 +80,10 @@ constexpr int kMaxChunk = 64;
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Cells of one grid at most: the kernels index a sample's four blocks with
+// 32-bit offsets up to 4 x cells, which must stay below 2^31.
+constexpr int64_t kMaxGridCells = int64_t(1) << 29;
+
 template <typename T>
 spde_status dev_alloc(T** p, size_t count) {
     *p = nullptr;
@@ -1211,6 +1215,8 @@ spde_status level_add_impl(spde_ctx* ctx, int level, const int n[3], const doubl
     for (int a = 0; a < 3; ++a)
         if (!is_pow2(n[a]) || n[a] < 4 || n[a] > 1024)
             return fail(SPDE_EINVAL, "cells per axis must be powers of two in [4, 1024]");
+    if ((int64_t)n[0] * n[1] * n[2] > kMaxGridCells)
+        return fail(SPDE_EINVAL, "at most 2^29 cells per grid (a cube of at most 512^3)");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a]))
             return fail(SPDE_EINVAL, "box must have hi > lo on every axis");
@@ -1239,7 +1245,7 @@ spde_status level_add_impl(spde_ctx* ctx, int level, const int n[3], const doubl
 }  // namespace
 
 spde_status spde_level_add(spde_ctx* ctx, int level, int n, const double lo[3], const double hi[3]) {
-    if (!is_pow2(n) || n < 4 || n > 1024) return fail(SPDE_EINVAL, "n must be a power of two in [4, 1024]");
+    if (!is_pow2(n) || n < 4 || n > 512) return fail(SPDE_EINVAL, "n must be a power of two in [4, 512]");
     if (lo && hi) {
         const double ext = hi[0] - lo[0];
         for (int a = 0; a < 3; ++a)
@@ -1714,7 +1720,7 @@ bool grid_dims_ok(const int n[3]) {
     if (!n) return false;
     for (int a = 0; a < 3; ++a)
         if (!is_pow2(n[a]) || n[a] < 4 || n[a] > 1024) return false;
-    return true;
+    return (int64_t)n[0] * n[1] * n[2] <= kMaxGridCells;
 }
 }  // namespace
 

@@ -146,6 +146,11 @@ def test_box_argument_errors():
         smp.add_level(0, (64, 32, 16), (0.0,) * 3, (1.0, 1.0, 0.25))
     with pytest.raises(pkg.SpdeError):  # not a power of two
         smp.add_level(0, (48, 32, 16), (0.0,) * 3, (1.5, 1.0, 0.5))
+    with pytest.raises(pkg.SpdeError):  # more than 2^29 cells
+        smp.add_level(0, 1024)
+    with pytest.raises(pkg.SpdeError):
+        smp.add_level(0, (1024, 1024, 1024), (0.0,) * 3, (1.0, 1.0, 1.0))
+    smp.add_level(0, (1024, 1024, 512), (0.0,) * 3, (1.0, 1.0, 0.5))  # 2^29 cells: accepted (nothing allocated)
     smp.close()
     sch = pkg.Sampler(pkg.SPDE_PREC_MIXED, solver=pkg.SPDE_SOLVER_SCHUR_CG)
     sch.add_level(0, (64, 32, 16), (0.0,) * 3, (2.0, 1.0, 0.5))
