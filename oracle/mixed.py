@@ -228,26 +228,27 @@ def _dct_matrix(n):
 def variance_exact(n, kappa, sigma, h=None):
     """Exact discrete variance of every cell: diag(g^2 S^{-1} W S^{-1}).
 
-    Returned as an [z, y, x] array.
+    n: cells per axis of a cube, or (nx, ny, nz).  Returned as an [z, y, x] array.
     """
-    h = (1.0 / n) if h is None else h
-    lam = schur_eigenvalues(n, h, kappa)
-    c2 = _dct_matrix(n) ** 2  # [k, i]
+    nx, ny, nz = _dims(n)
+    h = (1.0 / nx) if h is None else h
+    lam = schur_eigenvalues((nx, ny, nz), h, kappa)  # [kz, ky, kx]
     a = 1.0 / lam ** 2
-    # contract each frequency axis with C^2: var[z,y,x] = sum_k prod C^2 a
-    v = np.einsum("abc,ax->xbc", a, c2)
-    v = np.einsum("xbc,by->xyc", v, c2)
-    v = np.einsum("xyc,cz->xyz", v, c2)
+    # var[z, y, x] = sum_k C_z[kz, z]^2 C_y[ky, y]^2 C_x[kx, x]^2 a[kz, ky, kx]
+    v = np.einsum("abc,az->zbc", a, _dct_matrix(nz) ** 2)
+    v = np.einsum("zbc,by->zyc", v, _dct_matrix(ny) ** 2)
+    v = np.einsum("zyc,cx->zyx", v, _dct_matrix(nx) ** 2)
     return g_normaliser(kappa, sigma) ** 2 * h ** 3 * v
 
 
 def covariance_column(n, kappa, sigma, cell, h=None):
-    """Column g^2 h^3 C^T Lambda^{-2} C e_cell of the exact covariance, flat."""
-    h = (1.0 / n) if h is None else h
-    lam = schur_eigenvalues(n, h, kappa)
-    e = np.zeros(n ** 3)
+    """Column g^2 h^3 C^T Lambda^{-2} C e_cell of the exact covariance, flat (n: one extent or three)."""
+    nx, ny, nz = _dims(n)
+    h = (1.0 / nx) if h is None else h
+    lam = schur_eigenvalues((nx, ny, nz), h, kappa)
+    e = np.zeros(nx * ny * nz)
     e[cell] = 1.0
-    e = e.reshape(n, n, n)
+    e = e.reshape(nz, ny, nx)
     col = scipy.fft.idctn(scipy.fft.dctn(e, type=2, norm="ortho") / lam ** 2, type=2, norm="ortho")
     return g_normaliser(kappa, sigma) ** 2 * h ** 3 * col.ravel()
 

@@ -127,3 +127,22 @@ def test_restrict_noise_on_a_box():
             for i in range(nx):
                 ref[(i // 2) + (nx // 2) * ((j // 2) + (ny // 2) * (k // 2))] += xi[i + nx * (j + ny * k)]
     assert np.allclose(got, ref * 2.0 ** -1.5, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 2), (2, 5, 3)])
+def test_exact_covariance_on_a_box(dims):
+    """The DCT statements of the exact covariance g^2 S^{-1} W S^{-1} (its diagonal and one
+    column) equal the dense covariance of the assembled box system."""
+    nx, ny, nz = dims
+    h, kappa, sigma = 0.3, 2.2, 1.3
+    ms = mixed.MixedSystem(dims, h=h)
+    B = ms.B.toarray()
+    W = ms.W.toarray()
+    S = kappa ** 2 * W + B @ np.linalg.solve(ms.M.toarray(), B.T)
+    Si = np.linalg.inv(S)
+    cov = mixed.g_normaliser(kappa, sigma) ** 2 * Si @ W @ Si
+    var = mixed.variance_exact(dims, kappa, sigma, h=h)
+    assert var.shape == (nz, ny, nx)
+    assert np.allclose(var.ravel(), np.diag(cov), rtol=1e-11, atol=0)
+    cell = 1 + nx * (2 % ny + ny * (nz - 1))
+    assert np.allclose(mixed.covariance_column(dims, kappa, sigma, cell, h=h), cov[:, cell], rtol=1e-10, atol=1e-14)
