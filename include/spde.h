@@ -149,8 +149,9 @@ spde_status spde_level_add_box(spde_ctx* ctx, int level, const int n[3], const d
  *   tets host, [ntets][4] int32 vertex ids (either orientation; fixed on copy)
  * Both arrays are copied; the caller keeps them.  Every tet must lie inside
  * the box and have volume > 1e-9 h^3; every coupling row must sum to the
- * tet volume within 1e-10 relative -- else SPDE_EMESH naming the first bad
- * tet.  Synchronises the default stream of the context. */
+ * tet volume within 1e-10 |tau| + 1e-12 h^3 (slivers included: the pieces'
+ * rounding is at the scale of the cell) -- else SPDE_EMESH naming the first
+ * bad tet.  Synchronises the default stream of the context. */
 spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const double* xyz,
                              int64_t ntets, const int32_t* tets);
 
@@ -340,23 +341,43 @@ spde_status spde_precond_box(const int n[3], double h, double kappa, int nsample
  *     SPDE_EINVAL before any work (spde_last_error gives the need): the
  *     need is 2 sum_{l=1..L} (n/2^l)^3 elements per sample over the levels
  *     with n/2^(l-1) >= 32, e.g. about 2.4 MB per sample at n = 128 in FP32.
- *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *   - n is a power of two in [4, 512], as for spde_precond.
+ *   - The first call in a CUDA context looks up the array's device address
+ *     (with that device current) and caches it under the context's id; make
+ *     that first call before any stream capture.
+ *   - A timeout of a V-cycle sweep is reported by spde_precond_status, not by
+ *     this call (z's field block is then unspecified); the fault word it uses
+ *     is static as well and cleared at the start of every call.
  *   - All calls share the array: calls that overlap on the GPU race.  No
  *     scratch element needs clearing between calls (each call writes every
  *     element it reads). */
 spde_status spde_precond_noalloc(int n, double h, double kappa, int nsamples, int prec,
                                  const spde_opts* opts, const void* r, void* z, void* stream);
 
+/* Outcome of the step-level preconditioner calls (spde_precond,
+ * spde_precond_box, spde_precond_noalloc) on the current device.  Those calls
+ * return once their kernels are enqueued and never report SPDE_ETIMEOUT
+ * themselves.  If a V-cycle sweep of a call waits about one second for a
+ * plane copy and gives up, that call's z keeps a correct flux block, but
+ * its field block is unspecified (tiles skipped, or partly written).  Each
+ * call clears its fault word when it starts, so a timeout never makes a
+ * later call skip work.  This function synchronises `stream` and returns
+ * SPDE_ETIMEOUT when the last spde_precond / spde_precond_box call, or the
+ * last spde_precond_noalloc call, timed out (clearing the word), else SPDE_OK.
+ * Solves inside a context (spde_sample and the rest) check their own fault
+ * word and return SPDE_ETIMEOUT directly. */
+spde_status spde_precond_status(void* stream);
+
 /* Self-check of the bounded device waits (no paper counterpart: a safety
  * property of this implementation).  The multigrid sweeps wait on mbarriers
  * for their plane copies; every such wait gives up after about one second,
- * raises a device fault word and returns, and the solve then reports
- * SPDE_ETIMEOUT.  This call launches one CTA whose barrier never completes
- * and checks that path on `device`: SPDE_OK when the wait gave up and the
- * fault word was raised (then cleared), *waited_ms the time the wait took
- * (about 1000); the context stays usable.  Synchronises the device. */
+ * raises the fault word of its solve (one per workspace) and returns, and
+ * that solve then reports SPDE_ETIMEOUT.  This call launches one CTA whose
+ * barrier never completes, on a stream of its own with a fault word of its
+ * own, and checks that path on `device`: SPDE_OK when the wait gave up and
+ * its fault word was raised, *waited_ms the time the wait took (about 1000).
+ * Solves running meanwhile are not affected; the device stays usable.
+ * Synchronises its own stream only. */
 spde_status spde_check_wait_limit(int device, double* waited_ms);
 
 /* y = S x with the scaled Schur complement S = (kappa h)^2 I + D1 T^{-1} D1^T of

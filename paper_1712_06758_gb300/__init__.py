@@ -84,6 +84,7 @@ _SIGS = {
                          ctypes.POINTER(spde_opts), _P, _P, _P],
     "spde_precond_noalloc": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                              ctypes.POINTER(spde_opts), _P, _P, _P],
+    "spde_precond_status": [_P],
     "spde_schur_apply": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P],
     "spde_solve": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P],
     "spde_project": [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P],
@@ -317,6 +318,11 @@ def spde_precond_noalloc(n, h, kappa, nsamples, prec, r, z, opts=None, stream=No
     _check(lib().spde_precond_noalloc(n, h, kappa, nsamples, prec,
                                       ctypes.byref(opts) if opts is not None else None, _ptr(r), _ptr(z),
                                       _stream(stream)))
+
+
+def spde_precond_status(stream=None):
+    """Raises SpdeError(SPDE_ETIMEOUT) when the last step-level preconditioner call timed out."""
+    _check(lib().spde_precond_status(_stream(stream)))
 
 
 def spde_schur_apply(n, h, kappa, nsamples, prec, x, y, stream=None):

@@ -265,7 +265,7 @@ __global__ void k_tet_compact(int64_t ntets, const int64_t* __restrict__ cand_of
                               const double* __restrict__ cvol, const int32_t* __restrict__ ccell,
                               const int64_t* __restrict__ rowptr, const double* __restrict__ vol,
                               int32_t* __restrict__ col, double* __restrict__ gval, float* __restrict__ pi,
-                              unsigned long long* __restrict__ bad) {
+                              double h3, unsigned long long* __restrict__ bad) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= ntets) return;
     int64_t o = rowptr[t];
@@ -281,7 +281,11 @@ __global__ void k_tet_compact(int64_t ntets, const int64_t* __restrict__ cand_of
             ++o;
         }
     }
-    if (cand[t] > 0 && !(fabs(sum - vol[t]) <= 1e-10 * vol[t])) note_bad(bad, t, 3);
+    // coverage: the pieces must add up to the tet.  The fan sums of a piece carry
+    // rounding at the scale of the cell (terms of size h^3 that cancel down to a
+    // sliver's volume), so the bound has an absolute part of 1e-12 h^3 besides
+    // the relative one; a tet reaching out of the box misses far more.
+    if (cand[t] > 0 && !(fabs(sum - vol[t]) <= 1e-10 * vol[t] + 1e-12 * h3)) note_bad(bad, t, 3);
 }
 
 // ---- exclusive scan of int64 (three phases, no inter-block waiting) -------
@@ -407,7 +411,8 @@ cudaError_t build_coupling(const int n[3], double h, const double lo[3], int64_t
     CK(cudaMalloc(&col, (nnz + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&gv, (nnz + 1) * sizeof(double)));
     CK(cudaMalloc(&pv, (nnz + 1) * sizeof(float)));
-    k_tet_compact<<<tb, 256, 0, st>>>(ntets, cand_off, cand, cvol, ccell, rowptr, d_vol, col, gv, pv, bad);
+    k_tet_compact<<<tb, 256, 0, st>>>(ntets, cand_off, cand, cvol, ccell, rowptr, d_vol, col, gv, pv, h * h * h,
+                                       bad);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

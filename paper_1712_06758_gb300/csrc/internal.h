@@ -110,6 +110,9 @@ struct MGPlan {
     // per-cell diagonal s (a_c + c k_c) of every level (element type of the plan), for
     // cell-wise kappa; null: one coefficient for the whole level
     const void* D[16] = {};
+    // fault word of the solve (device int): a sweep whose bounded wait gives up raises it,
+    // and later sweeps of the same solve skip their work until the owner clears it
+    int* fault = nullptr;
 };
 
 // ---- noise.cu
@@ -196,13 +199,14 @@ cudaError_t launch_set_active(int S, const int* mask, MinresCol* st_, cudaStream
 cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStream_t st);
 
 // ---- mg.cu
-// the device fault word of the V-cycle sweeps (1: a wait for a plane copy gave up):
-// mg_fault_read enqueues a copy into *host on st (valid once st has synchronised),
-// mg_fault_clear resets it
-cudaError_t mg_fault_read(int* host, cudaStream_t st);
-// launches the bounded-wait self-check (one CTA whose wait must give up); its wait time goes to *elapsed_ns_dev
-cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, cudaStream_t st);
-cudaError_t mg_fault_clear(cudaStream_t st);
+// the fault word of a solve's V-cycle sweeps (a device int; 1: a wait for a plane copy
+// gave up): mg_fault_read enqueues a copy into *host on st (valid once st has
+// synchronised), mg_fault_clear enqueues its reset on st
+cudaError_t mg_fault_read(const int* fault, int* host, cudaStream_t st);
+// launches the bounded-wait self-check (one CTA whose wait must give up and raise *fault);
+// its wait time goes to *elapsed_ns_dev
+cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, int* fault, cudaStream_t st);
+cudaError_t mg_fault_clear(int* fault, cudaStream_t st);
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride,
                   double* dot_part, const int* active, int act_stride, cudaStream_t st);
@@ -270,5 +274,9 @@ cudaError_t launch_grid_out(int64_t ncell, int S, const double* x, int64_t x_str
 
 // set the message spde_last_error() returns on the calling thread
 void set_last_error(const char* msg);
+
+// noalloc.cu: reads and clears the fault word of the allocation-free preconditioner calls
+// on the current device (*raised = 1 when one of their sweeps gave up); synchronises st
+cudaError_t noalloc_take_fault(int* raised, cudaStream_t st);
 
 }  // namespace spde

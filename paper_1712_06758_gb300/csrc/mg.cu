@@ -133,8 +133,10 @@ __device__ __forceinline__ int kxy_of(int packed, int e) { return (packed >> (3 
 // "zero outside the box" the sweeps need.  One thread issues the copies into a
 // ring of plane slots, each completing on its own mbarrier.  Every wait is
 // bounded (about one second on the global timer); a wait that gives up sets
-// the CTA's abort flag and the device-wide fault word, later waits return at
-// once and the host reports SPDE_ETIMEOUT.
+// the CTA's abort flag and the fault word of the solve that launched the
+// sweep (a device int the caller owns, one per workspace), later waits and
+// later sweeps of that solve return at once and the host reports
+// SPDE_ETIMEOUT.  Other solves, with their own words, are not affected.
 // ---------------------------------------------------------------------------
 constexpr int kRing = 4;  // plane slots of the TMA ring (both sweeps): the z-march is unrolled by 4
 template <int K>
@@ -142,8 +144,6 @@ using IC = std::integral_constant<int, K>;
 constexpr int kProducer = kTileThreads - 32;  // issues the plane copies: lane 0 of the last warp, which has no
                                               // segment work in the residual and prolongation phases
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
-
-__device__ int g_mg_fault;
 
 template <typename T>
 __host__ __device__ constexpr int slot_elems(int rows) {  // a plane slot, rounded up to 128 bytes
@@ -214,6 +214,7 @@ struct PlaneRing {
     int slot;            // elements per slot
     uint64_t* bars;
     volatile int* abort;
+    int* fault;          // the solve's fault word
     uint32_t bytes;
     uint32_t ph = 0;     // bit s: parity of slot s's next completion
     uint32_t pend = 0;   // producer: bit s set while a copy into slot s is unobserved
@@ -233,7 +234,7 @@ struct PlaneRing {
             if (mbar_wait(bars + s, par)) pend &= ~(1u << s);
             else {
                 *abort = 1;
-                atomicExch(&g_mg_fault, 1);
+                atomicExch(fault, 1);
             }
         }
         return at(s);
@@ -249,8 +250,9 @@ struct PlaneRing {
 
 template <typename T, int NS>
 __device__ __forceinline__ PlaneRing<T, NS> ring_setup(unsigned char* raw, int rows, uint64_t* bars,
-                                                       volatile int* abort, int tid) {
+                                                       volatile int* abort, int* fault, int tid) {
     PlaneRing<T, NS> r;
+    r.fault = fault;
     const uint32_t a = smem_addr(raw);
     r.slots = reinterpret_cast<T*>(raw + ((128 - (a & 127)) & 127));
     r.slot = slot_elems<T>(rows);
@@ -283,16 +285,17 @@ constexpr int kRestrictBase = kTileThreads - RXY / 2;  // the restriction thread
 template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
     k_mg_down(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
-              int64_t bc_stride, const int* __restrict__ active, int act_stride, const T* __restrict__ Dg) {
+              int64_t bc_stride, const int* __restrict__ active, int act_stride, const T* __restrict__ Dg,
+              int* __restrict__ fault) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_oi[8], s_rcD[8];
     __shared__ uint64_t s_bar[kRing];
     __shared__ int s_abort;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
-    if (*(volatile int*)&g_mg_fault) return;  // an earlier sweep gave up: the host reports it, skip the work
+    if (*(volatile int*)fault) return;  // an earlier sweep of this solve gave up: the host reports it, skip the work
     const int tid = threadIdx.x + 32 * threadIdx.y;
-    PlaneRing<T, kRing> ring = ring_setup<T, kRing>(smem_raw, XH, s_bar, &s_abort, tid);
+    PlaneRing<T, kRing> ring = ring_setup<T, kRing>(smem_raw, XH, s_bar, &s_abort, fault, tid);
     T* const Xbase = ring.slots + kRing * ring.slot;  // 4 x0 plane slots, PW x XH
     T* const Rbase = Xbase + 4 * PW * XH;             // 2 residual plane slots, PW x RH
     T* const Rxy = Rbase + 2 * PW * RH;               // 4 ring planes of the x-y restricted residual
@@ -501,7 +504,7 @@ template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     k_mg_up(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
             int64_t ec_stride, T* __restrict__ y, int64_t y_stride, double* __restrict__ dot_part,
-            const int* __restrict__ active, int act_stride, const T* __restrict__ Dg) {
+            const int* __restrict__ active, int act_stride, const T* __restrict__ Dg, int* __restrict__ fault) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
     __shared__ T s_oi[8], s_ois[8];
@@ -509,9 +512,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     __shared__ int s_abort;
     const int col = blockIdx.y;
     if (active && !active[(int64_t)col * act_stride]) return;
-    if (*(volatile int*)&g_mg_fault) return;
+    if (*(volatile int*)fault) return;
     const int tid = threadIdx.x + 32 * threadIdx.y;
-    PlaneRing<T, kRing> ring = ring_setup<T, kRing>(smem_raw, BH, s_bar, &s_abort, tid);
+    PlaneRing<T, kRing> ring = ring_setup<T, kRing>(smem_raw, BH, s_bar, &s_abort, fault, tid);
     T* const Xbase = ring.slots + kRing * ring.slot;  // 4 x plane slots, PW x BH
     T* const Cbase = Xbase + 4 * PW * BH;             // 4 coarse plane slots, CW x CH
     auto Cs = [&](int Z) { return Cbase + ((Z + 4) & 3) * (CW * CH); };  // Z >= -4
@@ -1060,8 +1063,8 @@ static bool plane_map(CUtensorMap* m, const T* base, const Grid3& g, int S, int6
 
 // Self-check of the bounded wait: one CTA waits on an mbarrier that is set up
 // for one arrival which never comes, so phase 0 never completes; every thread
-// must give up after the limit, raise the fault word and return.
-__global__ void k_wait_probe(unsigned long long* elapsed_ns) {
+// must give up after the limit, raise the given fault word and return.
+__global__ void k_wait_probe(unsigned long long* elapsed_ns, int* fault) {
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar);
@@ -1069,25 +1072,21 @@ __global__ void k_wait_probe(unsigned long long* elapsed_ns) {
     }
     __syncthreads();
     const unsigned long long t0 = global_ns();
-    if (!mbar_wait(&bar, 0)) atomicExch(&g_mg_fault, 1);
+    if (!mbar_wait(&bar, 0)) atomicExch(fault, 1);
     __syncthreads();
     if (threadIdx.x == 0) *elapsed_ns = global_ns() - t0;
 }
 
-cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, cudaStream_t st) {
-    k_wait_probe<<<1, 32, 0, st>>>(elapsed_ns_dev);
+cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, int* fault, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(elapsed_ns_dev, fault);
     return cudaGetLastError();
 }
 
-cudaError_t mg_fault_read(int* host, cudaStream_t st) {
-    return cudaMemcpyFromSymbolAsync(host, g_mg_fault, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+cudaError_t mg_fault_read(const int* fault, int* host, cudaStream_t st) {
+    return cudaMemcpyAsync(host, fault, sizeof(int), cudaMemcpyDeviceToHost, st);
 }
 
-cudaError_t mg_fault_clear(cudaStream_t st) {
-    static const int zero = 0;
-    const cudaError_t e = cudaMemcpyToSymbolAsync(g_mg_fault, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
-    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
-}
+cudaError_t mg_fault_clear(int* fault, cudaStream_t st) { return cudaMemsetAsync(fault, 0, sizeof(int), st); }
 
 // once per instantiation and process (thread-safe static initialisation)
 template <typename T>
@@ -1101,6 +1100,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
                   const int* active, int act_stride, cudaStream_t st) {
     const double prof_cols = plan.prof_cols > 0 ? plan.prof_cols : (double)S;
     if (mg_attrs<T>() != cudaSuccess) return -1;
+    if (plan.lc > 0 && !plan.fault) return -1;  // the sweeps need the solve's fault word
     CoarseDesc d;
     d.lc = plan.lc;
     d.nlev = plan.nlev;
@@ -1138,10 +1138,10 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const T* Dl = static_cast<const T*>(plan.D[l]);
         if (Dl)
             k_mg_down<T, true><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
-                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, Dl);
+                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, Dl, plan.fault);
         else
             k_mg_down<T, false><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
-                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, nullptr);
+                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, nullptr, plan.fault);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)gf.cells() * w);
         in = out;
         in_stride = nc3;
@@ -1172,11 +1172,11 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         if (Dl)
             k_mg_up<T, true><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
                 map, gf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
-                (l == 0) ? dot_part : nullptr, active, act_stride, Dl);
+                (l == 0) ? dot_part : nullptr, active, act_stride, Dl, plan.fault);
         else
             k_mg_up<T, false><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
                 map, gf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
-                (l == 0) ? dot_part : nullptr, active, act_stride, nullptr);
+                (l == 0) ? dot_part : nullptr, active, act_stride, nullptr, plan.fault);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf3 * w);
         if (l == 0) nblk0 = nb;
     }

@@ -123,6 +123,7 @@ struct Workspace {
     double* h_tol = nullptr;   // pinned [S]
     MinresCol* st = nullptr;
     int* nact = nullptr;
+    int* fault = nullptr;    // fault word of this workspace's V-cycle sweeps
     int* h_nact = nullptr;   // pinned
     double* h_col = nullptr; // pinned [2S]
     MinresCol* h_st = nullptr;
@@ -145,6 +146,7 @@ struct Workspace {
         dev_free(coltol);
         dev_free(st);
         dev_free(nact);
+        dev_free(fault);
         dev_free(thetaT);
         dev_free(tri);
         dev_free(tri32);
@@ -284,6 +286,12 @@ spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64)
     STATUS_TRY(dev_alloc(&ws.cg, (size_t)S));
     // per MINRES iteration of a chunk: [2q] columns still active after it, [2q+1] columns it left an update pending
     STATUS_TRY(dev_alloc(&ws.nact, 2 * kMaxChunk));
+    STATUS_TRY(dev_alloc(&ws.fault, 1));
+    if (cudaMemset(ws.fault, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        ws.release();
+        return fail(SPDE_ECUDA, "clearing the fault word failed");
+    }
     STATUS_TRY(dev_alloc(&ws.thetaT, (size_t)S * n3));
     {
         // Thomas factors of tridiag(1/6, 2/3, 1/6) on the n-1 interior faces of a line of the
@@ -338,6 +346,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
     MGPlan plan;
     if (!mg_plan_init(plan, g, kh2, o.schur_c, o.omega)) return fail(SPDE_EINVAL, "grid shape not supported by the V-cycle");
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
+    plan.fault = ws.fault;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
@@ -444,6 +453,7 @@ spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Work
     MGPlan plan;
     mg_plan_init(plan, g, kh2, o.schur_c, o.omega);
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
+    plan.fault = ws.fault;
     plan.prof_cols = (double)S;
     const int act_stride = (int)(sizeof(CgCol) / sizeof(int));
     const int* act = &ws.cg[0].active;
@@ -496,10 +506,11 @@ spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Work
 }
 
 // a V-cycle sweep that gave up waiting for a plane copy leaves the columns of
-// that solve invalid: report it (and reset the fault word for later calls)
-static spde_status fault_status(int fault, cudaStream_t st) {
+// that solve invalid: report it (and reset the workspace's fault word for later calls)
+static spde_status fault_status(int fault, int* dev_fault, cudaStream_t st) {
     if (!fault) return SPDE_OK;
-    CUDA_TRY(mg_fault_clear(st));
+    CUDA_TRY(mg_fault_clear(dev_fault, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
     return fail(SPDE_ETIMEOUT, "a multigrid sweep gave up waiting for a plane copy; this solve's results are invalid");
 }
 
@@ -545,9 +556,9 @@ spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Works
         prof_end(st, (double)S * nb * 8.0);
         CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
         int fault = 0;
-        CUDA_TRY(mg_fault_read(&fault, st));
+        CUDA_TRY(mg_fault_read(ws.fault, &fault, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        STATUS_TRY(fault_status(fault, st));
+        STATUS_TRY(fault_status(fault, ws.fault, st));
         int nact = 0;
         worst = 0.0;
         for (int s = 0; s < S; ++s) {
@@ -874,9 +885,9 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
     CUDA_TRY(launch_reduce(S, ws.partR, nbr, ws.colv, st));
     CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
     int fault = 0;
-    CUDA_TRY(mg_fault_read(&fault, st));
+    CUDA_TRY(mg_fault_read(ws.fault, &fault, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    STATUS_TRY(fault_status(fault, st));
+    STATUS_TRY(fault_status(fault, ws.fault, st));
     std::vector<int> going;
     for (int c = 0; c < S; ++c) {
         Lane::Slot& sl = L->slots[c];
@@ -1757,6 +1768,7 @@ struct PrecondScratch {
 };
 std::mutex g_pc_mu;
 PrecondScratch g_pc;
+int* g_pc_fault = nullptr;  // fault word of the step-level preconditioner calls (kept until exit)
 }  // namespace
 
 spde_status spde_precond(int n, double h, double kappa, int nsamples, int prec, const spde_opts* opts, const void* r,
@@ -1791,11 +1803,16 @@ spde_status spde_precond_box(const int n[3], double h, double kappa, int nsample
         g_pc.S = nsamples;
         g_pc.prec = prec;
     }
+    if (!g_pc_fault) STATUS_TRY(dev_alloc(&g_pc_fault, 1));
     const double kh2 = (kappa * h) * (kappa * h);
     const int64_t n3 = gr.cells(), N4 = 4 * n3;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // each call starts with a clear fault word: a timeout is reported once, by
+    // spde_precond_status, and does not make later calls skip their sweeps
+    CUDA_TRY(mg_fault_clear(g_pc_fault, st));
     MGPlan plan;
     mg_plan_init(plan, gr, kh2, o.schur_c, o.omega);
+    plan.fault = g_pc_fault;
     if (prec == SPDE_PREC_FP64) {
         mg_plan_bind<double>(plan, nsamples, static_cast<double*>(g_pc.mg));
         const double* rr = static_cast<const double*>(r);
@@ -1815,22 +1832,44 @@ spde_status spde_precond_box(const int n[3], double h, double kappa, int nsample
     return SPDE_OK;
 }
 
+spde_status spde_precond_status(void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int a = 0, b = 0;
+    {
+        std::lock_guard<std::mutex> g(g_pc_mu);
+        if (g_pc_fault) {
+            CUDA_TRY(mg_fault_read(g_pc_fault, &a, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (a) CUDA_TRY(mg_fault_clear(g_pc_fault, st));
+        }
+    }
+    CUDA_TRY(noalloc_take_fault(&b, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (a || b)
+        return fail(SPDE_ETIMEOUT, "a V-cycle sweep of the last %s call gave up waiting for a plane copy; the field "
+                    "block of its z is unspecified", a ? "spde_precond / spde_precond_box" : "spde_precond_noalloc");
+    return SPDE_OK;
+}
+
 spde_status spde_check_wait_limit(int device, double* waited_ms) {
     if (!waited_ms) return fail(SPDE_EINVAL, "null argument");
     *waited_ms = 0.0;
     CUDA_TRY(cudaSetDevice(device));
+    // the probe raises a fault word of its own: solves running meanwhile on other
+    // streams or contexts keep theirs clear
     unsigned long long* d = nullptr;
-    CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long)));
+    CUDA_TRY(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    int* dfault = reinterpret_cast<int*>(d + 1);
     unsigned long long ns = 0;
     int fault = 0;
-    cudaError_t e = mg_fault_read(&fault, 0);  // a fault left by an earlier call is not this probe's
-    if (e == cudaSuccess && fault) e = mg_fault_clear(0);
-    if (e == cudaSuccess) e = mg_wait_probe(d, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&ns, d, sizeof(ns), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = mg_fault_read(&fault, 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
-    if (e == cudaSuccess && fault) e = mg_fault_clear(0);
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = mg_fault_clear(dfault, st);
+    if (e == cudaSuccess) e = mg_wait_probe(d, dfault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d, sizeof(ns), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = mg_fault_read(dfault, &fault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
     cudaFree(d);
     CUDA_TRY(e);
     *waited_ms = 1e-6 * (double)ns;

@@ -13,7 +13,9 @@ tetrahedra around its main diagonal v0 -> v7 (the Kuhn split, conforming
 across cubes).  Every vertex strictly inside D is moved by an independent
 U(-jitter*ht, +jitter*ht) offset per coordinate; vertices on the boundary
 of D (outer faces and the re-entrant faces of the L-prism) stay fixed, so
-the jittered tets still tile D exactly.
+the jittered tets still tile D exactly.  Tets the jitter inverts or flattens
+(volume <= min_rel times the undeformed volume, min_rel = 0 by default) get
+their interior vertices redrawn; slivers are kept.
 """
 from dataclasses import dataclass
 from itertools import permutations
@@ -21,7 +23,10 @@ from itertools import permutations
 import numpy as np
 
 
-MIN_REL = 0.02
+# Redraw threshold of the jitter, relative to the undeformed Kuhn tet: 0 keeps
+# every valid tet (slivers included) and redraws only inverted or flat ones;
+# 0.02 was an earlier, gentler default and stays available as an argument.
+MIN_REL = 0.0
 
 
 @dataclass(frozen=True)
@@ -32,6 +37,7 @@ class MeshSpec:
     lshape: bool
     jitter: float = 0.25
     seed: int = 1
+    min_rel: float = MIN_REL
 
 
 def _kept_cubes(m, lshape):
@@ -100,8 +106,10 @@ def kuhn_mesh(spec: MeshSpec):
 
     # A jitter of +-ht/4 can invert or flatten a Kuhn tet (the volume is cubic
     # in the offsets).  Redraw, from the same stream, the offsets of the
-    # interior vertices of every tet thinner than MIN_REL of its undeformed
+    # interior vertices of every tet thinner than min_rel of its undeformed
     # volume until none is left, so the mesh stays a valid tiling of D.
+    # min_rel = 0 redraws inverted and flat tets only and keeps the slivers the
+    # jitter makes (down to ~5e-6 h^3 on the 192^3-cube L-prism at n = 256).
     flat = pos.reshape(-1, 3)
     flat_interior = interior.reshape(-1)
     v_ref = float(np.prod(ht)) / 6.0
@@ -109,7 +117,7 @@ def kuhn_mesh(spec: MeshSpec):
         p = flat[tets]
         vol = np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]),
                         p[:, 3] - p[:, 0]) / 6.0
-        bad = vol < MIN_REL * v_ref
+        bad = vol <= spec.min_rel * v_ref
         if not bad.any():
             break
         verts = np.unique(tets[bad].reshape(-1))
@@ -128,9 +136,9 @@ def kuhn_mesh(spec: MeshSpec):
     return xyz, tets
 
 
-def box_mesh(lo, hi, m, jitter=0.25, seed=1):
-    return kuhn_mesh(MeshSpec(tuple(lo), tuple(hi), m, False, jitter, seed))
+def box_mesh(lo, hi, m, jitter=0.25, seed=1, min_rel=MIN_REL):
+    return kuhn_mesh(MeshSpec(tuple(lo), tuple(hi), m, False, jitter, seed, min_rel))
 
 
-def lprism_mesh(m, lo=(0.05, 0.05, 0.05), hi=(0.95, 0.95, 0.95), jitter=0.25, seed=1):
-    return kuhn_mesh(MeshSpec(tuple(lo), tuple(hi), m, True, jitter, seed))
+def lprism_mesh(m, lo=(0.05, 0.05, 0.05), hi=(0.95, 0.95, 0.95), jitter=0.25, seed=1, min_rel=MIN_REL):
+    return kuhn_mesh(MeshSpec(tuple(lo), tuple(hi), m, True, jitter, seed, min_rel))

@@ -137,3 +137,78 @@ def test_coincident_candidate_points():
     f = v / clip.tet_volume(p)
     assert abs(inside - f) < 5 * np.sqrt(f * (1 - f) / len(x)) + 1e-4
     assert 0.0 < f < 1.0
+
+
+# ---------------------------------------------------------------- exact statement
+from fractions import Fraction  # noqa: E402
+
+from synth.slivers import plane_tets, sliver_tets  # noqa: E402
+
+
+def test_exact_corner_simplex_cut_by_plane():
+    """Corner simplex cut at x = a keeps 1/6 - (1 - a)^3 / 6 on the side x <= a,
+    exactly; the cube [0, 1/2]^3 holds 1/8 - (1/2)^3 / 6 of it, exactly."""
+    for a in (Fraction(1, 4), Fraction(1, 2), Fraction(4, 5), Fraction(1, 3)):
+        v = clip.tet_box_volume_exact(CORNER, [-1, -1, -1], [a, 2, 2])
+        assert v == Fraction(1, 6) - (1 - a) ** 3 / 6
+    assert clip.tet_box_volume_exact(CORNER, [0, 0, 0], [0.5, 0.5, 0.5]) == Fraction(1, 8) - Fraction(1, 48)
+    assert clip.tet_box_volume_exact(CORNER, [0, 0, 0], [0.3, 0.3, 0.3]) == Fraction(0.3) ** 3
+    assert clip.tet_box_volume_exact(2.0 + CORNER, [0, 0, 0], [1, 1, 1]) == 0
+
+
+def test_exact_rows_sum_to_exact_tet_volume():
+    """Every cell's piece is computed on its own, so a dropped piece, a wrong
+    split or a sign slip shows up as an inexact row sum."""
+    xyz, tets = box_mesh((0.15,) * 3, (0.85,) * 3, 4)
+    rows = clip.coupling_rows_exact(xyz, tets, 7, rows=range(0, len(tets), 5))
+    for t, row in rows.items():
+        assert sum(row.values()) == clip.tet_volume_exact(xyz[tets[t]])
+    sx, st, _ = sliver_tets(16, per_case=1)
+    for t, row in clip.coupling_rows_exact(sx, st, 16).items():
+        assert sum(row.values()) == clip.tet_volume_exact(sx[st[t]])
+        assert len(row) > 1  # the sliver crosses grid planes
+
+
+def test_exact_matches_hull_statement_on_jittered_tets():
+    xyz, tets = box_mesh((0.15,) * 3, (0.85,) * 3, 5)
+    n = 8
+    ex = clip.coupling_rows_exact(xyz, tets, n, rows=range(0, len(tets), 9))
+    hu = clip.coupling_rows(xyz, tets, n, rows=ex.keys())
+    for t in ex:
+        for c in set(ex[t]) | set(hu[t]):
+            assert abs(float(ex[t].get(c, 0)) - hu[t].get(c, 0.0)) <= 1e-13 / n ** 3
+
+
+def test_exact_aligned_kuhn_cube_is_diagonal():
+    xyz, tets = box_mesh((0.0,) * 3, (1.0,) * 3, 4, jitter=0.0)
+    for t, row in clip.coupling_rows_exact(xyz, tets, 4).items():
+        assert list(row) == [t // 6]
+        assert row[t // 6] == Fraction(1, 6 * 64)
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_hull_statement_on_slivers_and_plane_faces(n):
+    """The hull statement decides membership by signed distances to the face
+    planes; barycentric coordinates of a flat tet lose digits and once dropped
+    real vertices of the intersection (errors up to 1e-6 h^3)."""
+    h = 1.0 / n
+    for xyz, tets, bound in (sliver_tets(n, per_case=2)[:2] + (1e-15,), plane_tets(n) + (5e-13,)):
+        ex = clip.coupling_rows_exact(xyz, tets, n)
+        hu = clip.coupling_rows(xyz, tets, n)
+        for t in ex:
+            for c in set(ex[t]) | set(hu[t]):
+                assert abs(float(ex[t].get(c, 0)) - hu[t].get(c, 0.0)) <= bound * h ** 3, (t, c)
+
+
+def test_sliver_generator_volumes_and_placement():
+    n = 16
+    xyz, tets, target = sliver_tets(n)
+    vol = np.array([clip.tet_volume(xyz[t]) for t in tets])
+    assert np.allclose(vol, target, rtol=1e-6)
+    assert xyz.min() > 0.0 and xyz.max() < 1.0
+    span = (xyz[tets].max(axis=1) - xyz[tets].min(axis=1)) * n
+    assert np.all(span.max(axis=1) > 1.0)  # every sliver is longer than a cell along some axis
+    pxyz, ptets = plane_tets(n)
+    for t in ptets:  # three vertices share one coordinate
+        p = pxyz[t]
+        assert any(p[0, a] == p[1, a] == p[2, a] for a in range(3))

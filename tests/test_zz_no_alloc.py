@@ -2,11 +2,12 @@
 
 It serves callers that cannot allocate device memory (memory owned by
 another allocator, or loops that cannot afford cudaMalloc's device
-synchronisation).  Through the C ABI, two calls in a row must match the
-allocating entry point spde_precond within the preconditioner tolerances
-used elsewhere in the suite; a request that needs more than the static
-scratch must be rejected before any work.  Kept in a file of its own that
-pytest collects last.
+synchronisation).  Through the C ABI, two calls in a row must give exactly
+what the allocating entry point spde_precond gives (same kernels, same plan,
+only the scratch lives elsewhere); a call on a shape never seen before must
+leave the device's free memory unchanged; a request that needs more than the
+static scratch, or a grid beyond the library's limit, must be rejected
+before any work.  Kept in a file of its own that pytest collects last.
 """
 import numpy as np
 import pytest
@@ -38,7 +39,6 @@ def _rand(n, ns, seed, dt):
 def test_noalloc_matches_allocating_entry_point(n, ns, prec):
     h, kappa = 1.0 / n, 20.0
     dt = torch.float64 if prec == pkg.SPDE_PREC_FP64 else torch.float32
-    tol = 1e-12 if prec == pkg.SPDE_PREC_FP64 else 2e-6
     for call, seed in enumerate((11, 12)):  # two calls in a row share the static scratch
         r = _rand(n, ns, seed + n, dt)
         ref = torch.full_like(r, float("nan"))
@@ -46,10 +46,26 @@ def test_noalloc_matches_allocating_entry_point(n, ns, prec):
         pkg.spde_precond(n, h, kappa, ns, prec, r, ref)
         pkg.spde_precond_noalloc(n, h, kappa, ns, prec, r, got)
         torch.cuda.synchronize()
-        a = got.cpu().numpy().astype(np.float64)
-        b = ref.cpu().numpy().astype(np.float64)
-        assert np.all(np.isfinite(a)), call
-        assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), call
+        assert torch.isfinite(got).all(), call
+        assert torch.equal(got, ref), call  # the same kernels on the same plan: bitwise equal
+    pkg.spde_precond_status()  # neither call's sweeps gave up
+
+
+def test_noalloc_allocates_no_device_memory():
+    n, ns, prec = 64, 6, pkg.SPDE_PREC_MIXED  # a shape no other call in this file uses
+    r = _rand(n, ns, 5, torch.float32)
+    z1 = torch.empty_like(r)
+    z2 = torch.empty_like(r)
+    warm = _rand(16, 1, 6, torch.float32)  # loads the kernels (module loading is lazy)
+    pkg.spde_precond_noalloc(16, 1.0 / 16, 20.0, 1, prec, warm, torch.empty_like(warm))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pkg.spde_precond_noalloc(n, 1.0 / n, 20.0, ns, prec, r, z1)
+    pkg.spde_precond_noalloc(n, 1.0 / n, 20.0, ns, prec, r, z2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(z1, z2) and torch.isfinite(z1).all()
 
 
 def test_noalloc_rejects_requests_beyond_the_static_scratch():
@@ -59,3 +75,7 @@ def test_noalloc_rejects_requests_beyond_the_static_scratch():
         pkg.spde_precond_noalloc(n, 1.0 / n, 20.0, 4, pkg.SPDE_PREC_FP64, r, r)
     assert ei.value.status == pkg.SPDE_EINVAL
     assert "static scratch" in str(ei.value)
+    with pytest.raises(pkg.SpdeError) as ei:  # beyond the grid limit of every entry point
+        pkg.spde_precond_noalloc(1024, 1.0 / 1024, 20.0, 1, pkg.SPDE_PREC_MIXED, r, r)
+    assert ei.value.status == pkg.SPDE_EINVAL
+    assert "static scratch" not in str(ei.value)
