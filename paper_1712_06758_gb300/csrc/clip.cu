@@ -68,12 +68,16 @@ __device__ int clip_axis(const D3* in, int m, D3* out, int ax, double bound, dou
     return k;
 }
 
-// clip polygon by {x : n.x - d <= 0} (unit n)
-__device__ int clip_plane(const D3* in, int m, D3* out, D3 n, double d) {
+// clip polygon by {x : n.(x - o) <= 0} (unit n, o a point of the plane).  The
+// distance is taken from a point of the plane, not as n.x - n.o: for a plane
+// nearly parallel to the polygon (a thin tet's side face over a cell face) the
+// second form cancels two numbers of size 1 down to ~1e-5 and moves the cut
+// points by ~1e-11, which the other half of the surface does not see.
+__device__ int clip_plane(const D3* in, int m, D3* out, D3 n, D3 o) {
     int k = 0;
     for (int i = 0; i < m; ++i) {
         const D3 a = in[i], b = in[(i + 1) % m];
-        const double da = dot3(n, a) - d, db = dot3(n, b) - d;
+        const double da = dot3(n, a - o), db = dot3(n, b - o);
         if (da <= 0.0 && k < kPolyMax) out[k++] = a;
         if ((da < 0.0 && db > 0.0) || (da > 0.0 && db < 0.0)) {
             if (k < kPolyMax) out[k++] = a + (da / (da - db)) * (b - a);
@@ -89,14 +93,14 @@ __device__ double tet_unit_cube_volume(const D3 p[4]) {
     D3 bufA[kPolyMax], bufB[kPolyMax];
     double v6 = 0.0;
     D3 nrm[4];
-    double off[4];
+    D3 anc[4];  // a vertex of each face: the origin of its distances
     for (int f = 0; f < 4; ++f) {
         const D3 a = p[F[f][0]], b = p[F[f][1]], c = p[F[f][2]];
         D3 nv = cross3(b - a, c - a);
         const double len = sqrt(dot3(nv, nv));
         nv = (1.0 / len) * nv;
         nrm[f] = nv;
-        off[f] = dot3(nv, a);
+        anc[f] = a;
         // (a) tet face clipped to the cell, unless it lies on a cell plane with
         // the same outward direction (then (b) supplies that face)
         bool skip = false;
@@ -134,10 +138,10 @@ __device__ double tet_unit_cube_volume(const D3 p[4]) {
                 bufA[q] = v;
             }
             int m = 4;
-            m = clip_plane(bufA, m, bufB, nrm[0], off[0]);
-            m = clip_plane(bufB, m, bufA, nrm[1], off[1]);
-            m = clip_plane(bufA, m, bufB, nrm[2], off[2]);
-            m = clip_plane(bufB, m, bufA, nrm[3], off[3]);
+            m = clip_plane(bufA, m, bufB, nrm[0], anc[0]);
+            m = clip_plane(bufB, m, bufA, nrm[1], anc[1]);
+            m = clip_plane(bufA, m, bufB, nrm[2], anc[2]);
+            m = clip_plane(bufB, m, bufA, nrm[3], anc[3]);
             if (m >= 3) v6 += fan6(bufA, m);
         }
     }
