@@ -18,9 +18,13 @@
  *     itself (grids, coupling matrices, solver workspace) is owned by the
  *     context and released by spde_destroy().
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *     stream).  Kernels are enqueued on it; functions that must inspect
- *     convergence synchronise it before returning (stated per function).
- *   - A context serialises calls on itself with an internal mutex.
+ *     stream).  Kernels are enqueued on it.  The sampling calls are
+ *     asynchronous on it (they return once the work is enqueued; the
+ *     solver's convergence is decided on the device) unless stated
+ *     otherwise; their outcome is collected by spde_wait.
+ *   - A context serialises calls on itself with an internal mutex; calls that
+ *     use the same level's workspace from different streams are ordered on
+ *     the device (the later one waits for the earlier one's completion event).
  *
  * Discrete system (scaled form).  Grid: N = nx ny nz cubes of edge h (a cube
  * n^3 from spde_level_add, a box from spde_level_add_box; "n^3" below means N
@@ -98,17 +102,24 @@ typedef struct {
     double omega;       /* damped-Jacobi weight of the V-cycle smoother; 0.8 */
     double schur_c;     /* weight c of the 7-point Schur approximation kappa^2 h^2 I + c L; 1.0 */
     double flux_diag;   /* flux-block preconditioner, a multiple of the identity; 1.5 = diag(T)^{-1} */
-    int check_every;    /* MINRES iterations between host convergence checks; 8 (at most 64 are used) */
+    int check_every;    /* synchronous path: MINRES iterations between host convergence checks;
+                           8 (at most 64 are used) */
     int device;         /* CUDA device ordinal; 0 */
-    int use_graphs;     /* capture the batched MINRES iteration in CUDA graphs; 1 */
+    int use_graphs;     /* 1 (default): each refinement solve runs as one captured CUDA graph whose
+                           conditional while-nodes run the refinement steps and the MINRES
+                           iterations, with every convergence test on the device, so the sampling
+                           calls return without synchronising.  0, per-kernel timing on, or the
+                           Schur-CG solver: the synchronous path (host loop, convergence read back
+                           every check_every iterations).  Both give the same bits. */
     int64_t serve_budget_bytes; /* device memory the serving lanes may hold; 120 GiB */
     int serve_max_batch;        /* columns per serving lane; 64 */
     int solver;                 /* SPDE_SOLVER_MINRES (default) or SPDE_SOLVER_SCHUR_CG */
 } spde_opts;
 
 typedef struct {
-    int outer_iters;        /* refinement steps of the last solve */
-    int inner_iters;        /* MINRES iterations summed over refinement steps (max over samples) */
+    int outer_iters;        /* refinement steps of the last call's solves (max) */
+    int inner_iters;        /* MINRES iterations summed over refinement steps (max over solves;
+                               the synchronous path counts in steps of check_every) */
     double max_rel_residual;/* max over samples of the final ||F - A x|| / ||F|| (FP64) */
     double setup_ms;        /* last spde_mesh_attach: clipping + CSR build on the device */
     int64_t nnz;            /* nonzeros of the last attached coupling matrix */
@@ -162,9 +173,16 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
  *   kappa > 0, sigma > 0 finite; nu is fixed at 1/2.
  *   out   device (or host) buffer of the layout `out_kind` states; host
  *         memory is detected and filled through an internal device buffer.
- * The call returns after the results are complete (it synchronises
- * `stream`).  SPDE_ENOCONV: tolerance not reached, `out` holds the last
- * iterate. */
+ * Asynchronous on `stream` (opts.use_graphs = 1 and no per-kernel timing):
+ * the call enqueues noise, one graph launch per batch (refinement and MINRES
+ * run on the device) and the projection, and returns; `out` is valid once
+ * `stream` has synchronised.  Argument errors are returned at once; the
+ * solver's outcome (SPDE_ENOCONV: tolerance not reached, `out` holds the
+ * last iterate; SPDE_ETIMEOUT) is returned by spde_wait.  With a host `out`
+ * the call returns after the copy, with that outcome.  The first call for a
+ * (level, batch size, kappa) captures the graph (a few ms).  On the
+ * synchronous path the call synchronises `stream` and returns the outcome
+ * itself. */
 spde_status spde_sample(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma,
                         uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream);
 
@@ -184,10 +202,12 @@ spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_
 
 /* spde_sample with the fields of spde_level_set_fields in place of one kappa
  * and sigma.  The mixed operator and the FP64 residual take kappa_c per
- * cell; the multigrid preconditioner uses the mean of (kappa_c h)^2, so the
+ * cell; the multigrid preconditioner takes per-cell diagonals on every
+ * level (the children's mean of (kappa_c h)^2 on coarse levels), so the
  * field is exact to the tolerance and only the iteration count depends on
- * how strongly kappa varies.  MINRES solver only (SPDE_EINVAL with
- * SPDE_SOLVER_SCHUR_CG); SPDE_EINVAL when the level has no fields. */
+ * how strongly kappa varies.  Asynchronous as spde_sample.  MINRES solver
+ * only (SPDE_EINVAL with SPDE_SOLVER_SCHUR_CG); SPDE_EINVAL when the level
+ * has no fields. */
 spde_status spde_sample_fields(spde_ctx* ctx, int level, int nsamples, uint64_t seed,
                                uint64_t first_sample, int out_kind, void* out, void* stream);
 
@@ -201,7 +221,7 @@ spde_status spde_sample_fields(spde_ctx* ctx, int level, int nsamples, uint64_t 
  *   coarse_level must have n_c = n_f / 2 on the same box;
  *   out_fine   device [nsamples][fine outputs], out_coarse device
  *   [nsamples][coarse outputs] (layout of out_kind on each level).
- * Synchronises `stream`; SPDE_ENOCONV as spde_sample. */
+ * Asynchronous as spde_sample (outcome by spde_wait). */
 spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level, int nsamples, double kappa,
                                 double sigma, uint64_t seed, uint64_t first_sample, int out_kind, void* out_fine,
                                 void* out_coarse, void* stream);
@@ -239,8 +259,19 @@ spde_status spde_cancel(spde_ctx* ctx, int64_t request);
  * level already holds (workspace of the selected precision path). */
 spde_status spde_query_footprint(spde_ctx* ctx, int level, int nsamples, int64_t* bytes);
 
-/* Statistics of the last solve / mesh attach on this context. */
+/* Statistics of the last call / mesh attach on this context (waits for the
+ * context's enqueued calls; after asynchronous calls not yet collected by
+ * spde_wait, the maxima over those calls). */
 spde_status spde_get_stats(spde_ctx* ctx, spde_stats* stats);
+
+/* Wait until every call enqueued on this context has finished and return the
+ * worst outcome of the asynchronous calls since the previous spde_wait:
+ * SPDE_OK, SPDE_ENOCONV (some solve stopped above the tolerance: its output
+ * holds the last iterate, spde_get_stats the residual) or SPDE_ETIMEOUT (a
+ * multigrid sweep gave up waiting for a plane copy: those outputs are
+ * invalid).  No paper counterpart: the collection point of the asynchronous
+ * calls. */
+spde_status spde_wait(spde_ctx* ctx);
 
 /* Size of the coupling matrix of `level`. */
 spde_status spde_mesh_info(spde_ctx* ctx, int level, int64_t* ntets, int64_t* nnz);

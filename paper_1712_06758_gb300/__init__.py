@@ -67,6 +67,7 @@ _SIGS = {
     "spde_cancel": [_P, ctypes.c_int64],
     "spde_query_footprint": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "spde_get_stats": [_P, ctypes.POINTER(spde_stats)],
+    "spde_wait": [_P],
     "spde_mesh_info": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "spde_mesh_copy_csr": [_P, ctypes.c_int, _P, _P, _P, _P],
     "spde_destroy": [_P],
@@ -239,6 +240,11 @@ def spde_get_stats(ctx):
     return {k: getattr(s, k) for k, _ in spde_stats._fields_}
 
 
+def spde_wait(ctx):
+    """Waits for the context's calls; raises SpdeError with their worst outcome."""
+    _check(lib().spde_wait(ctx))
+
+
 def spde_mesh_info(ctx, level):
     nt, nz = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().spde_mesh_info(ctx, level, ctypes.byref(nt), ctypes.byref(nz)))
@@ -366,7 +372,8 @@ class Sampler:
         return spde_mesh_info(self.ctx, level)[0]
 
     def sample(self, level, nsamples, kappa, sigma, seed, first_sample=0, out_kind=SPDE_OUT_LOGNORMAL, out=None,
-               stream=None):
+               stream=None, wait=True):
+        """spde_sample; with wait (the default) also spde_wait, so the outcome is raised here."""
         import torch
         if out is None:
             cells = self.levels[level][0]
@@ -374,6 +381,8 @@ class Sampler:
             dt = torch.float64 if out_kind & SPDE_OUT_F64 else torch.float32
             out = torch.empty((nsamples, per), dtype=dt, device="cuda")
         spde_sample(self.ctx, level, nsamples, kappa, sigma, seed, first_sample, out_kind, out, stream)
+        if wait:
+            spde_wait(self.ctx)
         return out
 
     def set_fields(self, level, kappa_cells, sigma_cells):
@@ -385,7 +394,7 @@ class Sampler:
         spde_level_set_fields(self.ctx, level, kappa_cells, sigma_cells)
 
     def sample_fields(self, level, nsamples, seed, first_sample=0, out_kind=SPDE_OUT_LOGNORMAL, out=None,
-                      stream=None):
+                      stream=None, wait=True):
         import torch
         if out is None:
             cells = self.levels[level][0]
@@ -393,6 +402,8 @@ class Sampler:
             dt = torch.float64 if out_kind & SPDE_OUT_F64 else torch.float32
             out = torch.empty((nsamples, per), dtype=dt, device="cuda")
         spde_sample_fields(self.ctx, level, nsamples, seed, first_sample, out_kind, out, stream)
+        if wait:
+            spde_wait(self.ctx)
         return out
 
     def stats(self):

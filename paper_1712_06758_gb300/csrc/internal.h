@@ -92,6 +92,26 @@ struct CgCol {
     int pad0, pad1;
 };
 
+// Device state of one refinement solve driven by a captured graph (no host
+// round trip): the control kernels of krylov.cu make the decisions the host
+// loop of the synchronous path makes, from the same FP64 numbers.
+struct RefineCtl {
+    int outer;    // corrections applied so far
+    int inner;    // inner-solver loop iterations executed in this solve (all steps)
+    int it;       // loop iterations of the current inner solve
+    int status;   // 0, 4 (tolerance not reached) or 5 (a sweep timed out) once stopped
+    int cnt[6];   // column counters of the Givens / CG steps of one loop body
+    double worst; // largest relative residual at the last check
+};
+
+// Outcome of the graph-driven solves of the calls since the host last read it
+// (solves on different streams update it with atomics; worst_bits holds the bits
+// of a non-negative double, whose integer order is its numeric order).
+struct CallAcc {
+    int outer, inner, status, nsolve;
+    unsigned long long worst_bits;
+};
+
 // Multigrid plan of one grid size for a batch of S columns.
 struct MGPlan {
     Grid3 g[16];        // grids of the levels: g[l + 1] = g[l].coarser(), g[nlev - 1] has one cell
@@ -132,6 +152,8 @@ cudaError_t launch_apply(const Grid3& g, double kh2, int S, const T* x, T* y, cu
 int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
                       float* r32, double* r64, double* part, const int* active, cudaStream_t st,
                       const double* kh2c = nullptr);
+// one-time kernel attributes of the flux line solves (done before any stream capture)
+cudaError_t flux_prepare();
 // the multigrid diagonal of a level with cell-wise (kappa h)^2: a_c = mean of the children's a
 // (a_0 = (kappa_c h)^2; gf is the finer grid), D = s (a_c q + c k_c) with k_c the cell's
 // existing neighbours and s, q the level's factors (2^l, 4^l on a cube)
@@ -147,9 +169,10 @@ cudaError_t launch_field_coefs(int64_t n3, double h, const double* kappa, const 
 cudaError_t launch_add_correction(int64_t nelem, int S, double* x, const float* d, const int* active,
                                   cudaStream_t st);
 // u = -T^{-1} D1^T theta into the flux blocks of x ([S][4 cells], FP64), line by line;
-// tri: Thomas factors of the longest extent tn (2 tn - 2 doubles, see k_flux_lines)
+// tri: Thomas factors of the longest extent tn (2 tn - 2 doubles, see k_flux_lines);
+// gate (device, optional): the kernels do nothing while *gate == 0
 cudaError_t launch_flux_from_theta(const Grid3& g, int S, double* x, int64_t col_stride, const double* tri,
-                                   cudaStream_t st);
+                                   cudaStream_t st, const int* gate = nullptr);
 // x cell block += d ([S][n^3]) for columns whose inner solve ran
 template <typename T>
 cudaError_t launch_add_theta(int64_t n3, int S, double* x, const T* d, const MinresCol* st_, cudaStream_t st);
@@ -182,8 +205,22 @@ int launch_precond_u(int64_t N4, int n3, int S, const T* r, T* y, double fd, dou
 cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cudaStream_t st);
 // nactive (optional, two ints): [0] += columns still active after this step,
 // [1] += columns whose w/x update this step left pending
+// max_iter: a column stops after this many iterations (the iteration cap of the solve)
 cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC,
-                          MinresCol* st_, int* nactive, cudaStream_t st);
+                          MinresCol* st_, int* nactive, cudaStream_t st, int max_iter = 1 << 30);
+// control kernels of the graph-driven refinement (one thread block each)
+cudaError_t launch_refine_init(RefineCtl* ctl, int* fault, unsigned long long h_outer, cudaStream_t st);
+// residual check of every column (colv: [S] |r|^2, then [S] |F|^2): mask, inner tolerances,
+// stop decision (-> h_outer), and the step count
+cudaError_t launch_refine_check(int S, const double* colv, double tol, double inner_tol, int fp64_inner,
+                                int max_outer, const int* fault, int* mask, double* coltol, RefineCtl* ctl,
+                                unsigned long long h_outer, cudaStream_t st);
+// end of a loop body: iterations += add, continue while columns counted in slot remain and
+// the iteration cap is not reached (-> h_loop); clears the counters
+cudaError_t launch_loop_ctl(RefineCtl* ctl, int slot, int add, int max_iter, unsigned long long h_loop,
+                            cudaStream_t st);
+// count_iters = 0: record the solve's residual and status only (the coarse solve of a coupled pair)
+cudaError_t launch_refine_finish(const RefineCtl* ctl, CallAcc* acc, int count_iters, cudaStream_t st);
 // col_tol (device [S], optional): each column's own stopping tolerance instead of tol
 cudaError_t launch_minres_init(int S, const double* partB, int nB, const double* partC, int nC,
                                double tol, MinresCol* st_, int* nactive, cudaStream_t st,
@@ -207,6 +244,8 @@ cudaError_t mg_fault_read(const int* fault, int* host, cudaStream_t st);
 // its wait time goes to *elapsed_ns_dev
 cudaError_t mg_wait_probe(unsigned long long* elapsed_ns_dev, int* fault, cudaStream_t st);
 cudaError_t mg_fault_clear(int* fault, cudaStream_t st);
+// one-time kernel attributes and driver entry points of the V-cycle (done before any stream capture)
+cudaError_t mg_prepare();
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride,
                   double* dot_part, const int* active, int act_stride, cudaStream_t st);
@@ -236,7 +275,7 @@ template <typename T>
 cudaError_t launch_cg_add(int64_t n3, int S, double* x, const T* d, const CgCol* st, cudaStream_t s);
 cudaError_t launch_cg_alpha(int S, const double* part, int nb, CgCol* st, cudaStream_t s);
 cudaError_t launch_cg_beta(int S, const double* prr, int nrr, const double* prz, int nrz, CgCol* st, int* nactive,
-                           cudaStream_t s);
+                           cudaStream_t s, int max_iter = 1 << 30);
 cudaError_t launch_cg_init(int S, const double* prz, int nrz, const double* prr, int nrr, double tol, CgCol* st,
                            int* nactive, cudaStream_t s);
 cudaError_t launch_cg_set_active(int S, const int* mask, CgCol* st, cudaStream_t s);

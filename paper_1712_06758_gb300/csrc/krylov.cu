@@ -92,6 +92,19 @@ __device__ __forceinline__ void apply_quad_fd(const T* __restrict__ us, const T*
     vc[3] = th4;
 }
 
+// The w/x update of one 4-cell vector (the D step), shared by the fused pass
+// and the final k_minres_D so that both produce the same bits:
+//   w' = (v / oldb - oldeps w1 - delta w2) / gamma,  x' = x + phi w'
+template <typename T>
+__device__ __forceinline__ void d_update4(const V4<T>& yv, const V4<T>& w1v, const V4<T>& w2v, const V4<T>& xv, T iv,
+                                          T oe, T de, T ig, T ph, V4<T>& wn, V4<T>& xn) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        wn.v[k] = (yv.v[k] * iv - oe * w1v.v[k] - de * w2v.v[k]) * ig;
+        xn.v[k] = xv.v[k] + ph * wn.v[k];
+    }
+}
+
 // CUBE: the grid is a cube (all extents and logs taken from x, which keeps the
 // index arithmetic and register use of the cubic case minimal)
 template <typename T, bool CUBE>
@@ -170,11 +183,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 
             const V4<T> w1v = (it >= 3) ? ld4(w1 + o3 + e0) : zero4<T>();
             const V4<T> xv = (it >= 2) ? ld4(xd + o3 + e0) : zero4<T>();
             V4<T> wn, xn;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                wn.v[k] = (yv.v[k] * iv - oe * w1v.v[k] - de * w2v.v[k]) * ig;
-                xn.v[k] = xv.v[k] + ph * wn.v[k];
-            }
+            d_update4<T>(yv, w1v, w2v, xv, iv, oe, de, ig, ph, wn, xn);
             st4(w1 + o3 + e0, wn);
             st4(xd + o3 + e0, xn);
         }
@@ -281,7 +290,8 @@ cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cud
 }
 
 __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB, int nB, const double* __restrict__ partC,
-                                                int nC, MinresCol* __restrict__ st, int* __restrict__ nactive) {
+                                                int nC, MinresCol* __restrict__ st, int* __restrict__ nactive,
+                                                int max_iter) {
     __shared__ double red[8];
     const int s = blockIdx.x;
     MinresCol& c = st[s];
@@ -325,15 +335,125 @@ __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB
     set_coef(c, KC_DE, c.d_delta);
     set_coef(c, KC_IG, 1.0 / c.d_gamma);
     set_coef(c, KC_PH, c.d_phi);
-    const bool done = !(beta2 > 0.0) || !isfinite(beta) || c.phibar <= c.tol * c.beta1;
+    const bool done = !(beta2 > 0.0) || !isfinite(beta) || c.phibar <= c.tol * c.beta1 || c.iters >= max_iter;
     if (nactive) atomicAdd(nactive + 1, 1);  // this column's update is pending
     if (done) c.active = 0;
     else if (nactive) atomicAdd(nactive, 1);
 }
 
 cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC, MinresCol* st_,
-                          int* nactive, cudaStream_t st) {
-    k_givens<<<S, 256, 0, st>>>(partB, nB, partC, nC, st_, nactive);
+                          int* nactive, cudaStream_t st, int max_iter) {
+    k_givens<<<S, 256, 0, st>>>(partB, nB, partC, nC, st_, nactive, max_iter);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Control of the graph-driven refinement.  The captured graph runs
+//   init; while (go) { residual; check -> go; inner solve; correction }
+// with the inner solve's iterations in a nested while; these kernels take the
+// decisions the synchronous host loop takes (same FP64 formulas, same order of
+// the per-column tests), so both paths produce the same bits.
+// ---------------------------------------------------------------------------
+__global__ void k_refine_init(RefineCtl* ctl, int* fault, cudaGraphConditionalHandle h_outer) {
+    ctl->outer = 0;
+    ctl->inner = 0;
+    ctl->it = 0;
+    ctl->status = 0;
+    for (int k = 0; k < 6; ++k) ctl->cnt[k] = 0;
+    ctl->worst = 0.0;
+    *fault = 0;  // a timeout of an earlier solve was reported with that solve
+    cudaGraphSetConditional(h_outer, 1u);
+}
+
+cudaError_t launch_refine_init(RefineCtl* ctl, int* fault, unsigned long long h_outer, cudaStream_t st) {
+    k_refine_init<<<1, 1, 0, st>>>(ctl, fault, (cudaGraphConditionalHandle)h_outer);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_refine_check(int S, const double* __restrict__ colv, double tol,
+                                                      double inner_tol, int fp64_inner, int max_outer,
+                                                      const int* __restrict__ fault, int* __restrict__ mask,
+                                                      double* __restrict__ coltol, RefineCtl* __restrict__ ctl,
+                                                      cudaGraphConditionalHandle h_outer) {
+    __shared__ double smax[8];
+    __shared__ int scnt[8];
+    double worst = 0.0;
+    int nact = 0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const double fn = colv[S + s];
+        const double rel = fn > 0.0 ? sqrt(colv[s] / fn) : 0.0;
+        worst = fmax(worst, rel);
+        nact += rel > tol ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+        nact += __shfl_xor_sync(0xffffffffu, nact, o);
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        smax[wid] = worst;
+        scnt[wid] = nact;
+    }
+    __syncthreads();
+    double W = 0.0;
+    int N = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        W = fmax(W, smax[k]);
+        N += scnt[k];
+    }
+    const int flt = *(volatile const int*)fault;
+    const bool stop = flt != 0 || N == 0 || ctl->outer >= max_outer;
+    const double wtol = fmax(0.1 * tol / fmax(W, 1e-300), 1e-15);  // FP64 inner: one reduction for all
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const double fn = colv[S + s];
+        const double rel = fn > 0.0 ? sqrt(colv[s] / fn) : 0.0;
+        mask[s] = (!stop && rel > tol) ? 1 : 0;
+        coltol[s] = fp64_inner ? wtol : fmax(inner_tol, 0.1 * tol / fmax(rel, 1e-300));
+    }
+    if (threadIdx.x == 0) {
+        ctl->worst = W;
+        ctl->it = 0;
+        for (int k = 0; k < 6; ++k) ctl->cnt[k] = 0;
+        if (stop) ctl->status = flt ? 5 : (W > tol ? 4 : 0);
+        else ctl->outer += 1;
+        cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
+    }
+}
+
+cudaError_t launch_refine_check(int S, const double* colv, double tol, double inner_tol, int fp64_inner,
+                                int max_outer, const int* fault, int* mask, double* coltol, RefineCtl* ctl,
+                                unsigned long long h_outer, cudaStream_t st) {
+    k_refine_check<<<1, 256, 0, st>>>(S, colv, tol, inner_tol, fp64_inner, max_outer, fault, mask, coltol, ctl,
+                                      (cudaGraphConditionalHandle)h_outer);
+    return cudaGetLastError();
+}
+
+__global__ void k_loop_ctl(RefineCtl* ctl, int slot, int add, int max_iter, cudaGraphConditionalHandle h_loop) {
+    const int active = ctl->cnt[2 * slot];
+    ctl->it += add;
+    ctl->inner += add;
+    for (int k = 0; k < 6; ++k) ctl->cnt[k] = 0;
+    cudaGraphSetConditional(h_loop, (active > 0 && ctl->it < max_iter) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_ctl(RefineCtl* ctl, int slot, int add, int max_iter, unsigned long long h_loop,
+                            cudaStream_t st) {
+    k_loop_ctl<<<1, 1, 0, st>>>(ctl, slot, add, max_iter, (cudaGraphConditionalHandle)h_loop);
+    return cudaGetLastError();
+}
+
+__global__ void k_refine_finish(const RefineCtl* ctl, CallAcc* acc, int count_iters) {
+    if (count_iters) {
+        atomicMax(&acc->outer, ctl->outer);
+        atomicMax(&acc->inner, ctl->inner);
+    }
+    atomicMax(&acc->status, ctl->status);
+    atomicAdd(&acc->nsolve, 1);
+    atomicMax(&acc->worst_bits, (unsigned long long)__double_as_longlong(fmax(ctl->worst, 0.0)));
+}
+
+cudaError_t launch_refine_finish(const RefineCtl* ctl, CallAcc* acc, int count_iters, cudaStream_t st) {
+    k_refine_finish<<<1, 1, 0, st>>>(ctl, acc, count_iters);
     return cudaGetLastError();
 }
 
@@ -404,11 +524,7 @@ __global__ void __launch_bounds__(256) k_minres_D(int64_t n3, const T* __restric
         const V4<T> w1v = (it >= 3) ? ld4(w1 + off + e) : zero4<T>();
         const V4<T> xv = (it >= 2) ? ld4(x + off + e) : zero4<T>();
         V4<T> wn, xn;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            wn.v[k] = (yv.v[k] * iv - oe * w1v.v[k] - de * w2v.v[k]) * ig;
-            xn.v[k] = xv.v[k] + ph * wn.v[k];
-        }
+        d_update4<T>(yv, w1v, w2v, xv, iv, oe, de, ig, ph, wn, xn);
         st4(w1 + off + e, wn);
         st4(x + off + e, xn);
     }

@@ -1095,6 +1095,13 @@ static cudaError_t mg_attrs() {
     return e;
 }
 
+cudaError_t mg_prepare() {
+    cudaError_t e = mg_attrs<float>();
+    if (e == cudaSuccess) e = mg_attrs<double>();
+    if (e == cudaSuccess && !encode_tiled()) e = cudaErrorNotSupported;
+    return e;
+}
+
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride, double* dot_part,
                   const int* active, int act_stride, cudaStream_t st) {

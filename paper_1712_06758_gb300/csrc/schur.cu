@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_cg_alpha(const double* __restrict__ par
 // after r update and z = M^{-1} r: convergence on ||r||, beta = rz_new / rz
 __global__ void __launch_bounds__(256) k_cg_beta(const double* __restrict__ part_rr, int nrr,
                                                  const double* __restrict__ part_rz, int nrz, CgCol* __restrict__ st,
-                                                 int* __restrict__ nactive) {
+                                                 int* __restrict__ nactive, int max_iter) {
     __shared__ double red[8];
     const int s = blockIdx.x;
     CgCol& c = st[s];
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_cg_beta(const double* __restrict__ part
     c.iters += 1;
     c.beta = (c.rz > 0.0) ? rz / c.rz : 0.0;
     c.rz = rz;
-    const bool done = !(rr > c.tol2 * c.rr0) || !(rz > 0.0) || !isfinite(rz);
+    const bool done = !(rr > c.tol2 * c.rr0) || !(rz > 0.0) || !isfinite(rz) || c.iters >= max_iter;
     if (done) c.active = 0;
     else if (nactive) atomicAdd(nactive, 1);
 }
@@ -337,8 +337,8 @@ cudaError_t launch_cg_alpha(int S, const double* part, int nb, CgCol* st, cudaSt
     return cudaGetLastError();
 }
 cudaError_t launch_cg_beta(int S, const double* prr, int nrr, const double* prz, int nrz, CgCol* st, int* nactive,
-                           cudaStream_t s) {
-    k_cg_beta<<<S, 256, 0, s>>>(prr, nrr, prz, nrz, st, nactive);
+                           cudaStream_t s, int max_iter) {
+    k_cg_beta<<<S, 256, 0, s>>>(prr, nrr, prz, nrz, st, nactive, max_iter);
     return cudaGetLastError();
 }
 cudaError_t launch_cg_init(int S, const double* prz, int nrz, const double* prr, int nrr, double tol, CgCol* st,

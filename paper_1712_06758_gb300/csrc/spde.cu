@@ -124,12 +124,41 @@ struct Workspace {
     MinresCol* st = nullptr;
     int* nact = nullptr;
     int* fault = nullptr;    // fault word of this workspace's V-cycle sweeps
+    // graph-driven solves: device control block, the columns to correct, the
+    // executable graphs captured for this workspace, and the event that marks the
+    // end of the last call enqueued on it (calls on other streams wait for it)
+    RefineCtl* ctl = nullptr;
+    int* mask = nullptr;
+    cudaEvent_t done = nullptr;
+    struct Graph {
+        int S, t64, warm, count;
+        const void* fields;
+        double kh2;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+
+    // wait until the last call enqueued on this workspace has finished
+    void quiesce() {
+        if (done) cudaEventSynchronize(done);
+        cudaGetLastError();
+    }
+    void drop_graphs() {
+        for (auto& gr : graphs) cudaGraphExecDestroy(gr.exec);
+        graphs.clear();
+    }
     int* h_nact = nullptr;   // pinned
     double* h_col = nullptr; // pinned [2S]
     MinresCol* h_st = nullptr;
     float* thetaT = nullptr; // [n^3][S]
 
     void release() {
+        quiesce();
+        drop_graphs();
+        if (done) cudaEventDestroy(done);
+        done = nullptr;
+        dev_free(ctl);
+        dev_free(mask);
         dev_free(x64);
         dev_free(F);
         for (auto& v : vec) {
@@ -245,6 +274,14 @@ struct spde_ctx {
     void* out_tmp = nullptr;
     size_t out_tmp_bytes = 0;
     Server* srv = nullptr;  // serving engine, started by the first spde_submit
+    // graph-driven (asynchronous) calls: capture streams, the device record of their
+    // solves' outcome (read by spde_wait / spde_get_stats), and whether it holds
+    // results the host has not read yet
+    cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+    CallAcc* d_acc = nullptr;
+    CallAcc* h_acc = nullptr;  // pinned
+    bool acc_pending = false;
+    int deferred = SPDE_OK;    // worst outcome of graph-driven calls not yet returned by spde_wait
 };
 
 namespace {
@@ -287,6 +324,14 @@ spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64)
     // per MINRES iteration of a chunk: [2q] columns still active after it, [2q+1] columns it left an update pending
     STATUS_TRY(dev_alloc(&ws.nact, 2 * kMaxChunk));
     STATUS_TRY(dev_alloc(&ws.fault, 1));
+    STATUS_TRY(dev_alloc(&ws.ctl, 1));
+    STATUS_TRY(dev_alloc(&ws.mask, (size_t)S));
+    if (cudaEventCreateWithFlags(&ws.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ws.done = nullptr;
+        ws.release();
+        return fail(SPDE_ECUDA, "event creation failed");
+    }
     if (cudaMemset(ws.fault, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         ws.release();
@@ -399,7 +444,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
             prof_end(st, 12.0 * n3d * w);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
             prof_begin(PK_GIVENS, st);
-            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, ws.nact + 2 * q, st));
+            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, ws.nact + 2 * q, st, o.max_iter));
             prof_end(st, (nB + nC) * 8.0);
             pending = true;
             last_itn = itn;
@@ -488,7 +533,8 @@ spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Work
             const int nrz = launch_vcycle<T>(plan, S, r, n3, z, n3, ws.partC, act, act_stride, st);
             if (k == chunk - 1) CUDA_TRY(cudaMemsetAsync(ws.nact, 0, sizeof(int), st));
             prof_begin(PK_GIVENS, st);
-            CUDA_TRY(launch_cg_beta(S, ws.partB, nrr, ws.partC, nrz, ws.cg, (k == chunk - 1) ? ws.nact : nullptr, st));
+            CUDA_TRY(launch_cg_beta(S, ws.partB, nrr, ws.partC, nrz, ws.cg, (k == chunk - 1) ? ws.nact : nullptr, st,
+                                    o.max_iter));
             prof_end(st, cols * (nrr + nrz) * 8.0);
             prof_begin(PK_CG_UPDATE, st);
             CUDA_TRY(launch_cg_p<T>(n3, S, p, z, ws.cg, st));
@@ -616,6 +662,275 @@ spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Works
     return SPDE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Graph-driven refinement (the asynchronous path).
+//
+// One solve of S columns is captured once per (workspace, S, precision, warm
+// start, fields, kappa) into a CUDA graph of the shape
+//     ||F||^2;  x = 0;  init
+//     while (go) {                         outer: refinement steps
+//         flux from theta; FP64 residual; check -> go, columns, inner tolerances
+//         y = P^{-1} r; MINRES start; iteration 1
+//         while (more) { iteration; iteration; count -> more }   inner
+//         final w/x update; theta += d
+//     }
+//     record the outcome
+// whose conditions are set on the device by the control kernels (krylov.cu).
+// It launches exactly the kernels of the synchronous path in the same order
+// with the same arguments; the only difference is that iterations after every
+// column has retired (at most one per loop body, where the host checks every
+// check_every iterations) run as no-ops on retired columns.  Two iterations
+// per loop body keep the ping-pong buffers in the same places at every test of
+// the condition, so the captured pointers stay valid.
+// ---------------------------------------------------------------------------
+struct CaptureGuard {  // ends captures still open when a capture step fails
+    cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+    ~CaptureGuard() {
+        for (int i = 2; i >= 0; --i)
+            if (st[i]) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(st[i], &g);
+                if (g && i == 0) cudaGraphDestroy(g);
+            }
+        cudaGetLastError();
+    }
+};
+
+// adds a while node at the capture point of `st` (which then depends on it) and
+// returns its body graph
+spde_status add_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(SPDE_ECUDA, "stream capture is not active");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return SPDE_OK;
+}
+
+spde_status ensure_capture_streams(spde_ctx* ctx) {
+    for (auto& c : ctx->cap)
+        if (!c) CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    if (!ctx->d_acc) {
+        STATUS_TRY(dev_alloc(&ctx->d_acc, 1));
+        if (cudaMallocHost(&ctx->h_acc, sizeof(CallAcc)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_acc = nullptr;
+            return fail(SPDE_ENOMEM, "pinned host allocation failed");
+        }
+    }
+    return SPDE_OK;
+}
+
+template <typename T>
+spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Workspace& ws, bool warm,
+                           const Fields* fl, bool count, cudaGraph_t* out) {
+    const spde_opts& o = ctx->opts;
+    const int64_t n3 = g.cells(), N4 = 4 * n3;
+    const bool t64 = std::is_same<T, double>::value;
+    cudaStream_t c0 = ctx->cap[0], c1 = ctx->cap[1], c2 = ctx->cap[2];
+    const T* kh2c = nullptr;
+    T* const* Dlev = nullptr;
+    if (fl) {
+        if constexpr (sizeof(T) == 4) {
+            kh2c = fl->kh2_32;
+            Dlev = fl->D32;
+        } else {
+            kh2c = fl->kh2_64;
+            Dlev = fl->D64;
+        }
+    }
+    MGPlan plan;
+    if (!mg_plan_init(plan, g, kh2, o.schur_c, o.omega)) return fail(SPDE_EINVAL, "grid shape not supported by the V-cycle");
+    mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
+    plan.fault = ws.fault;
+    if (Dlev)
+        for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
+    const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
+    const int* act = &ws.st[0].active;
+    T* d = static_cast<T*>(ws.vec[0]);
+    T* w1 = static_cast<T*>(ws.vec[1]);
+    T* w2 = static_cast<T*>(ws.vec[2]);
+    T* r1 = static_cast<T*>(ws.vec[3]);
+    T* r2 = static_cast<T*>(ws.vec[4]);
+    T* ycur = static_cast<T*>(ws.vec[5]);
+    T* ynext = static_cast<T*>(ws.vec[6]);
+    RefineCtl* ctl = ws.ctl;
+
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h_outer, h_inner;
+    if (cudaGraphConditionalHandleCreate(&h_outer, graph, 0, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        CUDA_TRY(cudaGetLastError());
+        return fail(SPDE_ECUDA, "conditional handle creation failed");
+    }
+    CaptureGuard guard;
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(c0, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    guard.st[0] = c0;
+    // ||F||^2 per column, x = 0 (cold start), control block
+    int nb = launch_sumsq(n3, S, ws.F, n3, ws.partR, c0);
+    CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv + S, c0));
+    if (!warm) CUDA_TRY(cudaMemsetAsync(ws.x64, 0, (size_t)S * N4 * sizeof(double), c0));
+    CUDA_TRY(launch_refine_init(ctl, ws.fault, h_outer, c0));
+    cudaGraph_t outer_body = nullptr;
+    STATUS_TRY(add_while(c0, h_outer, &outer_body));
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&h_inner, outer_body, 0, 0));
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(c1, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    guard.st[1] = c1;
+    {
+        // one refinement step: residual, decisions, inner MINRES, correction
+        CUDA_TRY(launch_flux_from_theta(g, S, ws.x64, N4, ws.tri, c1, warm ? nullptr : &ctl->outer));
+        float* r32 = t64 ? nullptr : reinterpret_cast<float*>(r2);
+        double* r64 = t64 ? reinterpret_cast<double*>(r2) : nullptr;
+        nb = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, c1, fl ? fl->kh2_64 : nullptr);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, c1));
+        CUDA_TRY(launch_refine_check(S, ws.colv, o.tol, o.inner_tol, t64 ? 1 : 0, o.max_outer, ws.fault, ws.mask,
+                                     ws.coltol, ctl, h_outer, c1));
+        CUDA_TRY(launch_set_active(S, ws.mask, ws.st, c1));
+        const int nB0 = launch_precond_u<T>(N4, (int)n3, S, r2, ycur, o.flux_diag, ws.partB, ws.st, c1);
+        const int nC0 = launch_vcycle<T>(plan, S, r2 + 3 * n3, N4, ycur + 3 * n3, N4, ws.partC, act, act_stride, c1);
+        if (nC0 < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
+        CUDA_TRY(launch_minres_init(S, ws.partB, nB0, ws.partC, nC0, o.inner_tol, ws.st, ctl->cnt + 4, c1, ws.coltol));
+        bool pending = false;
+        T* yprev = nullptr;
+        auto iteration = [&](cudaStream_t s, int slot) -> spde_status {
+            const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
+                                              pending ? yprev : nullptr, w1, w2, d, s, kh2c);
+            if (pending) std::swap(w1, w2);
+            CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, s));
+            const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, o.flux_diag, ws.partB, ws.st, s);
+            const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, s);
+            if (nC < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
+            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, ctl->cnt + 2 * slot, s, o.max_iter));
+            pending = true;
+            yprev = ycur;
+            std::swap(r1, r2);
+            std::swap(ycur, ynext);
+            return SPDE_OK;
+        };
+        STATUS_TRY(iteration(c1, 0));
+        CUDA_TRY(launch_loop_ctl(ctl, 0, 1, o.max_iter, h_inner, c1));
+        cudaGraph_t inner_body = nullptr;
+        STATUS_TRY(add_while(c1, h_inner, &inner_body));
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(c2, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        guard.st[2] = c2;
+        STATUS_TRY(iteration(c2, 0));
+        STATUS_TRY(iteration(c2, 1));
+        CUDA_TRY(launch_loop_ctl(ctl, 1, 2, o.max_iter, h_inner, c2));
+        guard.st[2] = nullptr;
+        cudaGraph_t tmp = nullptr;
+        CUDA_TRY(cudaStreamEndCapture(c2, &tmp));
+        // the pending update of the last iteration, then the correction of theta
+        CUDA_TRY(launch_minres_D<T>(n3, S, yprev, w1, w2, d, ws.st, c1));
+        CUDA_TRY(launch_add_theta<T>(n3, S, ws.x64, d, ws.st, c1));
+    }
+    guard.st[1] = nullptr;
+    {
+        cudaGraph_t tmp = nullptr;
+        CUDA_TRY(cudaStreamEndCapture(c1, &tmp));
+    }
+    CUDA_TRY(launch_refine_finish(ctl, ctx->d_acc, count ? 1 : 0, c0));
+    guard.st[0] = nullptr;
+    CUDA_TRY(cudaStreamEndCapture(c0, &graph));
+    *out = graph;
+    return SPDE_OK;
+}
+
+// the executable graph of this solve shape, captured on first use
+template <typename T>
+spde_status refine_graph(spde_ctx* ctx, const Grid3& g, double kh2, int S, Workspace& ws, bool warm, const Fields* fl,
+                         bool count, cudaGraphExec_t* exec) {
+    const int t64 = std::is_same<T, double>::value ? 1 : 0;
+    for (auto& gr : ws.graphs)
+        if (gr.S == S && gr.t64 == t64 && gr.warm == (int)warm && gr.count == (int)count &&
+            gr.fields == (const void*)fl && gr.kh2 == kh2) {
+            *exec = gr.exec;
+            return SPDE_OK;
+        }
+    STATUS_TRY(ensure_capture_streams(ctx));
+    CUDA_TRY(mg_prepare());  // one-time attributes are set outside the capture
+    CUDA_TRY(flux_prepare());
+    Profiler* saved = t_prof;  // nothing is timed inside a capture
+    t_prof = nullptr;
+    cudaGraph_t graph = nullptr;
+    const spde_status s = capture_refine<T>(ctx, g, kh2, S, ws, warm, fl, count, &graph);
+    t_prof = saved;
+    STATUS_TRY(s);
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(e);
+    if (ws.graphs.size() >= 8) {  // a few shapes per workspace (kappa changes re-capture)
+        cudaGraphExecDestroy(ws.graphs.front().exec);
+        ws.graphs.erase(ws.graphs.begin());
+    }
+    ws.graphs.push_back(Workspace::Graph{S, t64, (int)warm, (int)count, (const void*)fl, kh2, ex});
+    *exec = ex;
+    return SPDE_OK;
+}
+
+// enqueue the graph-driven solve of S columns (F, x64 in ws) on st; the outcome
+// goes to the context's device record
+template <typename T>
+spde_status refine_solve_async(spde_ctx* ctx, const Grid3& g, double kh2, int S, Workspace& ws, cudaStream_t st,
+                               bool warm = false, const Fields* fl = nullptr, bool count = true) {
+    cudaGraphExec_t ex = nullptr;
+    STATUS_TRY(refine_graph<T>(ctx, g, kh2, S, ws, warm, fl, count, &ex));
+    CUDA_TRY(cudaGraphLaunch(ex, st));
+    return SPDE_OK;
+}
+
+// start of a graph-driven call on st: its outcome record is fresh unless earlier
+// calls' outcomes are still unread; `ws` waits for the last call that used it
+spde_status async_call_begin(spde_ctx* ctx, cudaStream_t st) {
+    STATUS_TRY(ensure_capture_streams(ctx));
+    if (!ctx->acc_pending) {
+        CUDA_TRY(cudaMemsetAsync(ctx->d_acc, 0, sizeof(CallAcc), st));
+        ctx->acc_pending = true;
+        ctx->stats.outer_iters = 0;
+        ctx->stats.inner_iters = 0;
+        ctx->stats.max_rel_residual = 0.0;
+    }
+    return SPDE_OK;
+}
+
+// wait for every call enqueued on the context and fold the graph-driven solves'
+// outcome into ctx->stats and ctx->deferred; with take, return the deferred
+// outcome (SPDE_OK, ENOCONV or ETIMEOUT) and clear it
+spde_status drain_calls(spde_ctx* ctx, bool take) {
+    for (auto& L : ctx->lev) L.ws.quiesce();
+    if (ctx->acc_pending) {
+        CUDA_TRY(cudaMemcpy(ctx->h_acc, ctx->d_acc, sizeof(CallAcc), cudaMemcpyDeviceToHost));
+        ctx->acc_pending = false;
+        const CallAcc& a = *ctx->h_acc;
+        double worst = 0.0;
+        std::memcpy(&worst, &a.worst_bits, sizeof worst);
+        ctx->stats.outer_iters = std::max(ctx->stats.outer_iters, a.outer);
+        ctx->stats.inner_iters = std::max(ctx->stats.inner_iters, a.inner);
+        ctx->stats.max_rel_residual = std::max(ctx->stats.max_rel_residual, worst);
+        ctx->deferred = std::max(ctx->deferred, a.status);
+    }
+    if (!take) return SPDE_OK;
+    const int d = ctx->deferred;
+    ctx->deferred = SPDE_OK;
+    if (d == SPDE_ETIMEOUT)
+        return fail(SPDE_ETIMEOUT, "a multigrid sweep gave up waiting for a plane copy; those results are invalid");
+    if (d == SPDE_ENOCONV)
+        return fail(SPDE_ENOCONV, "tolerance not reached: relative residual %.3e", ctx->stats.max_rel_residual);
+    return SPDE_OK;
+}
+
 spde_status check_level(spde_ctx* ctx, int level) {
     if (!ctx) return fail(SPDE_EINVAL, "null context");
     if (level < 0 || level >= 16 || !ctx->lev[level].defined) return fail(SPDE_EINVAL, "level %d is not defined", level);
@@ -644,7 +959,7 @@ int batch_capacity(const Grid3& g, int S, bool inner64) {
 // With fl (a level with fields), kappa and sigma are ignored: the right-hand side
 // is -g_c h xi_c cell by cell and the operator takes (kappa_c h)^2 per cell.
 spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double sigma, uint64_t seed, uint64_t first,
-                          cudaStream_t st, const Fields* fl = nullptr) {
+                          cudaStream_t st, const Fields* fl = nullptr, bool graph = false) {
     const int64_t n3 = L.g.cells();
     const double kh2 = fl ? fl->kh2_mean : (kappa * L.h) * (kappa * L.h);
     // scaled RHS cell block: h^{-1/2} (-g h^{3/2} xi) = -g h xi
@@ -652,6 +967,10 @@ spde_status solve_samples(spde_ctx* ctx, Level& L, int S, double kappa, double s
     CUDA_TRY(launch_noise(n3, S, seed, first, fl ? 1.0 : -g_half(kappa, sigma) * L.h, L.ws.F, n3, st));
     if (fl) CUDA_TRY(launch_scale_cells(n3, S, L.ws.F, n3, fl->gh, st));
     prof_end(st, (double)S * (fl ? 24.0 : 8.0) * (double)n3);
+    if (graph) {
+        if (L.ws.inner64 == 1) return refine_solve_async<double>(ctx, L.g, kh2, S, L.ws, st, false, fl);
+        return refine_solve_async<float>(ctx, L.g, kh2, S, L.ws, st, false, fl);
+    }
     double rel = 0.0;
     int outer = 0, inner = 0;
     spde_status s;
@@ -1244,8 +1563,8 @@ spde_status level_add_impl(spde_ctx* ctx, int level, const int n[3], const doubl
     if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; grids cannot change");
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& L = ctx->lev[level];
+    L.ws.release();  // waits for calls still using the level
     L.mesh.release();
-    L.ws.release();
     L.fields.release();
     L.defined = true;
     L.g = gr;
@@ -1282,6 +1601,7 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
     if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; meshes cannot change");
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& L = ctx->lev[level];
+    L.ws.quiesce();  // a call still projecting onto the old mesh
     L.mesh.release();
     Mesh& m = L.mesh;
     cudaStream_t st = nullptr;
@@ -1349,6 +1669,8 @@ spde_status spde_level_set_fields(spde_ctx* ctx, int level, const double* kappa_
     if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; fields cannot change");
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& L = ctx->lev[level];
+    L.ws.quiesce();
+    L.ws.drop_graphs();  // captured graphs hold the old fields' addresses
     L.fields.release();
     if (!kappa_cells) return SPDE_OK;
     const int64_t n3 = L.g.cells();
@@ -1414,6 +1736,12 @@ spde_status spde_sample_fields(spde_ctx* ctx, int level, int nsamples, uint64_t 
 }
 
 namespace {
+// calls take the graph-driven path unless per-kernel timing is on (events cannot be
+// recorded inside a graph's loops), graphs are switched off, or the inner solver is CG
+bool graph_path(const spde_ctx* ctx) {
+    return ctx->opts.use_graphs != 0 && !ctx->prof.on && ctx->opts.solver == SPDE_SOLVER_MINRES;
+}
+
 spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, bool use_fields,
                         uint64_t seed, uint64_t first_sample, int out_kind, void* out, void* stream) {
     if (nsamples < 0) return fail(SPDE_EINVAL, "nsamples < 0");
@@ -1428,11 +1756,16 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
     if (kind != SPDE_OUT_GRID_GAUSSIAN && !L.mesh.rowptr) return fail(SPDE_EINVAL, "no mesh attached to level %d", level);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
+    const bool graph = graph_path(ctx);
     const size_t esz = (out_kind & SPDE_OUT_F64) ? 8 : 4;
     const bool host_out = is_host_pointer(out);
-    ctx->stats.outer_iters = 0;
-    ctx->stats.inner_iters = 0;
-    ctx->stats.max_rel_residual = 0.0;
+    if (graph) {
+        STATUS_TRY(async_call_begin(ctx, st));
+    } else {
+        ctx->stats.outer_iters = 0;
+        ctx->stats.inner_iters = 0;
+        ctx->stats.max_rel_residual = 0.0;
+    }
     // plain path: one sample per solve; mixed path: batches that fit in memory
     int cap = 1;
     if (!plain) {
@@ -1446,8 +1779,9 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
         STATUS_TRY(ensure_workspace(L.ws, L.g, plain ? 1 : std::min(cap, nsamples), plain));
+        if (graph) CUDA_TRY(cudaStreamWaitEvent(st, L.ws.done, 0));  // a call on another stream may still use it
         spde_status s = solve_samples(ctx, L, S, kappa, sigma, seed, first_sample + (uint64_t)s0, st,
-                                      use_fields ? &L.fields : nullptr);
+                                      use_fields ? &L.fields : nullptr, graph);
         if (s != SPDE_OK && s != SPDE_ENOCONV) return s;
         if (s == SPDE_ENOCONV) worst = s;
         const size_t per = out_elem_count(L, 1, out_kind);
@@ -1455,7 +1789,10 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
         if (host_out) {
             const size_t need = (size_t)S * per * esz;
             if (ctx->out_tmp_bytes < need) {
-                if (ctx->out_tmp) cudaFree(ctx->out_tmp);
+                if (ctx->out_tmp) {
+                    CUDA_TRY(cudaStreamSynchronize(st));
+                    cudaFree(ctx->out_tmp);
+                }
                 ctx->out_tmp = nullptr;
                 ctx->out_tmp_bytes = 0;
                 CUDA_TRY(cudaMalloc(&ctx->out_tmp, need));
@@ -1466,8 +1803,11 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
         } else {
             STATUS_TRY(write_output(L, S, out_kind, dst, st));
         }
+        if (graph) CUDA_TRY(cudaEventRecord(L.ws.done, st));
     }
+    if (graph && !host_out) return SPDE_OK;  // asynchronous: the outcome comes with spde_wait
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (graph) return drain_calls(ctx, true);  // host memory written: report the outcome now
     ctx->prof.flush();
     if (worst != SPDE_OK)
         return fail(worst, "tolerance not reached: relative residual %.3e", ctx->stats.max_rel_residual);
@@ -1572,10 +1912,15 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
     ProfScope ps(ctx->prof);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
+    const bool graph = graph_path(ctx);
     const size_t esz = (out_kind & SPDE_OUT_F64) ? 8 : 4;
-    ctx->stats.outer_iters = 0;
-    ctx->stats.inner_iters = 0;
-    ctx->stats.max_rel_residual = 0.0;
+    if (graph) {
+        STATUS_TRY(async_call_begin(ctx, st));
+    } else {
+        ctx->stats.outer_iters = 0;
+        ctx->stats.inner_iters = 0;
+        ctx->stats.max_rel_residual = 0.0;
+    }
     int cap = 1;
     if (!plain) {
         const int64_t per = workspace_bytes(F.g, 1, false) + workspace_bytes(C.g, 1, false);
@@ -1596,12 +1941,29 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
         const int S = std::min(cap, nsamples - s0);
         STATUS_TRY(ensure_workspace(F.ws, F.g, plain ? 1 : std::min(cap, nsamples), plain));
         STATUS_TRY(ensure_workspace(C.ws, C.g, plain ? 1 : std::min(cap, nsamples), plain));
+        if (graph) {
+            CUDA_TRY(cudaStreamWaitEvent(st, F.ws.done, 0));
+            CUDA_TRY(cudaStreamWaitEvent(st, C.ws.done, 0));
+        }
         // fine noise, then its restriction (Sec. 6.2: the same xi drives both levels)
         CUDA_TRY(launch_noise(nf3, S, seed, first_sample + (uint64_t)s0, -g_half(kappa, sigma) * F.h, F.ws.F, nf3, st));
         CUDA_TRY(launch_restrict_rhs(C.g, S, F.ws.F, nf3, C.ws.F, nc3, st));
         double rel = 0.0;
         int outer = 0, inner = 0;
         const double khc = (kappa * C.h) * (kappa * C.h), khf = (kappa * F.h) * (kappa * F.h);
+        if (graph) {
+            if (plain) STATUS_TRY(refine_solve_async<double>(ctx, C.g, khc, S, C.ws, st, false, nullptr, false));
+            else STATUS_TRY(refine_solve_async<float>(ctx, C.g, khc, S, C.ws, st, false, nullptr, false));
+            CUDA_TRY(launch_inject_theta(C.g, S, C.ws.x64, 4 * nc3, F.ws.x64, 4 * nf3, st));
+            if (plain) STATUS_TRY(refine_solve_async<double>(ctx, F.g, khf, S, F.ws, st, true));
+            else STATUS_TRY(refine_solve_async<float>(ctx, F.g, khf, S, F.ws, st, true));
+            const size_t perf = out_elem_count(F, 1, out_kind), perc = out_elem_count(C, 1, out_kind);
+            STATUS_TRY(write_output(F, S, out_kind, static_cast<char*>(out_fine) + (size_t)s0 * perf * esz, st));
+            STATUS_TRY(write_output(C, S, out_kind, static_cast<char*>(out_coarse) + (size_t)s0 * perc * esz, st));
+            CUDA_TRY(cudaEventRecord(F.ws.done, st));
+            CUDA_TRY(cudaEventRecord(C.ws.done, st));
+            continue;
+        }
         spde_status sc = plain ? refine_solve<double>(ctx, C.g, khc, S, C.ws, &rel, &outer, &inner, st)
                                : refine_solve<float>(ctx, C.g, khc, S, C.ws, &rel, &outer, &inner, st);
         if (sc != SPDE_OK && sc != SPDE_ENOCONV) return sc;
@@ -1620,6 +1982,7 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
         STATUS_TRY(write_output(F, S, out_kind, static_cast<char*>(out_fine) + (size_t)s0 * perf * esz, st));
         STATUS_TRY(write_output(C, S, out_kind, static_cast<char*>(out_coarse) + (size_t)s0 * perc * esz, st));
     }
+    if (graph) return SPDE_OK;  // asynchronous: the outcome comes with spde_wait
     CUDA_TRY(cudaStreamSynchronize(st));
     ctx->prof.flush();
     if (worst != SPDE_OK) return fail(worst, "tolerance not reached: %.3e", ctx->stats.max_rel_residual);
@@ -1637,8 +2000,18 @@ spde_status spde_query_footprint(spde_ctx* ctx, int level, int nsamples, int64_t
 
 spde_status spde_get_stats(spde_ctx* ctx, spde_stats* stats) {
     if (!ctx || !stats) return fail(SPDE_EINVAL, "null argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    STATUS_TRY(drain_calls(ctx, false));
     *stats = ctx->stats;
     return SPDE_OK;
+}
+
+spde_status spde_wait(spde_ctx* ctx) {
+    if (!ctx) return fail(SPDE_EINVAL, "null context");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    return drain_calls(ctx, true);
 }
 
 spde_status spde_mesh_info(spde_ctx* ctx, int level, int64_t* ntets, int64_t* nnz) {
@@ -1695,11 +2068,15 @@ spde_status spde_destroy(spde_ctx* ctx) {
         std::lock_guard<std::mutex> g(ctx->mu);
         cudaSetDevice(ctx->opts.device);
         for (auto& L : ctx->lev) {
-            L.mesh.release();
             L.ws.release();
+            L.mesh.release();
             L.fields.release();
         }
         if (ctx->out_tmp) cudaFree(ctx->out_tmp);
+        for (auto& c : ctx->cap)
+            if (c) cudaStreamDestroy(c);
+        dev_free(ctx->d_acc);
+        if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
     }
     delete ctx;
     return SPDE_OK;
@@ -1938,6 +2315,7 @@ spde_status spde_solve(spde_ctx* ctx, int level, int nsamples, double kappa, con
     std::lock_guard<std::mutex> g(ctx->mu);
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     Level& L = ctx->lev[level];
+    L.ws.quiesce();  // an asynchronous call may still use the workspace
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool plain = ctx->opts.precision == SPDE_PREC_FP64;
     const Grid3 gr = L.g;

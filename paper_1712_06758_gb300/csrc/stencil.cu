@@ -280,7 +280,8 @@ cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cuda
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_flux_lines(Grid3 g, int tn, int axis, const double* __restrict__ x,
                                                     double* __restrict__ xu, int64_t col_stride,
-                                                    const double* __restrict__ tri) {
+                                                    const double* __restrict__ tri, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int L = blockIdx.x * blockDim.x + threadIdx.x;
     const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int m = g.ext(axis);
@@ -334,8 +335,9 @@ static inline int row_lines(const Grid3& g) {
 
 __global__ void __launch_bounds__(128) k_flux_rows(Grid3 g, int tn, int lines_per_cta, const double* __restrict__ x,
                                                    double* __restrict__ xu, int64_t col_stride,
-                                                   const double* __restrict__ tri) {
+                                                   const double* __restrict__ tri, const int* __restrict__ gate) {
     extern __shared__ double srow[];  // lines_per_cta rows of nx + 1 (padded against bank conflicts)
+    if (gate && *gate == 0) return;
     const int n = g.nx, logn = g.lx;
     const int64_t off = (int64_t)blockIdx.y * col_stride;
     const int n3 = 1 << (g.lx + g.ly + g.lz);
@@ -377,19 +379,21 @@ static cudaError_t flux_rows_attr() {
     return e;
 }
 
+cudaError_t flux_prepare() { return flux_rows_attr(); }
+
 cudaError_t launch_flux_from_theta(const Grid3& g, int S, double* x, int64_t col_stride, const double* tri,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const int* gate) {
     const int tn = g.maxn();
     const int rows = 1 << (g.ly + g.lz);
     const int lr = row_lines(g);
     const cudaError_t ea = flux_rows_attr();
     if (ea != cudaSuccess) return ea;
     dim3 grow(rows / lr, S);
-    k_flux_rows<<<grow, 128, (size_t)lr * (g.nx + 1) * sizeof(double), st>>>(g, tn, lr, x, x, col_stride, tri);
+    k_flux_rows<<<grow, 128, (size_t)lr * (g.nx + 1) * sizeof(double), st>>>(g, tn, lr, x, x, col_stride, tri, gate);
     for (int axis = 1; axis < 3; ++axis) {
         const int lines = (int)(g.cells() / g.ext(axis));
         dim3 grid((lines + 255) / 256, S);
-        k_flux_lines<<<grid, 256, 0, st>>>(g, tn, axis, x, x, col_stride, tri);
+        k_flux_lines<<<grid, 256, 0, st>>>(g, tn, axis, x, x, col_stride, tri, gate);
     }
     return cudaGetLastError();
 }
