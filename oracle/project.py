@@ -10,6 +10,7 @@ coefficient is k = exp(theta), applied after the projection (workflow figure
 of Sec. 6).
 """
 import numpy as np
+import scipy.sparse as sp
 
 from .clip import tet_volume
 
@@ -31,3 +32,21 @@ def project_rows(xyz, tets, grows, theta_bar):
 
 def lognormal(theta_h):
     return np.exp(theta_h)
+
+
+def tet_volumes(xyz, tets):
+    """|tau| of every tet (vectorised determinant)."""
+    p = np.asarray(xyz, dtype=np.float64)[np.asarray(tets)]
+    return np.abs(np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])) / 6.0
+
+
+def projection_matrix(rowptr, col, g, vol, ncells):
+    """Pi = W_h^{-1} G as a SciPy CSR matrix [ntets, ncells] (Eq. proj_op)."""
+    vals = np.asarray(g, dtype=np.float64) / np.repeat(np.asarray(vol, dtype=np.float64), np.diff(rowptr))
+    return sp.csr_matrix((vals, col, rowptr), shape=(len(rowptr) - 1, ncells))
+
+
+def project_csr(pi, theta_bar):
+    """theta_h = Pi theta_bar for theta_bar [ncells] or [S, ncells] (one sparse product)."""
+    theta_bar = np.asarray(theta_bar, dtype=np.float64)
+    return (pi @ theta_bar.T).T

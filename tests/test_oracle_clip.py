@@ -212,3 +212,73 @@ def test_sliver_generator_volumes_and_placement():
     for t in ptets:  # three vertices share one coordinate
         p = pxyz[t]
         assert any(p[0, a] == p[1, a] == p[2, a] for a in range(3))
+
+
+# ---------------------------------------------------------------- C statement
+from oracle import clip_c  # noqa: E402
+
+
+def _rows_of(rp, col, val, t):
+    return dict(zip(col[rp[t]:rp[t + 1]].tolist(), val[rp[t]:rp[t + 1]].tolist()))
+
+
+def test_c_statement_matches_exact_on_slivers_and_plane_faces():
+    n = 16
+    h3 = (1.0 / n) ** 3
+    for xyz, tets in (sliver_tets(n, per_case=2)[:2],
+                      plane_tets(n, offsets=(0.0, 1e-13, 2e-12, 1e-9), heights=(0.8, 1e-5))):
+        rp, col, val = clip_c.coupling_csr(xyz, tets, n)
+        ex = clip.coupling_rows_exact(xyz, tets, n)
+        for t in ex:
+            got = _rows_of(rp, col, val, t)
+            for c in set(got) | set(ex[t]):
+                assert abs(got.get(c, 0.0) - float(ex[t].get(c, 0))) <= 1e-15 * h3, (t, c)
+
+
+def test_c_statement_matches_hull_and_sums_rows_on_a_jittered_box():
+    lo, hi, n, m = 0.15, 0.85, 8, 5
+    xyz, tets = box_mesh((lo,) * 3, (hi,) * 3, m)
+    rp, col, val = clip_c.coupling_csr(xyz, tets, n)
+    hu = clip.coupling_rows(xyz, tets, n, rows=range(0, len(tets), 3))
+    for t, ref in hu.items():
+        got = _rows_of(rp, col, val, t)
+        for c in set(got) | set(ref):
+            assert abs(got.get(c, 0.0) - ref.get(c, 0.0)) <= 1e-13 / n ** 3
+    vol = project.tet_volumes(xyz, tets)
+    assert np.allclose(np.add.reduceat(val, rp[:-1]), vol, rtol=1e-12, atol=0)
+    colsum = np.bincount(col, weights=val, minlength=n ** 3)
+    e = np.arange(n) / n
+    ov = np.clip(np.minimum(e + 1.0 / n, hi) - np.maximum(e, lo), 0.0, None)
+    assert np.allclose(colsum, (ov[None, None, :] * ov[None, :, None] * ov[:, None, None]).ravel(),
+                       rtol=1e-11, atol=1e-17)
+
+
+def test_c_statement_aligned_cubes_and_box_grid():
+    xyz, tets = box_mesh((0.0,) * 3, (1.0,) * 3, 4, jitter=0.0)
+    rp, col, val = clip_c.coupling_csr(xyz, tets, 4)
+    assert np.array_equal(np.diff(rp), np.ones(len(tets), dtype=np.int64))
+    assert np.array_equal(col, np.arange(len(tets)) // 6)
+    assert np.allclose(val, 1.0 / (6 * 64), rtol=1e-14)
+    # a box grid with an offset origin: the same as the hull statement
+    xyz, tets = box_mesh((0.3, 0.2, 0.25), (0.9, 0.55, 0.45), 3)
+    dims, h, lo = (8, 4, 2), 0.125, (0.2, 0.1, 0.2)
+    rp, col, val = clip_c.coupling_csr(xyz, tets, dims, lo=lo, h=h)
+    hu = clip.coupling_rows(xyz, tets, dims, lo=lo, h=h)
+    for t, ref in hu.items():
+        got = _rows_of(rp, col, val, t)
+        for c in set(got) | set(ref):
+            assert abs(got.get(c, 0.0) - ref.get(c, 0.0)) <= 1e-13 * h ** 3
+
+
+def test_csr_projection_matches_row_statement():
+    xyz, tets = box_mesh((0.15,) * 3, (0.85,) * 3, 4)
+    n = 8
+    rp, col, val = clip_c.coupling_csr(xyz, tets, n)
+    pi = project.projection_matrix(rp, col, val, project.tet_volumes(xyz, tets), n ** 3)
+    th = np.random.default_rng(2).standard_normal((3, n ** 3))
+    got = project.project_csr(pi, th)
+    rows = clip.coupling_rows(xyz, tets, n)
+    ref = project.project_rows(xyz, tets, rows, th)
+    for t, v in ref.items():
+        assert np.allclose(got[:, t], v, rtol=1e-12, atol=1e-12)
+    assert np.allclose(project.project_csr(pi, np.ones(n ** 3)), 1.0, rtol=1e-12)
