@@ -205,20 +205,102 @@ def run_serving(pkg, smp, outbufs, reqs, poll_sleep=0.0005):
             "all_ok": all(st == pkg.SPDE_OK for st in statuses)}
 
 
+_MESHES = {}
+
+
+def lprism_cached(m):
+    """The jittered L-prism of m^3 cubes (generated once per process)."""
+    if m not in _MESHES:
+        from synth import lprism_mesh
+        _MESHES[m] = lprism_mesh(m)
+    return _MESHES[m]
+
+
 def serving_setup(pkg, local):
     """Sampler with the 4-level hierarchy and per-level shared output buffers (throughput runs
     overwrite them; serving correctness is covered by the tests)."""
     import torch
-    from synth import lprism_mesh
     smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=1e-8, device=local)
     outbufs = {}
     for lvl, (n, m) in enumerate(SERVE_LEVELS):
-        xyz, tets = lprism_mesh(m)
+        xyz, tets = lprism_cached(m)
         smp.add_level(lvl, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
         smp.attach_mesh(lvl, xyz, tets)
         outbufs[lvl] = torch.empty((256, len(tets)), dtype=torch.float32, device="cuda")
-        del xyz, tets
     return smp, outbufs
+
+
+MLMC_SAMPLES = (4096, 1024, 256, 64)
+
+
+def timed_call(pkg, smp, stream, fn):
+    """Device time (ms) of fn() on `stream`, CUDA events on that stream, outcome collected after."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    pkg.spde_wait(smp.ctx)
+    return a.elapsed_time(b)
+
+
+def run_mlmc_levels(pkg, local, stream, modes=(1, 0)):
+    """The 4-level MLMC batch: 32^3/64^3/128^3/256^3 grids with L-prism 24^3/48^3/96^3/192^3 meshes,
+    4096/1024/256/64 samples, kappa 20, tol 1e-8, lognormal FP32 out.  Each level has its own context
+    (one level's workspace at a time); one call per level after a warm-up call, timed with CUDA events,
+    through the graph-driven path (one graph launch per level and batch) and the synchronous host loop."""
+    import torch
+    rows, tot = [], {"graphs": 0.0, "host_loop": 0.0}
+    for (n, m), S in zip(SERVE_LEVELS, MLMC_SAMPLES):
+        xyz, tets = lprism_cached(m)
+        row = {"grid": n, "mesh": "L-prism %d^3 cubes" % m, "ntets": int(len(tets)), "samples": S}
+        out = torch.empty((S, len(tets)), dtype=torch.float32, device="cuda")
+        for g in modes:
+            key = "graphs" if g else "host_loop"
+            smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=1e-8, device=local, use_graphs=g)
+            smp.add_level(0, n)
+            smp.attach_mesh(0, xyz, tets)
+            smp.sample(0, S, 20.0, 1.0, 3, 10 ** 7, pkg.SPDE_OUT_LOGNORMAL, out, stream)  # warm-up
+            ms = timed_call(pkg, smp, stream, lambda: pkg.spde_sample(smp.ctx, 0, S, 20.0, 1.0, 3, 0,
+                                                                       pkg.SPDE_OUT_LOGNORMAL, out, stream))
+            st = smp.stats()
+            row[key] = {"samples_per_s": S / (ms / 1000.0), "ms": ms, "outer_iters": st["outer_iters"],
+                        "inner_iters": st["inner_iters"], "max_rel_residual": st["max_rel_residual"]}
+            tot[key] += ms
+            smp.close()
+        del out
+        rows.append(row)
+    total = sum(MLMC_SAMPLES)
+    return {"levels": rows, "kappa": 20.0, "sigma": 1.0, "tol": 1e-8, "output": "lognormal f32 on tets",
+            "hierarchy_ms": tot, "hierarchy_samples": total,
+            "hierarchy_samples_per_s": {k: total / (v / 1000.0) for k, v in tot.items() if v > 0}}
+
+
+def run_large(pkg, local, stream):
+    """The large single level: 512^3 grid, kappa 40, batch of 2, tol 1e-8, L-prism 160^3 cubes
+    (18.4 M tets), lognormal FP32 out; one timed call after a warm-up call."""
+    import torch
+    n, m, S, kappa = 512, 160, 2, 40.0
+    xyz, tets = lprism_cached(m)
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=1e-8, device=local)
+    smp.add_level(0, n)
+    smp.attach_mesh(0, xyz, tets)
+    setup = smp.stats()
+    out = torch.empty((S, len(tets)), dtype=torch.float32, device="cuda")
+    smp.sample(0, S, kappa, 1.0, 3, 10 ** 7, pkg.SPDE_OUT_LOGNORMAL, out, stream)
+    ms = timed_call(pkg, smp, stream, lambda: pkg.spde_sample(smp.ctx, 0, S, kappa, 1.0, 3, 0,
+                                                               pkg.SPDE_OUT_LOGNORMAL, out, stream))
+    st = smp.stats()
+    fp = pkg.spde_query_footprint(smp.ctx, 0, S)
+    smp.close()
+    del out
+    return {"value": S / (ms / 1000.0), "unit": "samples/s", "ms_per_call": ms, "samples": S, "grid": "512^3",
+            "kappa": kappa, "tol": 1e-8, "mesh": "L-prism %d^3 cubes" % m, "ntets": int(len(tets)),
+            "nnz": setup["nnz"], "clip_ms": setup["setup_ms"], "solver_workspace_GB": fp / 1e9,
+            "outer_iters": st["outer_iters"], "inner_iters": st["inner_iters"],
+            "max_rel_residual": st["max_rel_residual"], "coarse_storage": "fp32"}
 
 
 # ---------------------------------------------------------------- CPU oracle arm
@@ -477,15 +559,34 @@ def run_ours(args):
     e2e = {"value": world * args.steps * S / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": int(S * ntets * 4)}
 
-    # serving: a bounded open-loop stream on the 4-level hierarchy (tol 1e-8)
-    log("serving")
-    smp_s, outbufs = serving_setup(pkg, local)
-    serving = run_serving(pkg, smp_s, outbufs, serve_requests(args.serve_requests, args.serve_rate, seed=7 + rank))
-    serving.update({"rate_req_per_s": args.serve_rate, "levels": [n for n, _ in SERVE_LEVELS],
-                    "meshes": ["L-prism %d^3 cubes" % m for _, m in SERVE_LEVELS], "tol": 1e-8,
-                    "budget_GiB": 120, "note": "open loop, Poisson arrivals; latency = submit to completion"})
-    smp_s.close()
-    del outbufs
+    # the same steps through the graph-driven path (per-kernel timing off): every call returns once
+    # enqueued, convergence is decided on the device, the outcome is collected at the end
+    log("graph path")
+    step(2000, out)  # captures the graph
+    torch.cuda.synchronize()
+    pkg.spde_wait(smp.ctx)
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ga.record(stream)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(3000 + i, out)
+    host_enqueue_s = time.perf_counter() - t0
+    gb.record(stream)
+    torch.cuda.synchronize()
+    pkg.spde_wait(smp.ctx)
+    barrier(world)
+    graph_ms = reduce_max(ga.elapsed_time(gb), world)
+    gst = smp.stats()
+    graphs = {"value": world * args.steps * S / (graph_ms / 1000.0), "unit": "samples/s",
+              "ms_per_step": graph_ms / args.steps, "host_enqueue_ms_per_step": 1000.0 * host_enqueue_s / args.steps,
+              "outer_iters": gst["outer_iters"], "inner_iters": gst["inner_iters"],
+              "note": "spde_sample with use_graphs = 1: one graph launch per 64-sample call"}
+
+    # serving: the open-loop stream on the 4-level hierarchy (tol 1e-8) swept over the request rates
+    log("serving sweep")
+    serving = serve_sweep(pkg, local, args.serve_requests)
 
     line = None
     if rank == 0:
@@ -646,6 +747,11 @@ def run_ours(args):
                 tf = fl * float(n) ** 3 * S * kk["launches"] / (kk["ms"] / 1000.0) / 1e12
                 fp64["kernels"][name] = {"tflops": tf, "frac": tf / fp64_peak, "flops_per_cell": fl,
                                          "hbm_frac": kk["GBps"] / peak if kk["GBps"] else None}
+        # the 4-level MLMC batch and the large single level
+        log("mlmc levels")
+        mlmc = run_mlmc_levels(pkg, local, stream)
+        log("512^3 level")
+        large = run_large(pkg, local, stream)
         # the oracle on the host cores: whole samples of the same workload
         log("cpu baseline")
         oc = OracleSampler(xyz, tets)
@@ -661,6 +767,9 @@ def run_ours(args):
                 "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                "per": "one %d-sample batch call" % S},
                 "serving": serving,
+                "graphs": graphs,
+                "mlmc_levels": mlmc,
+                "large_512": large,
                 "plain_fp64": {"value": plain_rate, "unit": "samples/s", "samples": nplain,
                                "ratio": value / world / plain_rate, "inner_iters": pst["inner_iters"],
                                "max_rel_l2_vs_mixed": float(d.max())},
@@ -691,22 +800,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+SERVE_RATES = (10.0, 30.0, 100.0, 300.0, 1000.0)
+
+
+def serve_sweep(pkg, local, nreq):
+    """The serving stream at 10, 30, 100, 300 and 1000 req/s, nreq requests per rate (open loop)."""
+    smp, outbufs = serving_setup(pkg, local)
+    rows = []
+    for rate in SERVE_RATES:
+        log("serving at %g req/s" % rate)
+        r = run_serving(pkg, smp, outbufs, serve_requests(nreq, rate, seed=int(rate)))
+        r["rate_req_per_s"] = rate
+        rows.append(r)
+    smp.close()
+    sat = max(r["samples_per_s"] for r in rows)
+    return {"rows": rows, "requests_per_rate": nreq, "levels": [n for n, _ in SERVE_LEVELS],
+            "meshes": ["L-prism %d^3 cubes" % m for _, m in SERVE_LEVELS], "tol": 1e-8, "budget_GiB": 120,
+            "saturation_samples_per_s": sat,
+            "note": "open loop, Poisson arrivals; latency = submit to completion; request mix per rate seeded by the rate"}
+
+
 def run_serve_sweep(args):
     """The serving sweep: rates 10, 30, 100, 300, 1000 req/s, fixed request count per rate."""
     import torch
     import paper_1712_06758_gb300 as pkg
     _, _, local = dist_env()
     torch.cuda.set_device(local)
-    smp, outbufs = serving_setup(pkg, local)
-    rows = []
-    for rate in (10.0, 30.0, 100.0, 300.0, 1000.0):
-        log("serving at %g req/s" % rate)
-        r = run_serving(pkg, smp, outbufs, serve_requests(args.serve_requests, rate, seed=int(rate)))
-        r["rate_req_per_s"] = rate
-        rows.append(r)
-    smp.close()
-    print(json.dumps({"metric": "serving latency p50/p99 and samples/s vs request rate", "levels":
-                      [n for n, _ in SERVE_LEVELS], "tol": 1e-8, "rows": rows}), flush=True)
+    print(json.dumps(serve_sweep(pkg, local, args.serve_requests)), flush=True)
 
 
 def main(argv=None):
@@ -720,8 +840,7 @@ def main(argv=None):
     ap.add_argument("--plain-samples", type=int, default=8)
     ap.add_argument("--batch", type=int, default=0, help="override the 64-sample batch (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="headline loop only (profiling runs)")
-    ap.add_argument("--serve-rate", type=float, default=10.0, help="request rate of the serving stream")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests per rate of the serving sweep")
     ap.add_argument("--serve-sweep", action="store_true", help="only the serving sweep over 10..1000 req/s")
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -114,6 +114,9 @@ typedef struct {
     int64_t serve_budget_bytes; /* device memory the serving lanes may hold; 120 GiB */
     int serve_max_batch;        /* columns per serving lane; 64 */
     int solver;                 /* SPDE_SOLVER_MINRES (default) or SPDE_SOLVER_SCHUR_CG */
+    int sweep_planes;           /* fine z planes per CTA of the V-cycle sweeps: 8, 16 or 32 where a
+                                   level's z extent allows; 0 (default) = per level, the longest
+                                   march that still gives 4 CTAs per SM */
 } spde_opts;
 
 typedef struct {
@@ -124,6 +127,17 @@ typedef struct {
     double setup_ms;        /* last spde_mesh_attach: clipping + CSR build on the device */
     int64_t nnz;            /* nonzeros of the last attached coupling matrix */
 } spde_stats;
+
+/* Schedule of a level's solver (spde_autotune / spde_level_set_tuning). */
+typedef struct {
+    double omega;        /* damped-Jacobi weight of the V-cycle smoother, in (0, 1) */
+    double inner_tol;    /* reduction asked of the FP32 inner solve per refinement step, in (0, 1) */
+    double flux_diag;    /* flux-block preconditioner (a multiple of the identity), > 0 */
+    int sweep_planes;    /* z planes per CTA of the V-cycle sweeps (0, 8, 16, 32; see spde_opts) */
+    double ms_per_call;  /* (spde_autotune) device time of one call with this schedule */
+    double default_ms;   /* (spde_autotune) the same with the context's options */
+    int evaluated;       /* (spde_autotune) schedules timed */
+} spde_tuning;
 
 typedef struct spde_ctx spde_ctx;
 
@@ -300,6 +314,25 @@ spde_status spde_profile_enable(spde_ctx* ctx, int enable);
  * Any output pointer may be NULL. */
 spde_status spde_profile_read(spde_ctx* ctx, int k, const char** name, int64_t* launches, double* ms,
                               double* bytes);
+
+/* Autotuner (no paper counterpart; the sampler's own schedule choice).  Times
+ * whole spde_sample calls of `nsamples` columns on `level` (kappa, sigma;
+ * grid output, a fixed seed, one warm-up and one timed call per candidate)
+ * and searches, one knob at a time and twice over, the V-cycle smoother
+ * weight omega in {0.7, 0.8, 0.9}, the inner reduction in {1e-4, 1e-5,
+ * 1e-6}, the flux-block diagonal in {1.25, 1.5, 2} and the sweep planes per
+ * CTA in {0, 8, 16, 32}; a candidate replaces the current choice only when
+ * it is at least 1 % faster and the call reaches the tolerance.  The best
+ * schedule is kept on the level (every later call on it, serving included,
+ * runs with it) and returned in *best.  Synchronises the device; allocates a
+ * temporary output buffer of nsamples x cells floats. */
+spde_status spde_autotune(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, spde_tuning* best);
+
+/* Set the schedule of `level` (e.g. an entry of a stored tuning table; only
+ * omega, inner_tol, flux_diag and sweep_planes are read), or return it to
+ * the context's options with tuning = NULL.  Waits for calls still using the
+ * level; SPDE_EBUSY while serving requests are in flight. */
+spde_status spde_level_set_tuning(spde_ctx* ctx, int level, const spde_tuning* tuning);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* spde_last_error(void);

@@ -29,12 +29,18 @@ class spde_opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("max_iter", ctypes.c_int), ("omega", ctypes.c_double),
                 ("schur_c", ctypes.c_double), ("flux_diag", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("device", ctypes.c_int), ("use_graphs", ctypes.c_int), ("serve_budget_bytes", ctypes.c_int64),
-                ("serve_max_batch", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("serve_max_batch", ctypes.c_int), ("solver", ctypes.c_int), ("sweep_planes", ctypes.c_int)]
 
 
 class spde_stats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("max_rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double), ("nnz", ctypes.c_int64)]
+
+
+class spde_tuning(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("inner_tol", ctypes.c_double), ("flux_diag", ctypes.c_double),
+                ("sweep_planes", ctypes.c_int), ("ms_per_call", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("evaluated", ctypes.c_int)]
 
 
 class SpdeError(RuntimeError):
@@ -68,6 +74,8 @@ _SIGS = {
     "spde_query_footprint": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
     "spde_get_stats": [_P, ctypes.POINTER(spde_stats)],
     "spde_wait": [_P],
+    "spde_autotune": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.POINTER(spde_tuning)],
+    "spde_level_set_tuning": [_P, ctypes.c_int, ctypes.POINTER(spde_tuning)],
     "spde_mesh_info": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "spde_mesh_copy_csr": [_P, ctypes.c_int, _P, _P, _P, _P],
     "spde_destroy": [_P],
@@ -243,6 +251,24 @@ def spde_get_stats(ctx):
 def spde_wait(ctx):
     """Waits for the context's calls; raises SpdeError with their worst outcome."""
     _check(lib().spde_wait(ctx))
+
+
+def spde_autotune(ctx, level, nsamples, kappa, sigma):
+    """Runs the autotuner on `level`; returns the chosen schedule as a dict (kept on the level)."""
+    t = spde_tuning()
+    _check(lib().spde_autotune(ctx, level, nsamples, kappa, sigma, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in spde_tuning._fields_}
+
+
+def spde_level_set_tuning(ctx, level, tuning):
+    """Puts a schedule (a dict with omega, inner_tol, flux_diag, sweep_planes) on `level`; None clears it."""
+    if tuning is None:
+        _check(lib().spde_level_set_tuning(ctx, level, None))
+        return
+    t = spde_tuning()
+    for k in ("omega", "inner_tol", "flux_diag", "sweep_planes"):
+        setattr(t, k, tuning[k])
+    _check(lib().spde_level_set_tuning(ctx, level, ctypes.byref(t)))
 
 
 def spde_mesh_info(ctx, level):

@@ -133,6 +133,9 @@ struct MGPlan {
     // fault word of the solve (device int): a sweep whose bounded wait gives up raises it,
     // and later sweeps of the same solve skip their work until the owner clears it
     int* fault = nullptr;
+    // z planes per CTA of the tiled sweeps: 8, 16 or 32 where the level's z extent
+    // allows, 0 = chosen per level for occupancy
+    int sz_pref = 0;
 };
 
 // ---- noise.cu

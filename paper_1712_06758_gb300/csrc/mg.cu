@@ -1002,7 +1002,8 @@ void mg_plan_bind(MGPlan& plan, int S, T* scratch) {
 
 // z planes per CTA for the level sweeps: the longest march (fewest halo planes)
 // that still gives at least four CTAs per SM of a 152-SM GPU
-static int pick_sz(const Grid3& g, int S) {
+static int pick_sz(const Grid3& g, int S, int pref) {
+    if ((pref == 8 || pref == 16 || pref == 32) && g.nz % pref == 0) return pref;
     const int base = (g.nx / SX) * (g.ny / SY);
     for (int sz = 32; sz > 8; sz >>= 1)
         if (g.nz % sz == 0 && (int64_t)base * (g.nz / sz) * S >= 4 * 152) return sz;
@@ -1135,7 +1136,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     for (int l = 0; l < plan.lc; ++l) {
         const Grid3& gf = plan.g[l];
         const int64_t nc3 = plan.g[l + 1].cells();
-        const int sz = pick_sz(gf, S);
+        const int sz = pick_sz(gf, S, plan.sz_pref);
         const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
@@ -1164,7 +1165,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     for (int l = plan.lc - 1; l >= 0; --l) {
         const Grid3& gf = plan.g[l];
         const int64_t nf3 = gf.cells(), nc3 = plan.g[l + 1].cells();
-        const int sz = pick_sz(gf, S);
+        const int sz = pick_sz(gf, S, plan.sz_pref);
         const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
         dim3 grid(nb, S);

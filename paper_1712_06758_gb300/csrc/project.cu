@@ -4,7 +4,7 @@
 //
 // Pi is CSR with rows = tets.  The grid fields of a batch are first
 // transposed to thetaT[cell][sample] (FP32) so one CSR entry feeds all
-// samples from one contiguous row; a warp computes one tet for 32 samples
+// samples from one contiguous row; a warp computes one tet for 64 samples
 // and a shared-memory tile turns the result into coalesced rows of
 // out[sample][tet].
 #include "device.cuh"
@@ -43,36 +43,75 @@ __device__ __forceinline__ O out_map(float acc, int kind) {
     return (O)(kind == 0 ? expf(acc) : acc);
 }
 
-// warp per tet, lanes over 32 samples; block = 8 warps x 4 tets = 32 tets
-template <typename O>
-__global__ void __launch_bounds__(256) k_project_warp(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
+// A CTA of 8 warps projects 32 tets, 4 per warp, for a chunk of up to 64
+// samples: lane l holds samples 2l, 2l+1 of the chunk, so one pass over a
+// tet's CSR row reads whole 256-byte rows of thetaT (one float2 per lane).
+// The lanes first load up to 32 of the row's (pi, col) pairs together and
+// hand them round by shuffles, so the row's thetaT gathers are independent
+// and can be in flight at once; the sum still runs over the row in CSR
+// order (the same fmaf sequence as the other projection kernels).  A
+// shared-memory tile turns the 32 x 64 results into coalesced rows of
+// out[sample][tet].
+constexpr int kProjTets = 32, kProjChunk = 64;
+
+template <typename O, int VEC>
+__global__ void __launch_bounds__(256) k_project_rows(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ pi,
                                                       const float* __restrict__ thetaT, int kind, O* __restrict__ out) {
-    __shared__ float tile[32][33];
+    __shared__ float tile[kProjChunk][kProjTets + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t t0 = (int64_t)blockIdx.x * 32;
-    for (int s0 = 0; s0 < S; s0 += 32) {
-        const int s = s0 + lane;
+    const int64_t t0 = (int64_t)blockIdx.x * kProjTets;
+    for (int s0 = 0; s0 < S; s0 += kProjChunk) {
+        const int sl = s0 + VEC * lane;  // this lane's first sample
+        const bool on0 = sl < S, on1 = VEC == 2 && sl + 1 < S;
         for (int rr = 0; rr < 4; ++rr) {
             const int r = warp * 4 + rr;
             const int64_t t = t0 + r;
-            float acc = 0.0f;
+            float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;  // acc2: the second sample of a VEC = 1 lane
             if (t < ntets) {
                 const int64_t a = rowptr[t], b = rowptr[t + 1];
-                for (int64_t j = a; j < b; ++j) {
-                    const float w = pi[j];
-                    const int64_t c = col[j];
-                    if (s < S) acc = fmaf(w, thetaT[c * S + s], acc);
+                for (int64_t base = a; base < b; base += 32) {
+                    const int m = (b - base) < 32 ? (int)(b - base) : 32;
+                    float wl = 0.0f;
+                    int cl = 0;
+                    if (lane < m) {
+                        wl = pi[base + lane];
+                        cl = col[base + lane];
+                    }
+#pragma unroll 8
+                    for (int k = 0; k < m; ++k) {
+                        const float w = __shfl_sync(0xffffffffu, wl, k);
+                        const int64_t c = __shfl_sync(0xffffffffu, cl, k);
+                        const float* row = thetaT + c * S;
+                        if constexpr (VEC == 2) {
+                            if (on1) {
+                                const float2 v = *reinterpret_cast<const float2*>(row + sl);
+                                acc0 = fmaf(w, v.x, acc0);
+                                acc1 = fmaf(w, v.y, acc1);
+                            } else if (on0) {
+                                acc0 = fmaf(w, row[sl], acc0);
+                            }
+                        } else {
+                            if (on0) acc0 = fmaf(w, row[sl], acc0);
+                            if (sl + 32 < S && s0 + 32 + lane < S) acc2 = fmaf(w, row[s0 + 32 + lane], acc2);
+                        }
+                    }
                 }
             }
-            tile[r][lane] = acc;
+            if constexpr (VEC == 2) {
+                tile[2 * lane][r] = acc0;
+                tile[2 * lane + 1][r] = acc1;
+            } else {
+                tile[lane][r] = acc0;
+                tile[32 + lane][r] = acc2;
+            }
         }
         __syncthreads();
-        // write rows out[s][t0 .. t0+31]
-        for (int q = warp; q < 32; q += 8) {
+        // rows out[s][t0 .. t0 + 31]
+        for (int q = warp; q < kProjChunk; q += 8) {
             const int ss = s0 + q;
             const int64_t t = t0 + lane;
-            if (ss < S && t < ntets) out[(int64_t)ss * ntets + t] = out_map<O>(tile[lane][q], kind);
+            if (ss < S && t < ntets) out[(int64_t)ss * ntets + t] = out_map<O>(tile[q][lane], kind);
         }
         __syncthreads();
     }
@@ -96,11 +135,15 @@ __global__ void __launch_bounds__(256) k_project_thread(int64_t ntets, int S, co
 cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const int32_t* col, const float* pi,
                            const float* thetaT, int kind, int out64, void* out, cudaStream_t st) {
     if (S >= 8) {
-        const unsigned nb = (unsigned)((ntets + 31) / 32);
-        if (out64)
-            k_project_warp<double><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
-        else
-            k_project_warp<float><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+        const unsigned nb = (unsigned)((ntets + kProjTets - 1) / kProjTets);
+        // float2 gathers need even rows of thetaT (S even)
+        if (S % 2 == 0) {
+            if (out64) k_project_rows<double, 2><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
+            else k_project_rows<float, 2><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+        } else {
+            if (out64) k_project_rows<double, 1><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
+            else k_project_rows<float, 1><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+        }
     } else {
         const unsigned nb = (unsigned)((ntets + 255) / 256);
         if (out64)

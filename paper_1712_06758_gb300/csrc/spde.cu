@@ -130,6 +130,9 @@ struct Workspace {
     RefineCtl* ctl = nullptr;
     int* mask = nullptr;
     cudaEvent_t done = nullptr;
+    // the options the solves on this workspace run with (the context's, with the level's
+    // tuning applied; set by every call before it solves)
+    spde_opts o{};
     struct Graph {
         int S, t64, warm, count;
         const void* fields;
@@ -257,7 +260,21 @@ struct Level {
     Mesh mesh;
     Workspace ws;
     Fields fields;
+    bool tuned = false;  // spde_autotune / spde_level_set_tuning picked this level's schedule
+    spde_tuning tune{};
 };
+
+// the options a level's solves run with: the context's, with the level's tuning
+spde_opts level_opts(const spde_opts& base, const Level& L) {
+    spde_opts o = base;
+    if (L.tuned) {
+        o.omega = L.tune.omega;
+        o.inner_tol = L.tune.inner_tol;
+        o.flux_diag = L.tune.flux_diag;
+        o.sweep_planes = L.tune.sweep_planes;
+    }
+    return o;
+}
 
 }  // namespace
 
@@ -392,6 +409,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
     if (!mg_plan_init(plan, g, kh2, o.schur_c, o.omega)) return fail(SPDE_EINVAL, "grid shape not supported by the V-cycle");
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.fault = ws.fault;
+    plan.sz_pref = o.sweep_planes;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
@@ -499,6 +517,7 @@ spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Work
     mg_plan_init(plan, g, kh2, o.schur_c, o.omega);
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.fault = ws.fault;
+    plan.sz_pref = o.sweep_planes;
     plan.prof_cols = (double)S;
     const int act_stride = (int)(sizeof(CgCol) / sizeof(int));
     const int* act = &ws.cg[0].active;
@@ -567,7 +586,7 @@ template <typename T>
 spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Workspace& ws, double* maxrel,
                          int* outer_out, int* inner_out, cudaStream_t st, bool warm = false,
                          const Fields* fl = nullptr) {
-    const spde_opts& o = ctx->opts;
+    const spde_opts& o = ws.o;
     const int64_t n3 = g.cells(), N4 = 4 * n3;
     // ||F||^2 per column
     prof_begin(PK_SUMSQ, st);
@@ -734,7 +753,7 @@ spde_status ensure_capture_streams(spde_ctx* ctx) {
 template <typename T>
 spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Workspace& ws, bool warm,
                            const Fields* fl, bool count, cudaGraph_t* out) {
-    const spde_opts& o = ctx->opts;
+    const spde_opts& o = ws.o;
     const int64_t n3 = g.cells(), N4 = 4 * n3;
     const bool t64 = std::is_same<T, double>::value;
     cudaStream_t c0 = ctx->cap[0], c1 = ctx->cap[1], c2 = ctx->cap[2];
@@ -753,6 +772,7 @@ spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Wor
     if (!mg_plan_init(plan, g, kh2, o.schur_c, o.omega)) return fail(SPDE_EINVAL, "grid shape not supported by the V-cycle");
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.fault = ws.fault;
+    plan.sz_pref = o.sweep_planes;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
@@ -1158,8 +1178,9 @@ spde_status lane_alloc(Lane* L, const Grid3& g) {
 // One refinement step of every occupied column (no lock held).
 spde_status lane_round(Lane* L, std::vector<int>& finished) {
     spde_ctx* ctx = L->srv->ctx;
-    const spde_opts& o = ctx->opts;
     Level& LV = ctx->lev[L->level];
+    L->ws.o = level_opts(ctx->opts, LV);
+    const spde_opts& o = L->ws.o;
     const Grid3 g = LV.g;
     const int S = L->cap;
     const int64_t n3 = g.cells(), N4 = 4 * n3;
@@ -1509,6 +1530,7 @@ spde_status spde_opts_init(spde_opts* o) {
     o->serve_budget_bytes = (int64_t)120 << 30;
     o->serve_max_batch = 64;
     o->solver = SPDE_SOLVER_MINRES;
+    o->sweep_planes = 0;
     return SPDE_OK;
 }
 
@@ -1526,6 +1548,8 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
     if (!(o.schur_c > 0.0) || !(o.flux_diag > 0.0)) return fail(SPDE_EINVAL, "preconditioner weights must be > 0");
     if (o.serve_budget_bytes <= 0 || o.serve_max_batch < 1 || o.serve_max_batch > 65535)
         return fail(SPDE_EINVAL, "bad serving budget or batch size");
+    if (o.sweep_planes != 0 && o.sweep_planes != 8 && o.sweep_planes != 16 && o.sweep_planes != 32)
+        return fail(SPDE_EINVAL, "sweep_planes must be 0, 8, 16 or 32");
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (o.device < 0 || o.device >= ndev) return fail(SPDE_EINVAL, "device %d not present", o.device);
@@ -1779,6 +1803,7 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
         STATUS_TRY(ensure_workspace(L.ws, L.g, plain ? 1 : std::min(cap, nsamples), plain));
+        L.ws.o = level_opts(ctx->opts, L);
         if (graph) CUDA_TRY(cudaStreamWaitEvent(st, L.ws.done, 0));  // a call on another stream may still use it
         spde_status s = solve_samples(ctx, L, S, kappa, sigma, seed, first_sample + (uint64_t)s0, st,
                                       use_fields ? &L.fields : nullptr, graph);
@@ -1941,6 +1966,8 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
         const int S = std::min(cap, nsamples - s0);
         STATUS_TRY(ensure_workspace(F.ws, F.g, plain ? 1 : std::min(cap, nsamples), plain));
         STATUS_TRY(ensure_workspace(C.ws, C.g, plain ? 1 : std::min(cap, nsamples), plain));
+        F.ws.o = level_opts(ctx->opts, F);
+        C.ws.o = level_opts(ctx->opts, C);
         if (graph) {
             CUDA_TRY(cudaStreamWaitEvent(st, F.ws.done, 0));
             CUDA_TRY(cudaStreamWaitEvent(st, C.ws.done, 0));
@@ -2004,6 +2031,140 @@ spde_status spde_get_stats(spde_ctx* ctx, spde_stats* stats) {
     CUDA_TRY(cudaSetDevice(ctx->opts.device));
     STATUS_TRY(drain_calls(ctx, false));
     *stats = ctx->stats;
+    return SPDE_OK;
+}
+
+namespace {
+spde_status check_tuning(const spde_tuning& t) {
+    if (!(t.omega > 0.0 && t.omega < 1.0) || !(t.inner_tol > 0.0 && t.inner_tol < 1.0) || !(t.flux_diag > 0.0) ||
+        (t.sweep_planes != 0 && t.sweep_planes != 8 && t.sweep_planes != 16 && t.sweep_planes != 32))
+        return fail(SPDE_EINVAL, "bad tuning (omega, inner_tol in (0, 1), flux_diag > 0, sweep_planes 0/8/16/32)");
+    return SPDE_OK;
+}
+
+// put `t` (or nothing) on the level: later solves capture new graphs
+spde_status set_tuning_locked(spde_ctx* ctx, Level& L, const spde_tuning* t) {
+    L.ws.quiesce();
+    L.ws.drop_graphs();
+    L.tuned = t != nullptr;
+    if (t) L.tune = *t;
+    return SPDE_OK;
+}
+}  // namespace
+
+spde_status spde_level_set_tuning(spde_ctx* ctx, int level, const spde_tuning* tuning) {
+    STATUS_TRY(check_level(ctx, level));
+    if (tuning) STATUS_TRY(check_tuning(*tuning));
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight; the schedule cannot change");
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    return set_tuning_locked(ctx, ctx->lev[level], tuning);
+}
+
+spde_status spde_autotune(spde_ctx* ctx, int level, int nsamples, double kappa, double sigma, spde_tuning* best) {
+    STATUS_TRY(check_level(ctx, level));
+    STATUS_TRY(check_params(kappa, sigma));
+    if (!best || nsamples < 1) return fail(SPDE_EINVAL, "bad argument");
+    if (serving_busy(ctx)) return fail(SPDE_EBUSY, "requests are in flight");
+    Level& L = ctx->lev[level];
+    CUDA_TRY(cudaSetDevice(ctx->opts.device));
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        STATUS_TRY(drain_calls(ctx, true));
+    }
+    void* out = nullptr;
+    CUDA_TRY(cudaMalloc(&out, (size_t)nsamples * (size_t)L.g.cells() * sizeof(float)));
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(out);
+        if (st) cudaStreamDestroy(st);
+        return fail(SPDE_ECUDA, "autotune set-up failed: %s", cudaGetErrorString(ce));
+    }
+    const bool had = L.tuned;
+    const spde_tuning old = L.tune;
+    uint64_t first = 0;
+    // device time of one call with schedule t (infinite when it fails or misses the tolerance)
+    auto measure = [&](const spde_tuning& t, double* ms) -> spde_status {
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            STATUS_TRY(set_tuning_locked(ctx, L, &t));
+        }
+        *ms = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) {  // warm-up (graph capture), then the timed call
+            CUDA_TRY(cudaEventRecord(e0, st));
+            spde_status s = sample_impl(ctx, level, nsamples, kappa, sigma, false, 0x5eedULL, first,
+                                        SPDE_OUT_GRID_GAUSSIAN, out, st);
+            first += (uint64_t)nsamples;
+            CUDA_TRY(cudaEventRecord(e1, st));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            if (s == SPDE_OK) s = spde_wait(ctx);
+            if (s == SPDE_ENOCONV || s == SPDE_ETIMEOUT) return SPDE_OK;  // not a usable schedule
+            STATUS_TRY(s);
+        }
+        float f = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&f, e0, e1));
+        *ms = f;
+        return SPDE_OK;
+    };
+    const spde_opts base = level_opts(ctx->opts, L);
+    spde_tuning cur{};
+    cur.omega = base.omega;
+    cur.inner_tol = base.inner_tol;
+    cur.flux_diag = base.flux_diag;
+    cur.sweep_planes = base.sweep_planes;
+    double cur_ms = INFINITY;
+    int evaluated = 0;
+    spde_status s = measure(cur, &cur_ms);
+    ++evaluated;
+    const double default_ms = cur_ms;
+    const double omegas[] = {0.7, 0.8, 0.9};
+    const double itols[] = {1e-4, 1e-5, 1e-6};
+    const double fds[] = {1.25, 1.5, 2.0};
+    const int planes[] = {0, 8, 16, 32};
+    for (int pass = 0; pass < 2 && s == SPDE_OK; ++pass) {
+        for (int knob = 0; knob < 4 && s == SPDE_OK; ++knob) {
+            const int nc = knob == 3 ? 4 : 3;
+            for (int c = 0; c < nc && s == SPDE_OK; ++c) {
+                spde_tuning t = cur;
+                if (knob == 0) t.omega = omegas[c];
+                else if (knob == 1) t.inner_tol = itols[c];
+                else if (knob == 2) t.flux_diag = fds[c];
+                else t.sweep_planes = planes[c];
+                if (t.omega == cur.omega && t.inner_tol == cur.inner_tol && t.flux_diag == cur.flux_diag &&
+                    t.sweep_planes == cur.sweep_planes)
+                    continue;
+                double ms = INFINITY;
+                s = measure(t, &ms);
+                ++evaluated;
+                if (s == SPDE_OK && ms < 0.99 * cur_ms) {
+                    cur = t;
+                    cur_ms = ms;
+                }
+            }
+        }
+    }
+    cudaFree(out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (s != SPDE_OK || !std::isfinite(cur_ms)) {
+            set_tuning_locked(ctx, L, had ? &old : nullptr);
+            if (s != SPDE_OK) return s;
+            return fail(SPDE_ENOCONV, "no schedule reached the tolerance");
+        }
+        cur.ms_per_call = cur_ms;
+        cur.default_ms = default_ms;
+        cur.evaluated = evaluated;
+        set_tuning_locked(ctx, L, &cur);
+    }
+    *best = cur;
     return SPDE_OK;
 }
 
@@ -2336,6 +2497,7 @@ spde_status spde_solve(spde_ctx* ctx, int level, int nsamples, double kappa, con
     for (int s0 = 0; s0 < nsamples; s0 += cap) {
         const int S = std::min(cap, nsamples - s0);
         STATUS_TRY(ensure_workspace(L.ws, gr, plain ? 1 : std::min(cap, nsamples), plain));
+        L.ws.o = level_opts(ctx->opts, L);
         CUDA_TRY(cudaMemcpyAsync(L.ws.F, rhs + (size_t)s0 * n3, (size_t)S * n3 * sizeof(double),
                                  cudaMemcpyDeviceToDevice, st));
         double rel = 0.0;
