@@ -820,6 +820,43 @@ def serve_sweep(pkg, local, nreq):
             "note": "open loop, Poisson arrivals; latency = submit to completion; request mix per rate seeded by the rate"}
 
 
+TUNING_TABLE = os.path.join(ROOT, "paper_1712_06758_gb300", "tuning_table.json")
+TUNE_CASES = [(128, 96, 64)] + [(n, m, s) for (n, m), s in zip(SERVE_LEVELS, MLMC_SAMPLES)]
+
+
+def tuning_for(n, batch, kappa=20.0):
+    """The stored schedule of (grid n^3, batch, kappa), or None."""
+    try:
+        with open(TUNING_TABLE) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return table.get("entries", {}).get("%d^3/%d/%g" % (n, batch, kappa))
+
+
+def run_autotune(args):
+    """Runs the library's autotuner on the headline and MLMC workloads and writes the table."""
+    import torch
+    import paper_1712_06758_gb300 as pkg
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    entries = {}
+    for n, m, S in TUNE_CASES:
+        log("autotune %d^3 x %d" % (n, S))
+        tol = WORKLOAD["tol"] if (n, S) == (128, 64) else 1e-8
+        smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=tol, device=local)
+        smp.add_level(0, n)
+        t = pkg.spde_autotune(smp.ctx, 0, S, 20.0, 1.0)
+        t.update({"tol": tol})
+        entries["%d^3/%d/%g" % (n, S, 20.0)] = t
+        smp.close()
+    table = {"what": "schedules picked by spde_autotune (device time of one grid-output call per candidate)",
+             "gpu": torch.cuda.get_device_name(local), "entries": entries}
+    with open(TUNING_TABLE, "w") as f:
+        json.dump(table, f, indent=1)
+    print(json.dumps(table), flush=True)
+
+
 def run_serve_sweep(args):
     """The serving sweep: rates 10, 30, 100, 300, 1000 req/s, fixed request count per rate."""
     import torch
@@ -842,11 +879,14 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="headline loop only (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=200, help="requests per rate of the serving sweep")
     ap.add_argument("--serve-sweep", action="store_true", help="only the serving sweep over 10..1000 req/s")
+    ap.add_argument("--autotune", action="store_true", help="run the autotuner and write the tuning table")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
     elif args.serve_sweep:
         run_serve_sweep(args)
+    elif args.autotune:
+        run_autotune(args)
     else:
         run_ours(args)
 

@@ -242,8 +242,9 @@ spde_status spde_sample_coupled(spde_ctx* ctx, int fine_level, int coarse_level,
 
 /* ---- serving (continuous batching) ---------------------------------------
  * Requests for samples from several levels, kappas and sigmas are served
- * concurrently.  Samples of one (level, kappa) run as columns of one batch
- * ("lane": its own stream, host thread and workspace); a lane works in
+ * concurrently.  Samples of one level run as columns of one batch ("lane":
+ * its own stream, host thread and workspace), each column with its own kappa
+ * and sigma (the operator and the V-cycle take kappa per column); a lane works in
  * refinement steps and, at every step boundary, retires converged columns
  * into their requests' outputs and admits queued samples into the freed
  * columns.  Lanes are created on demand within opts.serve_budget_bytes and

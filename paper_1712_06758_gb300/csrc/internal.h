@@ -136,7 +136,17 @@ struct MGPlan {
     // z planes per CTA of the tiled sweeps: 8, 16 or 32 where the level's z extent
     // allows, 0 = chosen per level for occupancy
     int sz_pref = 0;
+    // one kappa per column (serving lanes): kh2col [S] (kappa h)^2 of level 0 (FP64), and
+    // per tiled level l a table qtab[l] [S][21] (element type of the plan) of the
+    // kappa-dependent sweep coefficients (mg_coef_row); null: plan.kh2 for every column
+    const double* kh2col = nullptr;
+    const void* qtab[16] = {};
 };
+
+// the kappa-dependent sweep coefficients of tiled level l for (kappa h)^2 = kh2 (the
+// rest of the plan as given): omega / D(k), omega s c / D(k), (1/omega - 1) D(k), k = 0..6
+template <typename T>
+void mg_coef_row(const MGPlan& plan, int l, double kh2, T out[21]);
 
 // ---- noise.cu
 cudaError_t launch_noise(int64_t ncells, int S, uint64_t seed, uint64_t first, double scale,
@@ -152,9 +162,10 @@ template <typename T>
 cudaError_t launch_apply(const Grid3& g, double kh2, int S, const T* x, T* y, cudaStream_t st);
 // r = [0; F] - A x (FP64), written to r32 (float, may be null) and r64 (double, may be
 // null); partial sums of r.r per column into part [S][nblk]; returns nblk
+// kh2c: (kappa h)^2 per cell (fields), kh2s: per column (serving lanes), else kh2
 int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
                       float* r32, double* r64, double* part, const int* active, cudaStream_t st,
-                      const double* kh2c = nullptr);
+                      const double* kh2c = nullptr, const double* kh2s = nullptr);
 // one-time kernel attributes of the flux line solves (done before any stream capture)
 cudaError_t flux_prepare();
 // the multigrid diagonal of a level with cell-wise (kappa h)^2: a_c = mean of the children's a
@@ -196,7 +207,7 @@ cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cuda
 template <typename T>
 int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
                     MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st,
-                    const T* kh2c = nullptr);
+                    const T* kh2c = nullptr, const T* kh2s = nullptr);
 // r1 -= (alpha / beta) r2 and the flux part of the next beta^2 (the flux block of
 // the next preconditioned vector is fd * r1 and is not stored)
 template <typename T>

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 
                                                      double* __restrict__ partA, const MinresCol* __restrict__ st,
                                                      const T* __restrict__ yprev, T* __restrict__ w1,
                                                      const T* __restrict__ w2, T* __restrict__ xd,
-                                                     const T* __restrict__ kh2c) {
+                                                     const T* __restrict__ kh2c, const T* __restrict__ kh2s) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     const MinresCol& cs = st[s];
@@ -140,11 +140,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 
             const QuadPos p = quad_pos(q, g);
             T yu[4], yv[4], yw[4], yt[4];
             V4<T> vc[4];
-            V4<T> k4;  // (kappa h)^2 per cell: one value, or the level's field
+            V4<T> k4;  // (kappa h)^2 per cell: one value (per call or per column), or the level's field
             if (kh2c) k4 = ld4(kh2c + p.c);
             else
 #pragma unroll
-                for (int e = 0; e < 4; ++e) k4.v[e] = kh2;
+                for (int e = 0; e < 4; ++e) k4.v[e] = kh2s ? kh2s[s] : kh2;
             apply_quad_fd<T>(us, ys + 3 * n3, fd, g, p, k4, yu, yv, yw, yt, vc);
             const V4<T> v0 = vc[0], v1 = vc[1], v2 = vc[2], v3 = vc[3];
             V4<T> z0, z1, z2, z3;
@@ -196,13 +196,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 
 
 template <typename T>
 int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
-                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st, const T* kh2c) {
+                    MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st, const T* kh2c,
+                    const T* kh2s) {
     const int nb = cell_blocks(g.cells() / 16);  // four quads per thread: one reduction per 1024 quads
     dim3 grid(nb, S);
     if (g.cube())
-        k_minres_A<T, true><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c);
+        k_minres_A<T, true><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c,
+                                                  kh2s);
     else
-        k_minres_A<T, false><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c);
+        k_minres_A<T, false><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c,
+                                                   kh2s);
     return nb;
 }
 
@@ -550,7 +553,7 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 
 #define SPDE_KRYLOV_INST(T)                                                                                        \
     template int launch_minres_A<T>(const Grid3&, double, int, const T*, const T*, double, T*, double*, MinresCol*,        \
-                                    const T*, T*, const T*, T*, cudaStream_t, const T*);                           \
+                                    const T*, T*, const T*, T*, cudaStream_t, const T*, const T*);                 \
     template int launch_minres_B<T>(int64_t, int, int, T*, const T*, double, double*, MinresCol*, cudaStream_t);   \
     template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \
                                      cudaStream_t);                                                                \

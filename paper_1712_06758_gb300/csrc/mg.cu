@@ -286,7 +286,7 @@ template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
     k_mg_down(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<T> q, T* __restrict__ bc,
               int64_t bc_stride, const int* __restrict__ active, int act_stride, const T* __restrict__ Dg,
-              int* __restrict__ fault) {
+              int* __restrict__ fault, const T* __restrict__ qtab) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ T s_oi[8], s_rcD[8];
     __shared__ uint64_t s_bar[kRing];
@@ -299,12 +299,19 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
     T* const Xbase = ring.slots + kRing * ring.slot;  // 4 x0 plane slots, PW x XH
     T* const Rbase = Xbase + 4 * PW * XH;             // 2 residual plane slots, PW x RH
     T* const Rxy = Rbase + 2 * PW * RH;               // 4 ring planes of the x-y restricted residual
-#pragma unroll
-    for (int k = 0; k < 7; ++k)  // constant indices: the parameter struct stays in the constant bank
-        if (tid == k) {
-            s_oi[k] = q.oi[k];
-            s_rcD[k] = q.rcD[k];
+    if (qtab) {  // this column's own kappa (serving lanes)
+        if (tid < 7) {
+            s_oi[tid] = qtab[(int64_t)col * 21 + tid];
+            s_rcD[tid] = qtab[(int64_t)col * 21 + 14 + tid];
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)  // constant indices: the parameter struct stays in the constant bank
+            if (tid == k) {
+                s_oi[k] = q.oi[k];
+                s_rcD[k] = q.rcD[k];
+            }
+    }
     const int nfx = gf.nx, nfy = gf.ny, nfz = gf.nz;  // all three halve (tiled levels)
     const int ncx = nfx >> 1, ncy = nfy >> 1, ncz = nfz >> 1;
     const int64_t fplane = (int64_t)nfx * nfy;
@@ -504,7 +511,8 @@ template <typename T, bool PC>  // PC: per-cell diagonal (cell-wise kappa) in Dg
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     k_mg_up(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<T> q, const T* __restrict__ ec,
             int64_t ec_stride, T* __restrict__ y, int64_t y_stride, double* __restrict__ dot_part,
-            const int* __restrict__ active, int act_stride, const T* __restrict__ Dg, int* __restrict__ fault) {
+            const int* __restrict__ active, int act_stride, const T* __restrict__ Dg, int* __restrict__ fault,
+            const T* __restrict__ qtab) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kTileThreads / 32];
     __shared__ T s_oi[8], s_ois[8];
@@ -518,12 +526,19 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     T* const Xbase = ring.slots + kRing * ring.slot;  // 4 x plane slots, PW x BH
     T* const Cbase = Xbase + 4 * PW * BH;             // 4 coarse plane slots, CW x CH
     auto Cs = [&](int Z) { return Cbase + ((Z + 4) & 3) * (CW * CH); };  // Z >= -4
-#pragma unroll
-    for (int k = 0; k < 7; ++k)
-        if (tid == k) {
-            s_oi[k] = q.oi[k];
-            s_ois[k] = q.ois[k];
+    if (qtab) {  // this column's own kappa (serving lanes)
+        if (tid < 7) {
+            s_oi[tid] = qtab[(int64_t)col * 21 + tid];
+            s_ois[tid] = qtab[(int64_t)col * 21 + 7 + tid];
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if (tid == k) {
+                s_oi[k] = q.oi[k];
+                s_ois[k] = q.ois[k];
+            }
+    }
     const int nfx = gf.nx, nfy = gf.ny, nfz = gf.nz;  // all three halve (tiled levels)
     const int ncx = nfx >> 1, ncy = nfy >> 1, ncz = nfz >> 1;
     const int ntx = nfx / SX, nty = nfy / SY, ntz = nfz / SZ;
@@ -730,24 +745,26 @@ struct CoarseDesc {
     double kh2, c, omega;
     double ls[16], lq[16];  // level factors s_l, q_l
     const void* D[16];  // per-cell diagonals of the levels (cell-wise kappa), or null
+    const double* kh2col;  // (kappa h)^2 of level 0 per column (serving lanes), or null: kh2
 };
 
 template <typename T>
-__device__ __forceinline__ T cz_invD(const CoarseDesc& d, int l, int k) {
+__device__ __forceinline__ T cz_invD(const CoarseDesc& d, int l, int k, double kh2) {
     const T s = (T)d.ls[l];
-    const T a = (T)(d.kh2 * d.lq[l]);
+    const T a = (T)(kh2 * d.lq[l]);
     return T(1) / (s * (a + (T)d.c * (T)k));
 }
 
 // 1 / diagonal of cell f (neighbour count kc) on level l
 template <typename T>
-__device__ __forceinline__ T cz_invDf(const CoarseDesc& d, int l, int kc, int f) {
+__device__ __forceinline__ T cz_invDf(const CoarseDesc& d, int l, int kc, int f, double kh2) {
     if (d.D[l]) return T(1) / static_cast<const T*>(d.D[l])[f];
-    return cz_invD<T>(d, l, kc);
+    return cz_invD<T>(d, l, kc, kh2);
 }
 
 template <typename T>
-__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, const Grid3& g, int i, int j, int k) {
+__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, const Grid3& g, int i, int j, int k,
+                                   double kh2) {
     const int sy = g.nx, sz = g.nx * g.ny;
     const int f = i + g.nx * (j + g.ny * k);
     const T x0 = x[f];
@@ -769,7 +786,7 @@ __device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, const
     if (k > 0) lap += x0 - x[f - sz];
     if (k < g.nz - 1) lap += x0 - x[f + sz];
     const T s = (T)d.ls[l];
-    const T a = (T)(d.kh2 * d.lq[l]);
+    const T a = (T)(kh2 * d.lq[l]);
     return s * (a * x0 + (T)d.c * lap);
 }
 
@@ -812,6 +829,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int col = blockIdx.x;
     if (active && !active[(int64_t)col * act_stride]) return;
+    const double kh2 = d.kh2col ? d.kh2col[col] : d.kh2;
     // layout: b_l and x_l for l = lc .. nlev-1, then a temp of level lc's size
     int offb[16], offx[16];
     int o = 0;
@@ -839,12 +857,12 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
         T* x = sm + offx[l];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
-            x[f] = om * b[f] * cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f);
+            x[f] = om * b[f] * cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f, kh2);
         }
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
-            tmp[f] = b[f] - cz_Ax<T>(d, l, x, g, i, j, k);
+            tmp[f] = b[f] - cz_Ax<T>(d, l, x, g, i, j, k, kh2);
         }
         __syncthreads();
         T* bc = sm + offb[l + 1];
@@ -880,7 +898,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     // bottom: one cell, exact
     {
         const int l = d.nlev - 1;
-        if (threadIdx.x == 0) sm[offx[l]] = sm[offb[l]] * cz_invDf<T>(d, l, 0, 0);
+        if (threadIdx.x == 0) sm[offx[l]] = sm[offb[l]] * cz_invDf<T>(d, l, 0, 0, kh2);
         __syncthreads();
     }
     // up
@@ -907,8 +925,8 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
-            const T iD = cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f);
-            x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, g, i, j, k));
+            const T iD = cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f, kh2);
+            x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, g, i, j, k, kh2));
         }
         __syncthreads();
     }
@@ -1001,7 +1019,11 @@ void mg_plan_bind(MGPlan& plan, int S, T* scratch) {
 }
 
 // z planes per CTA for the level sweeps: the longest march (fewest halo planes)
-// that still gives at least four CTAs per SM of a 152-SM GPU
+// that still gives at least four CTAs per SM of a 152-SM GPU.  The choice
+// partitions the b.y partial sums of the up sweep, so it must not depend on
+// how many columns share a batch: the FP32 path decides it for a batch of 64
+// whatever the batch (a column gives the same bits alone, in a bigger batch or
+// in a serving lane); the FP64 path, which runs one column at a time, for its S.
 static int pick_sz(const Grid3& g, int S, int pref) {
     if ((pref == 8 || pref == 16 || pref == 32) && g.nz % pref == 0) return pref;
     const int base = (g.nx / SX) * (g.ny / SY);
@@ -1096,6 +1118,20 @@ static cudaError_t mg_attrs() {
     return e;
 }
 
+template <typename T>
+void mg_coef_row(const MGPlan& plan, int l, double kh2, T out[21]) {
+    MGPlan p = plan;
+    p.kh2 = kh2;
+    const LevelCoef<T> q = level_coef<T>(p, l);
+    for (int k = 0; k < 7; ++k) {
+        out[k] = q.oi[k];
+        out[7 + k] = q.ois[k];
+        out[14 + k] = q.rcD[k];
+    }
+}
+template void mg_coef_row<float>(const MGPlan&, int, double, float*);
+template void mg_coef_row<double>(const MGPlan&, int, double, double*);
+
 cudaError_t mg_prepare() {
     cudaError_t e = mg_attrs<float>();
     if (e == cudaSuccess) e = mg_attrs<double>();
@@ -1113,6 +1149,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     d.lc = plan.lc;
     d.nlev = plan.nlev;
     d.kh2 = plan.kh2;
+    d.kh2col = plan.kh2col;
     d.c = plan.c;
     d.omega = plan.omega;
     for (int l = 0; l < 16; ++l) {
@@ -1136,7 +1173,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     for (int l = 0; l < plan.lc; ++l) {
         const Grid3& gf = plan.g[l];
         const int64_t nc3 = plan.g[l + 1].cells();
-        const int sz = pick_sz(gf, S, plan.sz_pref);
+        const int sz = pick_sz(gf, sizeof(T) == 4 ? 64 : S, plan.sz_pref);
         const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
@@ -1144,12 +1181,13 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         if (!plane_map<T>(&map, in, gf, S, in_stride, XH)) return -1;
         prof_begin(PK_MG_DOWN, st);
         const T* Dl = static_cast<const T*>(plan.D[l]);
+        const T* qt = static_cast<const T*>(plan.qtab[l]);
         if (Dl)
             k_mg_down<T, true><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
-                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, Dl, plan.fault);
+                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, Dl, plan.fault, qt);
         else
             k_mg_down<T, false><<<grid, dim3(32, 8), down_smem_bytes<T>(), st>>>(
-                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, nullptr, plan.fault);
+                map, gf, sz, level_coef<T>(plan, l), out, nc3, active, act_stride, nullptr, plan.fault, qt);
         prof_end(st, prof_cols * (1.0 + 0.125) * (double)gf.cells() * w);
         in = out;
         in_stride = nc3;
@@ -1165,7 +1203,7 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     for (int l = plan.lc - 1; l >= 0; --l) {
         const Grid3& gf = plan.g[l];
         const int64_t nf3 = gf.cells(), nc3 = plan.g[l + 1].cells();
-        const int sz = pick_sz(gf, S, plan.sz_pref);
+        const int sz = pick_sz(gf, sizeof(T) == 4 ? 64 : S, plan.sz_pref);
         const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
         dim3 grid(nb, S);
@@ -1177,14 +1215,15 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         if (!plane_map<T>(&map, bl, gf, S, bls, BH)) return -1;
         prof_begin(PK_MG_UP, st);
         const T* Dl = static_cast<const T*>(plan.D[l]);
+        const T* qt = static_cast<const T*>(plan.qtab[l]);
         if (Dl)
             k_mg_up<T, true><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
                 map, gf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
-                (l == 0) ? dot_part : nullptr, active, act_stride, Dl, plan.fault);
+                (l == 0) ? dot_part : nullptr, active, act_stride, Dl, plan.fault, qt);
         else
             k_mg_up<T, false><<<grid, dim3(32, 8), up_smem_bytes<T>(), st>>>(
                 map, gf, sz, level_coef<T>(plan, l), static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
-                (l == 0) ? dot_part : nullptr, active, act_stride, nullptr, plan.fault);
+                (l == 0) ? dot_part : nullptr, active, act_stride, nullptr, plan.fault, qt);
         prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf3 * w);
         if (l == 0) nblk0 = nb;
     }

@@ -393,10 +393,19 @@ spde_status ensure_workspace(Workspace& ws, const Grid3& g, int S, bool inner64)
 
 // Batched MINRES on the scaled mixed system for the columns flagged in
 // st[].active; right-hand sides in r2 (inner type T), solution in d.
+// One kappa per column (serving lanes): (kappa h)^2 per column in FP64 and in the
+// inner type, and the per-column sweep coefficients of every tiled level.
+struct ColKappa {
+    const double* kh2_64 = nullptr;
+    const void* kh2_t = nullptr;
+    const void* qtab[16] = {};
+};
+
 template <typename T>
 spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Workspace& ws, double inner_tol,
                          int* iters_out, cudaStream_t st, const T* kh2c = nullptr, T* const* Dlev = nullptr,
-                         const double* col_tol = nullptr) {
+                         const double* col_tol = nullptr, const ColKappa* ck = nullptr) {
+    const T* kh2s = ck ? static_cast<const T*>(ck->kh2_t) : nullptr;
     const int64_t n3 = g.cells(), N4 = 4 * n3;
     T* d = static_cast<T*>(ws.vec[0]);
     T* w1 = static_cast<T*>(ws.vec[1]);
@@ -412,6 +421,10 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
     plan.sz_pref = o.sweep_planes;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
+    if (ck) {
+        plan.kh2col = ck->kh2_64;
+        for (int l = 0; l < 16; ++l) plan.qtab[l] = ck->qtab[l];
+    }
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
     const int* act = &ws.st[0].active;
     const double w = (double)sizeof(T);
@@ -449,7 +462,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
             // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
             const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
-                                              pending ? yprev : nullptr, w1, w2, d, st, kh2c);
+                                              pending ? yprev : nullptr, w1, w2, d, st, kh2c, kh2s);
             a_bytes[q] = ((itn >= 2 ? 12.0 : 8.0) + (kh2c ? 1.0 : 0.0)) * n3d * w;
             d_bytes[q] = pending ? (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0;
             prof_end(st, 0.0);
@@ -1052,15 +1065,19 @@ namespace {
 // ============================================================================
 // Serving: continuous batching of sample requests.
 //
-// One lane per (level, kappa): its own stream, worker thread and workspace of
-// `cap` columns.  A lane works in rounds; a round is one refinement step of
-// every occupied column (residual -> retire converged columns into their
-// requests' outputs -> one batched inner MINRES solve -> correction).  Free
-// columns take the next queued samples at every round boundary, so requests
-// that arrive while others run join the batch without waiting for it to
-// drain, and lanes of different levels / kappa overlap on the device.  Each
-// column follows exactly the per-column sequence of spde_sample, so a
-// sample's result does not depend on the mix it ran in.
+// One lane per level: its own stream, worker thread and workspace of `cap`
+// columns.  Every column carries its own kappa (the operator's (kappa h)^2 and
+// the V-cycle's level coefficients per column), so requests for different
+// kappa and sigma share a batch.  A lane works in rounds; a round is one
+// refinement step of every occupied column (residual -> retire converged
+// columns into their requests' outputs -> one batched inner MINRES solve ->
+// correction).  Free columns take the next queued samples at every round
+// boundary, so requests that arrive while others run join the batch without
+// waiting for it to drain, and lanes of different levels overlap on the
+// device.  Each column follows exactly the per-column sequence of
+// spde_sample (the per-column coefficients are computed by the same host code
+// as spde_sample's single ones), so a sample's result does not depend on the
+// mix it ran in.
 // ============================================================================
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -1090,7 +1107,6 @@ struct Lane {
     };
     Server* srv = nullptr;
     int level = 0;
-    double kappa = 0.0;
     int cap = 0;
     int64_t bytes = 0;
     cudaStream_t st = nullptr;
@@ -1101,6 +1117,12 @@ struct Lane {
     double *d_scale = nullptr, *h_scale = nullptr;
     int *d_mask = nullptr, *h_mask = nullptr, *d_cols = nullptr, *h_cols = nullptr;
     int *d_fresh = nullptr, *h_fresh = nullptr;  // separate buffer: its copy may still be pending
+    // each column's own kappa: (kappa h)^2 in FP64 and FP32, and the V-cycle sweep coefficients
+    // of the tiled levels ([level][column][21], FP32)
+    double *d_kh2 = nullptr, *h_kh2 = nullptr;
+    float *d_kh2f = nullptr, *h_kh2f = nullptr;
+    float *d_qtab = nullptr, *h_qtab = nullptr;
+    int ntiled = 0;
     void **d_outs = nullptr, **h_outs = nullptr;
     std::thread th;
     std::condition_variable cv;
@@ -1119,7 +1141,7 @@ struct Server {
     int64_t used_bytes = 0;
 };
 
-int64_t lane_param_bytes(int cap) { return (int64_t)cap * (8 + 8 + 8 + 4 + 4 + 4 + 8) * 2; }
+int64_t lane_param_bytes(int cap) { return (int64_t)cap * ((8 + 8 + 8 + 4 + 4 + 4 + 8 + 8 + 4) * 2 + 16 * 21 * 4 * 2); }
 
 void lane_free(Lane* L) {
     L->ws.release();
@@ -1129,6 +1151,15 @@ void lane_free(Lane* L) {
     dev_free(L->d_mask);
     dev_free(L->d_fresh);
     dev_free(L->d_cols);
+    dev_free(L->d_kh2);
+    dev_free(L->d_kh2f);
+    dev_free(L->d_qtab);
+    if (L->h_kh2) cudaFreeHost(L->h_kh2);
+    if (L->h_kh2f) cudaFreeHost(L->h_kh2f);
+    if (L->h_qtab) cudaFreeHost(L->h_qtab);
+    L->h_kh2 = nullptr;
+    L->h_kh2f = nullptr;
+    L->h_qtab = nullptr;
     if (L->d_outs) cudaFree(L->d_outs);
     L->d_outs = nullptr;
     if (L->h_seed) cudaFreeHost(L->h_seed);
@@ -1160,6 +1191,20 @@ spde_status lane_alloc(Lane* L, const Grid3& g) {
     STATUS_TRY(dev_alloc(&L->d_mask, cap));
     STATUS_TRY(dev_alloc(&L->d_fresh, cap));
     STATUS_TRY(dev_alloc(&L->d_cols, cap));
+    {
+        MGPlan p;
+        mg_plan_init(p, g, 0.0, 1.0, 0.8);
+        L->ntiled = p.lc;
+    }
+    STATUS_TRY(dev_alloc(&L->d_kh2, cap));
+    STATUS_TRY(dev_alloc(&L->d_kh2f, cap));
+    STATUS_TRY(dev_alloc(&L->d_qtab, (size_t)std::max(L->ntiled, 1) * cap * 21));
+    if (cudaMallocHost(&L->h_kh2, cap * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&L->h_kh2f, cap * sizeof(float)) != cudaSuccess ||
+        cudaMallocHost(&L->h_qtab, (size_t)std::max(L->ntiled, 1) * cap * 21 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SPDE_ENOMEM, "lane parameter allocation failed");
+    }
     if (cudaMalloc(&L->d_outs, cap * sizeof(void*)) != cudaSuccess ||
         cudaMallocHost(&L->h_seed, cap * sizeof(uint64_t)) != cudaSuccess ||
         cudaMallocHost(&L->h_sample, cap * sizeof(uint64_t)) != cudaSuccess ||
@@ -1184,10 +1229,33 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
     const Grid3 g = LV.g;
     const int S = L->cap;
     const int64_t n3 = g.cells(), N4 = 4 * n3;
-    const double kh2 = (L->kappa * LV.h) * (L->kappa * LV.h);
     Workspace& ws = L->ws;
     cudaStream_t st = L->st;
     finished.clear();
+    // every column carries its own kappa: (kappa h)^2 and the sweep coefficients of the
+    // tiled levels, computed exactly as spde_sample computes them for one kappa
+    double kh2 = 1.0;  // the scalar arguments (the per-column values take precedence)
+    {
+        MGPlan base;
+        mg_plan_init(base, g, 1.0, o.schur_c, o.omega);
+        for (int c = 0; c < S; ++c) {
+            const Lane::Slot& sl = L->slots[c];
+            const double k2 = sl.used ? (sl.req->kappa * LV.h) * (sl.req->kappa * LV.h) : 1.0;
+            if (sl.used) kh2 = k2;
+            L->h_kh2[c] = k2;
+            L->h_kh2f[c] = (float)k2;
+            for (int l = 0; l < L->ntiled; ++l) mg_coef_row<float>(base, l, k2, L->h_qtab + ((size_t)l * S + c) * 21);
+        }
+        CUDA_TRY(cudaMemcpyAsync(L->d_kh2, L->h_kh2, S * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(L->d_kh2f, L->h_kh2f, S * sizeof(float), cudaMemcpyHostToDevice, st));
+        if (L->ntiled)
+            CUDA_TRY(cudaMemcpyAsync(L->d_qtab, L->h_qtab, (size_t)L->ntiled * S * 21 * sizeof(float),
+                                     cudaMemcpyHostToDevice, st));
+    }
+    ColKappa ck;
+    ck.kh2_64 = L->d_kh2;
+    ck.kh2_t = L->d_kh2f;
+    for (int l = 0; l < L->ntiled; ++l) ck.qtab[l] = L->d_qtab + (size_t)l * S * 21;
     // fresh columns: noise, zero iterate, ||F||^2
     bool any_fresh = false, any_old = false;
     for (int c = 0; c < S; ++c) {
@@ -1197,7 +1265,7 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
             any_fresh = true;
             L->h_seed[c] = sl.req->seed;
             L->h_sample[c] = sl.req->first + (uint64_t)sl.j;
-            L->h_scale[c] = -g_half(L->kappa, sl.req->sigma) * LV.h;
+            L->h_scale[c] = -g_half(sl.req->kappa, sl.req->sigma) * LV.h;
         } else {
             L->h_seed[c] = 0;
             L->h_sample[c] = 0;
@@ -1221,7 +1289,7 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
     CUDA_TRY(cudaMemcpyAsync(L->d_mask, L->h_mask, S * sizeof(int), cudaMemcpyHostToDevice, st));
     if (any_old) CUDA_TRY(launch_flux_from_theta(g, S, ws.x64, N4, ws.tri, st));
     const int nbr = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, static_cast<float*>(ws.vec[4]), nullptr, ws.partR,
-                                      L->d_mask, st);
+                                      L->d_mask, st, nullptr, L->d_kh2);
     CUDA_TRY(launch_reduce(S, ws.partR, nbr, ws.colv, st));
     CUDA_TRY(cudaMemcpyAsync(ws.h_col, ws.colv, 2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
     int fault = 0;
@@ -1292,7 +1360,7 @@ spde_status lane_round(Lane* L, std::vector<int>& finished) {
         CUDA_TRY(launch_set_active(S, L->d_mask, ws.st, st));
         int its = 0;
         CUDA_TRY(cudaMemcpyAsync(ws.coltol, ws.h_tol, S * sizeof(double), cudaMemcpyHostToDevice, st));
-        STATUS_TRY(minres_batch<float>(o, g, kh2, S, ws, o.inner_tol, &its, st, nullptr, nullptr, ws.coltol));
+        STATUS_TRY(minres_batch<float>(o, g, kh2, S, ws, o.inner_tol, &its, st, nullptr, nullptr, ws.coltol, &ck));
         CUDA_TRY(launch_add_theta<float>(n3, S, ws.x64, static_cast<const float*>(ws.vec[0]), ws.st, st));
         for (int c : going) L->slots[c].outer += 1;
     }
@@ -1389,7 +1457,7 @@ void lane_main(Lane* L) {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->used_bytes -= L->bytes;
     L->dead = true;
-    auto it = srv->lanes.find({L->level, L->kappa});
+    auto it = srv->lanes.find({L->level, 0.0});
     if (it != srv->lanes.end() && it->second.get() == L) {
         srv->graveyard.push_back(std::move(it->second));
         srv->lanes.erase(it);
@@ -1414,7 +1482,7 @@ void server_dispatch(Server* srv) {
             }
             continue;
         }
-        auto key = std::make_pair(r->level, r->kappa);
+        auto key = std::make_pair(r->level, 0.0);  // one lane per level: columns carry their own kappa
         auto it = srv->lanes.find(key);
         if (it != srv->lanes.end() && !it->second->dead) {
             it->second->queue.push_back(r);
@@ -1438,7 +1506,6 @@ void server_dispatch(Server* srv) {
         std::unique_ptr<Lane> L(new Lane());
         L->srv = srv;
         L->level = r->level;
-        L->kappa = r->kappa;
         L->cap = cap;
         L->bytes = need;
         cudaSetDevice(ctx->opts.device);

@@ -54,10 +54,12 @@ template cudaError_t launch_apply<double>(const Grid3&, double, int, const doubl
 __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const double* __restrict__ F, int64_t F_stride,
                                                     const double* __restrict__ x, float* __restrict__ r32,
                                                     double* __restrict__ r64, double* __restrict__ part,
-                                                    const int* __restrict__ active, const double* __restrict__ kh2c) {
+                                                    const int* __restrict__ active, const double* __restrict__ kh2c,
+                                                    const double* __restrict__ kh2s) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     if (active && !active[s]) return;
+    const double kh2v = kh2s ? kh2s[s] : kh2;  // one (kappa h)^2 per column (serving lanes) or per call
     const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int64_t off = (int64_t)s * 4 * n3;
     const double* xs = x + off;
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const d
         if (kh2c) k4 = ld4(kh2c + c);
         else
 #pragma unroll
-            for (int e = 0; e < 4; ++e) k4.v[e] = kh2;
+            for (int e = 0; e < 4; ++e) k4.v[e] = kh2v;
         V4<double> d;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -120,10 +122,11 @@ __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const d
 }
 
 int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
-                      float* r32, double* r64, double* part, const int* active, cudaStream_t st, const double* kh2c) {
+                      float* r32, double* r64, double* part, const int* active, cudaStream_t st, const double* kh2c,
+                      const double* kh2s) {
     const int nb = stencil_blocks(g.cells() / 4);
     dim3 grid(nb, S);
-    k_residual64<<<grid, 256, 0, st>>>(g, kh2, F, F_stride, x, r32, r64, part, active, kh2c);
+    k_residual64<<<grid, 256, 0, st>>>(g, kh2, F, F_stride, x, r32, r64, part, active, kh2c, kh2s);
     return nb;
 }
 

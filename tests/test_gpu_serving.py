@@ -56,7 +56,7 @@ def test_mixed_stream_matches_alone():
     reqs = []
     for k in range(14):
         lvl = int(rng.integers(0, 2))
-        kappa = [10.0, 20.0][int(rng.integers(0, 2))]
+        kappa = [10.0, 20.0, 40.0][int(rng.integers(0, 3))]  # kappas share a level's lane
         sigma = float(rng.uniform(0.5, 2.0))
         ns = int(rng.integers(1, 9))
         kind = [pkg.SPDE_OUT_LOGNORMAL, pkg.SPDE_OUT_GAUSSIAN | pkg.SPDE_OUT_F64,
@@ -128,4 +128,23 @@ def test_admission_under_a_small_budget():
         alone = torch.full_like(out, float("nan"))
         pkg.spde_sample(smp.ctx, lvl, 3, kappa, 1.0, 50 + k, 0, pkg.SPDE_OUT_GRID_GAUSSIAN, alone)
         assert torch.equal(out, alone)
+    smp.close()
+
+
+def test_batch_size_does_not_change_a_column():
+    """A column's bits do not depend on how many columns share its batch: the same
+    samples drawn 3 at a time, 64 at a time and through a serving lane (64^3, where
+    the sweeps' tiling could depend on the batch size)."""
+    n, kind = 64, pkg.SPDE_OUT_GRID_GAUSSIAN | pkg.SPDE_OUT_F64
+    smp = pkg.Sampler(pkg.SPDE_PREC_MIXED)
+    smp.add_level(0, n)
+    big = smp.sample(0, 64, 20.0, 1.0, 8, 0, kind)
+    small = smp.sample(0, 3, 20.0, 1.0, 8, 5, kind)
+    torch.cuda.synchronize()
+    assert torch.equal(big[5:8], small)
+    out = torch.empty((3, n ** 3), dtype=torch.float64, device="cuda")
+    rid = pkg.spde_submit(smp.ctx, 0, 3, 20.0, 1.0, 8, 5, kind, out)
+    _, st = _wait(smp, [rid])[rid]
+    assert st == pkg.SPDE_OK
+    assert torch.equal(out, small)
     smp.close()
