@@ -249,19 +249,25 @@ def timed_call(pkg, smp, stream, fn):
 def run_mlmc_levels(pkg, local, stream, modes=(1, 0)):
     """The 4-level MLMC batch: 32^3/64^3/128^3/256^3 grids with L-prism 24^3/48^3/96^3/192^3 meshes,
     4096/1024/256/64 samples, kappa 20, tol 1e-8, lognormal FP32 out.  Each level has its own context
-    (one level's workspace at a time); one call per level after a warm-up call, timed with CUDA events,
-    through the graph-driven path (one graph launch per level and batch) and the synchronous host loop."""
+    (one level's workspace at a time) with the schedule the autotuner stored for (grid, batch); one call
+    per level after a warm-up call, timed with CUDA events, through the graph-driven path (one graph
+    launch per level and batch) and the synchronous host loop."""
     import torch
     rows, tot = [], {"graphs": 0.0, "host_loop": 0.0}
     for (n, m), S in zip(SERVE_LEVELS, MLMC_SAMPLES):
         xyz, tets = lprism_cached(m)
         row = {"grid": n, "mesh": "L-prism %d^3 cubes" % m, "ntets": int(len(tets)), "samples": S}
         out = torch.empty((S, len(tets)), dtype=torch.float32, device="cuda")
+        tune = tuning_for(n, S)
+        row["schedule"] = ({k: tune[k] for k in ("omega", "inner_tol", "flux_diag", "sweep_planes")}
+                           if tune else "context defaults")
         for g in modes:
             key = "graphs" if g else "host_loop"
             smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=1e-8, device=local, use_graphs=g)
             smp.add_level(0, n)
             smp.attach_mesh(0, xyz, tets)
+            if tune:
+                pkg.spde_level_set_tuning(smp.ctx, 0, tune)
             smp.sample(0, S, 20.0, 1.0, 3, 10 ** 7, pkg.SPDE_OUT_LOGNORMAL, out, stream)  # warm-up
             ms = timed_call(pkg, smp, stream, lambda: pkg.spde_sample(smp.ctx, 0, S, 20.0, 1.0, 3, 0,
                                                                        pkg.SPDE_OUT_LOGNORMAL, out, stream))
@@ -276,6 +282,32 @@ def run_mlmc_levels(pkg, local, stream, modes=(1, 0)):
     return {"levels": rows, "kappa": 20.0, "sigma": 1.0, "tol": 1e-8, "output": "lognormal f32 on tets",
             "hierarchy_ms": tot, "hierarchy_samples": total,
             "hierarchy_samples_per_s": {k: total / (v / 1000.0) for k, v in tot.items() if v > 0}}
+
+
+def run_fp16_coarse(pkg, local, stream):
+    """Iterations and residual with the coarse kernel's levels stored in FP16 against FP32, on the
+    headline grid (128^3, kappa 20, 64 samples, tol 1e-10) and the large level (512^3, kappa 40,
+    2 samples, tol 1e-8); grid output, one timed call after a warm-up call per setting."""
+    import torch
+    res = {}
+    for n, kappa, S, tol in ((128, 20.0, 64, 1e-10), (512, 40.0, 2, 1e-8)):
+        out = torch.empty((S, n ** 3), dtype=torch.float32, device="cuda")
+        row = {"kappa": kappa, "samples": S, "tol": tol}
+        for fp16 in (0, 1):
+            smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=tol, device=local, coarse_fp16=fp16)
+            smp.add_level(0, n)
+            smp.sample(0, S, kappa, 1.0, 3, 10 ** 7, pkg.SPDE_OUT_GRID_GAUSSIAN, out, stream)
+            ms = timed_call(pkg, smp, stream, lambda: pkg.spde_sample(smp.ctx, 0, S, kappa, 1.0, 3, 0,
+                                                                       pkg.SPDE_OUT_GRID_GAUSSIAN, out, stream))
+            st = smp.stats()
+            row["fp16" if fp16 else "fp32"] = {"ms": ms, "outer_iters": st["outer_iters"],
+                                               "inner_iters": st["inner_iters"],
+                                               "max_rel_residual": st["max_rel_residual"]}
+            smp.close()
+        del out
+        res["%d^3" % n] = row
+    res["levels_in_fp16"] = "those of the one-CTA coarse kernel (<= 4096 cells: 16^3 and below on a cube)"
+    return res
 
 
 def run_large(pkg, local, stream):
@@ -752,6 +784,8 @@ def run_ours(args):
         mlmc = run_mlmc_levels(pkg, local, stream)
         log("512^3 level")
         large = run_large(pkg, local, stream)
+        log("fp16 coarse levels")
+        fp16c = run_fp16_coarse(pkg, local, stream)
         # the oracle on the host cores: whole samples of the same workload
         log("cpu baseline")
         oc = OracleSampler(xyz, tets)
@@ -770,6 +804,7 @@ def run_ours(args):
                 "graphs": graphs,
                 "mlmc_levels": mlmc,
                 "large_512": large,
+                "fp16_coarse": fp16c,
                 "plain_fp64": {"value": plain_rate, "unit": "samples/s", "samples": nplain,
                                "ratio": value / world / plain_rate, "inner_iters": pst["inner_iters"],
                                "max_rel_l2_vs_mixed": float(d.max())},

@@ -117,6 +117,9 @@ typedef struct {
     int sweep_planes;           /* fine z planes per CTA of the V-cycle sweeps: 8, 16 or 32 where a
                                    level's z extent allows; 0 (default) = per level, the longest
                                    march that still gives 4 CTAs per SM */
+    int coarse_fp16;            /* 1: the V-cycle levels held by the one-CTA coarse kernel (at most 4096
+                                   cells, 16^3 on a cube) are stored in FP16, each column scaled by its
+                                   largest value, arithmetic in FP32 (FP32 path only); 0 (default): FP32 */
 } spde_opts;
 
 typedef struct {

@@ -136,6 +136,8 @@ struct MGPlan {
     // z planes per CTA of the tiled sweeps: 8, 16 or 32 where the level's z extent
     // allows, 0 = chosen per level for occupancy
     int sz_pref = 0;
+    // FP16 storage of the levels the one-CTA coarse kernel holds (FP32 path)
+    bool coarse_fp16 = false;
     // one kappa per column (serving lanes): kh2col [S] (kappa h)^2 of level 0 (FP64), and
     // per tiled level l a table qtab[l] [S][21] (element type of the plan) of the
     // kappa-dependent sweep coefficients (mg_coef_row); null: plan.kh2 for every column

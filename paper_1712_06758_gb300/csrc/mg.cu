@@ -26,6 +26,8 @@
 // per sample in shared memory.
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "device.cuh"
@@ -748,6 +750,18 @@ struct CoarseDesc {
     const double* kh2col;  // (kappa h)^2 of level 0 per column (serving lanes), or null: kh2
 };
 
+// storage of the one-CTA levels: the compute type, or FP16 (values scaled into range)
+template <typename T, typename SM>
+__device__ __forceinline__ T cz_ld(const SM* p, int i) {
+    if constexpr (std::is_same<SM, __half>::value) return (T)__half2float(p[i]);
+    else return p[i];
+}
+template <typename T, typename SM>
+__device__ __forceinline__ void cz_st(SM* p, int i, T v) {
+    if constexpr (std::is_same<SM, __half>::value) p[i] = __float2half_rn((float)v);
+    else p[i] = v;
+}
+
 template <typename T>
 __device__ __forceinline__ T cz_invD(const CoarseDesc& d, int l, int k, double kh2) {
     const T s = (T)d.ls[l];
@@ -762,29 +776,29 @@ __device__ __forceinline__ T cz_invDf(const CoarseDesc& d, int l, int kc, int f,
     return cz_invD<T>(d, l, kc, kh2);
 }
 
-template <typename T>
-__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const T* x, const Grid3& g, int i, int j, int k,
+template <typename T, typename SM>
+__device__ __forceinline__ T cz_Ax(const CoarseDesc& d, int l, const SM* x, const Grid3& g, int i, int j, int k,
                                    double kh2) {
     const int sy = g.nx, sz = g.nx * g.ny;
     const int f = i + g.nx * (j + g.ny * k);
-    const T x0 = x[f];
+    const T x0 = cz_ld<T>(x, f);
     if (d.D[l]) {  // per-cell diagonal: D x0 - s c (sum of existing neighbours)
         T nb = T(0);
-        if (i > 0) nb += x[f - 1];
-        if (i < g.nx - 1) nb += x[f + 1];
-        if (j > 0) nb += x[f - sy];
-        if (j < g.ny - 1) nb += x[f + sy];
-        if (k > 0) nb += x[f - sz];
-        if (k < g.nz - 1) nb += x[f + sz];
+        if (i > 0) nb += cz_ld<T>(x, f - 1);
+        if (i < g.nx - 1) nb += cz_ld<T>(x, f + 1);
+        if (j > 0) nb += cz_ld<T>(x, f - sy);
+        if (j < g.ny - 1) nb += cz_ld<T>(x, f + sy);
+        if (k > 0) nb += cz_ld<T>(x, f - sz);
+        if (k < g.nz - 1) nb += cz_ld<T>(x, f + sz);
         return static_cast<const T*>(d.D[l])[f] * x0 - (T)d.ls[l] * (T)d.c * nb;
     }
     T lap = T(0);
-    if (i > 0) lap += x0 - x[f - 1];
-    if (i < g.nx - 1) lap += x0 - x[f + 1];
-    if (j > 0) lap += x0 - x[f - sy];
-    if (j < g.ny - 1) lap += x0 - x[f + sy];
-    if (k > 0) lap += x0 - x[f - sz];
-    if (k < g.nz - 1) lap += x0 - x[f + sz];
+    if (i > 0) lap += x0 - cz_ld<T>(x, f - 1);
+    if (i < g.nx - 1) lap += x0 - cz_ld<T>(x, f + 1);
+    if (j > 0) lap += x0 - cz_ld<T>(x, f - sy);
+    if (j < g.ny - 1) lap += x0 - cz_ld<T>(x, f + sy);
+    if (k > 0) lap += x0 - cz_ld<T>(x, f - sz);
+    if (k < g.nz - 1) lap += x0 - cz_ld<T>(x, f + sz);
     const T s = (T)d.ls[l];
     const T a = (T)(kh2 * d.lq[l]);
     return s * (a * x0 + (T)d.c * lap);
@@ -819,14 +833,15 @@ __device__ __forceinline__ void prolong_taps(bool coarsened, int i, int nc, int 
     w[1] = 0.25f;
 }
 
-template <typename T>
+template <typename T, typename SM>
 __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, const T* __restrict__ bin, int64_t b_stride,
                                                               T* __restrict__ eout, int64_t e_stride,
                                                               double* __restrict__ dot_part,
                                                               const int* __restrict__ active, int act_stride) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[kCoarseThreads / 32];
-    T* sm = reinterpret_cast<T*>(smem_raw);
+    SM* sm = reinterpret_cast<SM*>(smem_raw);
+    __shared__ T s_scale;
     const int col = blockIdx.x;
     if (active && !active[(int64_t)col * act_stride]) return;
     const double kh2 = d.kh2col ? d.kh2col[col] : d.kh2;
@@ -840,12 +855,31 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
         offx[l] = o;
         o += nl;
     }
-    T* tmp = sm + o;
+    SM* tmp = sm + o;
     const T* bs = bin + (int64_t)col * b_stride;
     T* es = eout + (int64_t)col * e_stride;
+    // FP16 storage: the column is scaled by 1 / max |b| (the V-cycle is linear), so every
+    // stored value lies within FP16 range; the result is scaled back on the way out
+    T scale = T(1);
+    if constexpr (std::is_same<SM, __half>::value) {
+        const int n3 = (int)d.g[d.lc].cells();
+        float mx = 0.0f;
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) mx = fmaxf(mx, fabsf((float)bs[f]));
+        for (int of = 16; of > 0; of >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, of));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = 0.0f;
+            for (int w = 0; w < kCoarseThreads / 32; ++w) m = fmaxf(m, (float)red[w]);
+            s_scale = m > 0.0f ? (T)m : T(1);
+        }
+        __syncthreads();
+        scale = s_scale;
+    }
     {
         const int n3 = (int)d.g[d.lc].cells();
-        for (int f = threadIdx.x; f < n3; f += blockDim.x) sm[offb[d.lc] + f] = bs[f];
+        const T inv = T(1) / scale;
+        for (int f = threadIdx.x; f < n3; f += blockDim.x) cz_st<T>(sm, offb[d.lc] + f, bs[f] * inv);
     }
     __syncthreads();
     const T om = (T)d.omega;
@@ -853,19 +887,20 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     for (int l = d.lc; l < d.nlev - 1; ++l) {
         const Grid3 g = d.g[l], gc = d.g[l + 1];
         const int n3 = (int)g.cells();
-        T* b = sm + offb[l];
-        T* x = sm + offx[l];
+        SM* b = sm + offb[l];
+        SM* x = sm + offx[l];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
-            x[f] = om * b[f] * cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f, kh2);
+            cz_st<T>(x, f, om * cz_ld<T>(b, f) *
+                                cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f, kh2));
         }
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
-            tmp[f] = b[f] - cz_Ax<T>(d, l, x, g, i, j, k, kh2);
+            cz_st<T>(tmp, f, cz_ld<T>(b, f) - cz_Ax<T>(d, l, x, g, i, j, k, kh2));
         }
         __syncthreads();
-        T* bc = sm + offb[l + 1];
+        SM* bc = sm + offb[l + 1];
         const int nc3 = (int)gc.cells();
         for (int C = threadIdx.x; C < nc3; C += blockDim.x) {
             const int I = C % gc.nx, J = (C / gc.nx) % gc.ny, K = C / (gc.nx * gc.ny);
@@ -887,27 +922,27 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
                         const int fi = fi0 + a3;
                         const T w = (T)wxs[a3] * wy;
                         if (w == T(0)) continue;
-                        acc += w * tmp[fi + g.nx * (fj + g.ny * fk)];
+                        acc += w * cz_ld<T>(tmp, fi + g.nx * (fj + g.ny * fk));
                     }
                 }
             }
-            bc[C] = acc;
+            cz_st<T>(bc, C, acc);
         }
         __syncthreads();
     }
     // bottom: one cell, exact
     {
         const int l = d.nlev - 1;
-        if (threadIdx.x == 0) sm[offx[l]] = sm[offb[l]] * cz_invDf<T>(d, l, 0, 0, kh2);
+        if (threadIdx.x == 0) cz_st<T>(sm, offx[l], cz_ld<T>(sm, offb[l]) * cz_invDf<T>(d, l, 0, 0, kh2));
         __syncthreads();
     }
     // up
     for (int l = d.nlev - 2; l >= d.lc; --l) {
         const Grid3 g = d.g[l], gc = d.g[l + 1];
         const int n3 = (int)g.cells();
-        const T* b = sm + offb[l];
-        T* x = sm + offx[l];
-        const T* e = sm + offx[l + 1];
+        const SM* b = sm + offb[l];
+        SM* x = sm + offx[l];
+        const SM* e = sm + offx[l + 1];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
             int px[2], py[2], pz[2];
@@ -919,14 +954,15 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
             for (int c3 = 0; c3 < 2; ++c3)
                 for (int b3 = 0; b3 < 2; ++b3)
                     for (int a3 = 0; a3 < 2; ++a3)
-                        pe += (T)wx[a3] * (T)wy[b3] * (T)wz[c3] * e[px[a3] + gc.nx * (py[b3] + gc.ny * pz[c3])];
-            tmp[f] = x[f] + pe;
+                        pe += (T)wx[a3] * (T)wy[b3] * (T)wz[c3] *
+                              cz_ld<T>(e, px[a3] + gc.nx * (py[b3] + gc.ny * pz[c3]));
+            cz_st<T>(tmp, f, cz_ld<T>(x, f) + pe);
         }
         __syncthreads();
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
             const int i = f % g.nx, j = (f / g.nx) % g.ny, k = f / (g.nx * g.ny);
             const T iD = cz_invDf<T>(d, l, nb_count1(i, g.nx) + nb_count1(j, g.ny) + nb_count1(k, g.nz), f, kh2);
-            x[f] = tmp[f] + om * iD * (b[f] - cz_Ax<T>(d, l, tmp, g, i, j, k, kh2));
+            cz_st<T>(x, f, cz_ld<T>(tmp, f) + om * iD * (cz_ld<T>(b, f) - cz_Ax<T>(d, l, tmp, g, i, j, k, kh2)));
         }
         __syncthreads();
     }
@@ -934,11 +970,11 @@ __global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(CoarseDesc d, cons
     double dacc = 0.0;
     {
         const int n3 = (int)d.g[d.lc].cells();
-        const T* x = sm + offx[d.lc];
-        const T* b = sm + offb[d.lc];
+        const SM* x = sm + offx[d.lc];
         for (int f = threadIdx.x; f < n3; f += blockDim.x) {
-            es[f] = x[f];
-            dacc += (double)(b[f] * x[f]);
+            const T xv = cz_ld<T>(x, f) * scale;
+            es[f] = xv;
+            dacc += (double)(bs[f] * xv);
         }
     }
     if (dot_part) {
@@ -1034,8 +1070,11 @@ static int pick_sz(const Grid3& g, int S, int pref) {
 
 template <typename T>
 static cudaError_t mg_set_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kCoarseSmemElemsMax * (int)sizeof(T));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mg_coarse<T, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kCoarseSmemElemsMax * (int)sizeof(__half));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_down<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
     if (e == cudaSuccess)
@@ -1158,12 +1197,18 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         d.lq[l] = plan.lq[l];
         d.D[l] = plan.D[l];
     }
-    const size_t csm = (size_t)coarse_smem_elems(plan) * sizeof(T);
+    // FP16 storage of the one-CTA levels (FP32 path only, when asked for)
+    const bool half = plan.coarse_fp16 && sizeof(T) == 4;
+    const size_t csm = (size_t)coarse_smem_elems(plan) * (half ? sizeof(__half) : sizeof(T));
     const double w = (double)sizeof(T);
     const int64_t s3 = plan.g[plan.lc].cells();
     if (plan.lc == 0) {
         prof_begin(PK_MG_COARSE, st);
-        k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, b, b_stride, y, y_stride, dot_part, active, act_stride);
+        if (half)
+            k_mg_coarse<T, __half><<<S, kCoarseThreads, csm, st>>>(d, b, b_stride, y, y_stride, dot_part, active,
+                                                                   act_stride);
+        else
+            k_mg_coarse<T, T><<<S, kCoarseThreads, csm, st>>>(d, b, b_stride, y, y_stride, dot_part, active, act_stride);
         prof_end(st, prof_cols * 2.0 * (double)s3 * w);
         return 1;
     }
@@ -1194,9 +1239,14 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
     }
     {
         prof_begin(PK_MG_COARSE, st);
-        k_mg_coarse<T><<<S, kCoarseThreads, csm, st>>>(d, static_cast<const T*>(plan.b[plan.lc]), s3,
-                                                       static_cast<T*>(plan.e[plan.lc]), s3, nullptr, active,
-                                                       act_stride);
+        if (half)
+            k_mg_coarse<T, __half><<<S, kCoarseThreads, csm, st>>>(d, static_cast<const T*>(plan.b[plan.lc]), s3,
+                                                                   static_cast<T*>(plan.e[plan.lc]), s3, nullptr, active,
+                                                                   act_stride);
+        else
+            k_mg_coarse<T, T><<<S, kCoarseThreads, csm, st>>>(d, static_cast<const T*>(plan.b[plan.lc]), s3,
+                                                              static_cast<T*>(plan.e[plan.lc]), s3, nullptr, active,
+                                                              act_stride);
         prof_end(st, prof_cols * 2.0 * (double)s3 * w);
     }
     int nblk0 = 1;

@@ -165,6 +165,8 @@ extern "C" spde_status spde_precond_noalloc(int n, double h, double kappa, int n
     MGPlan plan;
     mg_plan_init(plan, n, kh2, o.schur_c, o.omega);
     plan.fault = fault;
+    plan.sz_pref = o.sweep_planes;
+    plan.coarse_fp16 = o.coarse_fp16 != 0;
     int nb;
     if (prec == SPDE_PREC_FP64) {
         mg_plan_bind<double>(plan, nsamples, static_cast<double*>(scratch));

@@ -419,6 +419,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.fault = ws.fault;
     plan.sz_pref = o.sweep_planes;
+    plan.coarse_fp16 = o.coarse_fp16 != 0;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     if (ck) {
@@ -531,6 +532,7 @@ spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Work
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.fault = ws.fault;
     plan.sz_pref = o.sweep_planes;
+    plan.coarse_fp16 = o.coarse_fp16 != 0;
     plan.prof_cols = (double)S;
     const int act_stride = (int)(sizeof(CgCol) / sizeof(int));
     const int* act = &ws.cg[0].active;
@@ -786,6 +788,7 @@ spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Wor
     mg_plan_bind<T>(plan, S, static_cast<T*>(ws.mg));
     plan.fault = ws.fault;
     plan.sz_pref = o.sweep_planes;
+    plan.coarse_fp16 = o.coarse_fp16 != 0;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
@@ -1598,6 +1601,7 @@ spde_status spde_opts_init(spde_opts* o) {
     o->serve_max_batch = 64;
     o->solver = SPDE_SOLVER_MINRES;
     o->sweep_planes = 0;
+    o->coarse_fp16 = 0;
     return SPDE_OK;
 }
 
@@ -2418,6 +2422,8 @@ spde_status spde_precond_box(const int n[3], double h, double kappa, int nsample
     MGPlan plan;
     mg_plan_init(plan, gr, kh2, o.schur_c, o.omega);
     plan.fault = g_pc_fault;
+    plan.sz_pref = o.sweep_planes;
+    plan.coarse_fp16 = o.coarse_fp16 != 0;
     if (prec == SPDE_PREC_FP64) {
         mg_plan_bind<double>(plan, nsamples, static_cast<double*>(g_pc.mg));
         const double* rr = static_cast<const double*>(r);
