@@ -505,9 +505,12 @@ def run_ours(args):
     if args.batch:
         W["batch"] = args.batch
         W["workload"] += "_batch%d" % args.batch
+    if args.grid:  # a smaller grid and its L-prism mesh (profiling runs)
+        W.update(grid_n=args.grid, ntets=None, mesh="L-prism %d^3 cubes x 6 tets, jitter +-h/4 (seed 1)" % (3 * args.grid // 4))
+        W["workload"] = "spde_sampler_%dcube_lprism%d" % (args.grid, 3 * args.grid // 4)
     S, n = W["batch"], W["grid_n"]
     log("mesh")
-    xyz, tets = lprism_mesh(96)
+    xyz, tets = lprism_cached(3 * n // 4)
     log("attach")
     smp = pkg.Sampler(pkg.SPDE_PREC_MIXED, tol=W["tol"], device=local)
     smp.add_level(0, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
@@ -912,6 +915,7 @@ def main(argv=None):
     ap.add_argument("--plain-samples", type=int, default=8)
     ap.add_argument("--batch", type=int, default=0, help="override the 64-sample batch (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="headline loop only (profiling runs)")
+    ap.add_argument("--grid", type=int, default=0, help="another grid n^3 with an L-prism of (3n/4)^3 cubes (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=200, help="requests per rate of the serving sweep")
     ap.add_argument("--serve-sweep", action="store_true", help="only the serving sweep over 10..1000 req/s")
     ap.add_argument("--autotune", action="store_true", help="run the autotuner and write the tuning table")
