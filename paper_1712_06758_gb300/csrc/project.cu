@@ -117,6 +117,73 @@ __global__ void __launch_bounds__(256) k_project_rows(int64_t ntets, int S, cons
     }
 }
 
+// S a multiple of 4: a half-warp per tet, a float4 of samples per lane (16 lanes
+// cover a 64-sample chunk of a thetaT row), so one warp instruction gathers the
+// rows of two tets.  Each half loads up to 16 of its row's (pi, col) pairs at
+// once and hands them round by width-16 shuffles; the sum runs over the row in
+// CSR order, as in the other projection kernels.
+template <typename O>
+__global__ void __launch_bounds__(256) k_project_quad(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col, const float* __restrict__ pi,
+                                                      const float* __restrict__ thetaT, int kind, O* __restrict__ out) {
+    __shared__ float tile[kProjChunk][kProjTets + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4, hl = lane & 15;
+    const int64_t t0 = (int64_t)blockIdx.x * kProjTets;
+    const int S4 = S >> 2;
+    const float4* T4 = reinterpret_cast<const float4*>(thetaT);
+    for (int s0 = 0; s0 < S; s0 += kProjChunk) {
+        const int q = (s0 >> 2) + hl;  // this lane's float4 of the row
+        const bool on = q < S4;
+        for (int rr = 0; rr < 2; ++rr) {
+            const int r = warp * 4 + rr * 2 + half;
+            const int64_t t = t0 + r;
+            int64_t a = 0, b = 0;
+            if (t < ntets) {
+                a = rowptr[t];
+                b = rowptr[t + 1];
+            }
+            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int64_t base = a;; base += 16) {
+                const int64_t left = b - base;
+                const int mh = left <= 0 ? 0 : (left < 16 ? (int)left : 16);
+                const int mo = __shfl_xor_sync(0xffffffffu, mh, 16);
+                if (mh == 0 && mo == 0) break;  // both rows done (warp-uniform)
+                float wl = 0.0f;
+                int cl = 0;
+                if (hl < mh) {
+                    wl = pi[base + hl];
+                    cl = col[base + hl];
+                }
+                const int mm = mh > mo ? mh : mo;
+#pragma unroll 4
+                for (int k = 0; k < mm; ++k) {
+                    const float w = __shfl_sync(0xffffffffu, wl, k, 16);
+                    const int c = __shfl_sync(0xffffffffu, cl, k, 16);
+                    if (k < mh && on) {
+                        const float4 v = T4[(int64_t)c * S4 + q];
+                        acc.x = fmaf(w, v.x, acc.x);
+                        acc.y = fmaf(w, v.y, acc.y);
+                        acc.z = fmaf(w, v.z, acc.z);
+                        acc.w = fmaf(w, v.w, acc.w);
+                    }
+                }
+            }
+            tile[4 * hl][r] = acc.x;
+            tile[4 * hl + 1][r] = acc.y;
+            tile[4 * hl + 2][r] = acc.z;
+            tile[4 * hl + 3][r] = acc.w;
+        }
+        __syncthreads();
+        for (int qq = warp; qq < kProjChunk; qq += 8) {
+            const int ss = s0 + qq;
+            const int64_t t = t0 + lane;
+            if (ss < S && t < ntets) out[(int64_t)ss * ntets + t] = out_map<O>(tile[qq][lane], kind);
+        }
+        __syncthreads();
+    }
+}
+
 // thread per tet, loop over the few samples
 template <typename O>
 __global__ void __launch_bounds__(256) k_project_thread(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
@@ -136,8 +203,11 @@ cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const in
                            const float* thetaT, int kind, int out64, void* out, cudaStream_t st) {
     if (S >= 8) {
         const unsigned nb = (unsigned)((ntets + kProjTets - 1) / kProjTets);
-        // float2 gathers need even rows of thetaT (S even)
-        if (S % 2 == 0) {
+        // float4 / float2 gathers need rows of thetaT on 16 / 8 bytes (S a multiple of 4 / 2)
+        if (S % 4 == 0) {
+            if (out64) k_project_quad<double><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
+            else k_project_quad<float><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+        } else if (S % 2 == 0) {
             if (out64) k_project_rows<double, 2><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
             else k_project_rows<float, 2><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
         } else {

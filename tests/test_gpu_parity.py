@@ -270,7 +270,7 @@ def test_mesh_orientation_and_rejections():
 
 
 # ----------------------------------------------------------- projection (K7)
-@pytest.mark.parametrize("ns", [1, 3, 8, 40])
+@pytest.mark.parametrize("ns", [1, 3, 8, 9, 10, 40, 64])
 @pytest.mark.parametrize("kind", [pkg.SPDE_OUT_GAUSSIAN, pkg.SPDE_OUT_LOGNORMAL,
                                   pkg.SPDE_OUT_LOGNORMAL | pkg.SPDE_OUT_F64])
 def test_project_matches_oracle(ns, kind):
