@@ -68,3 +68,20 @@ def test_bench_dct_leg_matches_oracle(n):
     x = torch.tensor(xi[0].reshape(n, n, n))
     for d in range(3):
         assert torch.allclose(bench.idct_ortho(bench.dct_ortho(x, d), d), x, atol=1e-13)
+
+
+def test_reference_arm_reports_the_time_it_spent(capsys):
+    """The reference arm times whole oracle samples of the headline workload; its ms_per_step must be
+    wall time it actually spent (steps x ms_per_step fits in the call's own duration)."""
+    import json
+    import time
+    args = type("A", (), {"steps": 2, "warmup": 1, "gpus": 1})()
+    t0 = time.perf_counter()
+    bench.run_reference(args)
+    wall = time.perf_counter() - t0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "samples/s"
+    assert line["steps"] * line["ms_per_step"] / 1000.0 <= wall
+    assert abs(line["value"] - 1000.0 / line["ms_per_step"]) <= 1e-9 * line["value"]
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["config"]["grid_n"] == 128 and line["config"]["batch"] == 64
