@@ -120,6 +120,12 @@ typedef struct {
     int coarse_fp16;            /* 1: the V-cycle levels held by the one-CTA coarse kernel (at most 4096
                                    cells, 16^3 on a cube) are stored in FP16, each column scaled by its
                                    largest value, arithmetic in FP32 (FP32 path only); 0 (default): FP32 */
+    int sweep_rows;             /* 1 (default): the FP32 V-cycle sweeps of levels 32, 64 or 128 cells
+                                   wide (constant kappa, or one kappa per column) run on whole-row
+                                   tiles; every cell takes the same arithmetic in the same order as
+                                   on the 32 x 16 tiles, so the V-cycle gives the same bits (only the
+                                   per-CTA partial sums of b.y that MINRES reads are grouped
+                                   differently).  0: the 32 x 16 tiles on every level */
 } spde_opts;
 
 typedef struct {

@@ -30,7 +30,7 @@ class spde_opts(ctypes.Structure):
                 ("schur_c", ctypes.c_double), ("flux_diag", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("device", ctypes.c_int), ("use_graphs", ctypes.c_int), ("serve_budget_bytes", ctypes.c_int64),
                 ("serve_max_batch", ctypes.c_int), ("solver", ctypes.c_int), ("sweep_planes", ctypes.c_int),
-                ("coarse_fp16", ctypes.c_int)]
+                ("coarse_fp16", ctypes.c_int), ("sweep_rows", ctypes.c_int)]
 
 
 class spde_stats(ctypes.Structure):

@@ -138,6 +138,9 @@ struct MGPlan {
     int sz_pref = 0;
     // FP16 storage of the levels the one-CTA coarse kernel holds (FP32 path)
     bool coarse_fp16 = false;
+    // FP32 sweeps of levels 32, 64 or 128 cells wide (constant kappa or one per column) on
+    // whole-row tiles (k_mg_down_rows / k_mg_up_rows); 0: the 32 x 16 tiles everywhere
+    bool sweep_rows = true;
     // one kappa per column (serving lanes): kh2col [S] (kappa h)^2 of level 0 (FP64), and
     // per tiled level l a table qtab[l] [S][21] (element type of the plan) of the
     // kappa-dependent sweep coefficients (mg_coef_row); null: plan.kh2 for every column

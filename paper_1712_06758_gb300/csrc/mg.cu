@@ -98,6 +98,26 @@ __device__ __forceinline__ V2<T> ld2(const T* p) {
     return r;
 }
 
+// Sums of products with the rounding spelled out (which product is fused is otherwise the
+// compiler's choice), so that sweeps that tile the grid differently give the same bits.
+template <typename T>
+__device__ __forceinline__ T mad2(T a, T b, T c, T d) {  // a b + c d
+    return fma(a, b, c * d);
+}
+template <typename T>
+__device__ __forceinline__ T mad4(const T w[4], T a, T b, T c, T d) {  // w0 a + w1 b + w2 c + w3 d
+    return fma(w[3], d, fma(w[2], c, fma(w[1], b, w[0] * a)));
+}
+// prolongation weights 3/4 (own coarse cell) and 1/4 (its neighbour) along one axis, then two
+template <typename T>
+__device__ __forceinline__ T blend2(T own, T nb) {
+    return mad2(T(0.75), own, T(0.25), nb);
+}
+template <typename T>
+__device__ __forceinline__ T blend4(T a, T c, T b, T d) {  // a, b: own z plane; c, d: its neighbour
+    return mad2(T(0.75), blend2(a, c), T(0.25), blend2(b, d));
+}
+
 template <typename T>
 __device__ __forceinline__ void st2(T* p, T a, T b) {
     if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
@@ -437,10 +457,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
                         for (int e = 0; e < 4; ++e) r.v[e] = rc * dd.v[e] * c.v[e] + sc * nbs[e];
                     } else if (!wall) {
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) r.v[e] = rI[e] * c.v[e] + sc * nbs[e];
+                        for (int e = 0; e < 4; ++e) r.v[e] = mad2(rI[e], c.v[e], sc, nbs[e]);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) r.v[e] = s_rcD[kxy_of(r_k, e) + 1] * c.v[e] + sc * nbs[e];
+                        for (int e = 0; e < 4; ++e) r.v[e] = mad2(s_rcD[kxy_of(r_k, e) + 1], c.v[e], sc, nbs[e]);
                     }
                 }
                 st4(Rbase + ((K + 1) & 1) * (PW * RH) + r_off, r);
@@ -454,8 +474,8 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
                     const T* row = Rp + q_off + PW * b3;
                     const T a0 = row[0], a5 = row[5];
                     const V4<T> v = ld4(row + 1);
-                    const T p0 = wa[0] * a0 + wa[1] * v.v[0] + wa[2] * v.v[1] + wa[3] * v.v[2];
-                    const T p1 = wb[0] * v.v[1] + wb[1] * v.v[2] + wb[2] * v.v[3] + wb[3] * a5;
+                    const T p0 = mad4(wa, a0, v.v[0], v.v[1], v.v[2]);
+                    const T p1 = mad4(wb, v.v[1], v.v[2], v.v[3], a5);
                     acc0 += wy[b3] * p0;
                     acc1 += wy[b3] * p1;
                 }
@@ -549,7 +569,6 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     const T* es = ec + (int64_t)col * ec_stride;
     T* ys = y + (int64_t)col * y_stride;
     const T om1 = T(1) - q.omega;
-    const T w0 = T(0.75), w1 = T(0.25);
     const int nplanes = SZ + 2;  // b planes fz0 - 1 .. fz0 + SZ per tile
     T dacc = T(0);  // per-thread partial of b.y in the element type; FP64 across warps
     __syncthreads();
@@ -635,9 +654,8 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                 T cy[4];
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
-                    cy[p] = w0 * (w0 * ar[p] + w1 * cr[p]) + w1 * (w0 * br[p] + w1 * dr[p]);
-                const T pe[4] = {w0 * cy[1] + w1 * cy[0], w0 * cy[1] + w1 * cy[2], w0 * cy[2] + w1 * cy[1],
-                                 w0 * cy[2] + w1 * cy[3]};
+                    cy[p] = blend4(ar[p], cr[p], br[p], dr[p]);
+                const T pe[4] = {blend2(cy[1], cy[0]), blend2(cy[1], cy[2]), blend2(cy[2], cy[1]), blend2(cy[2], cy[3])};
                 const V4<T> bb = ld4(Bg + x_off);
                 if constexpr (PC) {  // per-cell diagonal (cell-wise kappa)
                     const V4<T> dd = ld4(Dg + x_g + plane * g);
@@ -692,12 +710,12 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
                     for (int e = 0; e < 4; ++e) out.v[e] = om1 * c.v[e] + q.omega * (bb.v[e] + sc * nbs[e]) / dd.v[e];
                 } else if (!wall) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) out.v[e] = om1 * c.v[e] + oI[e] * bb.v[e] + sI[e] * nbs[e];
+                    for (int e = 0; e < 4; ++e) out.v[e] = fma(sI[e], nbs[e], fma(oI[e], bb.v[e], om1 * c.v[e]));
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int kw = kxy_of(o_k, e) + 1;
-                        out.v[e] = om1 * c.v[e] + s_oi[kw] * bb.v[e] + s_ois[kw] * nbs[e];
+                        out.v[e] = fma(s_ois[kw], nbs[e], fma(s_oi[kw], bb.v[e], om1 * c.v[e]));
                     }
                 }
 #pragma unroll
@@ -731,6 +749,445 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
     }
     if (dot_part) {
         const double tsum = block_sum_t<kTileThreads, T>(dacc, red);
+        if (tid == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Row-tile sweeps (FP32, grids whose x extent is 32, 64 or 128 cells).  A CTA
+// owns whole x rows: a tile is nx x TY cells in (x, y), marched along z.  A
+// thread owns one 4-cell x segment of one row for the whole march, so
+//   - the x neighbours of a segment come from the adjacent lanes by shuffles
+//     (a row is Q = nx / 4 consecutive lanes; the row ends are the walls),
+//   - its z neighbours (planes f - 1, f, f + 1) stay in a register ring,
+//   - only the y neighbours (other rows, other warps) go through shared memory,
+// and there is no halo in x.  The down sweep restricts in x inside the warp,
+// in y through one shared-memory pass and in z in registers.
+// ---------------------------------------------------------------------------
+template <int NX, int TY_>
+struct RowShape {
+    static constexpr int TY = TY_;       // rows per tile
+    static constexpr int Q = NX / 4;     // segments (lanes) per row
+    static constexpr int RPW = 32 / Q;   // rows per warp
+    static constexpr int R = TY + 4;     // rows of a plane slot: y from fy0 - 2
+    static constexpr int NW = R / RPW;   // warps
+    static constexpr int NT = 32 * NW;   // threads
+    static constexpr int PLANE = NX * R; // floats per plane slot
+    static constexpr int RXR = TY + 2;   // residual rows (y from fy0 - 1)
+    static constexpr int CXN = NX / 2;   // coarse x per row
+    static constexpr int NITEMS = (TY / 2) * (NX / 4);  // y-restriction items: coarse row x coarse x pair
+};
+
+template <int NX, int TY>
+__host__ __device__ constexpr int down_rows_smem_bytes() {
+    using Sh = RowShape<NX, TY>;
+    return 128 + (int)sizeof(float) * ((kRing + 4) * Sh::PLANE + 2 * Sh::RXR * Sh::CXN);
+}
+
+// TMA ring of plane slots of `elems` floats each (copies of `bytes`), producer = thread 0
+template <int NS>
+__device__ __forceinline__ PlaneRing<float, NS> ring_setup_rows(unsigned char* raw, int elems, uint32_t bytes,
+                                                                uint64_t* bars, volatile int* abort, int* fault,
+                                                                int tid) {
+    PlaneRing<float, NS> r;
+    r.fault = fault;
+    const uint32_t a = smem_addr(raw);
+    r.slots = reinterpret_cast<float*>(raw + ((128 - (a & 127)) & 127));
+    r.slot = elems;
+    r.bars = bars;
+    r.abort = abort;
+    r.bytes = bytes;
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(bars + i);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    return r;
+}
+
+template <int NX, int TY>
+__global__ void __launch_bounds__(RowShape<NX, TY>::NT, RowShape<NX, TY>::NT <= 384 ? 2 : 1)
+    k_mg_down_rows(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<float> q,
+                   float* __restrict__ bc, int64_t bc_stride, const int* __restrict__ active, int act_stride,
+                   int* __restrict__ fault, const float* __restrict__ qtab) {
+    using Sh = RowShape<NX, TY>;
+    constexpr int Q = Sh::Q, RPW = Sh::RPW, R = Sh::R, PLANE = Sh::PLANE, CXN = Sh::CXN;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ float s_oi[8], s_rcD[8];
+    __shared__ uint64_t s_bar[kRing];
+    __shared__ int s_abort;
+    const int col = blockIdx.y;
+    if (active && !active[(int64_t)col * act_stride]) return;
+    if (*(volatile int*)fault) return;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int qq = lane % Q;                  // segment: fine x 4 qq .. 4 qq + 3
+    const int ly = warp * RPW + lane / Q;     // slot row: fine y = fy0 - 2 + ly
+    PlaneRing<float, kRing> ring =
+        ring_setup_rows<kRing>(smem_raw, PLANE, (uint32_t)(PLANE * sizeof(float)), s_bar, &s_abort, fault, tid);
+    float* const Xs = ring.slots + kRing * PLANE;  // 4 x0 plane slots
+    float* const RX = Xs + 4 * PLANE;              // 2 buffers of x-restricted residual rows
+    if (qtab) {
+        if (tid < 7) {
+            s_oi[tid] = qtab[(int64_t)col * 21 + tid];
+            s_rcD[tid] = qtab[(int64_t)col * 21 + 14 + tid];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if (tid == k) {
+                s_oi[k] = q.oi[k];
+                s_rcD[k] = q.rcD[k];
+            }
+    }
+    const int nfy = gf.ny, nfz = gf.nz;
+    const int ncx = NX >> 1, ncy = nfy >> 1, ncz = nfz >> 1;
+    const int nty = nfy / TY, ntz = nfz / SZ;
+    const int ntiles = nty * ntz;
+    float* bcs = bc + (int64_t)col * bc_stride;
+    const float sc = q.s * q.c;
+    const int nplanes = SZ + 4;  // fine planes fz0 - 2 .. fz0 + SZ + 1 per tile
+    // x-restriction weights of this segment's two coarse x (taps fine 2I - 1 .. 2I + 2)
+    float wa[4], wb[4];
+#pragma unroll
+    for (int a3 = 0; a3 < 4; ++a3) {
+        wa[a3] = restrict_w(a3, 2 * qq, ncx);
+        wb[a3] = restrict_w(a3, 2 * qq + 1, ncx);
+    }
+    // y-restriction item of this thread: coarse row J, coarse x pair P
+    const bool has_item = tid < Sh::NITEMS;
+    const int iJ = tid / (NX / 4), iP = tid % (NX / 4);
+    __syncthreads();
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tY = tile % nty, tZ = tile / nty;
+        const int fy0 = tY * TY, fz0 = tZ * SZ;
+        const int cy0 = fy0 >> 1;
+        int issued = 0;  // producer: planes of this tile requested so far
+        auto issue_upto = [&](int jmax) {
+            for (; issued < nplanes && issued <= jmax; ++issued)
+                if (!ring.issue(issued & (kRing - 1), &bmap, 0, fy0 - 2, fz0 - 2 + issued, col)) break;
+        };
+        if (tid == 0) issue_upto(kRing - 1);
+        const int gy = fy0 - 2 + ly;
+        const bool yin = in_range(gy, nfy);
+        const bool has_r = ly >= 1 && ly <= R - 2;  // residual rows: y from fy0 - 1 to fy0 + TY
+        int kxy = 0;  // x-y neighbour counts of the segment's cells, 3 bits each
+        float cI[4], rI[4];  // x0 and residual factors of the segment's cells on interior planes
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = yin ? nb_count1(gy, nfy) + nb_count1(4 * qq + e, NX) : 0;
+            kxy |= k << (3 * e);
+            cI[e] = s_oi[k + 2];
+            rI[e] = s_rcD[k + 2];
+        }
+        float wy[4];
+#pragma unroll
+        for (int a3 = 0; a3 < 4; ++a3) wy[a3] = restrict_w(a3, cy0 + iJ, ncy);
+        V4<float> X0[4];  // x0 of this segment, tile plane j in X0[j & 3]
+        V2<float> Rv[4];  // this item's x-y restricted residual, fine plane fr in Rv[fr mod 4]
+        // x0 plane f = fz0 - 2 + j from tile plane j (TMA slot j mod 4): registers and x0 slot j mod 4
+        auto commit = [&](auto js, int f) {
+            constexpr int JS = decltype(js)::value;
+            const float* raw = ring.take(JS);
+            const V4<float> bv = ld4(raw + ly * NX + 4 * qq);
+            V4<float> v;
+            if (f != 0 && f != nfz - 1) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * cI[e];
+            } else {  // the z walls (b = 0 off the box, any factor will do)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v.v[e] = bv.v[e] * s_oi[kxy_of(kxy, e) + 1];
+            }
+            X0[JS] = v;
+            st4(Xs + JS * PLANE + ly * NX + 4 * qq, v);
+        };
+        // step t: commit f + 2 (tile plane t + 3), residual and x-restriction of f (plane t + 1),
+        // y- and z-restriction of f - 1 (from the previous step's rows)
+        auto step = [&](auto kc, int t) {
+            constexpr int K = decltype(kc)::value;  // t mod 4
+            const int f = fz0 - 1 + t;
+            if (t <= SZ) commit(IC<(K + 3) & 3>{}, f + 2);
+            if (t <= SZ + 1) {
+                const V4<float> c = X0[(K + 1) & 3], m = X0[K & 3], p = X0[(K + 2) & 3];
+                const float xl0 = __shfl_up_sync(0xffffffffu, c.v[3], 1, Q);
+                const float xr0 = __shfl_down_sync(0xffffffffu, c.v[0], 1, Q);
+                const float xl = qq > 0 ? xl0 : 0.0f, xr = qq < Q - 1 ? xr0 : 0.0f;
+                V4<float> r = zero4<float>();
+                if (has_r && yin && in_range(f, nfz)) {
+                    const float* Xf = Xs + ((K + 1) & 3) * PLANE + 4 * qq;
+                    const V4<float> u = ld4(Xf + (ly - 1) * NX), d = ld4(Xf + (ly + 1) * NX);
+                    float nbs[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float left = (e == 0) ? xl : c.v[e - 1];
+                        const float right = (e == 3) ? xr : c.v[e + 1];
+                        nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
+                    }
+                    if (f != 0 && f != nfz - 1) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) r.v[e] = mad2(rI[e], c.v[e], sc, nbs[e]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) r.v[e] = mad2(s_rcD[kxy_of(kxy, e) + 1], c.v[e], sc, nbs[e]);
+                    }
+                }
+                const float rl0 = __shfl_up_sync(0xffffffffu, r.v[3], 1, Q);
+                const float rr0 = __shfl_down_sync(0xffffffffu, r.v[0], 1, Q);
+                const float rl = qq > 0 ? rl0 : 0.0f, rr = qq < Q - 1 ? rr0 : 0.0f;
+                if (has_r) {
+                    const float x0v = mad4(wa, rl, r.v[0], r.v[1], r.v[2]);
+                    const float x1v = mad4(wb, r.v[1], r.v[2], r.v[3], rr);
+                    st2(RX + (K & 1) * (Sh::RXR * CXN) + (ly - 1) * CXN + 2 * qq, x0v, x1v);
+                }
+            }
+            if (t >= 1 && has_item) {
+                // fine plane fr = f - 1: rows 2J - 1 .. 2J + 2 of the previous step's buffer;
+                // the x-y restricted value of plane fr goes to register slot fr mod 4
+                const float* Rb = RX + ((K + 1) & 1) * (Sh::RXR * CXN) + 2 * iP;
+                float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+                for (int a3 = 0; a3 < 4; ++a3) {
+                    const V2<float> rv = ld2(Rb + (2 * iJ + a3) * CXN);
+                    v0 += wy[a3] * rv.v[0];
+                    v1 += wy[a3] * rv.v[1];
+                }
+                Rv[(K + 2) & 3].v[0] = v0;
+                Rv[(K + 2) & 3].v[1] = v1;
+                if ((K & 1) == 0 && t >= 4) {
+                    // coarse plane Z = fr/2 - 1 from the x-y restricted planes 2Z-1 .. 2Z+2 = fr-3 .. fr
+                    const int Z = (f - 3) >> 1;
+                    const float w3 = restrict_w(3, Z, ncz);
+                    float z0 = w3 * v0, z1 = w3 * v1;
+#pragma unroll
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        const float w = restrict_w(c3, Z, ncz);
+                        z0 += w * Rv[(K + 3 + c3) & 3].v[0];
+                        z1 += w * Rv[(K + 3 + c3) & 3].v[1];
+                    }
+                    st2(bcs + 2 * iP + (int64_t)ncx * ((cy0 + iJ) + (int64_t)ncy * Z), z0, z1);
+                }
+            }
+            __syncthreads();
+            // tile planes up to t + 3 are consumed: their slots are free
+            if (tid == 0) issue_upto(t + 3 + kRing);
+        };
+        commit(IC<0>{}, fz0 - 2);
+        commit(IC<1>{}, fz0 - 1);
+        commit(IC<2>{}, fz0);
+        __syncthreads();
+        if (tid == 0) issue_upto(2 + kRing);  // tile planes 0 .. 2 are consumed
+        const int nsteps = SZ + 3;  // f = fz0 - 1 .. fz0 + SZ + 1
+        for (int t0 = 0; t0 < nsteps; t0 += 4) {
+            step(IC<0>{}, t0);
+            if (t0 + 1 < nsteps) step(IC<1>{}, t0 + 1);
+            if (t0 + 2 < nsteps) step(IC<2>{}, t0 + 2);
+            if (t0 + 3 < nsteps) step(IC<3>{}, t0 + 3);
+        }
+        if (tid == 0 && s_abort) ring.drain();
+    }
+}
+
+
+// Up sweep on row tiles: the same x and y as k_mg_up, cell by cell.  Thread
+// rows as in the down sweep (fine y from fy0 - 2); rows fy0 - 1 .. fy0 + TY
+// form x, rows fy0 .. fy0 + TY - 1 form y.  The prolongation of a segment
+// needs the coarse x 2 qq - 1 .. 2 qq + 2: the thread blends its own pair
+// (2 qq, 2 qq + 1) in y and z and takes the outer two from its row neighbours
+// by shuffles (clamped at the x walls, the reflection of P).  Each thread
+// stages one element of every coarse plane (coarse rows cy0 - 1 .. cy0 + TY/2,
+// clamped, all coarse x): there are exactly as many as threads.
+template <int NX, int TY>
+__host__ __device__ constexpr int up_rows_smem_bytes() {
+    using Sh = RowShape<NX, TY>;
+    return 128 + (int)sizeof(float) * (2 * kRing * Sh::PLANE + 4 * Sh::NT);
+}
+
+template <int NX, int TY>
+__global__ void __launch_bounds__(RowShape<NX, TY>::NT, RowShape<NX, TY>::NT <= 384 ? 2 : 1)
+    k_mg_up_rows(const __grid_constant__ CUtensorMap bmap, Grid3 gf, int SZ, LevelCoef<float> q,
+                 const float* __restrict__ ec, int64_t ec_stride, float* __restrict__ y, int64_t y_stride,
+                 double* __restrict__ dot_part, const int* __restrict__ active, int act_stride,
+                 int* __restrict__ fault, const float* __restrict__ qtab) {
+    using Sh = RowShape<NX, TY>;
+    constexpr int Q = Sh::Q, RPW = Sh::RPW, R = Sh::R, PLANE = Sh::PLANE, CXN = Sh::CXN, NT = Sh::NT;
+    static_assert((TY / 2 + 2) * CXN == NT, "one coarse element per thread");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double red[NT / 32];
+    __shared__ float s_oi[8], s_ois[8];
+    __shared__ uint64_t s_bar[kRing];
+    __shared__ int s_abort;
+    const int col = blockIdx.y;
+    if (active && !active[(int64_t)col * act_stride]) return;
+    if (*(volatile int*)fault) return;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int qq = lane % Q;
+    const int ly = warp * RPW + lane / Q;  // fine y = fy0 - 2 + ly
+    PlaneRing<float, kRing> ring =
+        ring_setup_rows<kRing>(smem_raw, PLANE, (uint32_t)(PLANE * sizeof(float)), s_bar, &s_abort, fault, tid);
+    float* const Xs = ring.slots + kRing * PLANE;  // 4 x plane slots
+    float* const Cbase = Xs + 4 * PLANE;           // 4 coarse plane slots, NT elements each
+    auto Cs = [&](int Z) { return Cbase + ((Z + 4) & 3) * NT; };  // Z >= -4
+    if (qtab) {
+        if (tid < 7) {
+            s_oi[tid] = qtab[(int64_t)col * 21 + tid];
+            s_ois[tid] = qtab[(int64_t)col * 21 + 7 + tid];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if (tid == k) {
+                s_oi[k] = q.oi[k];
+                s_ois[k] = q.ois[k];
+            }
+    }
+    const int nfy = gf.ny, nfz = gf.nz;
+    const int ncx = NX >> 1, ncy = nfy >> 1, ncz = nfz >> 1;
+    const int nty = nfy / TY, ntz = nfz / SZ;
+    const int ntiles = nty * ntz;
+    const int64_t plane = (int64_t)NX * nfy, cplane = (int64_t)ncx * ncy;
+    const float* es = ec + (int64_t)col * ec_stride;
+    float* ys = y + (int64_t)col * y_stride;
+    const float om1 = 1.0f - q.omega;
+    const int nplanes = SZ + 2;  // b planes fz0 - 1 .. fz0 + SZ per tile
+    float dacc = 0.0f;
+    __syncthreads();
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tY = tile % nty, tZ = tile / nty;
+        const int fy0 = tY * TY, fz0 = tZ * SZ;
+        const int cy0 = fy0 >> 1, cz0 = fz0 >> 1;
+        int issued = 0;
+        auto issue_upto = [&](int jmax) {
+            for (; issued < nplanes && issued <= jmax; ++issued)
+                if (!ring.issue(issued & (kRing - 1), &bmap, 0, fy0 - 2, fz0 - 1 + issued, col)) break;
+        };
+        if (tid == 0) issue_upto(kRing - 1);
+        // this thread's coarse element: coarse row cy0 - 1 + tid / CXN (clamped), coarse x tid % CXN
+        const int c_src = (tid % CXN) + ncx * min(max(cy0 - 1 + tid / CXN, 0), ncy - 1);
+        auto fetch_c = [&](int Z) -> float { return es[c_src + cplane * min(max(Z, 0), ncz - 1)]; };
+        const int gy = fy0 - 2 + ly;
+        const bool yin = in_range(gy, nfy);
+        const bool x_row = yin && ly >= 1 && ly <= R - 2;   // forms x
+        const bool o_row = ly >= 2 && ly <= R - 3;          // forms y (always inside the grid)
+        // coarse rows of the prolongation: gy >> 1 and its other neighbour, in slot rows from cy0 - 1
+        const int p_r0 = x_row ? ((gy >> 1) - (cy0 - 1)) * CXN + 2 * qq : 0;
+        const int p_r1 = x_row ? p_r0 + ((gy & 1) ? CXN : -CXN) : 0;
+        int kxy = 0;
+        float xI[4], sI[4];  // interior-plane factors (x and y both take omega D^-1 = oi)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = yin ? nb_count1(gy, nfy) + nb_count1(4 * qq + e, NX) : 0;
+            kxy |= k << (3 * e);
+            xI[e] = s_oi[k + 2];
+            sI[e] = s_ois[k + 2];
+        }
+        V4<float> X[4];  // x of this segment, tile plane j (x(fz0 - 1 + j)) in X[j & 3]
+        // x(g) from b(g) = tile plane j = g - fz0 + 1 and the coarse planes g >> 1 (weight 3/4) and
+        // its z neighbour (Iz - 1 for even g, Iz + 1 for odd g)
+        auto make_x = [&](auto js, int g) {
+            constexpr int JS = decltype(js)::value;
+            const float* Bg = ring.take(JS);
+            const bool act = x_row && in_range(g, nfz);
+            float cyA = 0.0f, cyB = 0.0f;  // y-z blend of coarse x 2 qq and 2 qq + 1
+            if (act) {
+                const int Iz = g >> 1;
+                const float* C0 = Cs(Iz);
+                const float* C1 = Cs((g & 1) ? Iz + 1 : Iz - 1);
+                const V2<float> a = ld2(C0 + p_r0), b = ld2(C0 + p_r1);
+                const V2<float> c = ld2(C1 + p_r0), d = ld2(C1 + p_r1);
+                cyA = blend4(a.v[0], c.v[0], b.v[0], d.v[0]);
+                cyB = blend4(a.v[1], c.v[1], b.v[1], d.v[1]);
+            }
+            const float l0 = __shfl_up_sync(0xffffffffu, cyB, 1, Q);
+            const float r0 = __shfl_down_sync(0xffffffffu, cyA, 1, Q);
+            const float cyL = qq > 0 ? l0 : cyA, cyR = qq < Q - 1 ? r0 : cyB;
+            V4<float> v = zero4<float>();
+            if (act) {
+                const float pe[4] = {blend2(cyA, cyL), blend2(cyA, cyB), blend2(cyB, cyA), blend2(cyB, cyR)};
+                const V4<float> bb = ld4(Bg + ly * NX + 4 * qq);
+                if (g != 0 && g != nfz - 1) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v.v[e] = xI[e] * bb.v[e] + pe[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v.v[e] = s_oi[kxy_of(kxy, e) + 1] * bb.v[e] + pe[e];
+                }
+            }
+            X[JS] = v;
+            st4(Xs + JS * PLANE + ly * NX + 4 * qq, v);
+        };
+        float pc = 0.0f;
+        // step t (g = fz0 + t): x(g + 1) from tile plane t + 2, y(g - 1) from tile plane t
+        auto step = [&](auto kc, int t) {
+            constexpr int K = decltype(kc)::value;  // t mod 4
+            const int g = fz0 + t;
+            const int gn = g + 1;
+            if (gn <= fz0 + SZ) {
+                if ((K & 1) == 1) {  // gn even: coarse plane gn/2 + 1 (slot of gn/2 - 3, no longer read)
+                    Cs((gn >> 1) + 1)[tid] = pc;
+                    if (gn + 2 <= fz0 + SZ) pc = fetch_c((gn >> 1) + 2);
+                }
+                make_x(IC<(K + 2) & 3>{}, gn);
+            }
+            if (t >= 1) {
+                const int f = g - 1;  // x planes f - 1, f, f + 1 and b(f) (tile plane t)
+                const V4<float> c = X[K & 3], m = X[(K + 3) & 3], p = X[(K + 1) & 3];
+                const float xl0 = __shfl_up_sync(0xffffffffu, c.v[3], 1, Q);
+                const float xr0 = __shfl_down_sync(0xffffffffu, c.v[0], 1, Q);
+                const float xl = qq > 0 ? xl0 : 0.0f, xr = qq < Q - 1 ? xr0 : 0.0f;
+                if (o_row) {
+                    const float* Xf = Xs + (K & 3) * PLANE + 4 * qq;
+                    const V4<float> u = ld4(Xf + (ly - 1) * NX), d = ld4(Xf + (ly + 1) * NX);
+                    const V4<float> bb = ld4(ring.at(K & 3) + ly * NX + 4 * qq);
+                    float nbs[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float left = (e == 0) ? xl : c.v[e - 1];
+                        const float right = (e == 3) ? xr : c.v[e + 1];
+                        nbs[e] = (left + right) + (u.v[e] + d.v[e]) + (m.v[e] + p.v[e]);
+                    }
+                    V4<float> out;
+                    if (f != 0 && f != nfz - 1) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) out.v[e] = fma(sI[e], nbs[e], fma(xI[e], bb.v[e], om1 * c.v[e]));
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int kw = kxy_of(kxy, e) + 1;
+                            out.v[e] = fma(s_ois[kw], nbs[e], fma(s_oi[kw], bb.v[e], om1 * c.v[e]));
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dacc += bb.v[e] * out.v[e];
+                    st4(ys + 4 * qq + (int64_t)NX * gy + plane * f, out);
+                }
+            }
+            __syncthreads();
+            // tile planes up to t are consumed: their slots are free
+            if (tid == 0) issue_upto(t + kRing);
+        };
+        // prologue: coarse planes cz0 - 1 .. cz0 + 1, then x(fz0 - 1) and x(fz0)
+        Cs(cz0 - 1)[tid] = fetch_c(cz0 - 1);
+        Cs(cz0)[tid] = fetch_c(cz0);
+        Cs(cz0 + 1)[tid] = fetch_c(cz0 + 1);
+        pc = fetch_c(cz0 + 2);  // stored while x(fz0 + 2) is formed, first used by x(fz0 + 3)
+        __syncthreads();
+        make_x(IC<0>{}, fz0 - 1);
+        make_x(IC<1>{}, fz0);
+        __syncthreads();
+        if (tid == 0) issue_upto(kRing);  // tile plane 0 (b(fz0 - 1)) is consumed
+        const int nsteps = SZ + 1;  // g = fz0 .. fz0 + SZ
+        for (int t0 = 0; t0 < nsteps; t0 += 4) {
+            step(IC<0>{}, t0);
+            if (t0 + 1 < nsteps) step(IC<1>{}, t0 + 1);
+            if (t0 + 2 < nsteps) step(IC<2>{}, t0 + 2);
+            if (t0 + 3 < nsteps) step(IC<3>{}, t0 + 3);
+        }
+        if (tid == 0 && s_abort) ring.drain();
+    }
+    if (dot_part) {
+        const double tsum = block_sum_t<NT, float>(dacc, red);
         if (tid == 0) dot_part[(int64_t)col * kMaxPartials + blockIdx.x] = tsum;
     }
 }
@@ -1068,6 +1525,16 @@ static int pick_sz(const Grid3& g, int S, int pref) {
     return 8;
 }
 
+template <int NX, int TY>
+static cudaError_t rows_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_mg_down_rows<NX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         down_rows_smem_bytes<NX, TY>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mg_up_rows<NX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 up_rows_smem_bytes<NX, TY>());
+    return e;
+}
+
 template <typename T>
 static cudaError_t mg_set_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_mg_coarse<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1079,6 +1546,11 @@ static cudaError_t mg_set_attrs() {
         e = cudaFuncSetAttribute(k_mg_down<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_down<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, down_smem_bytes<T>());
+    if constexpr (sizeof(T) == 4) {
+        if (e == cudaSuccess) e = rows_attrs<128, 16>();
+        if (e == cudaSuccess) e = rows_attrs<64, 16>();
+        if (e == cudaSuccess) e = rows_attrs<32, 32>();
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mg_up<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, up_smem_bytes<T>());
     if (e == cudaSuccess)
@@ -1106,16 +1578,17 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// tensor map of S stacked grids (column stride col_stride elements), box PW x rows x 1 x 1
+// tensor map of S stacked grids (column stride col_stride elements), box boxw x rows x 1 x 1
 template <typename T>
-static bool plane_map(CUtensorMap* m, const T* base, const Grid3& g, int S, int64_t col_stride, int rows) {
+static bool plane_map(CUtensorMap* m, const T* base, const Grid3& g, int S, int64_t col_stride, int rows,
+                      int boxw = PW) {
     const EncodeTiledFn fn = encode_tiled();
     const size_t es = sizeof(T);
     if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || ((col_stride * es) & 15) || ((g.nx * es) & 15))
         return false;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)S};
     const cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)col_stride * es};
-    const cuuint32_t box[4] = {(cuuint32_t)PW, (cuuint32_t)rows, 1, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)boxw, (cuuint32_t)rows, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
               const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1178,6 +1651,91 @@ cudaError_t mg_prepare() {
     return e;
 }
 
+// z extent per row tile: the longest that still gives every SM a few CTAs
+static int pick_sz_rows(const Grid3& g, int ty, int S, int pref) {
+    if ((pref == 8 || pref == 16 || pref == 32) && g.nz % pref == 0) return pref;
+    for (int c = 32; c > 8; c >>= 1)
+        if (g.nz % c == 0 && (int64_t)(g.ny / ty) * (g.nz / c) * S >= 2 * 152) return c;
+    return 8;
+}
+
+// Row-tile down sweep of one level, FP32 with the level's constant diagonal: returns
+// false (nothing launched) when the level's shape does not fit the row tiles.
+template <int NX, int TY>
+static bool down_rows_nx(const MGPlan& plan, int l, int S, const float* in, int64_t in_stride, float* out,
+                         int64_t nc3, const int* active, int act_stride, cudaStream_t st) {
+    using Sh = RowShape<NX, TY>;
+    const Grid3& gf = plan.g[l];
+    if (gf.ny % Sh::TY || gf.nz % 8) return false;
+    const int sz = pick_sz_rows(gf, Sh::TY, S, plan.sz_pref);
+    const int ntiles = (gf.ny / Sh::TY) * (gf.nz / sz);
+    CUtensorMap map;
+    if (!plane_map<float>(&map, in, gf, S, in_stride, Sh::R, NX)) return false;
+    dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
+    k_mg_down_rows<NX, TY><<<grid, Sh::NT, down_rows_smem_bytes<NX, TY>(), st>>>(
+        map, gf, sz, level_coef<float>(plan, l), out, nc3, active, act_stride, plan.fault,
+        static_cast<const float*>(plan.qtab[l]));
+    return true;
+}
+
+// Row-tile up sweep of one level: returns the CTAs per column (the partials of b.y), or 0
+// (nothing launched) when the level's shape does not fit the row tiles.  The tiling depends
+// on the level's shape only, so each column's partial sums do not depend on the batch.
+template <int NX, int TY>
+static int up_rows_nx(const MGPlan& plan, int l, const float* b, int64_t b_stride, const float* ec, int64_t ec_stride,
+                      float* y, int64_t y_stride, double* dot_part, int S, const int* active, int act_stride,
+                      cudaStream_t st) {
+    using Sh = RowShape<NX, TY>;
+    const Grid3& gf = plan.g[l];
+    if (gf.ny % Sh::TY || gf.nz % 8) return 0;
+    const int sz = pick_sz_rows(gf, Sh::TY, 64, plan.sz_pref);
+    const int ntiles = (gf.ny / Sh::TY) * (gf.nz / sz);
+    const int nb = ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol;
+    CUtensorMap map;
+    if (!plane_map<float>(&map, b, gf, S, b_stride, Sh::R, NX)) return 0;
+    k_mg_up_rows<NX, TY><<<dim3(nb, S), Sh::NT, up_rows_smem_bytes<NX, TY>(), st>>>(
+        map, gf, sz, level_coef<float>(plan, l), ec, ec_stride, y, y_stride, dot_part, active, act_stride,
+        plan.fault, static_cast<const float*>(plan.qtab[l]));
+    return nb;
+}
+
+template <typename T>
+static int up_rows(const MGPlan& plan, int l, const T* b, int64_t b_stride, const T* ec, int64_t ec_stride, T* y,
+                   int64_t y_stride, double* dot_part, int S, const int* active, int act_stride, cudaStream_t st) {
+    if constexpr (sizeof(T) != 4) return 0;
+    else {
+        if (!plan.sweep_rows || plan.D[l]) return 0;
+        // rows per tile: 16 (32 on 32-wide levels, where a warp holds four rows); 8-row tiles
+        // (two CTAs per SM) measured slower on every level
+#define SPDE_UP_ROWS(NX, TY) \
+    up_rows_nx<NX, TY>(plan, l, b, b_stride, ec, ec_stride, y, y_stride, dot_part, S, active, act_stride, st)
+        switch (plan.g[l].nx) {
+            case 128: return SPDE_UP_ROWS(128, 16);
+            case 64: return SPDE_UP_ROWS(64, 16);
+            case 32: return SPDE_UP_ROWS(32, 32);
+            default: return 0;
+        }
+#undef SPDE_UP_ROWS
+    }
+}
+
+template <typename T>
+static bool down_rows(const MGPlan& plan, int l, int S, const T* in, int64_t in_stride, T* out, int64_t nc3,
+                      const int* active, int act_stride, cudaStream_t st) {
+    if constexpr (sizeof(T) != 4) return false;
+    else {
+        if (!plan.sweep_rows || plan.D[l]) return false;
+#define SPDE_DOWN_ROWS(NX, TY) down_rows_nx<NX, TY>(plan, l, S, in, in_stride, out, nc3, active, act_stride, st)
+        switch (plan.g[l].nx) {
+            case 128: return SPDE_DOWN_ROWS(128, 16);
+            case 64: return SPDE_DOWN_ROWS(64, 16);
+            case 32: return SPDE_DOWN_ROWS(32, 32);
+            default: return false;
+        }
+#undef SPDE_DOWN_ROWS
+    }
+}
+
 template <typename T>
 int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y, int64_t y_stride, double* dot_part,
                   const int* active, int act_stride, cudaStream_t st) {
@@ -1222,9 +1780,15 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const int ntiles = (gf.nx / SX) * (gf.ny / SY) * (gf.nz / sz);
         dim3 grid(ntiles < kMaxTilesPerCol ? ntiles : kMaxTilesPerCol, S);
         T* out = static_cast<T*>(plan.b[l + 1]);
+        prof_begin(PK_MG_DOWN, st);
+        if (down_rows<T>(plan, l, S, in, in_stride, out, nc3, active, act_stride, st)) {
+            prof_end(st, prof_cols * (1.0 + 0.125) * (double)gf.cells() * w);
+            in = out;
+            in_stride = nc3;
+            continue;
+        }
         CUtensorMap map;
         if (!plane_map<T>(&map, in, gf, S, in_stride, XH)) return -1;
-        prof_begin(PK_MG_DOWN, st);
         const T* Dl = static_cast<const T*>(plan.D[l]);
         const T* qt = static_cast<const T*>(plan.qtab[l]);
         if (Dl)
@@ -1261,9 +1825,16 @@ int launch_vcycle(const MGPlan& plan, int S, const T* b, int64_t b_stride, T* y,
         const int64_t bls = (l == 0) ? b_stride : nf3;
         T* yl = (l == 0) ? y : static_cast<T*>(plan.e[l]);
         const int64_t yls = (l == 0) ? y_stride : nf3;
+        prof_begin(PK_MG_UP, st);
+        const int nbr = up_rows<T>(plan, l, bl, bls, static_cast<const T*>(plan.e[l + 1]), nc3, yl, yls,
+                                   (l == 0) ? dot_part : nullptr, S, active, act_stride, st);
+        if (nbr > 0) {
+            prof_end(st, prof_cols * (2.0 + 0.125) * (double)nf3 * w);
+            if (l == 0) nblk0 = nbr;
+            continue;
+        }
         CUtensorMap map;
         if (!plane_map<T>(&map, bl, gf, S, bls, BH)) return -1;
-        prof_begin(PK_MG_UP, st);
         const T* Dl = static_cast<const T*>(plan.D[l]);
         const T* qt = static_cast<const T*>(plan.qtab[l]);
         if (Dl)

@@ -167,6 +167,7 @@ extern "C" spde_status spde_precond_noalloc(int n, double h, double kappa, int n
     plan.fault = fault;
     plan.sz_pref = o.sweep_planes;
     plan.coarse_fp16 = o.coarse_fp16 != 0;
+    plan.sweep_rows = o.sweep_rows != 0;
     int nb;
     if (prec == SPDE_PREC_FP64) {
         mg_plan_bind<double>(plan, nsamples, static_cast<double*>(scratch));

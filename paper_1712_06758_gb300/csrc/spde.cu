@@ -420,6 +420,7 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
     plan.fault = ws.fault;
     plan.sz_pref = o.sweep_planes;
     plan.coarse_fp16 = o.coarse_fp16 != 0;
+    plan.sweep_rows = o.sweep_rows != 0;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     if (ck) {
@@ -533,6 +534,7 @@ spde_status cg_batch(const spde_opts& o, const Grid3& g, double kh2, int S, Work
     plan.fault = ws.fault;
     plan.sz_pref = o.sweep_planes;
     plan.coarse_fp16 = o.coarse_fp16 != 0;
+    plan.sweep_rows = o.sweep_rows != 0;
     plan.prof_cols = (double)S;
     const int act_stride = (int)(sizeof(CgCol) / sizeof(int));
     const int* act = &ws.cg[0].active;
@@ -789,6 +791,7 @@ spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Wor
     plan.fault = ws.fault;
     plan.sz_pref = o.sweep_planes;
     plan.coarse_fp16 = o.coarse_fp16 != 0;
+    plan.sweep_rows = o.sweep_rows != 0;
     if (Dlev)
         for (int l = 0; l < plan.nlev && l < 16; ++l) plan.D[l] = Dlev[l];
     const int act_stride = (int)(sizeof(MinresCol) / sizeof(int));
@@ -1602,6 +1605,7 @@ spde_status spde_opts_init(spde_opts* o) {
     o->solver = SPDE_SOLVER_MINRES;
     o->sweep_planes = 0;
     o->coarse_fp16 = 0;
+    o->sweep_rows = 1;
     return SPDE_OK;
 }
 
@@ -2424,6 +2428,7 @@ spde_status spde_precond_box(const int n[3], double h, double kappa, int nsample
     plan.fault = g_pc_fault;
     plan.sz_pref = o.sweep_planes;
     plan.coarse_fp16 = o.coarse_fp16 != 0;
+    plan.sweep_rows = o.sweep_rows != 0;
     if (prec == SPDE_PREC_FP64) {
         mg_plan_bind<double>(plan, nsamples, static_cast<double*>(g_pc.mg));
         const double* rr = static_cast<const double*>(r);
