@@ -855,7 +855,8 @@ __global__ void __launch_bounds__(RowShape<NX, TY>::NT, RowShape<NX, TY>::NT <= 
         wa[a3] = restrict_w(a3, 2 * qq, ncx);
         wb[a3] = restrict_w(a3, 2 * qq + 1, ncx);
     }
-    // y-restriction item of this thread: coarse row J, coarse x pair P
+    // y-restriction item of this thread: coarse row J, coarse x pair P (whole warps: spreading
+    // the items over every warp measured slower, as every warp then runs the item code)
     const bool has_item = tid < Sh::NITEMS;
     const int iJ = tid / (NX / 4), iP = tid % (NX / 4);
     __syncthreads();

@@ -117,70 +117,114 @@ __global__ void __launch_bounds__(256) k_project_rows(int64_t ntets, int S, cons
     }
 }
 
-// S a multiple of 4: a half-warp per tet, a float4 of samples per lane (16 lanes
-// cover a 64-sample chunk of a thetaT row), so one warp instruction gathers the
-// rows of two tets.  Each half loads up to 16 of its row's (pi, col) pairs at
-// once and hands them round by width-16 shuffles; the sum runs over the row in
-// CSR order, as in the other projection kernels.
+// S a multiple of 4: a group of 4 lanes per tet, 16 samples per lane (float4 i of the
+// lane is the chunk's float4 gl + 4 i, so the group's four lanes read 64 contiguous bytes
+// of a thetaT row per instruction); a warp works on 8 consecutive tets and no warp waits
+// for another.  The entries of a row are loaded 16 at a time by the group's lanes
+// together and handed round by width-4 shuffles, so the gathers of a block wait for one
+// load latency.  The sum runs over the row in CSR order with the same fmaf sequence as
+// the other projection kernels, so all of them give the same bits.  The results go
+// straight from registers to out[sample][tet]: one store instruction writes, for each of
+// four samples, the warp's 8 consecutive tets (one full 32-byte sector each).
+constexpr int kGrpWarps = 4, kGrpTets = 8 * kGrpWarps;
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 template <typename O>
-__global__ void __launch_bounds__(256) k_project_quad(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
-                                                      const int32_t* __restrict__ col, const float* __restrict__ pi,
-                                                      const float* __restrict__ thetaT, int kind, O* __restrict__ out) {
-    __shared__ float tile[kProjChunk][kProjTets + 1];
+__global__ void __launch_bounds__(32 * kGrpWarps) k_project_grp(int64_t ntets, int S, const int64_t* __restrict__ rowptr,
+                                                                const int32_t* __restrict__ col, const float* __restrict__ pi,
+                                                                const float* __restrict__ thetaT, int kind,
+                                                                O* __restrict__ out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int half = lane >> 4, hl = lane & 15;
-    const int64_t t0 = (int64_t)blockIdx.x * kProjTets;
+    const int grp = lane >> 2, gl = lane & 3;
+    const int64_t t = (int64_t)blockIdx.x * kGrpTets + warp * 8 + grp;
     const int S4 = S >> 2;
     const float4* T4 = reinterpret_cast<const float4*>(thetaT);
+    int64_t a = 0, b = 0;
+    if (t < ntets) {
+        a = rowptr[t];
+        b = rowptr[t + 1];
+    }
+    const int nblk = warp_max((int)((b - a + 15) >> 4));  // every group runs the warp's count
     for (int s0 = 0; s0 < S; s0 += kProjChunk) {
-        const int q = (s0 >> 2) + hl;  // this lane's float4 of the row
-        const bool on = q < S4;
-        for (int rr = 0; rr < 2; ++rr) {
-            const int r = warp * 4 + rr * 2 + half;
-            const int64_t t = t0 + r;
-            int64_t a = 0, b = 0;
-            if (t < ntets) {
-                a = rowptr[t];
-                b = rowptr[t + 1];
+        const int q0 = (s0 >> 2) + gl;  // float4 i of this lane: q0 + 4 i
+        bool on[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) on[i] = q0 + 4 * i < S4;
+        float4 acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int blk = 0; blk < nblk; ++blk) {
+            const int64_t base = a + 16 * (int64_t)blk;
+            const int64_t left = b - base;
+            const int len = left <= 0 ? 0 : (left < 16 ? (int)left : 16);
+            float wl[4];
+            int cl[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = gl + 4 * m;
+                wl[m] = k < len ? pi[base + k] : 0.0f;
+                cl[m] = k < len ? col[base + k] : 0;
             }
-            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            for (int64_t base = a;; base += 16) {
-                const int64_t left = b - base;
-                const int mh = left <= 0 ? 0 : (left < 16 ? (int)left : 16);
-                const int mo = __shfl_xor_sync(0xffffffffu, mh, 16);
-                if (mh == 0 && mo == 0) break;  // both rows done (warp-uniform)
-                float wl = 0.0f;
-                int cl = 0;
-                if (hl < mh) {
-                    wl = pi[base + hl];
-                    cl = col[base + hl];
-                }
-                const int mm = mh > mo ? mh : mo;
-#pragma unroll 4
-                for (int k = 0; k < mm; ++k) {
-                    const float w = __shfl_sync(0xffffffffu, wl, k, 16);
-                    const int c = __shfl_sync(0xffffffffu, cl, k, 16);
-                    if (k < mh && on) {
-                        const float4 v = T4[(int64_t)c * S4 + q];
-                        acc.x = fmaf(w, v.x, acc.x);
-                        acc.y = fmaf(w, v.y, acc.y);
-                        acc.z = fmaf(w, v.z, acc.z);
-                        acc.w = fmaf(w, v.w, acc.w);
+            const int lw = warp_max(len);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (4 * m >= lw) break;
+#pragma unroll
+                for (int kk = 0; kk < 4; kk += 2) {  // two entries per step: independent gathers
+                    const int k = 4 * m + kk;
+                    const float w0 = __shfl_sync(0xffffffffu, wl[m], kk, 4);
+                    const int c0 = __shfl_sync(0xffffffffu, cl[m], kk, 4);
+                    const float w1 = __shfl_sync(0xffffffffu, wl[m], kk + 1, 4);
+                    const int c1 = __shfl_sync(0xffffffffu, cl[m], kk + 1, 4);
+                    const bool h0 = k < len, h1 = k + 1 < len;
+                    const float4* row0 = T4 + (int64_t)c0 * S4;
+                    const float4* row1 = T4 + (int64_t)c1 * S4;
+                    float4 v0[4], v1[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (h0 && on[i]) v0[i] = row0[q0 + 4 * i];
+                        if (h1 && on[i]) v1[i] = row1[q0 + 4 * i];
+                    }
+                    if (h0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (on[i]) {
+                                acc[i].x = fmaf(w0, v0[i].x, acc[i].x);
+                                acc[i].y = fmaf(w0, v0[i].y, acc[i].y);
+                                acc[i].z = fmaf(w0, v0[i].z, acc[i].z);
+                                acc[i].w = fmaf(w0, v0[i].w, acc[i].w);
+                            }
+                    }
+                    if (h1) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (on[i]) {
+                                acc[i].x = fmaf(w1, v1[i].x, acc[i].x);
+                                acc[i].y = fmaf(w1, v1[i].y, acc[i].y);
+                                acc[i].z = fmaf(w1, v1[i].z, acc[i].z);
+                                acc[i].w = fmaf(w1, v1[i].w, acc[i].w);
+                            }
                     }
                 }
             }
-            tile[4 * hl][r] = acc.x;
-            tile[4 * hl + 1][r] = acc.y;
-            tile[4 * hl + 2][r] = acc.z;
-            tile[4 * hl + 3][r] = acc.w;
         }
-        __syncthreads();
-        for (int qq = warp; qq < kProjChunk; qq += 8) {
-            const int ss = s0 + qq;
-            const int64_t t = t0 + lane;
-            if (ss < S && t < ntets) out[(int64_t)ss * ntets + t] = out_map<O>(tile[qq][lane], kind);
+        if (t < ntets) {
+            // sample s0 + 4 (q0 - s0/4 + 4 i) + e = s0 + 4 (gl + 4 i) + e
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (on[i]) {
+                    O* o = out + (int64_t)(s0 + 4 * (gl + 4 * i)) * ntets + t;
+                    o[0] = out_map<O>(acc[i].x, kind);
+                    o[ntets] = out_map<O>(acc[i].y, kind);
+                    o[2 * ntets] = out_map<O>(acc[i].z, kind);
+                    o[3 * ntets] = out_map<O>(acc[i].w, kind);
+                }
         }
-        __syncthreads();
     }
 }
 
@@ -205,8 +249,13 @@ cudaError_t launch_project(int64_t ntets, int S, const int64_t* rowptr, const in
         const unsigned nb = (unsigned)((ntets + kProjTets - 1) / kProjTets);
         // float4 / float2 gathers need rows of thetaT on 16 / 8 bytes (S a multiple of 4 / 2)
         if (S % 4 == 0) {
-            if (out64) k_project_quad<double><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
-            else k_project_quad<float><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
+            const unsigned ng = (unsigned)((ntets + kGrpTets - 1) / kGrpTets);
+            if (out64)
+                k_project_grp<double><<<ng, 32 * kGrpWarps, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind,
+                                                                     (double*)out);
+            else
+                k_project_grp<float><<<ng, 32 * kGrpWarps, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind,
+                                                                    (float*)out);
         } else if (S % 2 == 0) {
             if (out64) k_project_rows<double, 2><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (double*)out);
             else k_project_rows<float, 2><<<nb, 256, 0, st>>>(ntets, S, rowptr, col, pi, thetaT, kind, (float*)out);
