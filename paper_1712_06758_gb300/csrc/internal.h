@@ -53,6 +53,7 @@ inline Grid3 make_grid(int n) { return make_grid(n, n, n); }
 struct MinresCol {
     double beta, oldb, alpha, dbar, epsln, oldeps, phibar, cs, sn, gamma, delta, phi, beta1;
     double tol;      // stop when phibar <= tol * beta1
+    double ry;       // r2.yprev of the last pass B: beta times the v.r1 term of the next alpha
     // coefficients of the pending w/x update (saved by the Givens step)
     double d_oldb, d_oldeps, d_delta, d_gamma, d_phi;
     // the per-column factors the vector passes use, computed once by the scalar
@@ -70,7 +71,7 @@ struct MinresCol {
 enum {
     KC_IB = 0,    // 1 / beta            (Lanczos pass)
     KC_COEF = 1,  // beta / oldb, 0 in the first iteration
-    KC_F = 2,     // alpha / beta        (second Lanczos pass)
+    KC_F = 2,     // alpha / beta        (pass B)
     KC_IV = 3,    // 1 / d_oldb          (w/x update)
     KC_OE = 4,    // d_oldeps
     KC_DE = 5,    // d_delta
@@ -207,17 +208,20 @@ int launch_sumsq(int64_t nelem, int S, const double* a, int64_t stride, double* 
 cudaError_t launch_reduce(int S, const double* part, int nblk, double* out, cudaStream_t st);
 
 // ---- krylov.cu
-// A(k+1) fused with the pending D(k) when yprev != null (see krylov.cu).  The
-// preconditioned Lanczos vector is fd * u on the flux blocks and y's cell block.
+// A(k+1) fused with the pending D(k) when yprev != null (see krylov.cu): partA gets
+// the partial sums of y.(A y).  The preconditioned Lanczos vector is fd * u on the
+// flux blocks and y's cell block.
 template <typename T>
-int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
+int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, double* partA,
                     MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st,
                     const T* kh2c = nullptr, const T* kh2s = nullptr);
-// r1 -= (alpha / beta) r2 and the flux part of the next beta^2 (the flux block of
-// the next preconditioned vector is fd * r1 and is not stored)
+// r1 = (A y) / beta - (beta / oldb) r1 - (alpha / beta) r2 in place, with the flux part
+// of the next beta^2 in partB (the flux block of the next preconditioned vector is
+// fd * r1 and is not stored) and r1.y in partE (the same block count)
 template <typename T>
-int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, double fd, double* partB, MinresCol* st_,
-                    cudaStream_t st);
+int launch_minres_B(const Grid3& g, double kh2, int S, const T* y, const T* r2, double fd, T* r1, double* partB,
+                    double* partE, MinresCol* st_, cudaStream_t st, const T* kh2c = nullptr,
+                    const T* kh2s = nullptr);
 template <typename T>
 int launch_precond_u(int64_t N4, int n3, int S, const T* r, T* y, double fd, double* part,
                      const MinresCol* st_, cudaStream_t st);
@@ -225,7 +229,8 @@ cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cud
 // nactive (optional, two ints): [0] += columns still active after this step,
 // [1] += columns whose w/x update this step left pending
 // max_iter: a column stops after this many iterations (the iteration cap of the solve)
-cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC,
+// partE: pass B's partial sums of r1.y (nB blocks), kept for the next alpha
+cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC, const double* partE,
                           MinresCol* st_, int* nactive, cudaStream_t st, int max_iter = 1 << 30);
 // control kernels of the graph-driven refinement (one thread block each)
 cudaError_t launch_refine_init(RefineCtl* ctl, int* fault, unsigned long long h_outer, cudaStream_t st);

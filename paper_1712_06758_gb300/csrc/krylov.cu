@@ -6,12 +6,18 @@
 // fixed-shape tree, then one fixed-order pass per column, so a column's
 // result does not depend on which other columns share the batch.
 //
-// One iteration (v = y / beta):
-//   A: z = A v - (beta / oldb) r1, alpha = v.z            (stencil, fused)
-//   B: r2' = z - (alpha / beta) r2, y' = P^{-1} r2'        (flux block here,
-//      field block by the V-cycle), beta'^2 = r2'.y'
+// One iteration k (v = y / beta, y = P^{-1} r2, r1 and r2 the last two
+// unpreconditioned Lanczos vectors):
+//   A: alpha = v.A v - (beta / oldb) v.r1                   (stencil, reads only)
+//   B: r1' = A v - (beta / oldb) r1 - (alpha / beta) r2      (stencil again, in place),
+//      y' = P^{-1} r1' (flux block here, field block by the V-cycle), beta'^2 = r1'.y'
 //   Givens rotation, residual estimate phibar, retirement
 //   D: w' = (v - oldeps w1 - delta w2) / gamma, x += phi w'
+// The term v.r1 of alpha is y_k.r_{k-1} / beta; P is symmetric, so it equals
+// r_k.y_{k-1} / beta, which pass B of the previous iteration forms from the
+// vectors it already holds.  A therefore writes nothing: the vector A v is
+// rebuilt by B instead of being stored by A and read back (4 + 13 words per
+// cell instead of 12 + 12).
 #include "device.cuh"
 #include "internal.h"
 
@@ -30,7 +36,7 @@ static inline int cell_blocks(int64_t n3) {
 
 // A(k+1) fused with D(k): both become ready after the Givens step of
 // iteration k and touch disjoint arrays, so one pass streams both.
-//   A part (column active):   z = A y / beta - (beta / oldb) r1 -> r1, alpha partial
+//   A part (column active):   partA = y.(A y)  (y unscaled; alpha is formed by k_alpha)
 //   D part (column upd set):  w' = (yprev_cell / oldb_D - oldeps w1 - delta w2) / gamma,
 //                             x += phi w'   (cell block, [S][n^3] arrays)
 // The D coefficients were saved by the Givens step in MinresCol (d_* fields)
@@ -39,7 +45,6 @@ __device__ __forceinline__ void set_coef(MinresCol& c, int k, double v) {
     c.kd[k] = v;
     c.kf[k] = (float)v;
 }
-
 // y = A v on a quad for a preconditioned Lanczos vector v whose flux blocks
 // are fd * u (the flux block of the preconditioner is fd I, so they are never
 // stored) and whose cell block is th; fd multiplies each flux sum once.  The
@@ -108,7 +113,28 @@ __device__ __forceinline__ void d_update4(const V4<T>& yv, const V4<T>& w1v, con
 // CUBE: the grid is a cube (all extents and logs taken from x, which keeps the
 // index arithmetic and register use of the cubic case minimal)
 template <typename T, bool CUBE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 gin, T kh2, const T* __restrict__ y, const T* __restrict__ u, T fd, T* __restrict__ r1,
+__device__ __forceinline__ Grid3 pass_grid(const Grid3& gin) {
+    Grid3 g = gin;
+    if constexpr (CUBE) {
+        g.ny = g.nz = gin.nx;
+        g.lx = g.ly = g.lz = ilog2(gin.nx);
+    }
+    return g;
+}
+
+// (kappa h)^2 of a quad: one value (per call or per column), or the level's field
+template <typename T>
+__device__ __forceinline__ V4<T> quad_kh2(T kh2, const T* __restrict__ kh2c, const T* __restrict__ kh2s, int s, int c) {
+    V4<T> k4;
+    if (kh2c) k4 = ld4(kh2c + c);
+    else
+#pragma unroll
+        for (int e = 0; e < 4; ++e) k4.v[e] = kh2s ? kh2s[s] : kh2;
+    return k4;
+}
+
+template <typename T, bool CUBE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 gin, T kh2, const T* __restrict__ y, const T* __restrict__ u, T fd,
                                                      double* __restrict__ partA, const MinresCol* __restrict__ st,
                                                      const T* __restrict__ yprev, T* __restrict__ w1,
                                                      const T* __restrict__ w2, T* __restrict__ xd,
@@ -119,55 +145,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 
     const bool doA = cs.active != 0;
     const bool doD = yprev != nullptr && cs.upd != 0;
     if (!doA && !doD) return;
-    Grid3 g = gin;
-    if constexpr (CUBE) {
-        g.ny = g.nz = gin.nx;
-        g.lx = g.ly = g.lz = ilog2(gin.nx);
-    }
+    const Grid3 g = pass_grid<T, CUBE>(gin);
     const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int nq = n3 >> 2;
     const int64_t off = (int64_t)s * 4 * n3;
     const T* ys = y + off;   // only its cell block is read
     const T* us = u + off;   // flux blocks of the Lanczos vector: y's are fd times these
-    T* rs = r1 + off;
     T acc = T(0);
     if (doA) {
-        const T ib = col_coef<T>(cs, KC_IB);
-        const T coef = col_coef<T>(cs, KC_COEF);
-        // r1 holds no data before the second iteration (coef == 0): do not read it
-        const bool use_r1 = coef != T(0);
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
             const QuadPos p = quad_pos(q, g);
             T yu[4], yv[4], yw[4], yt[4];
             V4<T> vc[4];
-            V4<T> k4;  // (kappa h)^2 per cell: one value (per call or per column), or the level's field
-            if (kh2c) k4 = ld4(kh2c + p.c);
-            else
+            apply_quad_fd<T>(us, ys + 3 * n3, fd, g, p, quad_kh2<T>(kh2, kh2c, kh2s, s, p.c), yu, yv, yw, yt, vc);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) k4.v[e] = kh2s ? kh2s[s] : kh2;
-            apply_quad_fd<T>(us, ys + 3 * n3, fd, g, p, k4, yu, yv, yw, yt, vc);
-            const V4<T> v0 = vc[0], v1 = vc[1], v2 = vc[2], v3 = vc[3];
-            V4<T> z0, z1, z2, z3;
-            if (use_r1) {
-                z0 = ld4(rs + p.c);
-                z1 = ld4(rs + n3 + p.c);
-                z2 = ld4(rs + 2 * n3 + p.c);
-                z3 = ld4(rs + 3 * n3 + p.c);
-            } else {
-                z0 = z1 = z2 = z3 = zero4<T>();
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                z0.v[e] = yu[e] * ib - coef * z0.v[e];
-                z1.v[e] = yv[e] * ib - coef * z1.v[e];
-                z2.v[e] = yw[e] * ib - coef * z2.v[e];
-                z3.v[e] = yt[e] * ib - coef * z3.v[e];
-                acc += (fd * (v0.v[e] * z0.v[e] + v1.v[e] * z1.v[e] + v2.v[e] * z2.v[e]) + v3.v[e] * z3.v[e]) * ib;
-            }
-            st4(rs + p.c, z0);
-            st4(rs + n3 + p.c, z1);
-            st4(rs + 2 * n3 + p.c, z2);
-            st4(rs + 3 * n3 + p.c, z3);
+            for (int e = 0; e < 4; ++e)
+                acc += fd * (vc[0].v[e] * yu[e] + vc[1].v[e] * yv[e] + vc[2].v[e] * yw[e]) + vc[3].v[e] * yt[e];
         }
     }
     if (doD) {
@@ -195,51 +188,94 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_A(Grid3 
 }
 
 template <typename T>
-int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, T* r1, double* partA,
+int launch_minres_A(const Grid3& g, double kh2, int S, const T* y, const T* u, double fd, double* partA,
                     MinresCol* st_, const T* yprev, T* w1, const T* w2, T* xd, cudaStream_t st, const T* kh2c,
                     const T* kh2s) {
     const int nb = cell_blocks(g.cells() / 16);  // four quads per thread: one reduction per 1024 quads
     dim3 grid(nb, S);
     if (g.cube())
-        k_minres_A<T, true><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c,
-                                                  kh2s);
+        k_minres_A<T, true><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, partA, st_, yprev, w1, w2, xd, kh2c, kh2s);
     else
-        k_minres_A<T, false><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, r1, partA, st_, yprev, w1, w2, xd, kh2c,
-                                                   kh2s);
+        k_minres_A<T, false><<<grid, 256, 0, st>>>(g, (T)kh2, y, u, (T)fd, partA, st_, yprev, w1, w2, xd, kh2c, kh2s);
     return nb;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_minres_B(int64_t N4, int64_t n3u, T* __restrict__ r1, const T* __restrict__ r2,
-                                                  T fd, double* __restrict__ partB, const MinresCol* __restrict__ st) {
+// B(k): the next unpreconditioned Lanczos vector, in place over r1,
+//   r1' = (A y) / beta - (beta / oldb) r1 - (alpha / beta) r2
+// (A y rebuilt from the flux blocks of r2 and the cell block of y, as in pass
+// A), with two partial sums per block:
+//   partB: the flux part of beta'^2 = r1'.y', i.e. r1'_flux . (fd r1'_flux)
+//          (the flux block of the next preconditioned vector, never stored);
+//   partE: r1'.y = fd r1'_flux . r2_flux + r1'_cell . y_cell, the v.r1 term of
+//          the next iteration's alpha (times its beta).
+// Each thread reads r1 and writes r1' at its own cells only; r2 and y are
+// not written.
+template <typename T, bool CUBE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_minres_B(Grid3 gin, T kh2, const T* __restrict__ y, const T* __restrict__ r2, T fd,
+                                                     T* __restrict__ r1, double* __restrict__ partB,
+                                                     double* __restrict__ partE, const MinresCol* __restrict__ st,
+                                                     const T* __restrict__ kh2c, const T* __restrict__ kh2s) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     const MinresCol& cs = st[s];
     if (!cs.active) return;
+    const Grid3 g = pass_grid<T, CUBE>(gin);
+    const int n3 = 1 << (g.lx + g.ly + g.lz);
+    const int nq = n3 >> 2;
+    const int64_t off = (int64_t)s * 4 * n3;
+    const T* ys = y + off;
+    const T* us = r2 + off;
+    T* rs = r1 + off;
+    const T ib = col_coef<T>(cs, KC_IB);
+    const T coef = col_coef<T>(cs, KC_COEF);
     const T f = col_coef<T>(cs, KC_F);
-    const int64_t off = (int64_t)s * N4;
-    const int64_t nq = N4 >> 2, nqu = n3u >> 2;  // 4-vectors; the flux blocks end on a vector boundary
-    T acc = T(0);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
-        V4<T> z = ld4(r1 + off + 4 * q);
-        const V4<T> p = ld4(r2 + off + 4 * q);
+    // r1 holds no data before the second iteration (coef == 0): do not read it
+    const bool use_r1 = coef != T(0);
+    T accB = T(0), accE = T(0);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const QuadPos p = quad_pos(q, g);
+        T yu[4], yv[4], yw[4], yt[4];
+        V4<T> vc[4];
+        apply_quad_fd<T>(us, ys + 3 * n3, fd, g, p, quad_kh2<T>(kh2, kh2c, kh2s, s, p.c), yu, yv, yw, yt, vc);
+        const V4<T> pt = ld4(us + 3 * n3 + p.c);  // cell block of r2 (its flux blocks are vc[0..2])
+        V4<T> z0, z1, z2, z3;
+        if (use_r1) {
+            z0 = ld4(rs + p.c);
+            z1 = ld4(rs + n3 + p.c);
+            z2 = ld4(rs + 2 * n3 + p.c);
+            z3 = ld4(rs + 3 * n3 + p.c);
+        } else {
+            z0 = z1 = z2 = z3 = zero4<T>();
+        }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) z.v[e] = z.v[e] - f * p.v[e];
-        st4(r1 + off + 4 * q, z);
-        if (q < nqu)  // flux block of the next preconditioned vector, never stored
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc += z.v[e] * (fd * z.v[e]);
+        for (int e = 0; e < 4; ++e) {
+            z0.v[e] = (yu[e] * ib - coef * z0.v[e]) - f * vc[0].v[e];
+            z1.v[e] = (yv[e] * ib - coef * z1.v[e]) - f * vc[1].v[e];
+            z2.v[e] = (yw[e] * ib - coef * z2.v[e]) - f * vc[2].v[e];
+            z3.v[e] = (yt[e] * ib - coef * z3.v[e]) - f * pt.v[e];
+            accB += z0.v[e] * (fd * z0.v[e]) + z1.v[e] * (fd * z1.v[e]) + z2.v[e] * (fd * z2.v[e]);
+            accE += fd * (z0.v[e] * vc[0].v[e] + z1.v[e] * vc[1].v[e] + z2.v[e] * vc[2].v[e]) + z3.v[e] * vc[3].v[e];
+        }
+        st4(rs + p.c, z0);
+        st4(rs + n3 + p.c, z1);
+        st4(rs + 2 * n3 + p.c, z2);
+        st4(rs + 3 * n3 + p.c, z3);
     }
-    const double t = block_sum_t<256, T>(acc, red);
-    if (threadIdx.x == 0) partB[(int64_t)s * kMaxPartials + blockIdx.x] = t;
+    const double tB = block_sum_t<256, T>(accB, red);
+    if (threadIdx.x == 0) partB[(int64_t)s * kMaxPartials + blockIdx.x] = tB;
+    const double tE = block_sum_t<256, T>(accE, red);
+    if (threadIdx.x == 0) partE[(int64_t)s * kMaxPartials + blockIdx.x] = tE;
 }
 
 template <typename T>
-int launch_minres_B(int64_t N4, int n3, int S, T* r1, const T* r2, double fd, double* partB, MinresCol* st_,
-                    cudaStream_t st) {
-    const int nb = elem_blocks(N4 / 16);  // sixteen 4-vectors per thread at n = 128: one reduction per 4096 values
+int launch_minres_B(const Grid3& g, double kh2, int S, const T* y, const T* r2, double fd, T* r1, double* partB,
+                    double* partE, MinresCol* st_, cudaStream_t st, const T* kh2c, const T* kh2s) {
+    const int nb = cell_blocks(g.cells() / 16);
     dim3 grid(nb, S);
-    k_minres_B<T><<<grid, 256, 0, st>>>(N4, 3 * (int64_t)n3, r1, r2, (T)fd, partB, st_);
+    if (g.cube())
+        k_minres_B<T, true><<<grid, 256, 0, st>>>(g, (T)kh2, y, r2, (T)fd, r1, partB, partE, st_, kh2c, kh2s);
+    else
+        k_minres_B<T, false><<<grid, 256, 0, st>>>(g, (T)kh2, y, r2, (T)fd, r1, partB, partE, st_, kh2c, kh2s);
     return nb;
 }
 
@@ -280,10 +316,13 @@ __global__ void __launch_bounds__(256) k_alpha(const double* __restrict__ partA,
     __shared__ double red[8];
     const int s = blockIdx.x;
     if (!st[s].active) return;
-    const double a = col_sum(partA, s, nA, red);
+    const double a = col_sum(partA, s, nA, red);  // y.(A y), y = beta v
     if (threadIdx.x == 0) {
-        st[s].alpha = a;
-        set_coef(st[s], KC_F, a / st[s].beta);
+        MinresCol& c = st[s];
+        // alpha = v.A v - (beta / oldb) v.r1, with v.r1 = (r2.yprev) / beta kept by the Givens step
+        const double alpha = a / (c.beta * c.beta) - (c.oldb > 0.0 ? c.ry / c.oldb : 0.0);
+        c.alpha = alpha;
+        set_coef(c, KC_F, alpha / c.beta);
     }
 }
 
@@ -293,8 +332,8 @@ cudaError_t launch_alpha(int S, const double* partA, int nA, MinresCol* st_, cud
 }
 
 __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB, int nB, const double* __restrict__ partC,
-                                                int nC, MinresCol* __restrict__ st, int* __restrict__ nactive,
-                                                int max_iter) {
+                                                int nC, const double* __restrict__ partE, MinresCol* __restrict__ st,
+                                                int* __restrict__ nactive, int max_iter) {
     __shared__ double red[8];
     const int s = blockIdx.x;
     MinresCol& c = st[s];
@@ -304,9 +343,11 @@ __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB
     }
     const double b2 = col_sum(partB, s, nB, red);
     const double b3 = col_sum(partC, s, nC, red);
+    const double ry = col_sum(partE, s, nB, red);  // r'.y of pass B (same blocks as partB)
     if (threadIdx.x != 0) return;
     const double beta2 = b2 + b3;
     const double beta = sqrt(fmax(beta2, 0.0));
+    c.ry = ry;
     c.oldb = c.beta;
     c.beta = beta;
     c.oldeps = c.epsln;
@@ -344,9 +385,9 @@ __global__ void __launch_bounds__(256) k_givens(const double* __restrict__ partB
     else if (nactive) atomicAdd(nactive, 1);
 }
 
-cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC, MinresCol* st_,
-                          int* nactive, cudaStream_t st, int max_iter) {
-    k_givens<<<S, 256, 0, st>>>(partB, nB, partC, nC, st_, nactive, max_iter);
+cudaError_t launch_givens(int S, const double* partB, int nB, const double* partC, int nC, const double* partE,
+                          MinresCol* st_, int* nactive, cudaStream_t st, int max_iter) {
+    k_givens<<<S, 256, 0, st>>>(partB, nB, partC, nC, partE, st_, nactive, max_iter);
     return cudaGetLastError();
 }
 
@@ -489,6 +530,7 @@ __global__ void __launch_bounds__(256) k_minres_init(const double* __restrict__ 
     c.delta = 0.0;
     c.phi = 0.0;
     c.beta1 = beta1;
+    c.ry = 0.0;
     c.tol = col_tol ? col_tol[s] : tol;
     c.upd = 0;
     c.iters = 0;
@@ -552,9 +594,10 @@ cudaError_t launch_active_flags(int S, const MinresCol* st_, int* flags, cudaStr
 }
 
 #define SPDE_KRYLOV_INST(T)                                                                                        \
-    template int launch_minres_A<T>(const Grid3&, double, int, const T*, const T*, double, T*, double*, MinresCol*,        \
+    template int launch_minres_A<T>(const Grid3&, double, int, const T*, const T*, double, double*, MinresCol*,    \
                                     const T*, T*, const T*, T*, cudaStream_t, const T*, const T*);                 \
-    template int launch_minres_B<T>(int64_t, int, int, T*, const T*, double, double*, MinresCol*, cudaStream_t);   \
+    template int launch_minres_B<T>(const Grid3&, double, int, const T*, const T*, double, T*, double*, double*,    \
+                                    MinresCol*, cudaStream_t, const T*, const T*);                                 \
     template int launch_precond_u<T>(int64_t, int, int, const T*, T*, double, double*, const MinresCol*,          \
                                      cudaStream_t);                                                                \
     template cudaError_t launch_minres_D<T>(int64_t, int, const T*, T*, const T*, T*, const MinresCol*,          \

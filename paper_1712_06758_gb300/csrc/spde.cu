@@ -463,22 +463,24 @@ spde_status minres_batch(const spde_opts& o, const Grid3& g, double kh2, int S, 
             rec[q] = t_prof ? t_prof->mark() : 0;
             // A(itn) fused with the pending w/x update D(itn - 1) (cell block only)
             prof_begin(PK_MINRES_A, st);
-            const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
+            const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, ws.partA, ws.st,
                                               pending ? yprev : nullptr, w1, w2, d, st, kh2c, kh2s);
-            a_bytes[q] = ((itn >= 2 ? 12.0 : 8.0) + (kh2c ? 1.0 : 0.0)) * n3d * w;
+            a_bytes[q] = (4.0 + (kh2c ? 1.0 : 0.0)) * n3d * w;
             d_bytes[q] = pending ? (itn - 1 >= 3 ? 6.0 : (itn - 1 == 2 ? 5.0 : 3.0)) * n3d * w : 0.0;
             prof_end(st, 0.0);
             if (pending) std::swap(w1, w2);
             prof_begin(PK_ALPHA, st);
             CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, st));
             prof_end(st, nA * 8.0);
+            // pass B: partA (consumed by the alpha step) now takes its partial sums of r1.y
             prof_begin(PK_MINRES_B, st);
-            const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, o.flux_diag, ws.partB, ws.st, st);
-            prof_end(st, 12.0 * n3d * w);
+            const int nB = launch_minres_B<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partB, ws.partA, ws.st, st,
+                                              kh2c, kh2s);
+            prof_end(st, ((itn >= 2 ? 13.0 : 9.0) + (kh2c ? 1.0 : 0.0)) * n3d * w);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, st);
             prof_begin(PK_GIVENS, st);
-            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, ws.nact + 2 * q, st, o.max_iter));
-            prof_end(st, (nB + nC) * 8.0);
+            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.partA, ws.st, ws.nact + 2 * q, st, o.max_iter));
+            prof_end(st, (2 * nB + nC) * 8.0);
             pending = true;
             last_itn = itn;
             yprev = ycur;
@@ -844,14 +846,15 @@ spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Wor
         bool pending = false;
         T* yprev = nullptr;
         auto iteration = [&](cudaStream_t s, int slot) -> spde_status {
-            const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partA, ws.st,
+            const int nA = launch_minres_A<T>(g, kh2, S, ycur, r2, o.flux_diag, ws.partA, ws.st,
                                               pending ? yprev : nullptr, w1, w2, d, s, kh2c);
             if (pending) std::swap(w1, w2);
             CUDA_TRY(launch_alpha(S, ws.partA, nA, ws.st, s));
-            const int nB = launch_minres_B<T>(N4, (int)n3, S, r1, r2, o.flux_diag, ws.partB, ws.st, s);
+            // partA, consumed by the alpha step, takes pass B's partial sums of r1.y
+            const int nB = launch_minres_B<T>(g, kh2, S, ycur, r2, o.flux_diag, r1, ws.partB, ws.partA, ws.st, s, kh2c);
             const int nC = launch_vcycle<T>(plan, S, r1 + 3 * n3, N4, ynext + 3 * n3, N4, ws.partC, act, act_stride, s);
             if (nC < 0) return fail(SPDE_ECUDA, "V-cycle launch configuration failed");
-            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.st, ctl->cnt + 2 * slot, s, o.max_iter));
+            CUDA_TRY(launch_givens(S, ws.partB, nB, ws.partC, nC, ws.partA, ws.st, ctl->cnt + 2 * slot, s, o.max_iter));
             pending = true;
             yprev = ycur;
             std::swap(r1, r2);
