@@ -114,9 +114,10 @@ typedef struct {
     int64_t serve_budget_bytes; /* device memory the serving lanes may hold; 120 GiB */
     int serve_max_batch;        /* columns per serving lane; 64 */
     int solver;                 /* SPDE_SOLVER_MINRES (default) or SPDE_SOLVER_SCHUR_CG */
-    int sweep_planes;           /* fine z planes per CTA of the V-cycle sweeps: 8, 16 or 32 where a
-                                   level's z extent allows; 0 (default) = per level, the longest
-                                   march that still gives 4 CTAs per SM */
+    int sweep_planes;           /* fine z planes per CTA of the V-cycle sweeps: 8, 16, 32 or 64 (64:
+                                   whole-row tiles only; the 32 x 16 tiles take the default) where a
+                                   level's z extent allows; 0 (default) = per level, the longest march
+                                   that still gives every SM a few CTAs */
     int coarse_fp16;            /* 1: the V-cycle levels held by the one-CTA coarse kernel (at most 4096
                                    cells, 16^3 on a cube) are stored in FP16, each column scaled by its
                                    largest value, arithmetic in FP32 (FP32 path only); 0 (default): FP32 */
@@ -142,7 +143,7 @@ typedef struct {
     double omega;        /* damped-Jacobi weight of the V-cycle smoother, in (0, 1) */
     double inner_tol;    /* reduction asked of the FP32 inner solve per refinement step, in (0, 1) */
     double flux_diag;    /* flux-block preconditioner (a multiple of the identity), > 0 */
-    int sweep_planes;    /* z planes per CTA of the V-cycle sweeps (0, 8, 16, 32; see spde_opts) */
+    int sweep_planes;    /* z planes per CTA of the V-cycle sweeps (0, 8, 16, 32, 64; see spde_opts) */
     double ms_per_call;  /* (spde_autotune) device time of one call with this schedule */
     double default_ms;   /* (spde_autotune) the same with the context's options */
     int evaluated;       /* (spde_autotune) schedules timed */

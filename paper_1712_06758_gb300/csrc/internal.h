@@ -171,7 +171,8 @@ cudaError_t launch_apply(const Grid3& g, double kh2, int S, const T* x, T* y, cu
 // kh2c: (kappa h)^2 per cell (fields), kh2s: per column (serving lanes), else kh2
 int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
                       float* r32, double* r64, double* part, const int* active, cudaStream_t st,
-                      const double* kh2c = nullptr, const double* kh2s = nullptr);
+                      const double* kh2c = nullptr, const double* kh2s = nullptr, int xzero = 0,
+                      const int* zgate = nullptr);
 // one-time kernel attributes of the flux line solves (done before any stream capture)
 cudaError_t flux_prepare();
 // the multigrid diagonal of a level with cell-wise (kappa h)^2: a_c = mean of the children's a

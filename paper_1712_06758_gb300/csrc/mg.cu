@@ -1652,9 +1652,11 @@ cudaError_t mg_prepare() {
     return e;
 }
 
-// z extent per row tile: the longest that still gives every SM a few CTAs
+// z extent per row tile: the longest that still gives every SM a few CTAs (64 planes,
+// which halve the halo planes of 32, only where that leaves four waves of CTAs)
 static int pick_sz_rows(const Grid3& g, int ty, int S, int pref) {
-    if ((pref == 8 || pref == 16 || pref == 32) && g.nz % pref == 0) return pref;
+    if ((pref == 8 || pref == 16 || pref == 32 || pref == 64) && g.nz % pref == 0) return pref;
+    if (g.nz % 64 == 0 && (int64_t)(g.ny / ty) * (g.nz / 64) * S >= 4 * 152) return 64;
     for (int c = 32; c > 8; c >>= 1)
         if (g.nz % c == 0 && (int64_t)(g.ny / ty) * (g.nz / c) * S >= 2 * 152) return c;
     return 8;

@@ -2,7 +2,6 @@
 // driver (noise -> FP64 iterative refinement around batched MINRES ->
 // projection + exp).  Every numerical step runs in this library's kernels.
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
@@ -631,9 +630,13 @@ spde_status refine_solve(spde_ctx* ctx, const Grid3& g, double kh2, int S, Works
             CUDA_TRY(launch_flux_from_theta(g, S, ws.x64, N4, ws.tri, st));
             prof_end(st, (double)S * 96.0 * (double)n3);
         }
+        // x = 0 in the first step of a cold start: the residual is F, read without x
+        const int xzero = (outer == 0 && !warm) ? 1 : 0;
         prof_begin(PK_RESIDUAL, st);
-        nb = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st, fl ? fl->kh2_64 : nullptr);
-        prof_end(st, (double)S * (40.0 + 4.0 * sizeof(T) + (fl ? 8.0 : 0.0)) * (double)n3);
+        nb = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, st, fl ? fl->kh2_64 : nullptr,
+                               nullptr, xzero);
+        prof_end(st, (double)S * (xzero ? 8.0 + 4.0 * sizeof(T) : 40.0 + 4.0 * sizeof(T) + (fl ? 8.0 : 0.0)) *
+                         (double)n3);
         CUDA_TRY(cudaGetLastError());
         prof_begin(PK_OTHER, st);
         CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, st));
@@ -833,7 +836,8 @@ spde_status capture_refine(spde_ctx* ctx, const Grid3& g, double kh2, int S, Wor
         CUDA_TRY(launch_flux_from_theta(g, S, ws.x64, N4, ws.tri, c1, warm ? nullptr : &ctl->outer));
         float* r32 = t64 ? nullptr : reinterpret_cast<float*>(r2);
         double* r64 = t64 ? reinterpret_cast<double*>(r2) : nullptr;
-        nb = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, c1, fl ? fl->kh2_64 : nullptr);
+        nb = launch_residual64(g, kh2, S, ws.F, n3, ws.x64, r32, r64, ws.partR, nullptr, c1, fl ? fl->kh2_64 : nullptr,
+                               nullptr, 0, warm ? nullptr : &ctl->outer);
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(launch_reduce(S, ws.partR, nb, ws.colv, c1));
         CUDA_TRY(launch_refine_check(S, ws.colv, o.tol, o.inner_tol, t64 ? 1 : 0, o.max_outer, ws.fault, ws.mask,
@@ -1626,8 +1630,9 @@ spde_status spde_grid_create(spde_ctx** ctx, const spde_opts* opts) {
     if (!(o.schur_c > 0.0) || !(o.flux_diag > 0.0)) return fail(SPDE_EINVAL, "preconditioner weights must be > 0");
     if (o.serve_budget_bytes <= 0 || o.serve_max_batch < 1 || o.serve_max_batch > 65535)
         return fail(SPDE_EINVAL, "bad serving budget or batch size");
-    if (o.sweep_planes != 0 && o.sweep_planes != 8 && o.sweep_planes != 16 && o.sweep_planes != 32)
-        return fail(SPDE_EINVAL, "sweep_planes must be 0, 8, 16 or 32");
+    if (o.sweep_planes != 0 && o.sweep_planes != 8 && o.sweep_planes != 16 && o.sweep_planes != 32 &&
+        o.sweep_planes != 64)
+        return fail(SPDE_EINVAL, "sweep_planes must be 0, 8, 16, 32 or 64");
     int ndev = 0;
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (o.device < 0 || o.device >= ndev) return fail(SPDE_EINVAL, "device %d not present", o.device);
@@ -2115,8 +2120,9 @@ spde_status spde_get_stats(spde_ctx* ctx, spde_stats* stats) {
 namespace {
 spde_status check_tuning(const spde_tuning& t) {
     if (!(t.omega > 0.0 && t.omega < 1.0) || !(t.inner_tol > 0.0 && t.inner_tol < 1.0) || !(t.flux_diag > 0.0) ||
-        (t.sweep_planes != 0 && t.sweep_planes != 8 && t.sweep_planes != 16 && t.sweep_planes != 32))
-        return fail(SPDE_EINVAL, "bad tuning (omega, inner_tol in (0, 1), flux_diag > 0, sweep_planes 0/8/16/32)");
+        (t.sweep_planes != 0 && t.sweep_planes != 8 && t.sweep_planes != 16 && t.sweep_planes != 32 &&
+         t.sweep_planes != 64))
+        return fail(SPDE_EINVAL, "bad tuning (omega, inner_tol in (0, 1), flux_diag > 0, sweep_planes 0/8/16/32/64)");
     return SPDE_OK;
 }
 
@@ -2203,10 +2209,10 @@ spde_status spde_autotune(spde_ctx* ctx, int level, int nsamples, double kappa, 
     const double omegas[] = {0.7, 0.8, 0.9};
     const double itols[] = {1e-4, 1e-5, 1e-6};
     const double fds[] = {1.25, 1.5, 2.0};
-    const int planes[] = {0, 8, 16, 32};
+    const int planes[] = {0, 8, 16, 32, 64};
     for (int pass = 0; pass < 2 && s == SPDE_OK; ++pass) {
         for (int knob = 0; knob < 4 && s == SPDE_OK; ++knob) {
-            const int nc = knob == 3 ? 4 : 3;
+            const int nc = knob == 3 ? 5 : 3;
             for (int c = 0; c < nc && s == SPDE_OK; ++c) {
                 spde_tuning t = cur;
                 if (knob == 0) t.omega = omegas[c];

@@ -45,20 +45,49 @@ cudaError_t launch_apply(const Grid3& g, double kh2, int S, const T* x, T* y, cu
 template cudaError_t launch_apply<float>(const Grid3&, double, int, const float*, float*, cudaStream_t);
 template cudaError_t launch_apply<double>(const Grid3&, double, int, const double*, double*, cudaStream_t);
 
+// the residual of one quad: flux rows zero, cell row d, as float and/or double
+__device__ __forceinline__ void residual_store(float* __restrict__ r32, double* __restrict__ r64, int64_t off, int n3,
+                                               int c, const V4<double>& d) {
+    if (r32) {
+        float* o = r32 + off;
+        const V4<float> z = zero4<float>();
+        V4<float> fd;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) fd.v[e] = (float)d.v[e];
+        st4(o + c, z);
+        st4(o + n3 + c, z);
+        st4(o + 2 * n3 + c, z);
+        st4(o + 3 * n3 + c, fd);
+    }
+    if (r64) {
+        double* o = r64 + off;
+        const V4<double> z = zero4<double>();
+        st4(o + c, z);
+        st4(o + n3 + c, z);
+        st4(o + 2 * n3 + c, z);
+        st4(o + 3 * n3 + c, d);
+    }
+}
+
 // r = [0; F] - A x in FP64; optional float and double copies; partial r.r.
 // Every caller forms the flux of x exactly from its cell field first
 // (u = -T^{-1} D1^T theta by FP64 line solves, or x = 0), so the flux rows of
 // r vanish up to the rounding of those solves: they are written as zeros and
 // only the cell row  F - (D1 u - (kappa h)^2 theta)  is formed (the FP64
 // arithmetic, the rate-limiting unit here, drops to a third).
+// x is known to be zero (the first step of a cold start) when xzero is set or
+// *zgate is 0: the cell row is then F itself, taken without reading x (the same
+// bits: every term of A x is +0).
 __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const double* __restrict__ F, int64_t F_stride,
                                                     const double* __restrict__ x, float* __restrict__ r32,
                                                     double* __restrict__ r64, double* __restrict__ part,
                                                     const int* __restrict__ active, const double* __restrict__ kh2c,
-                                                    const double* __restrict__ kh2s) {
+                                                    const double* __restrict__ kh2s, int xzero,
+                                                    const int* __restrict__ zgate) {
     __shared__ double red[8];
     const int s = blockIdx.y;
     if (active && !active[s]) return;
+    const bool zero = xzero || (zgate && *zgate == 0);
     const double kh2v = kh2s ? kh2s[s] : kh2;  // one (kappa h)^2 per column (serving lanes) or per call
     const int n3 = 1 << (g.lx + g.ly + g.lz);
     const int64_t off = (int64_t)s * 4 * n3;
@@ -73,6 +102,13 @@ __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const d
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (n3 >> 2); q += gridDim.x * blockDim.x) {
         const QuadPos p = quad_pos(q, g);
         const int c = p.c;
+        if (zero) {
+            const V4<double> d = ld4(Fs + c);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc += d.v[e] * d.v[e];
+            residual_store(r32, r64, off, n3, c, d);
+            continue;
+        }
         const bool jl = p.j > 0, jh = p.j < g.ny - 1;
         const bool kl = p.k > 0, kh = p.k < g.nz - 1;
         const V4<double> ux4 = ld4(ux + c), uy4 = ld4(uy + c), uz4 = ld4(uz + c), th4 = ld4(th + c);
@@ -97,25 +133,7 @@ __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const d
             d.v[e] = f.v[e] - yt;
             acc += d.v[e] * d.v[e];
         }
-        if (r32) {
-            float* o = r32 + off;
-            const V4<float> z = zero4<float>();
-            V4<float> fd;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) fd.v[e] = (float)d.v[e];
-            st4(o + c, z);
-            st4(o + n3 + c, z);
-            st4(o + 2 * n3 + c, z);
-            st4(o + 3 * n3 + c, fd);
-        }
-        if (r64) {
-            double* o = r64 + off;
-            const V4<double> z = zero4<double>();
-            st4(o + c, z);
-            st4(o + n3 + c, z);
-            st4(o + 2 * n3 + c, z);
-            st4(o + 3 * n3 + c, d);
-        }
+        residual_store(r32, r64, off, n3, c, d);
     }
     const double t = block_sum<256>(acc, red);
     if (threadIdx.x == 0) part[(int64_t)s * kMaxPartials + blockIdx.x] = t;
@@ -123,10 +141,10 @@ __global__ void __launch_bounds__(256) k_residual64(Grid3 g, double kh2, const d
 
 int launch_residual64(const Grid3& g, double kh2, int S, const double* F, int64_t F_stride, const double* x,
                       float* r32, double* r64, double* part, const int* active, cudaStream_t st, const double* kh2c,
-                      const double* kh2s) {
+                      const double* kh2s, int xzero, const int* zgate) {
     const int nb = stencil_blocks(g.cells() / 4);
     dim3 grid(nb, S);
-    k_residual64<<<grid, 256, 0, st>>>(g, kh2, F, F_stride, x, r32, r64, part, active, kh2c, kh2s);
+    k_residual64<<<grid, 256, 0, st>>>(g, kh2, F, F_stride, x, r32, r64, part, active, kh2c, kh2s, xzero, zgate);
     return nb;
 }
 

@@ -67,10 +67,10 @@ def test_rows_give_the_same_bits_on_boxes(dims):
     pkg.spde_precond_status()
 
 
-@pytest.mark.parametrize("planes", [8, 16, 32])
-def test_rows_with_each_march_length(planes):
+@pytest.mark.parametrize("n,planes", [(64, 8), (64, 16), (64, 32), (64, 64), (128, 64)])
+def test_rows_with_each_march_length(n, planes):
     """The z extent per CTA (sweep_planes) changes the tiling, not a bit of the V-cycle."""
-    n, ns = 64, 3
+    ns = 3
     r = _rand((n, n, n), ns, 7)
     ref = torch.full_like(r, float("nan"))
     pkg.spde_precond(n, 1.0 / n, 20.0, ns, pkg.SPDE_PREC_MIXED, r, ref, _opts(0))
