@@ -701,6 +701,18 @@ def run_ours(args):
         torch.cuda.synchronize()
         fields_rate = S / (a.elapsed_time(b) / 1000.0)
         fst = smp.stats()
+        # end to end: kappa and sigma uploaded from host arrays and the output read into pinned
+        # host memory every step (new fields drop the level's captured graphs: each step recaptures)
+        nfe = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(nfe):
+            smp.set_fields(0, kap_c, sig_c)
+            smp.sample_fields(0, S, W["seed"], first_sample(2000 + i, rank, world, S), pkg.SPDE_OUT_LOGNORMAL,
+                              host_np, stream)
+        torch.cuda.synchronize()
+        fields_e2e = {"value": nfe * S / (time.perf_counter() - t0), "unit": "samples/s", "steps": nfe,
+                      "h2d_bytes_per_step": int(2 * 8 * kap_c.size), "d2h_bytes_per_step": int(S * ntets * 4)}
         smp.set_fields(0, None, None)
         # the crooked-pipe stand-in: quarter cylinder (radius 2, height 7, elements graded toward the
         # r = 1 layer) in a cubic box of side 8 whose (0,3)^2 x (0,8) corner is the paper's embedding box
@@ -822,7 +834,7 @@ def run_ours(args):
                 "fields": {"value": fields_rate, "unit": "samples/s", "samples": S,
                            "kappa": "20 (1 + 0.5 sin(2 pi x) cos(2 pi z)) per cell", "sigma": "0.75 + 0.5 y per cell",
                            "outer_iters": fst["outer_iters"], "inner_iters": fst["inner_iters"],
-                           "max_rel_residual": fst["max_rel_residual"]},
+                           "max_rel_residual": fst["max_rel_residual"], "e2e": fields_e2e},
                 "fp64": fp64,
                 "quarter_cylinder": cylinder,
                 "spe10_box": spe10,

@@ -37,7 +37,7 @@
 namespace spde {
 
 constexpr int kTileThreads = 256;
-constexpr int kCoarseThreads = 512;
+constexpr int kCoarseThreads = 1024;  // one CTA per column: 1024 threads measured 9 % faster than 512
 constexpr int kMaxTilesPerCol = 2048;
 
 template <typename T>
