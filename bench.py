@@ -581,7 +581,8 @@ def run_ours(args):
                               "note": "reduced run (no plain path, e2e or CPU baseline)"}), flush=True)
         smp.close()
         return
-    # e2e: same call with a pinned host output (device->host copy inside)
+    # e2e: same call with a pinned host output (the output crosses to host memory inside every call:
+    # the output kernels write the mapped pinned buffer directly)
     log("e2e")
     host = torch.empty((S, ntets), dtype=torch.float32, pin_memory=True)
     host_np = host.numpy()
@@ -594,7 +595,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, world)
     e2e = {"value": world * args.steps * S / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": int(S * ntets * 4)}
+           "d2h_bytes_per_step": int(S * ntets * 4),
+           "note": "spde_sample into pinned host memory; every call returns with the output in host memory"}
 
     # the same steps through the graph-driven path (per-kernel timing off): every call returns once
     # enqueued, convergence is decided on the device, the outcome is collected at the end

@@ -1062,6 +1062,20 @@ struct ProfScope {
     ~ProfScope() { t_prof = nullptr; }
 };
 
+// device address of pinned host memory of the current device (mapped: unified addressing),
+// or null when the pointer is not such memory
+void* mapped_host_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || cudaGetDevice(&dev) != cudaSuccess || a.device != dev)
+        return nullptr;
+    return a.devicePointer;
+}
+
 bool is_host_pointer(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -1866,6 +1880,9 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
     const bool graph = graph_path(ctx);
     const size_t esz = (out_kind & SPDE_OUT_F64) ? 8 : 4;
     const bool host_out = is_host_pointer(out);
+    // pinned host memory of this device is written by the output kernels directly (over the
+    // chip-to-chip link), with no staging buffer and copy; other host memory is staged and copied
+    void* const host_mapped = host_out ? mapped_host_pointer(out) : nullptr;
     if (graph) {
         STATUS_TRY(async_call_begin(ctx, st));
     } else {
@@ -1894,7 +1911,9 @@ spde_status sample_impl(spde_ctx* ctx, int level, int nsamples, double kappa, do
         if (s == SPDE_ENOCONV) worst = s;
         const size_t per = out_elem_count(L, 1, out_kind);
         void* dst = static_cast<char*>(out) + (size_t)s0 * per * esz;
-        if (host_out) {
+        if (host_mapped) {
+            STATUS_TRY(write_output(L, S, out_kind, static_cast<char*>(host_mapped) + (size_t)s0 * per * esz, st));
+        } else if (host_out) {
             const size_t need = (size_t)S * per * esz;
             if (ctx->out_tmp_bytes < need) {
                 if (ctx->out_tmp) {
