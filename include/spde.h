@@ -196,14 +196,17 @@ spde_status spde_mesh_attach(spde_ctx* ctx, int level, int64_t nverts, const dou
  * (seed, sample index, level grid, mesh, kappa, sigma).
  *   kappa > 0, sigma > 0 finite; nu is fixed at 1/2.
  *   out   device (or host) buffer of the layout `out_kind` states; host
- *         memory is detected and filled through an internal device buffer.
+ *         memory is detected and filled before the call returns: pinned host
+ *         memory of this device is written by the output kernels directly (it
+ *         is mapped into the device's address space), other host memory
+ *         through an internal device buffer and one copy.
  * Asynchronous on `stream` (opts.use_graphs = 1 and no per-kernel timing):
  * the call enqueues noise, one graph launch per batch (refinement and MINRES
  * run on the device) and the projection, and returns; `out` is valid once
  * `stream` has synchronised.  Argument errors are returned at once; the
  * solver's outcome (SPDE_ENOCONV: tolerance not reached, `out` holds the
  * last iterate; SPDE_ETIMEOUT) is returned by spde_wait.  With a host `out`
- * the call returns after the copy, with that outcome.  The first call for a
+ * the call returns once `out` holds the result, with that outcome.  The first call for a
  * (level, batch size, kappa) captures the graph (a few ms).  On the
  * synchronous path the call synchronises `stream` and returns the outcome
  * itself. */
