@@ -113,7 +113,7 @@ struct Workspace {
     float* tri32 = nullptr;  // the same in FP32 (Schur-complement operator)
     CgCol* cg = nullptr;     // Schur-complement CG state [S]
     void* mg = nullptr;      // V-cycle scratch
-    double* partA = nullptr; // partial sums [S][kMaxPartials]
+    double* partA = nullptr; // partial sums [S][kMaxPartials]: y.Ay of Lanczos pass A, then r1.y of pass B
     double* partB = nullptr;
     double* partC = nullptr;
     double* partR = nullptr;
